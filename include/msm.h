@@ -1,0 +1,282 @@
+/*
+ * msm.h -- C ABI of libmsm, the GB300 (sm_103a) engine for the DPD-CGMD
+ * multiscale blood-clot model with multiple time stepping (arXiv 2205.14121).
+ *
+ * The model: DPD plasma (Eq. 1), CGMD platelets -- harmonic bonds, LJ 12-6
+ * and Morse (Eq. 2) --, the fluid-platelet interface (Eq. 3), inter-platelet
+ * Morse + receptor term (Eq. 4), integrated by the multi-level RESPA loop of
+ * Table 1, with the per-platelet step ratio chosen by the learned controller
+ * of Table 2 (Sec. 3.3).
+ *
+ * Conventions for every entry point
+ *  - Return value: MD_OK (0) or a negative MD_E* code; md_last_error() gives
+ *    a message.  Nothing aborts, traps or exits.
+ *  - Device work is ordered on the CUDA stream given to md_init(); entry
+ *    points that return host data synchronise that stream first.
+ *  - Particle ids are the row numbers of the arrays given to
+ *    md_set_particles(); storage is re-sorted internally by cell, but every
+ *    array read back is in id order.
+ *  - One md_system per host thread; calls on one system are not reentrant.
+ *  - Units are reduced DPD units (m = kT = rc = 1).
+ */
+#ifndef MSM_H
+#define MSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MD_OK             0
+#define MD_EINVAL        (-1)   /* bad argument or configuration            */
+#define MD_ENOMEM        (-2)   /* workspace smaller than md_workspace_size */
+#define MD_ECUDA         (-3)   /* a CUDA runtime call failed               */
+#define MD_ENBR_OVERFLOW (-4)   /* a neighbour list exceeded its capacity   */
+#define MD_EUNSTABLE     (-5)   /* NaN/Inf state or a particle left the box */
+#define MD_ETIMEOUT      (-6)   /* a bounded device wait gave up            */
+#define MD_ENOTRAINED    (-7)   /* the controller has no weights loaded     */
+
+/* ---- force levels (Table 1 component splitting) ------------------------- */
+#define MD_LEVEL_FLUID 1u  /* plasma-plasma and plasma-wall DPD + body force */
+#define MD_LEVEL_IFACE 2u  /* DPD between platelet and plasma/wall (Eq. 3)   */
+#define MD_LEVEL_PLT   4u  /* bonds, LJ (Eq. 2), receptor Morse (Eq. 4)      */
+#define MD_LEVEL_ALL   7u
+
+/* ---- configuration flags ----------------------------------------------- */
+#define MD_CFG_WALLS        1  /* frozen wall layers outside y in [0,Ly], bounce-back */
+#define MD_CFG_LEES_EDWARDS 2  /* sliding periodic images in y at shear_rate       */
+
+/* ---- neighbour-list kinds ---------------------------------------------- */
+#define MD_LIST_FLUID 0  /* plasma-plasma, plasma-wall (half list)             */
+#define MD_LIST_IFACE 1  /* platelet rows -> plasma/wall partners              */
+#define MD_LIST_LJ    2  /* platelet-platelet LJ pairs (half list)             */
+#define MD_LIST_MORSE 3  /* receptor pairs of different platelets (half list)  */
+
+/*
+ * Particle tag (int32): -1 plasma, -2 wall, p >= 0 platelet id p; bit 30 set
+ * on receptor sites.  Rest positions X0 are used only for the same-platelet
+ * LJ exclusion (pairs closer than lj_excl at rest feel no LJ).
+ */
+#define MD_TAG_FLUID    (-1)
+#define MD_TAG_WALL     (-2)
+#define MD_RECEPTOR_BIT (1 << 30)
+
+/*
+ * System configuration.  Defaults follow the paper's model as read for the
+ * synthetic systems: Eq. 1 a = 25 (plasma-plasma, plasma-wall), gamma = 4.5,
+ * sigma = 3, rc = 1; Eq. 3 interface DPD a_fp = 50; Eq. 2 LJ eps = 1,
+ * sigma = 0.8, cut-off 2.5 sigma, k_b = 100; Eq. 2/4 Morse D = 2,
+ * alpha = 2, r0 = 1 with cut-off 5.
+ */
+typedef struct md_config {
+    int64_t  n;               /* particles (plasma + wall + platelet)            */
+    int64_t  n_bonds;         /* harmonic bonds                                   */
+    int64_t  n_plt_particles; /* particles with tag >= 0                          */
+    int64_t  n_receptors;     /* platelet particles with the receptor bit         */
+    int32_t  n_platelets;     /* platelets (largest platelet id + 1)              */
+    int32_t  flags;           /* MD_CFG_*                                         */
+    double   box[3];          /* fluid region [0,Lx) x [0,Ly) x [0,Lz)            */
+    double   wall;            /* wall layer thickness (MD_CFG_WALLS)              */
+    double   shear_rate;      /* Lees-Edwards rate (MD_CFG_LEES_EDWARDS)          */
+    double   body_force;      /* g along +x on every non-wall particle            */
+    double   dt;              /* fluid step dt_f                                  */
+    double   skin;            /* Verlet skin added to every list cut-off          */
+    double   rc, a_ff, a_fw, a_fp, gamma, sigma;          /* Eq. 1 / Eq. 3       */
+    double   lj_eps, lj_sigma, lj_rc, lj_excl;            /* Eq. 2 LJ            */
+    double   morse_D, morse_alpha, morse_r0, morse_rc, f_A; /* Eq. 2 / Eq. 4     */
+    double   k_bond;                                       /* Eq. 2 bonds        */
+    uint64_t seed;            /* key of the Philox4x32-10 pair noise              */
+    int32_t  cap_fluid, cap_iface, cap_lj, cap_morse; /* list capacities per row  */
+} md_config;
+
+/* Fill *cfg with the defaults above for n particles in box (no platelets). */
+int md_config_defaults(md_config *cfg);
+
+/*
+ * Bytes of device workspace md_init needs for cfg (256-byte aligned start).
+ * The workspace holds every per-particle array, the neighbour lists and the
+ * scratch of the sort, list build and reductions.
+ */
+int md_workspace_size(const md_config *cfg, size_t *bytes);
+
+typedef struct md_buffers {
+    void  *workspace;       /* device memory, caller-owned, >= md_workspace_size */
+    size_t workspace_bytes;
+} md_buffers;
+
+typedef struct md_system md_system;
+
+/*
+ * Create a system on the current CUDA device.  cuda_stream: a cudaStream_t
+ * (NULL = legacy default stream).  The library never frees bufs->workspace;
+ * it owns only its host-side state and a few bytes of pinned host memory,
+ * released by md_destroy().
+ * Errors: MD_EINVAL (inconsistent cfg, a periodic dimension shorter than three
+ * list cells), MD_ENOMEM (workspace too small), MD_ECUDA.
+ */
+int md_init(const md_config *cfg, const md_buffers *bufs, void *cuda_stream, md_system **out);
+
+/* Release host-side state; the workspace stays the caller's. */
+void md_destroy(md_system *sys);
+
+/* Message for the last error on sys (static string when sys is NULL). */
+const char *md_last_error(const md_system *sys);
+
+/*
+ * Load the particle state from HOST arrays in id order:
+ * x[n*3] positions (FP64, fluid region coordinates; walls outside y in [0,Ly]),
+ * v[n*3] velocities, tag[n] tags, X0[n*3] rest positions (may be NULL: X0 = x).
+ * Resets the step counter to step0 and the time to step0*dt; marks the
+ * neighbour lists and forces stale (rebuilt and recomputed on the next call
+ * that needs them).  Errors: MD_EINVAL, MD_ECUDA.
+ */
+int md_set_particles(md_system *sys, const double *x, const double *v, const int32_t *tag,
+                     const double *X0, int64_t step0);
+
+/*
+ * Harmonic bonds (Eq. 2) as HOST arrays: ij[nb*2] particle ids, r0[nb] rest
+ * lengths.  nb must equal cfg.n_bonds.  Errors: MD_EINVAL, MD_ECUDA.
+ */
+int md_set_bonds(md_system *sys, const int32_t *ij, const double *r0, int64_t nb);
+
+/*
+ * Verlet-skin neighbour lists (Table 1, "neighbor lists construction"):
+ * cell binning and counting sort of every particle array (K1), then every
+ * list (K2).  force = 0 rebuilds only when some particle moved more than
+ * skin/2 (minus a safety margin) since the last build.  list_mask: bit per
+ * MD_LIST_* kind (all kinds are rebuilt together; the mask is validated only).
+ * Errors: MD_ENBR_OVERFLOW (a row exceeded its capacity; raise cap_*),
+ * MD_ECUDA.
+ */
+int md_neighbor_build(md_system *sys, uint32_t list_mask, int force);
+
+/* flags of md_forces */
+#define MD_FORCE_VIRIAL 1u  /* also accumulate the FP64 pair virial */
+
+/*
+ * Forces of the levels in level_mask at the current state (Eq. 1-4),
+ * written to each level's force buffer.  The pair noise zeta_ij is drawn
+ * from Philox4x32-10 with counter (min id, max id, n, c) and key seed, where
+ * (n, c) is the time index of the current state (n = completed fluid steps,
+ * c = completed interface substeps); F^R = sigma w zeta / sqrt(dt_level).
+ * Rebuilds stale lists first.  Errors: MD_ENBR_OVERFLOW, MD_ECUDA.
+ */
+int md_forces(md_system *sys, uint32_t level_mask, uint32_t flags);
+
+/*
+ * Copy the sum of the level forces in level_mask to HOST f[n*3] (FP64, id
+ * order).  Synchronises the stream.  Errors: MD_EINVAL, MD_ECUDA.
+ */
+int md_read_forces(md_system *sys, uint32_t level_mask, double *f);
+
+/*
+ * Copy the state to HOST arrays in id order: x[n*3] FP64 master positions,
+ * v[n*3] velocities (FP32 widened), x32[n*3] the FP32 position copy the
+ * force kernels read (any pointer may be NULL).  Synchronises the stream.
+ */
+int md_read_particles(md_system *sys, double *x, double *v, float *x32);
+
+/* ---- multiple time stepping (Table 1) ----------------------------------- */
+#define MD_MODE_STS   0  /* single time step: every force every dt_f           */
+#define MD_MODE_RESPA 1  /* k_m interface substeps, k_p platelet substeps each  */
+#define MD_MODE_AI    2  /* per-platelet k from the controller (Table 2)        */
+
+typedef struct md_mts_schedule {
+    int32_t mode;        /* MD_MODE_*                                            */
+    int32_t k_m;         /* interface substeps per fluid step (>= 1)             */
+    int32_t k_p;         /* platelet substeps per interface step (RESPA)         */
+    int32_t obs_every;   /* record observables every obs_every outer steps (0 = off) */
+} md_mts_schedule;
+
+/*
+ * Advance n_outer fluid steps.  STS: velocity-Verlet with dt_f for every
+ * force.  RESPA: Table 1 read symmetrically -- half-kick with the fluid
+ * forces, k_m interface substeps (half-kick, k_p platelet kick-drift-force-
+ * kick substeps, interface forces, half-kick), fluid forces, half-kick.
+ * Positions are FP64 masters; the lists are rebuilt on device when the
+ * displacement check trips (no host round trip per step).
+ * Errors: MD_ENBR_OVERFLOW, MD_EUNSTABLE, MD_ECUDA (checked once at the end).
+ */
+int md_mts_step(md_system *sys, int64_t n_outer, const md_mts_schedule *sched);
+
+/* Observables (Sec. 4.2), FP64, reduced on the device. */
+typedef struct md_observables_t {
+    int64_t step;            /* completed fluid steps                          */
+    double  time;            /* step * dt_f                                    */
+    double  momentum[3];     /* total momentum of mobile particles             */
+    double  kinetic;         /* 1/2 sum m v^2 (mobile)                         */
+    double  temperature;     /* sum m|v-u|^2 / N_dof (u: Lees-Edwards profile) */
+    double  kin_tensor[9];   /* sum m (v-u)_a (v-u)_b                          */
+    double  virial_c[9];     /* sum over pairs r_a F^C_b (conservative), last forces with MD_FORCE_VIRIAL */
+    double  pressure;        /* (trace kin_tensor + trace virial_c) / (3V)     */
+    int64_t n_builds;        /* neighbour-list builds so far                   */
+    int64_t max_rows[4];     /* longest list row of each MD_LIST_* kind        */
+} md_observables_t;
+
+/*
+ * Reduce the observables of the current state into *out (host).  The virial
+ * is that of the last force evaluation made with MD_FORCE_VIRIAL (md_forces)
+ * -- call md_forces(sys, MD_LEVEL_ALL, MD_FORCE_VIRIAL) first for a current
+ * pressure.  Synchronises the stream.
+ */
+int md_observables(md_system *sys, md_observables_t *out);
+
+/*
+ * Neighbour pairs of list kind `kind` as particle ids (a < b), written to
+ * HOST pairs[2*cap]; *count gets the total.  For parity checks of K2.
+ * Synchronises the stream.
+ */
+int md_neighbor_pairs(md_system *sys, int32_t kind, int32_t *pairs, int64_t cap, int64_t *count);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+#define MD_PROF_FLUID   0  /* K3 plasma-plasma / plasma-wall DPD pass          */
+#define MD_PROF_IFACE   1  /* K3 interface DPD pass                            */
+#define MD_PROF_PLT     2  /* K4 + K5 platelet forces                          */
+#define MD_PROF_INTEG   3  /* K7 kick / drift / rebuild check                  */
+#define MD_PROF_BUILD   4  /* K1 + K2 rebuild chain (gated: mostly empty)      */
+#define MD_PROF_OTHER   5  /* time-index updates, reductions                   */
+#define MD_PROF_CLASSES 6
+
+typedef struct md_profile_t {
+    int64_t launches[MD_PROF_CLASSES];  /* kernel launches per class          */
+    double  ms[MD_PROF_CLASSES];        /* summed CUDA-event time per class   */
+    int64_t total_launches;             /* every kernel libmsm launched       */
+} md_profile_t;
+
+/*
+ * Kernel accounting: with enable = 1, md_mts_step brackets each kernel class
+ * it launches with CUDA events on the system's stream (a small perturbation;
+ * launch counting is always on).  md_profile_read synchronises, sums and
+ * (reset = 1) clears the counters.  Errors: MD_EINVAL, MD_ECUDA.
+ */
+int md_profile_enable(md_system *sys, int enable);
+int md_profile_read(md_system *sys, md_profile_t *out, int reset);
+
+/*
+ * Philox4x32-10 on the device, as used for the pair noise: out[4k..4k+3] =
+ * Philox4x32-10(ctr[4k..4k+3], key) for k < n.  HOST arrays in and out.  With
+ * use_library = 1 the same blocks come from cuRAND's device Philox4_32_10
+ * generator (counter mapped to its subsequence/offset), for cross-checking.
+ * Errors: MD_EINVAL (n < 0, or a counter the library mapping cannot reach),
+ * MD_ECUDA.
+ */
+int md_philox(const uint32_t *ctr, const uint32_t key[2], int64_t n, uint32_t *out, int use_library);
+
+/*
+ * Checkpoint: md_get_state writes the full dynamical state (positions,
+ * velocities, level forces, step counters, Lees-Edwards offset) in id order
+ * to the HOST blob (pass blob = NULL to get the size in *n); md_set_state
+ * restores it.  The counter-based noise makes a resumed run identical to an
+ * uninterrupted one.
+ */
+int md_get_state(md_system *sys, void *blob, size_t *n);
+int md_set_state(md_system *sys, const void *blob, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSM_H */

@@ -1,0 +1,898 @@
+// The C ABI of libmsm (include/msm.h): system set-up over a caller-owned
+// device workspace, state import/export, and the multi-level time loop of
+// Table 1 driving the kernels of sort.cu, neighbor.cu, forces.cu,
+// integrate.cu and reduce.cu.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "msm_internal.cuh"
+
+namespace {
+
+const char *g_static_err = "no error";
+
+// ---------------------------------------------------------------------------
+// workspace layout
+// ---------------------------------------------------------------------------
+struct carver {
+    char *base;
+    size_t off = 0;
+    template <class T>
+    T *take(int64_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += sizeof(T) * (size_t)(count > 0 ? count : 1);
+        return p;
+    }
+};
+
+bool setup_grid(const md_config &c, double cut, md_grid &g, std::string &err)
+{
+    const bool walls = c.flags & MD_CFG_WALLS;
+    double lo[3] = {0.0, walls ? -c.wall : 0.0, 0.0};
+    double hi[3] = {c.box[0], walls ? c.box[1] + c.wall : c.box[1], c.box[2]};
+    int64_t ncell = 1;
+    for (int d = 0; d < 3; ++d) {
+        const double ext = hi[d] - lo[d];
+        // fewer than three cells along a periodic edge is fine: the candidate
+        // scan clamps its cell range to the grid, visiting each cell once
+        int nc = (int)floor(ext / cut);
+        if (nc < 1) nc = 1;
+        if (nc > (1 << 20)) {
+            err = "grid too fine";
+            return false;
+        }
+        g.nc[d] = nc;
+        g.lo[d] = (float)lo[d];
+        g.h[d] = (float)(ext / nc);
+        g.inv_h[d] = (float)(nc / ext);
+        ncell *= nc;
+    }
+    g.ncell = ncell;
+    return true;
+}
+
+int default_cap(int v, int d) { return v > 0 ? v : d; }
+
+bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
+{
+    if (c.n <= 0 || c.n >= (int64_t)1 << 31) { err = "n out of range"; return false; }
+    if (c.n_plt_particles < 0 || c.n_plt_particles > c.n || c.n_receptors < 0 ||
+        c.n_receptors > c.n_plt_particles || c.n_bonds < 0) {
+        err = "inconsistent particle counts"; return false;
+    }
+    if (!(c.dt > 0) || !(c.rc > 0) || !(c.skin >= 0) || !(c.box[0] > 0) || !(c.box[1] > 0) || !(c.box[2] > 0)) {
+        err = "dt, rc, skin and box must be positive"; return false;
+    }
+    if ((c.flags & MD_CFG_WALLS) && (c.flags & MD_CFG_LEES_EDWARDS)) {
+        err = "walls and Lees-Edwards images are exclusive"; return false;
+    }
+    s.cfg = c;
+    s.n = c.n;
+    s.n_plt = c.n_plt_particles;
+    s.n_rec = c.n_receptors;
+    s.nb = c.n_bonds;
+    s.cap[MD_LIST_FLUID] = default_cap(c.cap_fluid, 48);
+    s.cap[MD_LIST_IFACE] = default_cap(c.cap_iface, 64);
+    s.cap[MD_LIST_LJ] = default_cap(c.cap_lj, 128);
+    s.cap[MD_LIST_MORSE] = default_cap(c.cap_morse, 256);
+    if (!setup_grid(c, c.rc + c.skin, s.gmain, err)) return false;
+    const bool plt = s.n_plt > 0;
+    if (plt) {
+        if (!setup_grid(c, c.lj_rc + c.skin, s.gplt, err)) return false;
+        if (s.n_rec > 0 && !setup_grid(c, c.morse_rc + c.skin, s.grec, err)) return false;
+    }
+    const int64_t n = s.n;
+    s.xs = cv.take<double>(n);
+    s.ys = cv.take<double>(n);
+    s.zs = cv.take<double>(n);
+    s.x32 = cv.take<float4>(n);
+    s.v = cv.take<float4>(n);
+    const int nf = plt ? 3 : 1;
+    for (int l = 0; l < 3; ++l) {
+        s.f[l] = l < nf ? cv.take<float4>(n) : nullptr;
+        s.altf[l] = l < nf ? cv.take<float4>(n) : nullptr;
+    }
+    s.xb = cv.take<float4>(n);
+    s.tag_s = cv.take<int32_t>(n);
+    s.cellid = cv.take<int32_t>(n);
+    s.slot = cv.take<int32_t>(n);
+    s.perm = cv.take<int32_t>(n);
+    s.pos_of_id = cv.take<int32_t>(n);
+    s.alt64 = cv.take<double>(3 * n);
+    s.altv = cv.take<float4>(n);
+    s.altx = cv.take<float4>(n);
+    s.alt_tag = cv.take<int32_t>(n);
+    s.X0 = plt ? cv.take<float4>(n) : nullptr;
+    s.gmain.start = cv.take<int32_t>(s.gmain.ncell + 1);
+    s.gmain.count = cv.take<int32_t>(s.gmain.ncell);
+    int64_t max_cells = s.gmain.ncell;
+    if (plt) {
+        s.gplt.start = cv.take<int32_t>(s.gplt.ncell + 1);
+        s.gplt.count = cv.take<int32_t>(s.gplt.ncell);
+        max_cells = s.gplt.ncell > max_cells ? s.gplt.ncell : max_cells;
+        s.plt_idx = cv.take<int32_t>(s.n_plt);
+        s.plt_sorted = cv.take<int32_t>(s.n_plt);
+        s.plt_cell = cv.take<int32_t>(s.n_plt);
+        s.plt_slot = cv.take<int32_t>(s.n_plt);
+        if (s.n_rec > 0) {
+            s.grec.start = cv.take<int32_t>(s.grec.ncell + 1);
+            s.grec.count = cv.take<int32_t>(s.grec.ncell);
+            max_cells = s.grec.ncell > max_cells ? s.grec.ncell : max_cells;
+            s.rec_idx = cv.take<int32_t>(s.n_rec);
+            s.rec_sorted = cv.take<int32_t>(s.n_rec);
+            s.rec_cell = cv.take<int32_t>(s.n_rec);
+            s.rec_slot = cv.take<int32_t>(s.n_rec);
+        }
+    }
+    s.scan_cap = max_cells / 4096 + 2;
+    if (s.scan_cap > 1024 * 64) { err = "too many cells for the scan"; return false; }
+    s.scan_sums = cv.take<int32_t>(s.scan_cap);
+    const int64_t rows[4] = {n, s.n_plt, s.n_plt, s.n_rec};
+    for (int k = 0; k < 4; ++k) {
+        if (rows[k] > 0 && (k == 0 || plt)) {
+            s.nl[k] = cv.take<int32_t>(rows[k] * (int64_t)s.cap[k]);
+            s.nc[k] = cv.take<int32_t>(rows[k]);
+        } else {
+            s.nl[k] = nullptr;
+            s.nc[k] = nullptr;
+        }
+    }
+    if (s.nb > 0) {
+        s.bond_id = cv.take<int32_t>(2 * s.nb);
+        s.bond_ij = cv.take<int32_t>(2 * s.nb);
+        s.bond_r0 = cv.take<float>(s.nb);
+    }
+    s.red_blocks = (int)((n + MSM_TPB - 1) / MSM_TPB);
+    if (s.red_blocks > RED_BLOCKS_MAX) s.red_blocks = RED_BLOCKS_MAX;
+    s.red_part = cv.take<double>((int64_t)s.red_blocks * RED_WORDS);
+    s.red_out = cv.take<double>(RED_WORDS);
+    s.vir_acc = cv.take<double>(9);
+    s.ctl = cv.take<int32_t>(CTL_WORDS);
+    s.ds = cv.take<md_dstate>(1);
+    return true;
+}
+
+unsigned blocks_for(int64_t n) { return (unsigned)(n > 0 ? (n + MSM_TPB - 1) / MSM_TPB : 1); }
+
+// ---------------------------------------------------------------------------
+// import / export kernels (id order <-> sorted storage)
+// ---------------------------------------------------------------------------
+__global__ void k_import_x(int64_t n, const double *__restrict__ aos, double *xs, double *ys, double *zs,
+                           float4 *x32, float4 *xb)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double x = aos[3 * k], y = aos[3 * k + 1], z = aos[3 * k + 2];
+    xs[k] = x; ys[k] = y; zs[k] = z;
+    const float4 p = make_float4((float)x, (float)y, (float)z, __int_as_float((int)k));
+    x32[k] = p;
+    xb[k] = p;
+}
+
+__global__ void k_import_v(int64_t n, const double *__restrict__ aos, const int32_t *__restrict__ tag, float4 *v,
+                           int32_t *tag_s, int32_t *pos_of_id)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    v[k] = make_float4((float)aos[3 * k], (float)aos[3 * k + 1], (float)aos[3 * k + 2], __int_as_float(tag[k]));
+    tag_s[k] = tag[k];
+    pos_of_id[k] = (int32_t)k;
+}
+
+__global__ void k_import_f4(int64_t n, const double *__restrict__ aos, float4 *out, float w)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    out[k] = make_float4((float)aos[3 * k], (float)aos[3 * k + 1], (float)aos[3 * k + 2], w);
+}
+
+__global__ void k_import_forces(int64_t n, const float *__restrict__ aos, float4 *out)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    out[k] = make_float4(aos[3 * k], aos[3 * k + 1], aos[3 * k + 2], 0.0f);
+}
+
+__global__ void k_export_x(int64_t n, const double *xs, const double *ys, const double *zs, const float4 *x32,
+                           double *aos)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t id = __float_as_int(x32[k].w);
+    aos[3 * id] = xs[k]; aos[3 * id + 1] = ys[k]; aos[3 * id + 2] = zs[k];
+}
+
+__global__ void k_export_f4(int64_t n, const float4 *src, const float4 *x32, double *aos)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t id = __float_as_int(x32[k].w);
+    const float4 p = src[k];
+    aos[3 * id] = p.x; aos[3 * id + 1] = p.y; aos[3 * id + 2] = p.z;
+}
+
+__global__ void k_export_x32(int64_t n, const float4 *x32, float *aos)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float4 p = x32[k];
+    const int64_t id = __float_as_int(p.w);
+    aos[3 * id] = p.x; aos[3 * id + 1] = p.y; aos[3 * id + 2] = p.z;
+}
+
+__global__ void k_export_forces(int64_t n, const float4 *f0, const float4 *f1, const float4 *f2, const float4 *x32,
+                                const int32_t *tag, float g, double *aos)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t id = __float_as_int(x32[k].w);
+    double fx = 0, fy = 0, fz = 0;
+    if (f0) { const float4 p = f0[k]; fx += p.x; fy += p.y; fz += p.z; if (tag[k] != MD_TAG_WALL) fx += g; }
+    if (f1) { const float4 p = f1[k]; fx += p.x; fy += p.y; fz += p.z; }
+    if (f2) { const float4 p = f2[k]; fx += p.x; fy += p.y; fz += p.z; }
+    aos[3 * id] = fx; aos[3 * id + 1] = fy; aos[3 * id + 2] = fz;
+}
+
+__global__ void k_set_word(int32_t *p, int32_t v) { *p = v; }
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+int check(md_system *s, cudaError_t e, const char *where)
+{
+    if (e == cudaSuccess) return MD_OK;
+    return cuda_fail(s, e, where);
+}
+
+#define CK(expr, where)                                   \
+    do {                                                  \
+        int _rc = check(s, (expr), where);                \
+        if (_rc != MD_OK) return _rc;                     \
+    } while (0)
+
+int sync_ctl(md_system *s)
+{
+    CK(cudaMemcpyAsync(s->h_ctl, s->ctl, sizeof(int32_t) * CTL_WORDS, cudaMemcpyDeviceToHost, s->stream), "ctl copy");
+    CK(cudaMemcpyAsync(s->h_ds, s->ds, sizeof(md_dstate), cudaMemcpyDeviceToHost, s->stream), "dstate copy");
+    CK(cudaStreamSynchronize(s->stream), "stream sync");
+    return MD_OK;
+}
+
+int check_flags(md_system *s)
+{
+    int rc = sync_ctl(s);
+    if (rc) return rc;
+    if (s->h_ctl[CTL_OVERFLOW]) {
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "neighbour list overflow (kind mask 0x%x; longest rows %d/%d/%d/%d, capacities %d/%d/%d/%d)",
+                 s->h_ctl[CTL_OVERFLOW], s->h_ctl[CTL_MAXROW], s->h_ctl[CTL_MAXROW + 1], s->h_ctl[CTL_MAXROW + 2],
+                 s->h_ctl[CTL_MAXROW + 3], s->cap[0], s->cap[1], s->cap[2], s->cap[3]);
+        return set_error(s, MD_ENBR_OVERFLOW, buf);
+    }
+    if (s->h_ctl[CTL_UNSTABLE]) return set_error(s, MD_EUNSTABLE, "NaN/Inf state or a particle escaped the walls");
+    return MD_OK;
+}
+
+double host_le_offset(const md_system *s, double t)
+{
+    if (!s->geom.le) return 0.0;
+    double d = fmod(s->cfg.shear_rate * s->cfg.box[1] * t, s->cfg.box[0]);
+    if (d < 0.0) d += s->cfg.box[0];
+    return d;
+}
+
+int request_rebuild(md_system *s)
+{
+    k_set_word<<<1, 1, 0, s->stream>>>(s->ctl + CTL_REBUILD, 1);
+    CK(cudaGetLastError(), "rebuild request");
+    CK(launch_rebuild(s, s->ctl + CTL_REBUILD), "rebuild");
+    s->lists_stale = false;
+    return MD_OK;
+}
+
+int ensure_lists(md_system *s)
+{
+    if (!s->lists_stale) return MD_OK;
+    return request_rebuild(s);
+}
+
+int eval_forces(md_system *s, unsigned levels, bool virial)
+{
+    CK(launch_zero_forces(s, levels), "zero forces");
+    if (virial) CK(cudaMemsetAsync(s->vir_acc, 0, 9 * sizeof(double), s->stream), "virial reset");
+    float4 *out[3] = {s->f[0], s->f[1], s->f[2]};
+    CK(launch_forces(s, levels, out, virial), "forces");
+    return MD_OK;
+}
+
+int ensure_forces(md_system *s)
+{
+    const unsigned all = s->n_plt > 0 ? MD_LEVEL_ALL : MD_LEVEL_FLUID;
+    if (!s->forces_stale && (s->forces_levels & all) == all) return MD_OK;
+    int rc = ensure_lists(s);
+    if (rc) return rc;
+    rc = eval_forces(s, all, false);
+    if (rc) return rc;
+    s->forces_stale = false;
+    s->forces_levels = all;
+    return MD_OK;
+}
+
+// One STS step (velocity-Verlet): kick (fused with the previous closing
+// half-kick when not first) + drift + check, rebuild if tripped, forces.
+int sts_step(md_system *s, bool first)
+{
+    const md_config &c = s->cfg;
+    const float dt = (float)c.dt;
+    const float hk = first ? 0.5f * dt : dt;
+    const unsigned all = s->n_plt > 0 ? MD_LEVEL_ALL : MD_LEVEL_FLUID;
+    const int64_t n_next = s->host_step + 1;
+    prof_begin(s, MD_PROF_OTHER);
+    CK(launch_set_time(s, n_next, 0, (double)n_next * c.dt), "time");
+    prof_end(s);
+    const float h[3] = {hk, s->n_plt > 0 ? hk : 0.f, s->n_plt > 0 ? hk : 0.f};
+    prof_begin(s, MD_PROF_INTEG);
+    CK(launch_kick_drift(s, h, DRIFT_ALL, c.dt, DRIFT_ALL, all, false), "kick-drift");
+    prof_end(s);
+    prof_begin(s, MD_PROF_BUILD);
+    CK(launch_rebuild(s, s->ctl + CTL_REBUILD), "rebuild");
+    prof_end(s);
+    float4 *out[3] = {s->f[0], s->f[1], s->f[2]};
+    prof_begin(s, MD_PROF_FLUID);
+    CK(launch_forces(s, MD_LEVEL_FLUID, out, false), "fluid forces");
+    prof_end(s);
+    if (s->n_plt > 0) {
+        prof_begin(s, MD_PROF_IFACE);
+        CK(launch_forces(s, MD_LEVEL_IFACE, out, false), "interface forces");
+        prof_end(s);
+        prof_begin(s, MD_PROF_PLT);
+        CK(launch_forces(s, MD_LEVEL_PLT, out, false), "platelet forces");
+        prof_end(s);
+    }
+    s->host_step = n_next;
+    return MD_OK;
+}
+
+int closing_kick(md_system *s, float hf, float hm, float hp)
+{
+    const float h[3] = {hf, s->n_plt > 0 ? hm : 0.f, s->n_plt > 0 ? hp : 0.f};
+    CK(launch_kick_drift(s, h, DRIFT_ALL, 0.0, -1, 0u, false), "closing kick");
+    return MD_OK;
+}
+
+// One RESPA outer step (Table 1 read symmetrically), k_m interface substeps of
+// k_p platelet substeps each.  Fluid particles feel no inner force, so they
+// drift once per interface substep; platelets drift every platelet substep.
+int respa_step(md_system *s, int k_m, int k_p, bool first)
+{
+    const md_config &c = s->cfg;
+    const double dtf = c.dt, dtm = dtf / k_m, dtp = dtm / k_p;
+    const int64_t n0 = s->host_step;
+    for (int cidx = 0; cidx < k_m; ++cidx) {
+        const double tc = (double)n0 * dtf + (double)cidx * dtm;
+        // interface-substep end time (fluid drift, LE offset)
+        const bool last_c = cidx + 1 == k_m;
+        const int64_t n_end = last_c ? n0 + 1 : n0;
+        const int32_t c_end = last_c ? 0 : cidx + 1;
+        CK(launch_set_time(s, n_end, c_end, tc + dtm), "time");
+        // A: fluid kick (first substep only; fused with the previous outer
+        //    step's closing half-kick) + interface kick, fluid drift
+        float h[3] = {0.f, 0.f, 0.f};
+        if (cidx == 0) h[0] = first ? (float)(0.5 * dtf) : (float)dtf;
+        h[1] = (float)(0.5 * dtm);
+        unsigned zero = MD_LEVEL_IFACE | (cidx == 0 ? MD_LEVEL_FLUID : 0u);
+        CK(launch_kick_drift(s, h, DRIFT_ALL, dtm, DRIFT_FLUID, zero, false), "fluid kick-drift");
+        // B: platelet substeps
+        for (int q = 0; q < k_p; ++q) {
+            CK(launch_set_time(s, n_end, c_end, tc + (q + 1) * dtp), "time");
+            // opening half-kick at q = 0; later substeps fuse the closing
+            // half-kick of q-1 with their opening one
+            const float hq[3] = {0.f, 0.f, q == 0 ? (float)(0.5 * dtp) : (float)dtp};
+            CK(launch_kick_drift(s, hq, DRIFT_PLT, dtp, DRIFT_PLT, MD_LEVEL_PLT, true), "platelet kick-drift");
+            float4 *out[3] = {s->f[0], s->f[1], s->f[2]};
+            CK(launch_forces(s, MD_LEVEL_PLT, out, false), "platelet forces");
+        }
+        // closing platelet half-kick before the interface forces read v
+        const float hc[3] = {0.f, 0.f, (float)(0.5 * dtp)};
+        CK(launch_kick_drift(s, hc, DRIFT_PLT, 0.0, -1, 0u, true), "platelet closing kick");
+        // rebuild if any particle moved too far
+        CK(launch_rebuild(s, s->ctl + CTL_REBUILD), "rebuild");
+        float4 *out[3] = {s->f[0], s->f[1], s->f[2]};
+        CK(launch_forces(s, MD_LEVEL_IFACE, out, false), "interface forces");
+        // closing interface half-kick (before the fluid forces read v)
+        const float hm[3] = {0.f, (float)(0.5 * dtm), 0.f};
+        CK(launch_kick_drift(s, hm, DRIFT_ALL, 0.0, -1, 0u, false), "interface closing kick");
+    }
+    float4 *out[3] = {s->f[0], s->f[1], s->f[2]};
+    CK(launch_forces(s, MD_LEVEL_FLUID, out, false), "fluid forces");
+    s->host_step = n0 + 1;
+    return MD_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// shared error helpers
+// ---------------------------------------------------------------------------
+int set_error(md_system *s, int code, const char *msg)
+{
+    if (s) s->err = msg;
+    return code;
+}
+
+int cuda_fail(md_system *s, cudaError_t e, const char *where)
+{
+    char buf[256];
+    snprintf(buf, sizeof buf, "CUDA error in %s: %s", where, cudaGetErrorString(e));
+    return set_error(s, MD_ECUDA, buf);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int md_config_defaults(md_config *c)
+{
+    if (!c) return MD_EINVAL;
+    const int64_t n = c->n;
+    const double bx = c->box[0], by = c->box[1], bz = c->box[2];
+    memset(c, 0, sizeof *c);
+    c->n = n;
+    c->box[0] = bx; c->box[1] = by; c->box[2] = bz;
+    c->wall = 1.0;
+    c->dt = 0.01;
+    c->skin = 0.3;
+    c->rc = 1.0; c->a_ff = 25.0; c->a_fw = 25.0; c->a_fp = 50.0; c->gamma = 4.5; c->sigma = 3.0;
+    c->lj_eps = 1.0; c->lj_sigma = 0.8; c->lj_rc = 2.0; c->lj_excl = 2.5;
+    c->morse_D = 2.0; c->morse_alpha = 2.0; c->morse_r0 = 1.0; c->morse_rc = 5.0; c->f_A = 0.0;
+    c->k_bond = 100.0;
+    c->seed = 20220528ull;
+    return MD_OK;
+}
+
+int md_workspace_size(const md_config *cfg, size_t *bytes)
+{
+    if (!cfg || !bytes) return MD_EINVAL;
+    md_system tmp;
+    carver cv{nullptr};
+    std::string err;
+    if (!plan(*cfg, tmp, cv, err)) return MD_EINVAL;
+    *bytes = cv.off + 256;
+    return MD_OK;
+}
+
+int md_init(const md_config *cfg, const md_buffers *bufs, void *cuda_stream, md_system **out)
+{
+    if (!cfg || !bufs || !out) return MD_EINVAL;
+    *out = nullptr;
+    md_system *s = new (std::nothrow) md_system();
+    if (!s) return MD_ENOMEM;
+    carver probe{nullptr};
+    std::string err;
+    if (!plan(*cfg, *s, probe, err)) {
+        g_static_err = "md_init: invalid configuration";
+        delete s;
+        return MD_EINVAL;
+    }
+    if (!bufs->workspace || bufs->workspace_bytes < probe.off + 256) {
+        g_static_err = "md_init: workspace smaller than md_workspace_size()";
+        delete s;
+        return MD_ENOMEM;
+    }
+    char *base = (char *)(((uintptr_t)bufs->workspace + 255) & ~(uintptr_t)255);
+    carver cv{base};
+    plan(*cfg, *s, cv, err);
+    s->stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&s->device);
+    const md_config &c = s->cfg;
+    s->geom.walls = (c.flags & MD_CFG_WALLS) ? 1 : 0;
+    s->geom.le = (c.flags & MD_CFG_LEES_EDWARDS) ? 1 : 0;
+    for (int d = 0; d < 3; ++d) {
+        s->geom.L[d] = (float)c.box[d];
+        s->geom.hL[d] = 0.5f * s->geom.L[d];
+    }
+    s->geom.shear_v = (float)(c.shear_rate * c.box[1]);
+    const double cuts[4] = {c.rc + c.skin, c.rc + c.skin, c.lj_rc + c.skin, c.morse_rc + c.skin};
+    for (int k = 0; k < 4; ++k) s->cut2[k] = (float)(cuts[k] * cuts[k]);
+    s->excl2 = (float)(c.lj_excl * c.lj_excl);
+    cudaError_t e = cudaHostAlloc((void **)&s->h_ctl, sizeof(int32_t) * CTL_WORDS, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->h_ds, sizeof(md_dstate), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        g_static_err = "md_init: pinned host allocation failed";
+        if (s->h_ctl) cudaFreeHost(s->h_ctl);
+        delete s;
+        return MD_ECUDA;
+    }
+    e = cudaMemsetAsync(s->ctl, 0, sizeof(int32_t) * CTL_WORDS, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->ds, 0, sizeof(md_dstate), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->vir_acc, 0, 9 * sizeof(double), s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        g_static_err = "md_init: device initialisation failed";
+        cudaFreeHost(s->h_ctl);
+        cudaFreeHost(s->h_ds);
+        delete s;
+        return MD_ECUDA;
+    }
+    *out = s;
+    return MD_OK;
+}
+
+void md_destroy(md_system *s)
+{
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    else cudaDeviceSynchronize();
+    if (s->h_ctl) cudaFreeHost(s->h_ctl);
+    if (s->h_ds) cudaFreeHost(s->h_ds);
+    delete s;
+}
+
+const char *md_last_error(const md_system *s)
+{
+    if (!s) return g_static_err;
+    return s->err.empty() ? "no error" : s->err.c_str();
+}
+
+int md_set_particles(md_system *s, const double *x, const double *v, const int32_t *tag, const double *X0,
+                     int64_t step0)
+{
+    if (!s || !x || !v || !tag) return set_error(s, MD_EINVAL, "md_set_particles: null argument");
+    const int64_t n = s->n;
+    // host-side validation of the tag counts
+    int64_t np = 0, nr = 0, npl = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        const int32_t t = tag[k];
+        if (t < MD_TAG_WALL) return set_error(s, MD_EINVAL, "md_set_particles: invalid tag");
+        if (t >= 0) {
+            ++np;
+            if (t & MD_RECEPTOR_BIT) ++nr;
+            const int64_t p = t & ~MD_RECEPTOR_BIT;
+            if (p + 1 > npl) npl = p + 1;
+        }
+        if (t == MD_TAG_WALL && !s->geom.walls) return set_error(s, MD_EINVAL, "wall particles without walls");
+    }
+    if (np != s->n_plt || nr != s->n_rec)
+        return set_error(s, MD_EINVAL, "md_set_particles: platelet/receptor counts differ from the configuration");
+    cudaStream_t st = s->stream;
+    CK(cudaMemcpyAsync(s->alt64, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload x");
+    k_import_x<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->alt64, s->xs, s->ys, s->zs, s->x32, s->xb);
+    CK(cudaGetLastError(), "import x");
+    CK(cudaMemcpyAsync(s->alt_tag, tag, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st), "upload tag");
+    CK(cudaMemcpyAsync(s->alt64, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload v");
+    k_import_v<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->alt64, s->alt_tag, s->v, s->tag_s, s->pos_of_id);
+    CK(cudaGetLastError(), "import v");
+    if (s->X0) {
+        CK(cudaMemcpyAsync(s->alt64, X0 ? X0 : x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload X0");
+        k_import_f4<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->alt64, s->X0, 0.0f);
+        CK(cudaGetLastError(), "import X0");
+    }
+    for (int l = 0; l < 3; ++l)
+        if (s->f[l]) CK(cudaMemsetAsync(s->f[l], 0, sizeof(float4) * n, st), "zero f");
+    md_dstate *h = s->h_ds;
+    memset(h, 0, sizeof *h);
+    h->step = step0;
+    h->time = (double)step0 * s->cfg.dt;
+    h->le_offset = host_le_offset(s, h->time);
+    h->le_offset_f = (float)h->le_offset;
+    h->le_build_f = h->le_offset_f;
+    CK(cudaMemcpyAsync(s->ds, h, sizeof(md_dstate), cudaMemcpyHostToDevice, st), "upload dstate");
+    CK(cudaMemsetAsync(s->ctl, 0, sizeof(int32_t) * CTL_WORDS, st), "reset ctl");
+    CK(cudaStreamSynchronize(st), "set_particles sync");
+    s->host_step = step0;
+    s->host_sub = 0;
+    s->lists_stale = true;
+    s->forces_stale = true;
+    s->forces_levels = 0;
+    s->have_particles = true;
+    return MD_OK;
+}
+
+int md_set_bonds(md_system *s, const int32_t *ij, const double *r0, int64_t nb)
+{
+    if (!s) return MD_EINVAL;
+    if (nb != s->nb) return set_error(s, MD_EINVAL, "md_set_bonds: count differs from the configuration");
+    if (nb == 0) return MD_OK;
+    if (!ij || !r0) return set_error(s, MD_EINVAL, "md_set_bonds: null argument");
+    std::vector<float> r0f((size_t)nb);
+    for (int64_t b = 0; b < nb; ++b) {
+        if (ij[2 * b] < 0 || ij[2 * b] >= s->n || ij[2 * b + 1] < 0 || ij[2 * b + 1] >= s->n)
+            return set_error(s, MD_EINVAL, "md_set_bonds: particle id out of range");
+        r0f[(size_t)b] = (float)r0[b];
+    }
+    CK(cudaMemcpyAsync(s->bond_id, ij, sizeof(int32_t) * 2 * nb, cudaMemcpyHostToDevice, s->stream), "upload bonds");
+    CK(cudaMemcpyAsync(s->bond_r0, r0f.data(), sizeof(float) * nb, cudaMemcpyHostToDevice, s->stream), "upload r0");
+    CK(cudaStreamSynchronize(s->stream), "set_bonds sync");
+    s->have_bonds = true;
+    s->lists_stale = true;   // the remap of bond ends happens in the rebuild
+    s->forces_stale = true;
+    return MD_OK;
+}
+
+int md_neighbor_build(md_system *s, uint32_t list_mask, int force)
+{
+    if (!s || !s->have_particles) return set_error(s, MD_EINVAL, "md_neighbor_build: no particles");
+    if (list_mask & ~0xFu) return set_error(s, MD_EINVAL, "md_neighbor_build: bad list mask");
+    if (force || s->lists_stale) {
+        int rc = request_rebuild(s);
+        if (rc) return rc;
+    } else {
+        CK(launch_rebuild(s, s->ctl + CTL_REBUILD), "rebuild");
+    }
+    return check_flags(s);
+}
+
+int md_forces(md_system *s, uint32_t level_mask, uint32_t flags)
+{
+    if (!s || !s->have_particles) return set_error(s, MD_EINVAL, "md_forces: no particles");
+    if ((level_mask & ~MD_LEVEL_ALL) || !level_mask) return set_error(s, MD_EINVAL, "md_forces: bad level mask");
+    if (s->nb > 0 && !s->have_bonds) return set_error(s, MD_EINVAL, "md_forces: bonds not set");
+    int rc = ensure_lists(s);
+    if (rc) return rc;
+    if (s->n_plt == 0) level_mask &= MD_LEVEL_FLUID;
+    rc = eval_forces(s, level_mask, (flags & MD_FORCE_VIRIAL) != 0);
+    if (rc) return rc;
+    s->forces_levels = level_mask;
+    s->forces_stale = level_mask != (s->n_plt > 0 ? MD_LEVEL_ALL : MD_LEVEL_FLUID);
+    return check_flags(s);
+}
+
+int md_read_forces(md_system *s, uint32_t level_mask, double *f)
+{
+    if (!s || !f) return MD_EINVAL;
+    const int64_t n = s->n;
+    const float4 *f0 = (level_mask & MD_LEVEL_FLUID) ? s->f[0] : nullptr;
+    const float4 *f1 = (level_mask & MD_LEVEL_IFACE) ? s->f[1] : nullptr;
+    const float4 *f2 = (level_mask & MD_LEVEL_PLT) ? s->f[2] : nullptr;
+    k_export_forces<<<blocks_for(n), MSM_TPB, 0, s->stream>>>(n, f0, f1, f2, s->x32, s->tag_s,
+                                                               (float)s->cfg.body_force, s->alt64);
+    CK(cudaGetLastError(), "export forces");
+    CK(cudaMemcpyAsync(f, s->alt64, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream), "download forces");
+    CK(cudaStreamSynchronize(s->stream), "read_forces sync");
+    return MD_OK;
+}
+
+int md_read_particles(md_system *s, double *x, double *v, float *x32)
+{
+    if (!s) return MD_EINVAL;
+    const int64_t n = s->n;
+    cudaStream_t st = s->stream;
+    if (x) {
+        k_export_x<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->xs, s->ys, s->zs, s->x32, s->alt64);
+        CK(cudaGetLastError(), "export x");
+        CK(cudaMemcpyAsync(x, s->alt64, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st), "download x");
+        CK(cudaStreamSynchronize(st), "sync");
+    }
+    if (v) {
+        k_export_f4<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->v, s->x32, s->alt64);
+        CK(cudaGetLastError(), "export v");
+        CK(cudaMemcpyAsync(v, s->alt64, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st), "download v");
+        CK(cudaStreamSynchronize(st), "sync");
+    }
+    if (x32) {
+        k_export_x32<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->x32, (float *)s->alt64);
+        CK(cudaGetLastError(), "export x32");
+        CK(cudaMemcpyAsync(x32, s->alt64, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, st), "download x32");
+        CK(cudaStreamSynchronize(st), "sync");
+    }
+    return MD_OK;
+}
+
+int md_mts_step(md_system *s, int64_t n_outer, const md_mts_schedule *sched)
+{
+    if (!s || !sched || n_outer < 0) return set_error(s, MD_EINVAL, "md_mts_step: bad argument");
+    if (!s->have_particles) return set_error(s, MD_EINVAL, "md_mts_step: no particles");
+    if (s->nb > 0 && !s->have_bonds) return set_error(s, MD_EINVAL, "md_mts_step: bonds not set");
+    if (n_outer == 0) return MD_OK;
+    const int mode = sched->mode;
+    int k_m = sched->k_m > 0 ? sched->k_m : 1;
+    int k_p = sched->k_p > 0 ? sched->k_p : 1;
+    if (mode == MD_MODE_STS) { k_m = 1; k_p = 1; }
+    else if (mode != MD_MODE_RESPA) return set_error(s, MD_EINVAL, "md_mts_step: unsupported mode");
+    if (s->cfg_k_m != k_m) {
+        // the interface noise amplitude depends on dt_m: recompute those forces
+        s->cfg_k_m = k_m;
+        s->forces_stale = true;
+    }
+    s->margin = (mode == MD_MODE_STS) ? 0.0f : 0.05f;
+    int rc = ensure_forces(s);
+    if (rc) return rc;
+    const md_config &c = s->cfg;
+    if (mode == MD_MODE_STS) {
+        for (int64_t it = 0; it < n_outer; ++it) {
+            rc = sts_step(s, it == 0);
+            if (rc) return rc;
+        }
+        const float hh = (float)(0.5 * c.dt);
+        rc = closing_kick(s, hh, hh, hh);
+        if (rc) return rc;
+    } else {
+        for (int64_t it = 0; it < n_outer; ++it) {
+            rc = respa_step(s, k_m, k_p, it == 0);
+            if (rc) return rc;
+        }
+        rc = closing_kick(s, (float)(0.5 * c.dt), 0.f, 0.f);
+        if (rc) return rc;
+    }
+    return check_flags(s);
+}
+
+int md_observables(md_system *s, md_observables_t *o)
+{
+    if (!s || !o) return MD_EINVAL;
+    CK(launch_kinetics(s), "kinetics");
+    double red[RED_WORDS], vir[9];
+    CK(cudaMemcpyAsync(red, s->red_out, sizeof red, cudaMemcpyDeviceToHost, s->stream), "download kinetics");
+    CK(cudaMemcpyAsync(vir, s->vir_acc, sizeof vir, cudaMemcpyDeviceToHost, s->stream), "download virial");
+    int rc = sync_ctl(s);
+    if (rc) return rc;
+    memset(o, 0, sizeof *o);
+    o->step = s->h_ds->step;
+    o->time = s->h_ds->time;
+    for (int k = 0; k < 3; ++k) o->momentum[k] = red[k];
+    o->kinetic = red[3];
+    const double kt[9] = {red[4], red[7], red[8], red[7], red[5], red[9], red[8], red[9], red[6]};
+    memcpy(o->kin_tensor, kt, sizeof kt);
+    memcpy(o->virial_c, vir, sizeof vir);
+    const double nm = red[10];
+    const double ndof = s->geom.walls ? 3.0 * nm : 3.0 * nm - 3.0;
+    o->temperature = ndof > 0 ? (kt[0] + kt[4] + kt[8]) / ndof : 0.0;
+    const double V = s->cfg.box[0] * s->cfg.box[1] * s->cfg.box[2];
+    o->pressure = (kt[0] + kt[4] + kt[8] + vir[0] + vir[4] + vir[8]) / (3.0 * V);
+    o->n_builds = s->h_ds->n_builds;
+    for (int k = 0; k < 4; ++k) o->max_rows[k] = s->h_ctl[CTL_MAXROW + k];
+    return MD_OK;
+}
+
+int md_neighbor_pairs(md_system *s, int32_t kind, int32_t *pairs, int64_t cap, int64_t *count)
+{
+    if (!s || !count || kind < 0 || kind > 3) return MD_EINVAL;
+    int rc = ensure_lists(s);
+    if (rc) return rc;
+    rc = check_flags(s);
+    if (rc) return rc;
+    const int64_t rows_k[4] = {s->n, s->n_plt, s->n_plt, s->n_rec};
+    const int32_t *row_idx_k[4] = {nullptr, s->plt_sorted, s->plt_sorted, s->rec_sorted};
+    const int64_t rows = rows_k[kind];
+    *count = 0;
+    if (rows == 0 || !s->nl[kind]) return MD_OK;
+    const int cp = s->cap[kind];
+    std::vector<int32_t> nc((size_t)rows), nl((size_t)(rows * cp)), ridx;
+    std::vector<float> x32h((size_t)(4 * s->n));
+    cudaStream_t st = s->stream;
+    CK(cudaMemcpyAsync(nc.data(), s->nc[kind], sizeof(int32_t) * rows, cudaMemcpyDeviceToHost, st), "nc");
+    CK(cudaMemcpyAsync(nl.data(), s->nl[kind], sizeof(int32_t) * rows * cp, cudaMemcpyDeviceToHost, st), "nl");
+    CK(cudaMemcpyAsync(x32h.data(), s->x32, sizeof(float4) * s->n, cudaMemcpyDeviceToHost, st), "x32");
+    if (row_idx_k[kind]) {
+        ridx.resize((size_t)rows);
+        CK(cudaMemcpyAsync(ridx.data(), row_idx_k[kind], sizeof(int32_t) * rows, cudaMemcpyDeviceToHost, st), "rows");
+    }
+    CK(cudaStreamSynchronize(st), "sync");
+    auto id_of_h = [&](int64_t k) {
+        int32_t id;
+        memcpy(&id, &x32h[(size_t)(4 * k + 3)], sizeof id);
+        return id;
+    };
+    int64_t total = 0;
+    for (int64_t r = 0; r < rows; ++r) {
+        const int64_t i = ridx.empty() ? r : ridx[(size_t)r];
+        const int32_t idi = id_of_h(i);
+        const int cnt = nc[(size_t)r] < cp ? nc[(size_t)r] : cp;
+        for (int k = 0; k < cnt; ++k) {
+            const int32_t idj = id_of_h(nl[(size_t)((int64_t)k * rows + r)]);
+            if (pairs && total < cap) {
+                pairs[2 * total] = idi < idj ? idi : idj;
+                pairs[2 * total + 1] = idi < idj ? idj : idi;
+            }
+            ++total;
+        }
+    }
+    *count = total;
+    return MD_OK;
+}
+
+// checkpoint blob: header, x64[3n] FP64, v[3n] FP32, forces nf x [3n] FP32
+struct blob_header {
+    uint64_t magic;
+    int64_t n, step;
+    int32_t sub, nf;
+    double time;
+};
+static const uint64_t BLOB_MAGIC = 0x4d534d5354415445ull;
+
+int md_get_state(md_system *s, void *blob, size_t *nbytes)
+{
+    if (!s || !nbytes) return MD_EINVAL;
+    const int64_t n = s->n;
+    const int nf = s->n_plt > 0 ? 3 : 1;
+    const size_t need = sizeof(blob_header) + sizeof(double) * 3 * n + sizeof(float) * 3 * n * (1 + nf);
+    if (!blob) { *nbytes = need; return MD_OK; }
+    if (*nbytes < need) return set_error(s, MD_EINVAL, "md_get_state: blob too small");
+    int rc = ensure_forces(s);
+    if (rc) return rc;
+    rc = sync_ctl(s);
+    if (rc) return rc;
+    blob_header h = {BLOB_MAGIC, n, s->host_step, s->host_sub, nf, s->h_ds->time};
+    char *p = (char *)blob;
+    memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    rc = md_read_particles(s, (double *)p, nullptr, nullptr);
+    if (rc) return rc;
+    p += sizeof(double) * 3 * n;
+    std::vector<double> tmp((size_t)(3 * n));
+    rc = md_read_particles(s, nullptr, tmp.data(), nullptr);
+    if (rc) return rc;
+    for (int64_t k = 0; k < 3 * n; ++k) ((float *)p)[k] = (float)tmp[(size_t)k];
+    p += sizeof(float) * 3 * n;
+    for (int l = 0; l < nf; ++l) {
+        k_export_f4<<<blocks_for(n), MSM_TPB, 0, s->stream>>>(n, s->f[l], s->x32, s->alt64);
+        CK(cudaGetLastError(), "export f");
+        CK(cudaMemcpyAsync(tmp.data(), s->alt64, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream), "f");
+        CK(cudaStreamSynchronize(s->stream), "sync");
+        for (int64_t k = 0; k < 3 * n; ++k) ((float *)p)[k] = (float)tmp[(size_t)k];
+        p += sizeof(float) * 3 * n;
+    }
+    *nbytes = need;
+    return MD_OK;
+}
+
+int md_set_state(md_system *s, const void *blob, size_t nbytes)
+{
+    if (!s || !blob || nbytes < sizeof(blob_header)) return MD_EINVAL;
+    blob_header h;
+    memcpy(&h, blob, sizeof h);
+    const int64_t n = s->n;
+    const int nf = s->n_plt > 0 ? 3 : 1;
+    if (h.magic != BLOB_MAGIC || h.n != n || h.nf != nf) return set_error(s, MD_EINVAL, "md_set_state: bad blob");
+    const size_t need = sizeof(blob_header) + sizeof(double) * 3 * n + sizeof(float) * 3 * n * (1 + nf);
+    if (nbytes < need) return set_error(s, MD_EINVAL, "md_set_state: blob too small");
+    // tags stay as they are: read them back in id order
+    std::vector<int32_t> tag((size_t)n);
+    std::vector<int32_t> tag_sorted((size_t)n);
+    std::vector<float> x32h((size_t)(4 * n));
+    CK(cudaMemcpyAsync(tag_sorted.data(), s->tag_s, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s->stream), "tags");
+    CK(cudaMemcpyAsync(x32h.data(), s->x32, sizeof(float4) * n, cudaMemcpyDeviceToHost, s->stream), "ids");
+    CK(cudaStreamSynchronize(s->stream), "sync");
+    for (int64_t k = 0; k < n; ++k) {
+        int32_t id;
+        memcpy(&id, &x32h[(size_t)(4 * k + 3)], sizeof id);
+        tag[(size_t)id] = tag_sorted[(size_t)k];
+    }
+    std::vector<double> X0;
+    if (s->X0) {
+        X0.resize((size_t)(3 * n));
+        std::vector<float> x0f((size_t)(4 * n));
+        CK(cudaMemcpyAsync(x0f.data(), s->X0, sizeof(float4) * n, cudaMemcpyDeviceToHost, s->stream), "X0");
+        CK(cudaStreamSynchronize(s->stream), "sync");
+        for (int64_t k = 0; k < n; ++k)
+            for (int d = 0; d < 3; ++d) X0[(size_t)(3 * k + d)] = x0f[(size_t)(4 * k + d)];
+    }
+    const char *p = (const char *)blob + sizeof h;
+    const double *x = (const double *)p;
+    p += sizeof(double) * 3 * n;
+    std::vector<double> v((size_t)(3 * n));
+    for (int64_t k = 0; k < 3 * n; ++k) v[(size_t)k] = ((const float *)p)[k];
+    p += sizeof(float) * 3 * n;
+    int rc = md_set_particles(s, x, v.data(), tag.data(), s->X0 ? X0.data() : nullptr, h.step);
+    if (rc) return rc;
+    for (int l = 0; l < nf; ++l) {
+        CK(cudaMemcpyAsync(s->alt64, p, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s->stream), "upload f");
+        k_import_forces<<<blocks_for(n), MSM_TPB, 0, s->stream>>>(n, (const float *)s->alt64, s->f[l]);
+        CK(cudaGetLastError(), "import f");
+        p += sizeof(float) * 3 * n;
+    }
+    CK(cudaStreamSynchronize(s->stream), "sync");
+    s->forces_stale = false;
+    s->forces_levels = s->n_plt > 0 ? MD_LEVEL_ALL : MD_LEVEL_FLUID;
+    return MD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,302 @@
+// K3-K5: pair and bond forces of the three levels.
+//
+//  K3  DPD (Eq. 1 plasma-plasma / plasma-wall on MD_LIST_FLUID; Eq. 3
+//      interface on MD_LIST_IFACE):
+//        F_ij = [a w - gamma w^2 (e.v_ij) + sigma w zeta_ij / sqrt(dt)] e_ij,
+//        w = 1 - r/rc, zeta_ij ~ N(0,1) from Philox4x32-10 keyed on
+//        (min id, max id, n, c) so that F^R_ji = -F^R_ij exactly.
+//  K4  harmonic bonds (Eq. 2): F_i = -2 k_b (r - r0) e_ij.
+//  K5  LJ 12-6 (Eq. 2) on MD_LIST_LJ and the printed-form Morse plus the
+//      receptor term f_A (1 - r/r0) (Eq. 2, Eq. 4) on MD_LIST_MORSE.
+//
+// One thread per list row: partner j's contribution is scattered with one
+// vector atomic (red.global.add.v4.f32), the row's own sum is added once at
+// the end.  The conservative virial (pressure, Sec. 4.2) is accumulated in
+// FP32 per thread and reduced in FP64 when requested.
+#include "msm_internal.cuh"
+
+namespace {
+
+struct pair_args {
+    int64_t rows;
+    const int32_t *row_idx;
+    const int32_t *nl, *nc;
+    int cap;
+    const float4 *x32, *v;
+    float4 *f;
+    md_geom geom;
+    const md_dstate *ds;
+    uint2 key;
+    // DPD
+    float a_same, a_wall, gamma, sig_isdt, rc2, inv_rc;
+    // LJ / Morse
+    float lj_eps24, lj_sig2, lj_rc2;
+    float m_Da_r0, m_alpha, m_inv_r0, m_rc2, f_A;
+    double *vir;
+};
+
+struct vir6 {
+    float xx, yy, zz, xy, xz, yz;
+    __device__ void add(float dx, float dy, float dz, float s)  // r (x) (s r)
+    {
+        xx += dx * dx * s; yy += dy * dy * s; zz += dz * dz * s;
+        xy += dx * dy * s; xz += dx * dz * s; yz += dy * dz * s;
+    }
+};
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void flush_virial(double *vir, const vir6 &w)
+{
+    const double c[6] = {w.xx, w.yy, w.zz, w.xy, w.xz, w.yz};
+    double s[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s[k] = warp_sum_d(c[k]);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&vir[0], s[0]); atomicAdd(&vir[4], s[1]); atomicAdd(&vir[8], s[2]);
+        atomicAdd(&vir[1], s[3]); atomicAdd(&vir[3], s[3]);
+        atomicAdd(&vir[2], s[4]); atomicAdd(&vir[6], s[4]);
+        atomicAdd(&vir[5], s[5]); atomicAdd(&vir[7], s[5]);
+    }
+}
+
+__device__ __forceinline__ void scatter(float4 *f, int32_t j, float fx, float fy, float fz)
+{
+    atomicAdd(&f[j], make_float4(fx, fy, fz, 0.0f));
+}
+
+// K3: DPD pair forces over one list (fluid level or interface level).
+template <bool VIR>
+__global__ void __launch_bounds__(MSM_TPB) k_dpd(pair_args a)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    vir6 w = {0, 0, 0, 0, 0, 0};
+    if (r < a.rows) {
+        const int32_t i = a.row_idx ? a.row_idx[r] : (int32_t)r;
+        const int cnt = min(a.nc[r], a.cap);
+        if (cnt > 0) {
+            const float4 xi = a.x32[i];
+            const float4 vi = a.v[i];
+            const uint32_t idi = id_of(xi);
+            const bool wi = tag_of(vi) == MD_TAG_WALL;
+            const uint32_t nt = (uint32_t)a.ds->step, cs = (uint32_t)a.ds->sub;
+            const float delta = a.ds->le_offset_f;
+            float fx = 0.f, fy = 0.f, fz = 0.f;
+            for (int k = 0; k < cnt; ++k) {
+                const int32_t j = a.nl[(int64_t)k * a.rows + r];
+                const float4 xj = a.x32[j];
+                float dx, dy, dz, vsh;
+                min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 >= a.rc2 || r2 == 0.0f) continue;
+                const float4 vj = a.v[j];
+                const float aij = (wi || tag_of(vj) == MD_TAG_WALL) ? a.a_wall : a.a_same;
+                const float inv_r = rsqrtf(r2);
+                const float rr = r2 * inv_r;
+                const float wr = 1.0f - rr * a.inv_rc;
+                const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
+                const float edv = ex * (vi.x - vj.x - vsh) + ey * (vi.y - vj.y) + ez * (vi.z - vj.z);
+                const float zeta = pair_zeta(idi, id_of(xj), nt, cs, a.key);
+                const float fc = aij * wr;
+                const float fp = fc - a.gamma * wr * wr * edv + a.sig_isdt * wr * zeta;
+                const float px = fp * ex, py = fp * ey, pz = fp * ez;
+                fx += px; fy += py; fz += pz;
+                scatter(a.f, j, -px, -py, -pz);
+                if (VIR) w.add(dx, dy, dz, fc * inv_r);
+            }
+            scatter(a.f, i, fx, fy, fz);
+        }
+    }
+    if (VIR) flush_virial(a.vir, w);
+}
+
+// K5a: LJ 12-6 (Eq. 2), shifted potential: the force is unshifted.
+template <bool VIR>
+__global__ void __launch_bounds__(MSM_TPB) k_lj(pair_args a)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    vir6 w = {0, 0, 0, 0, 0, 0};
+    if (r < a.rows) {
+        const int32_t i = a.row_idx[r];
+        const int cnt = min(a.nc[r], a.cap);
+        if (cnt > 0) {
+            const float4 xi = a.x32[i];
+            const float delta = a.ds->le_offset_f;
+            float fx = 0.f, fy = 0.f, fz = 0.f;
+            for (int k = 0; k < cnt; ++k) {
+                const int32_t j = a.nl[(int64_t)k * a.rows + r];
+                const float4 xj = a.x32[j];
+                float dx, dy, dz, vsh;
+                min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 >= a.lj_rc2 || r2 == 0.0f) continue;
+                const float inv_r2 = 1.0f / r2;
+                const float s2 = a.lj_sig2 * inv_r2;
+                const float s6 = s2 * s2 * s2;
+                const float fr = a.lj_eps24 * (2.0f * s6 * s6 - s6) * inv_r2;
+                const float px = fr * dx, py = fr * dy, pz = fr * dz;
+                fx += px; fy += py; fz += pz;
+                scatter(a.f, j, -px, -py, -pz);
+                if (VIR) w.add(dx, dy, dz, fr);
+            }
+            scatter(a.f, i, fx, fy, fz);
+        }
+    }
+    if (VIR) flush_virial(a.vir, w);
+}
+
+// K5b: Morse in the printed form of Eq. 2 plus the receptor term of Eq. 4.
+template <bool VIR>
+__global__ void __launch_bounds__(MSM_TPB) k_morse(pair_args a)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    vir6 w = {0, 0, 0, 0, 0, 0};
+    if (r < a.rows) {
+        const int32_t i = a.row_idx[r];
+        const int cnt = min(a.nc[r], a.cap);
+        if (cnt > 0) {
+            const float4 xi = a.x32[i];
+            const float delta = a.ds->le_offset_f;
+            float fx = 0.f, fy = 0.f, fz = 0.f;
+            for (int k = 0; k < cnt; ++k) {
+                const int32_t j = a.nl[(int64_t)k * a.rows + r];
+                const float4 xj = a.x32[j];
+                float dx, dy, dz, vsh;
+                min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 >= a.m_rc2 || r2 == 0.0f) continue;
+                const float inv_r = rsqrtf(r2);
+                const float rr = r2 * inv_r;
+                const float t = a.m_alpha * (1.0f - rr * a.m_inv_r0);
+                const float fm = a.m_Da_r0 * (expf(t) - expf(0.5f * t)) + a.f_A * (1.0f - rr * a.m_inv_r0);
+                const float s = fm * inv_r;
+                const float px = s * dx, py = s * dy, pz = s * dz;
+                fx += px; fy += py; fz += pz;
+                scatter(a.f, j, -px, -py, -pz);
+                if (VIR) w.add(dx, dy, dz, s);
+            }
+            scatter(a.f, i, fx, fy, fz);
+        }
+    }
+    if (VIR) flush_virial(a.vir, w);
+}
+
+// K4: harmonic bonds, one thread per bond.
+template <bool VIR>
+__global__ void __launch_bounds__(MSM_TPB) k_bonds(int64_t nb, const int32_t *__restrict__ ij,
+                                                  const float *__restrict__ r0, float kb2, const float4 *__restrict__ x32,
+                                                  float4 *f, md_geom geom, const md_dstate *ds, double *vir)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    vir6 w = {0, 0, 0, 0, 0, 0};
+    if (b < nb) {
+        const int32_t i = ij[2 * b], j = ij[2 * b + 1];
+        float dx, dy, dz, vsh;
+        min_image_f32(geom, ds->le_offset_f, x32[i], x32[j], dx, dy, dz, vsh);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 > 0.0f) {
+            const float inv_r = rsqrtf(r2);
+            const float rr = r2 * inv_r;
+            const float s = -kb2 * (rr - r0[b]) * inv_r;
+            scatter(f, i, s * dx, s * dy, s * dz);
+            scatter(f, j, -s * dx, -s * dy, -s * dz);
+            if (VIR) w.add(dx, dy, dz, s);
+        }
+    }
+    if (VIR) flush_virial(vir, w);
+}
+
+inline unsigned blocks_for(int64_t n) { return (unsigned)(n > 0 ? (n + MSM_TPB - 1) / MSM_TPB : 1); }
+
+}  // namespace
+
+// Forces of the levels in level_mask, accumulated into out[level] (the
+// buffers must be zero or hold partial sums of the same evaluation).
+cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3], bool virial)
+{
+    const md_config &c = s->cfg;
+    pair_args a;
+    a.x32 = s->x32;
+    a.v = s->v;
+    a.geom = s->geom;
+    a.ds = s->ds;
+    a.key = make_uint2((uint32_t)(c.seed & 0xffffffffu), (uint32_t)(c.seed >> 32));
+    a.gamma = (float)c.gamma;
+    a.rc2 = (float)(c.rc * c.rc);
+    a.inv_rc = (float)(1.0 / c.rc);
+    a.lj_eps24 = (float)(24.0 * c.lj_eps);
+    a.lj_sig2 = (float)(c.lj_sigma * c.lj_sigma);
+    a.lj_rc2 = (float)(c.lj_rc * c.lj_rc);
+    a.m_Da_r0 = (float)(c.morse_D * c.morse_alpha / c.morse_r0);
+    a.m_alpha = (float)c.morse_alpha;
+    a.m_inv_r0 = (float)(1.0 / c.morse_r0);
+    a.m_rc2 = (float)(c.morse_rc * c.morse_rc);
+    a.f_A = (float)c.f_A;
+    a.vir = s->vir_acc;
+    const int km = s->cfg_k_m > 0 ? s->cfg_k_m : 1;
+
+    if (level_mask & MD_LEVEL_FLUID) {
+        a.rows = s->n;
+        a.row_idx = nullptr;
+        a.nl = s->nl[MD_LIST_FLUID];
+        a.nc = s->nc[MD_LIST_FLUID];
+        a.cap = s->cap[MD_LIST_FLUID];
+        a.f = out[0];
+        a.a_same = (float)c.a_ff;
+        a.a_wall = (float)c.a_fw;
+        a.sig_isdt = (float)(c.sigma / sqrt(c.dt));
+        if (virial) k_dpd<true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        else k_dpd<false><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        MSM_COUNT(s, 1);
+    }
+    if ((level_mask & MD_LEVEL_IFACE) && s->n_plt > 0) {
+        a.rows = s->n_plt;
+        a.row_idx = s->plt_sorted;
+        a.nl = s->nl[MD_LIST_IFACE];
+        a.nc = s->nc[MD_LIST_IFACE];
+        a.cap = s->cap[MD_LIST_IFACE];
+        a.f = out[1];
+        a.a_same = (float)c.a_fp;
+        a.a_wall = (float)c.a_fp;
+        a.sig_isdt = (float)(c.sigma / sqrt(c.dt / km));
+        if (virial) k_dpd<true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        else k_dpd<false><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        MSM_COUNT(s, 1);
+    }
+    if ((level_mask & MD_LEVEL_PLT) && s->n_plt > 0) {
+        if (s->nb > 0) {
+            if (virial)
+                k_bonds<true><<<blocks_for(s->nb), MSM_TPB, 0, s->stream>>>(s->nb, s->bond_ij, s->bond_r0,
+                                                                           (float)(2.0 * c.k_bond), s->x32, out[2],
+                                                                           s->geom, s->ds, s->vir_acc);
+            else
+                k_bonds<false><<<blocks_for(s->nb), MSM_TPB, 0, s->stream>>>(s->nb, s->bond_ij, s->bond_r0,
+                                                                            (float)(2.0 * c.k_bond), s->x32, out[2],
+                                                                            s->geom, s->ds, s->vir_acc);
+        }
+        a.rows = s->n_plt;
+        a.row_idx = s->plt_sorted;
+        a.nl = s->nl[MD_LIST_LJ];
+        a.nc = s->nc[MD_LIST_LJ];
+        a.cap = s->cap[MD_LIST_LJ];
+        a.f = out[2];
+        if (virial) k_lj<true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        else k_lj<false><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        MSM_COUNT(s, 1 + (s->nb > 0 ? 1 : 0) + (s->n_rec > 0 ? 1 : 0));
+        if (s->n_rec > 0) {
+            a.rows = s->n_rec;
+            a.row_idx = s->rec_sorted;
+            a.nl = s->nl[MD_LIST_MORSE];
+            a.nc = s->nc[MD_LIST_MORSE];
+            a.cap = s->cap[MD_LIST_MORSE];
+            if (virial) k_morse<true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+            else k_morse<false><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        }
+    }
+    return cudaGetLastError();
+}

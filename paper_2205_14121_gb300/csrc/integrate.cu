@@ -1,0 +1,222 @@
+// K6/K7: velocity-Verlet kicks and drifts of the multi-level loop (Table 1)
+// with the rebuild check fused into the drift.
+//
+//  kick   v += sum_l h_l f_l  (+ h_fluid g x^: the body force belongs to the
+//         fluid level)
+//  drift  x64 += dt v (FP64 master positions), then the boundary:
+//           walls   bounce-back at y = 0 and y = Ly (position mirrored,
+//                   velocity reversed: no-slip, Sec. 3.1)
+//           LE      crossing y moves x by -/+ delta and v_x by -/+ rate*Ly
+//           periodic wrap in x, z (and y without walls)
+//         x32 = (float)x64; |x32 - x_build| (minimum image) against the
+//         skin threshold -> rebuild flag; NaN / escape -> unstable flag.
+//  zero   the level buffers the next force evaluation accumulates into.
+#include "msm_internal.cuh"
+
+namespace {
+
+struct kd_args {
+    int64_t n;
+    const int32_t *idx;    // null: thread k handles particle k; else particle idx[k]
+    double *xs, *ys, *zs;
+    float4 *x32, *v;
+    float4 *f[3];
+    const float4 *xb;
+    const int32_t *tag;
+    float h[3];            // kick factor per level (0: level not kicked)
+    int kick_which;        // DRIFT_* selector of kicked particles, -1: none
+    int drift_which;       // DRIFT_* selector of drifted particles, -1: none
+    unsigned zero_levels;
+    int nf;
+    float g;
+    double dt;
+    double L[3];
+    double wall;
+    double shear_v;
+    float skin_half, margin, skin;
+    md_geom geom;
+    const md_dstate *ds;
+    int32_t *ctl;
+};
+
+__device__ __forceinline__ bool selected(int which, int32_t t)
+{
+    if (which < 0 || t == MD_TAG_WALL) return false;
+    if (which == DRIFT_ALL) return true;
+    if (which == DRIFT_FLUID) return t < 0;
+    return t >= 0;
+}
+
+__global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.n) return;
+    const int64_t k = a.idx ? a.idx[r] : r;
+    const int32_t t = a.tag[k];
+    const bool kick = selected(a.kick_which, t);
+    const bool drift = selected(a.drift_which, t);
+    if (kick || drift) {
+        float4 vv = a.v[k];
+        if (kick) {
+            float ax = 0.f, ay = 0.f, az = 0.f;
+            for (int l = 0; l < a.nf; ++l) {
+                if (a.h[l] == 0.0f) continue;
+                const float4 fl = a.f[l][k];
+                ax += a.h[l] * fl.x; ay += a.h[l] * fl.y; az += a.h[l] * fl.z;
+            }
+            ax += a.h[0] * a.g;
+            vv.x += ax;
+            vv.y += ay;
+            vv.z += az;
+        }
+        if (drift) {
+            double x = a.xs[k] + a.dt * (double)vv.x;
+            double y = a.ys[k] + a.dt * (double)vv.y;
+            double z = a.zs[k] + a.dt * (double)vv.z;
+            const double Lx = a.L[0], Ly = a.L[1], Lz = a.L[2];
+            if (a.geom.walls) {
+                if (y < 0.0) {
+                    y = -y; vv.x = -vv.x; vv.y = -vv.y; vv.z = -vv.z;
+                } else if (y >= Ly) {
+                    y = 2.0 * Ly - y; vv.x = -vv.x; vv.y = -vv.y; vv.z = -vv.z;
+                }
+            } else if (a.geom.le) {
+                const double delta = a.ds->le_offset;
+                if (y >= Ly) {
+                    y -= Ly; x -= delta; vv.x -= (float)a.shear_v;
+                } else if (y < 0.0) {
+                    y += Ly; x += delta; vv.x += (float)a.shear_v;
+                }
+            } else {
+                if (y >= Ly) y -= Ly;
+                else if (y < 0.0) y += Ly;
+            }
+            if (x >= Lx) x -= Lx;
+            else if (x < 0.0) x += Lx;
+            if (x >= Lx) x -= Lx;       // a Lees-Edwards shift can add one more period
+            else if (x < 0.0) x += Lx;
+            if (z >= Lz) z -= Lz;
+            else if (z < 0.0) z += Lz;
+            a.xs[k] = x; a.ys[k] = y; a.zs[k] = z;
+            float4 xn = a.x32[k];
+            xn.x = (float)x; xn.y = (float)y; xn.z = (float)z;
+            a.x32[k] = xn;
+            // rebuild check against the positions of the last build
+            float dx, dy, dz, vs;
+            min_image_f32(a.geom, a.ds->le_offset_f, xn, a.xb[k], dx, dy, dz, vs);
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            float thr = a.skin_half - a.margin;
+            if (a.geom.le) {
+                float dd = fabsf(a.ds->le_offset_f - a.ds->le_build_f);
+                dd = fminf(dd, a.geom.L[0] - dd);
+                thr = 0.5f * (a.skin - dd) - a.margin;
+            }
+            if (!(d2 <= thr * thr) || thr <= 0.0f) a.ctl[CTL_REBUILD] = 1;
+            const bool bad = !(fabs(x) < 1e30) || !(fabsf(vv.x) + fabsf(vv.y) + fabsf(vv.z) < 1e30f) ||
+                             (a.geom.walls && (y < -a.wall || y > Ly + a.wall));
+            if (bad) a.ctl[CTL_UNSTABLE] = 1;
+        }
+        a.v[k] = vv;
+    }
+    for (int l = 0; l < a.nf; ++l)
+        if (a.zero_levels & (1u << l)) a.f[l][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Set the device time index (n, c) and the time n dt + c dt_m + q dt_p;
+// recompute the Lees-Edwards offset and check its drift since the build.
+__global__ void k_set_time(md_dstate *ds, int64_t n, int32_t c, double t, double rate_Ly, double Lx, int le,
+                           float skin, float margin, int32_t *ctl)
+{
+    ds->step = n;
+    ds->sub = c;
+    ds->time = t;
+    if (le) {
+        double d = fmod(rate_Ly * t, Lx);
+        if (d < 0.0) d += Lx;
+        ds->le_offset = d;
+        ds->le_offset_f = (float)d;
+        float dd = fabsf(ds->le_offset_f - ds->le_build_f);
+        dd = fminf(dd, (float)Lx - dd);
+        if (0.5f * (skin - dd) - margin <= 0.0f) ctl[CTL_REBUILD] = 1;
+    }
+}
+
+__global__ void k_zero_f4(float4 *p, int64_t n)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) p[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+inline unsigned blocks_for(int64_t n) { return (unsigned)(n > 0 ? (n + MSM_TPB - 1) / MSM_TPB : 1); }
+
+kd_args base_args(md_system *s)
+{
+    kd_args a;
+    a.n = s->n;
+    a.idx = nullptr;
+    a.xs = s->xs; a.ys = s->ys; a.zs = s->zs;
+    a.x32 = s->x32; a.v = s->v;
+    for (int l = 0; l < 3; ++l) { a.f[l] = s->f[l]; a.h[l] = 0.0f; }
+    a.nf = s->n_plt > 0 ? 3 : 1;
+    a.xb = s->xb;
+    a.tag = s->tag_s;
+    a.g = (float)s->cfg.body_force;
+    a.dt = 0.0;
+    for (int d = 0; d < 3; ++d) a.L[d] = s->cfg.box[d];
+    a.wall = s->cfg.wall;
+    a.shear_v = s->cfg.shear_rate * s->cfg.box[1];
+    a.skin = (float)s->cfg.skin;
+    a.skin_half = 0.5f * (float)s->cfg.skin;
+    a.margin = s->margin;
+    a.geom = s->geom;
+    a.ds = s->ds;
+    a.ctl = s->ctl;
+    a.kick_which = -1;
+    a.drift_which = -1;
+    a.zero_levels = 0;
+    return a;
+}
+
+}  // namespace
+
+// Kick (per-level factors h[3], selector kick_which) + drift by dt of the
+// drift_which subset + zeroing of zero_levels.  plt_rows: iterate only over
+// the platelet particles (the subset rows) instead of every particle.
+cudaError_t launch_kick_drift(md_system *s, const float h[3], int kick_which, double dt, int drift_which,
+                              unsigned zero_levels, bool plt_rows)
+{
+    kd_args a = base_args(s);
+    for (int l = 0; l < 3; ++l) a.h[l] = h[l];
+    a.kick_which = kick_which;
+    a.drift_which = drift_which;
+    a.dt = dt;
+    a.zero_levels = zero_levels;
+    if (plt_rows) {
+        a.idx = s->plt_sorted;
+        a.n = s->n_plt;
+    }
+    if (a.n <= 0) return cudaSuccess;
+    k_kick_drift<<<blocks_for(a.n), MSM_TPB, 0, s->stream>>>(a);
+    MSM_COUNT(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_time(md_system *s, int64_t n, int32_t c, double t)
+{
+    const md_config &cf = s->cfg;
+    k_set_time<<<1, 1, 0, s->stream>>>(s->ds, n, c, t, cf.shear_rate * cf.box[1], cf.box[0], s->geom.le,
+                                       (float)cf.skin, s->margin, s->ctl);
+    MSM_COUNT(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_forces(md_system *s, unsigned levels)
+{
+    const int nf = s->n_plt > 0 ? 3 : 1;
+    for (int l = 0; l < nf; ++l)
+        if (levels & (1u << l)) {
+            k_zero_f4<<<blocks_for(s->n), MSM_TPB, 0, s->stream>>>(s->f[l], s->n);
+            MSM_COUNT(s, 1);
+        }
+    return cudaGetLastError();
+}

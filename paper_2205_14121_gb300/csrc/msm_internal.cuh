@@ -1,0 +1,264 @@
+// Internal declarations of libmsm: system state, device helpers, kernel entry
+// points shared between the translation units.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "msm.h"
+
+#define MSM_TPB 256
+
+// ---------------------------------------------------------------------------
+// control words (device int32 array), see md_system::ctl
+// ---------------------------------------------------------------------------
+enum {
+    CTL_REBUILD = 0,     // displacement check tripped / build requested
+    CTL_OVERFLOW = 1,    // bit per list kind
+    CTL_UNSTABLE = 2,    // NaN/Inf or escape seen by the integrator
+    CTL_NPLT = 3,        // subset compaction counters
+    CTL_NREC = 4,
+    CTL_MAXROW = 8,      // 4 slots: longest row per list kind (this build)
+    CTL_WORDS = 16
+};
+
+// Step-dependent values read by the kernels; written on the device so that a
+// captured multi-step graph needs no host updates.
+struct md_dstate {
+    int64_t step;        // completed fluid steps n
+    int32_t sub;         // completed interface substeps c within the step
+    int32_t pad;
+    double  time;        // n dt + c dt_m
+    double  le_offset;   // Lees-Edwards image offset in [0, Lx)
+    float   le_offset_f; // its FP32 copy
+    float   le_build_f;  // offset at the last list build
+    int64_t n_builds;
+    int64_t steps_left;  // countdown of a captured loop
+};
+
+struct md_grid {
+    int   nc[3];
+    float lo[3];
+    float h[3];
+    float inv_h[3];
+    int64_t ncell;
+    int32_t *start;  // ncell + 1
+    int32_t *count;  // ncell
+};
+
+struct md_geom {
+    float L[3], hL[3];
+    int   walls, le;
+    float shear_v;   // shear_rate * Ly (image velocity jump)
+};
+
+struct md_system {
+    md_config cfg;
+    cudaStream_t stream;
+    int device;
+    std::string err;
+
+    int64_t n, n_plt, n_rec, nb;
+    int cap[4];
+
+    // particle arrays (cell-sorted)
+    double *xs, *ys, *zs;        // FP64 master positions
+    float4 *x32;                 // xyz + id bits
+    float4 *v;                   // v + tag bits
+    float4 *f[3];                // level forces (fluid, iface, platelet)
+    float4 *xb;                  // positions at the last build
+    int32_t *tag_s;              // tags in sorted order
+    int32_t *cellid, *slot, *perm, *pos_of_id;
+    double *alt64;               // 3n
+    float4 *altv, *altx, *altf[3];
+    int32_t *alt_tag;
+    float4 *X0;                  // rest positions, id order
+
+    // grids
+    md_grid gmain, gplt, grec;
+
+    // subsets
+    int32_t *plt_idx, *plt_sorted, *plt_cell, *plt_slot;
+    int32_t *rec_idx, *rec_sorted, *rec_cell, *rec_slot;
+
+    // lists (ELL, column-major: entry k of row r at k*rows + r)
+    int32_t *nl[4], *nc[4];
+
+    // bonds
+    int32_t *bond_id, *bond_ij;
+    float *bond_r0;
+
+    // scan scratch
+    int32_t *scan_sums;
+    int64_t scan_cap;
+
+    // reductions
+    double *red_part;            // partial sums [RED_BLOCKS][RED_WORDS]
+    double *red_out;             // [RED_WORDS]
+    double *vir_acc;             // 9 doubles (conservative virial)
+    int red_blocks;
+
+    // control
+    int32_t *ctl;
+    md_dstate *ds;
+    int32_t *h_ctl;              // pinned host mirror
+    md_dstate *h_ds;
+
+    md_geom geom;
+    float cut2[4];               // list cut-offs squared (FP32)
+    float excl2;
+    float disp2;                 // rebuild threshold on displacement^2
+
+    bool lists_stale = true;
+    bool forces_stale = true;
+    bool have_particles = false;
+    bool have_bonds = false;
+    int64_t host_step = 0;
+    int32_t host_sub = 0;
+    unsigned forces_levels = 0;  // levels whose buffers hold current forces
+    int cfg_k_m = 1;             // interface substeps of the active schedule
+    float margin = 0.0f;         // extra slack in the rebuild trigger (MTS)
+
+    // kernel accounting (md_profile_*)
+    int64_t nlaunch = 0;                      // every kernel launched
+    int64_t cls_launch[MD_PROF_CLASSES] = {};
+    double cls_ms[MD_PROF_CLASSES] = {};
+    bool prof_on = false;
+    struct prof_rec { int cls; cudaEvent_t a, b; };
+    std::vector<prof_rec> prof_pending;
+    std::vector<cudaEvent_t> ev_pool;
+    int prof_cls = -1;
+    cudaEvent_t prof_a = nullptr;
+    int64_t prof_mark = 0;
+};
+
+// kernel accounting helpers (diag.cu)
+void prof_begin(md_system *s, int cls);
+void prof_end(md_system *s);
+#define MSM_COUNT(s, k) ((s)->nlaunch += (k))
+
+// reductions layout
+enum { RED_WORDS = 16, RED_BLOCKS_MAX = 1024 };
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int tag_of(float4 v) { return __float_as_int(v.w); }
+__device__ __forceinline__ uint32_t id_of(float4 x) { return (uint32_t)__float_as_int(x.w); }
+
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the two multiply-xor
+// S-boxes with the Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Standard normal from two 32-bit words (Box-Muller on their top 24 bits).
+__device__ __forceinline__ float gauss_from_bits(uint32_t r0, uint32_t r1)
+{
+    const float u1 = (float)((r0 >> 8) + 1u) * (1.0f / 16777216.0f);
+    const float u2 = (float)(r1 >> 8) * (1.0f / 16777216.0f);
+    return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+// Pair noise zeta_ij at time index (nt, cs).
+__device__ __forceinline__ float pair_zeta(uint32_t a, uint32_t b, uint32_t nt, uint32_t cs, uint2 key)
+{
+    const uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
+    const uint4 r = philox4x32_10(make_uint4(lo, hi, nt, cs), key);
+    return gauss_from_bits(r.x, r.y);
+}
+
+// FP32 periodic difference with an exact shift of the far coordinate.
+__device__ __forceinline__ float img_sub(float a, float b, float L, float hL)
+{
+    float d = __fsub_rn(a, b);
+    if (d > hL) d = __fsub_rn(__fsub_rn(a, L), b);
+    else if (d < -hL) d = __fsub_rn(a, __fsub_rn(b, L));
+    return d;
+}
+
+// Minimum-image separation r_ij = x_i - x_j in FP32, the same operation
+// sequence as the list predicate.  *vshift gets the image velocity jump in x
+// to subtract from v_i - v_j (Lees-Edwards), 0 otherwise.
+__device__ __forceinline__ void min_image_f32(const md_geom &g, float delta, float4 xi, float4 xj,
+                                              float &dx, float &dy, float &dz, float &vshift)
+{
+    float xj0 = xj.x;
+    vshift = 0.0f;
+    if (g.walls) {
+        dy = __fsub_rn(xi.y, xj.y);
+    } else if (g.le) {
+        dy = __fsub_rn(xi.y, xj.y);
+        if (dy > g.hL[1]) {
+            dy = __fsub_rn(__fsub_rn(xi.y, g.L[1]), xj.y);
+            xj0 = __fadd_rn(xj0, delta);
+            if (xj0 >= g.L[0]) xj0 = __fsub_rn(xj0, g.L[0]);
+            vshift = g.shear_v;
+        } else if (dy < -g.hL[1]) {
+            dy = __fsub_rn(xi.y, __fsub_rn(xj.y, g.L[1]));
+            xj0 = __fsub_rn(xj0, delta);
+            if (xj0 < 0.0f) xj0 = __fadd_rn(xj0, g.L[0]);
+            vshift = -g.shear_v;
+        }
+    } else {
+        dy = img_sub(xi.y, xj.y, g.L[1], g.hL[1]);
+    }
+    dx = img_sub(xi.x, xj0, g.L[0], g.hL[0]);
+    dz = img_sub(xi.z, xj.z, g.L[2], g.hL[2]);
+}
+
+__device__ __forceinline__ float r2_f32(float dx, float dy, float dz)
+{
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__device__ __forceinline__ int cell_coord(const md_grid &g, int d, float x)
+{
+    return clampi(__float2int_rd((x - g.lo[d]) * g.inv_h[d]), 0, g.nc[d] - 1);
+}
+
+__device__ __forceinline__ int64_t cell_index(const md_grid &g, int cx, int cy, int cz)
+{
+    return ((int64_t)cz * g.nc[1] + cy) * g.nc[0] + cx;
+}
+
+__device__ __forceinline__ bool gate_closed(const int32_t *gate) { return gate && *gate == 0; }
+
+// ---------------------------------------------------------------------------
+// host-side launchers (one translation unit each)
+// ---------------------------------------------------------------------------
+// sort.cu
+cudaError_t launch_rebuild(md_system *s, const int32_t *gate);
+cudaError_t launch_scan(md_system *s, const int32_t *in, int32_t *out, int64_t count, int32_t *total_out,
+                        const int32_t *gate);
+// neighbor.cu
+cudaError_t launch_build_lists(md_system *s, const int32_t *gate);
+// forces.cu
+cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3], bool virial);
+// integrate.cu
+cudaError_t launch_kick_drift(md_system *s, const float h[3], int kick_which, double dt, int drift_which,
+                              unsigned zero_levels, bool plt_rows);
+cudaError_t launch_set_time(md_system *s, int64_t n, int32_t c, double t);
+cudaError_t launch_zero_forces(md_system *s, unsigned levels);
+// reduce.cu
+cudaError_t launch_kinetics(md_system *s);
+// api.cu helpers
+int set_error(md_system *s, int code, const char *msg);
+int cuda_fail(md_system *s, cudaError_t e, const char *where);
+
+// kick-drift subsets
+enum { DRIFT_ALL = 0, DRIFT_FLUID = 1, DRIFT_PLT = 2 };

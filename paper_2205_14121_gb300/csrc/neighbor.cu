@@ -1,0 +1,215 @@
+// K2: Verlet-skin neighbour lists (Table 1, "neighbor lists construction").
+//
+// One thread per list row scans the cells within reach of its particle and
+// appends every partner that passes the binary32 list predicate
+//     r2 = (dx*dx + dy*dy) + dz*dz < (cut + skin)^2        (no FMA)
+// computed from the minimum-image separation of min_image_f32(); a CPU
+// evaluation of the same operation sequence yields the identical pair set.
+//
+// Lists are ELL, column-major (entry k of row r at k*rows + r) so that the
+// force kernels, one thread per row, read them coalesced.  Row counts beyond
+// the capacity are recorded (overflow bit + longest row) and never written.
+//
+//   MD_LIST_FLUID  rows: every particle; partners j > i, plasma-plasma and
+//                  plasma-wall pairs (Eq. 1)
+//   MD_LIST_IFACE  rows: platelet particles; partners: every plasma or wall
+//                  particle (Eq. 3)
+//   MD_LIST_LJ     rows: platelet particles; partners j > i on the platelet
+//                  sub-grid, excluding same-platelet pairs closer than
+//                  lj_excl at rest (Eq. 2)
+//   MD_LIST_MORSE  rows: receptor sites; partners j > i on the receptor
+//                  sub-grid belonging to another platelet (Eq. 4)
+#include "msm_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ int wrapc(int c, int n)
+{
+    c %= n;
+    return c < 0 ? c + n : c;
+}
+
+// Visit every member of the cells within reach R of xi; LE rows that cross
+// the y boundary are shifted by the image offset.
+template <class F>
+__device__ __forceinline__ void for_candidates(const md_grid &g, const md_geom &geom, float delta, float4 xi,
+                                               float R, const int32_t *__restrict__ members, F fn)
+{
+    int zlo = __float2int_rd((xi.z - g.lo[2] - R) * g.inv_h[2]);
+    int zhi = __float2int_rd((xi.z - g.lo[2] + R) * g.inv_h[2]);
+    if (zhi - zlo + 1 > g.nc[2]) zhi = zlo + g.nc[2] - 1;
+    int ylo = __float2int_rd((xi.y - g.lo[1] - R) * g.inv_h[1]);
+    int yhi = __float2int_rd((xi.y - g.lo[1] + R) * g.inv_h[1]);
+    if (geom.walls) {
+        ylo = max(ylo, 0);
+        yhi = min(yhi, g.nc[1] - 1);
+    } else if (yhi - ylo + 1 > g.nc[1]) {
+        yhi = ylo + g.nc[1] - 1;
+    }
+    for (int cz = zlo; cz <= zhi; ++cz) {
+        const int wz = wrapc(cz, g.nc[2]);
+        for (int cy = ylo; cy <= yhi; ++cy) {
+            int wy = cy;
+            float sx = 0.0f;
+            if (!geom.walls) {
+                if (cy < 0) {
+                    wy = wrapc(cy, g.nc[1]);
+                    if (geom.le) sx = delta;
+                } else if (cy >= g.nc[1]) {
+                    wy = wrapc(cy, g.nc[1]);
+                    if (geom.le) sx = -delta;
+                }
+            }
+            int xlo = __float2int_rd((xi.x + sx - g.lo[0] - R) * g.inv_h[0]);
+            int xhi = __float2int_rd((xi.x + sx - g.lo[0] + R) * g.inv_h[0]);
+            if (xhi - xlo + 1 > g.nc[0]) xhi = xlo + g.nc[0] - 1;
+            for (int cx = xlo; cx <= xhi; ++cx) {
+                const int64_t c = cell_index(g, wrapc(cx, g.nc[0]), wy, wz);
+                const int32_t b = g.start[c], e = g.start[c + 1];
+                for (int32_t s = b; s < e; ++s) fn(members ? members[s] : s);
+            }
+        }
+    }
+}
+
+struct build_args {
+    int64_t n;
+    int64_t rows;
+    const int32_t *row_idx;     // null: row r is particle r
+    const float4 *x32;
+    const int32_t *tag;
+    const float4 *X0;           // rest positions by id (LJ kind)
+    md_grid g;
+    const int32_t *members;     // null: main grid
+    md_geom geom;
+    const md_dstate *ds;
+    float R, cut2, excl2;
+    int32_t *nl, *nc;
+    int cap;
+    int kind;
+    int32_t *ctl;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(MSM_TPB) k_build(build_args a, const int32_t *gate)
+{
+    if (gate_closed(gate)) return;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = r < a.rows;
+    int cnt = 0;
+    if (active) {
+        const int32_t i = a.row_idx ? a.row_idx[r] : (int32_t)r;
+        const int32_t ti = a.tag[i];
+        const float4 xi = a.x32[i];
+        const float delta = a.ds->le_offset_f;
+        const bool owns = KIND == MD_LIST_FLUID ? (ti < 0) : true;
+        if (owns) {
+            float4 x0i = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (KIND == MD_LIST_LJ) x0i = a.X0[__float_as_int(xi.w)];
+            const int64_t rows = a.rows;
+            for_candidates(a.g, a.geom, delta, xi, a.R, a.members, [&](int32_t j) {
+                const int32_t tj = a.tag[j];
+                if (KIND == MD_LIST_FLUID) {
+                    if (j <= i || tj >= 0) return;
+                    if (ti == MD_TAG_WALL && tj == MD_TAG_WALL) return;
+                } else if (KIND == MD_LIST_IFACE) {
+                    if (tj >= 0) return;
+                } else if (KIND == MD_LIST_LJ) {
+                    if (j <= i) return;
+                } else {  // MORSE
+                    if (j <= i) return;
+                    if ((ti & ~MD_RECEPTOR_BIT) == (tj & ~MD_RECEPTOR_BIT)) return;
+                }
+                const float4 xj = a.x32[j];
+                float dx, dy, dz, vs;
+                min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vs);
+                if (!(r2_f32(dx, dy, dz) < a.cut2)) return;
+                if (KIND == MD_LIST_LJ && (ti & ~MD_RECEPTOR_BIT) == (tj & ~MD_RECEPTOR_BIT)) {
+                    const float4 x0j = a.X0[__float_as_int(xj.w)];
+                    const float ex = __fsub_rn(x0i.x, x0j.x), ey = __fsub_rn(x0i.y, x0j.y),
+                                ez = __fsub_rn(x0i.z, x0j.z);
+                    if (r2_f32(ex, ey, ez) < a.excl2) return;
+                }
+                if (cnt < a.cap) a.nl[(int64_t)cnt * rows + r] = j;
+                ++cnt;
+            });
+        }
+    }
+    // every lane of the warp reaches the row bookkeeping (shuffle needs all)
+    if (active) a.nc[r] = cnt;
+    int m = active ? cnt : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) {
+        atomicMax(&a.ctl[CTL_MAXROW + KIND], m);
+        if (m > a.cap) atomicOr(&a.ctl[CTL_OVERFLOW], 1 << KIND);
+    }
+}
+
+inline unsigned blocks_for(int64_t n) { return (unsigned)(n > 0 ? (n + MSM_TPB - 1) / MSM_TPB : 1); }
+
+}  // namespace
+
+cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
+{
+    const float margin = 1.0f + 1e-5f;
+    build_args a;
+    a.n = s->n;
+    a.x32 = s->x32;
+    a.tag = s->tag_s;
+    a.X0 = s->X0;
+    a.geom = s->geom;
+    a.ds = s->ds;
+    a.ctl = s->ctl;
+    a.excl2 = s->excl2;
+
+    // plasma / wall list over the main grid
+    a.rows = s->n;
+    a.row_idx = nullptr;
+    a.g = s->gmain;
+    a.members = nullptr;
+    a.R = (float)(s->cfg.rc + s->cfg.skin) * margin;
+    a.cut2 = s->cut2[MD_LIST_FLUID];
+    a.nl = s->nl[MD_LIST_FLUID];
+    a.nc = s->nc[MD_LIST_FLUID];
+    a.cap = s->cap[MD_LIST_FLUID];
+    a.kind = MD_LIST_FLUID;
+    k_build<MD_LIST_FLUID><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
+
+    if (s->n_plt > 0) {
+        a.rows = s->n_plt;
+        a.row_idx = s->plt_sorted;
+        a.cut2 = s->cut2[MD_LIST_IFACE];
+        a.nl = s->nl[MD_LIST_IFACE];
+        a.nc = s->nc[MD_LIST_IFACE];
+        a.cap = s->cap[MD_LIST_IFACE];
+        a.kind = MD_LIST_IFACE;
+        k_build<MD_LIST_IFACE><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
+
+        a.g = s->gplt;
+        a.members = s->plt_sorted;
+        a.R = (float)(s->cfg.lj_rc + s->cfg.skin) * margin;
+        a.cut2 = s->cut2[MD_LIST_LJ];
+        a.nl = s->nl[MD_LIST_LJ];
+        a.nc = s->nc[MD_LIST_LJ];
+        a.cap = s->cap[MD_LIST_LJ];
+        a.kind = MD_LIST_LJ;
+        k_build<MD_LIST_LJ><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
+
+        if (s->n_rec > 0) {
+            a.rows = s->n_rec;
+            a.row_idx = s->rec_sorted;
+            a.g = s->grec;
+            a.members = s->rec_sorted;
+            a.R = (float)(s->cfg.morse_rc + s->cfg.skin) * margin;
+            a.cut2 = s->cut2[MD_LIST_MORSE];
+            a.nl = s->nl[MD_LIST_MORSE];
+            a.nc = s->nc[MD_LIST_MORSE];
+            a.cap = s->cap[MD_LIST_MORSE];
+            a.kind = MD_LIST_MORSE;
+            k_build<MD_LIST_MORSE><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
+        }
+    }
+    MSM_COUNT(s, 1 + (s->n_plt > 0 ? 2 + (s->n_rec > 0 ? 1 : 0) : 0));
+    return cudaGetLastError();
+}

@@ -1,0 +1,72 @@
+// K8: FP64 reductions of the observables (Sec. 4.2): total momentum,
+// kinetic energy and the peculiar kinetic tensor (velocity relative to the
+// imposed Lees-Edwards profile), in two passes (per-block partials, then one
+// block over the partials) so the result does not depend on atomic order.
+#include "msm_internal.cuh"
+
+namespace {
+
+// word layout of the partials / result
+enum { W_PX = 0, W_PY, W_PZ, W_KE, W_KXX, W_KYY, W_KZZ, W_KXY, W_KXZ, W_KYZ, W_N, W_COUNT };
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(MSM_TPB) k_kinetics(int64_t n, const float4 *__restrict__ v,
+                                                     const double *__restrict__ ys, const int32_t *__restrict__ tag,
+                                                     int le, double rate, double half_Ly, double *part)
+{
+    double acc[W_COUNT];
+#pragma unroll
+    for (int w = 0; w < W_COUNT; ++w) acc[w] = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        if (tag[k] == MD_TAG_WALL) continue;
+        const float4 vv = v[k];
+        const double vx = vv.x, vy = vv.y, vz = vv.z;
+        const double ux = le ? vx - rate * (ys[k] - half_Ly) : vx;
+        acc[W_PX] += vx; acc[W_PY] += vy; acc[W_PZ] += vz;
+        acc[W_KE] += 0.5 * (vx * vx + vy * vy + vz * vz);
+        acc[W_KXX] += ux * ux; acc[W_KYY] += vy * vy; acc[W_KZZ] += vz * vz;
+        acc[W_KXY] += ux * vy; acc[W_KXZ] += ux * vz; acc[W_KYZ] += vy * vz;
+        acc[W_N] += 1.0;
+    }
+    __shared__ double sh[MSM_TPB / 32][W_COUNT];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int w = 0; w < W_COUNT; ++w) {
+        const double s = warp_sum(acc[w]);
+        if (lane == 0) sh[wid][w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < W_COUNT) {
+        double s = 0.0;
+        for (int q = 0; q < MSM_TPB / 32; ++q) s += sh[q][threadIdx.x];
+        part[(int64_t)blockIdx.x * RED_WORDS + threadIdx.x] = s;
+    }
+}
+
+__global__ void k_reduce_final(const double *part, int nblocks, double *out)
+{
+    const int w = threadIdx.x;
+    if (w >= RED_WORDS) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * RED_WORDS + w];
+    out[w] = s;
+}
+
+}  // namespace
+
+cudaError_t launch_kinetics(md_system *s)
+{
+    const int nb = s->red_blocks;
+    k_kinetics<<<nb, MSM_TPB, 0, s->stream>>>(s->n, s->v, s->ys, s->tag_s, s->geom.le, s->cfg.shear_rate,
+                                              0.5 * s->cfg.box[1], s->red_part);
+    k_reduce_final<<<1, 32, 0, s->stream>>>(s->red_part, nb, s->red_out);
+    MSM_COUNT(s, 2);
+    return cudaGetLastError();
+}

@@ -227,6 +227,7 @@ def plasma_box(n=None, box=None, rho=3.0, walls=False, wall=1.0, body_force=0.0,
     rng = rng_for(seed)
     if box is None:
         L = (n / rho) ** (1.0 / 3.0)
+        L = float(np.float32(L))   # binary32-exact edge: FP32 and FP64 images agree
         box = (L, L, L)
     if n is None:
         n = int(round(rho * box[0] * box[1] * box[2]))

@@ -1,0 +1,231 @@
+"""GPU path (libmsm through the C ABI) against the FP64 oracle.
+
+Tolerances:
+ * neighbour sets: bit-exact (the oracle evaluates the same binary32 predicate);
+ * per-step forces: |F_gpu - F_orc|_inf <= 1e-5 (|F_orc,i| + F_rms) per particle,
+   the oracle fed the GPU's FP32 snapshot (positions, velocities, box, offset);
+ * FP64 reductions: 1e-10 relative on identical inputs;
+ * short trajectories: derived from FP32 force rounding (see each test).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def f32(a):
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+def make_gpu(s, step0=0, x=None, v=None, **kw):
+    import paper_2205_14121_gb300 as M
+    return M.System(s.box, s.x if x is None else x, s.v if v is None else v, s.tag, X0=s.X0, bonds=s.bonds,
+                    r0=s.r0, walls=s.walls, wall=s.wall, shear_rate=s.shear_rate, body_force=s.body_force,
+                    step0=step0, **kw)
+
+
+def le_offset_f32(s, step, dt=0.01):
+    if s.walls or not s.shear_rate:
+        return 0.0
+    return float(np.float32((s.shear_rate * s.box[1] * step * dt) % s.box[0]))
+
+
+def oracle_forces(s, x32, v, step, level_mask=O.LVL_ALL, dt=0.01, dt_m=None):
+    p = O.system_params(s, le_offset=le_offset_f32(s, step, dt))
+    f, acc = O.forces_brute(p, f32(x32), f32(v), s.tag, X0=f32(s.X0), bonds=s.bonds, r0=f32(s.r0),
+                            level_mask=level_mask, n_time=step, dt=dt, dt_m=dt_m)
+    return f, acc
+
+
+def assert_force_parity(f_gpu, f_orc, tol=TOL):
+    mag = np.sqrt((f_orc ** 2).sum(1))
+    frms = np.sqrt((mag ** 2).mean())
+    err = np.abs(f_gpu - f_orc).max(1)
+    bound = tol * (mag + frms)
+    worst = np.argmax(err / bound)
+    assert np.all(err <= bound), (f"particle {worst}: err {err[worst]:.3e} > {bound[worst]:.3e}; "
+                                  f"F_orc {f_orc[worst]}, F_gpu {f_gpu[worst]}")
+
+
+@pytest.fixture(scope="module")
+def plt_sys():
+    return synth.config_couette_platelet(seed=11, scale=0.6)   # 12^3 box, 5,184 plasma + 720 shell
+
+
+@pytest.fixture(scope="module")
+def wall_sys():
+    return synth.plasma_box(box=(9.0, 8.0, 7.0), walls=True, body_force=0.02, seed=12)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+def test_neighbor_sets_bit_exact(plt_sys, kind):
+    s = plt_sys
+    g = make_gpu(s, step0=17)
+    g.neighbor_build(force=True)
+    got = g.neighbor_pairs(kind)
+    _, _, x32 = g.read_particles()
+    cut = [1.3, 1.3, 2.3, 5.3][kind]
+    cut2 = np.float32(np.float32(cut) * 0 + cut * cut)
+    ref = O.pairs_f32(x32, s.tag, np.array(s.box, np.float32), kind, np.float32(cut * cut),
+                      X0f=s.X0.astype(np.float32), excl2=np.float32(2.5 * 2.5), le=True,
+                      delta=le_offset_f32(s, 17))
+    gs = set(map(tuple, got.tolist()))
+    rs = set(map(tuple, ref.tolist()))
+    assert len(got) == len(gs), "duplicate pairs in the GPU list"
+    assert gs == rs, (len(gs - rs), len(rs - gs))
+    assert len(rs) > 0 or kind == 3
+    del cut2
+
+
+def test_forces_match_oracle_all_levels(plt_sys):
+    s = plt_sys
+    import paper_2205_14121_gb300 as M
+    g = make_gpu(s, step0=5)
+    _, _, x32 = g.read_particles()
+    for mask in (M.MD_LEVEL_FLUID, M.MD_LEVEL_IFACE, M.MD_LEVEL_PLT, M.MD_LEVEL_ALL):
+        g.forces(mask)
+        fg = g.read_forces(mask)
+        fo, _ = oracle_forces(s, x32, s.v, 5, level_mask=mask)
+        assert_force_parity(fg, fo)
+
+
+def test_forces_walls_body_force(wall_sys):
+    s = wall_sys
+    g = make_gpu(s, step0=2)
+    g.forces()
+    fg = g.read_forces()
+    _, _, x32 = g.read_particles()
+    fo, _ = oracle_forces(s, x32, s.v, 2)
+    assert_force_parity(fg, fo)
+
+
+def test_net_force_vanishes(plt_sys):
+    """Pairwise antisymmetry (Eq. 1 noise keyed symmetrically): sum F ~ 0 up to
+    FP32 accumulation."""
+    g = make_gpu(plt_sys, step0=9)
+    g.forces()
+    f = g.read_forces()
+    assert np.abs(f.sum(0)).max() < 1e-5 * np.abs(f).sum()
+
+
+def test_virial_and_kinetics_match_oracle(plt_sys):
+    s = plt_sys
+    g = make_gpu(s, step0=4)
+    g.forces(virial=True)
+    o = g.observables()
+    _, v, x32 = g.read_particles()
+    _, acc = oracle_forces(s, x32, v, 4)
+    p = O.system_params(s, le_offset=le_offset_f32(s, 4))
+    kin = O.kinetics(p, s.x, v, s.tag)
+    assert np.allclose(o["momentum"], kin["momentum"], rtol=0, atol=1e-9 * np.abs(v).sum())
+    assert o["kinetic"] == pytest.approx(kin["ke"], rel=1e-10)
+    assert np.allclose(o["virial_c"], acc["vir_c"], rtol=1e-4, atol=1e-4 * np.abs(acc["vir_c"]).max())
+
+
+def test_sts_trajectory_tracks_oracle(plt_sys):
+    """Five velocity-Verlet steps from identical FP32-exact states: positions
+    agree to 1e-4 (FP32 force rounding ~1e-5 F times dt^2 growth) and
+    velocities to 5e-3 of their rms."""
+    s = plt_sys
+    x0, v0 = f32(s.x), f32(s.v)
+    g = make_gpu(s, step0=0, x=x0, v=v0)
+    g.mts_step(5)
+    xg, vg, _ = g.read_particles()
+    p = O.system_params(s)
+    xo, vo, _ = O.run_respa(p, x0, v0, s.tag, X0=f32(s.X0), bonds=s.bonds, r0=f32(s.r0), dt_f=0.01, n_outer=5)
+    dx = xg - xo
+    L = np.array(s.box)
+    dx -= L * np.round(dx / L)
+    assert np.abs(dx).max() < 1e-4
+    assert np.abs(vg - vo).max() < 5e-3 * np.sqrt((vo ** 2).mean())
+
+
+def test_respa_k1_matches_sts(plt_sys):
+    """RESPA with k_m = k_p = 1 is velocity-Verlet (Table 1 collapses)."""
+    import paper_2205_14121_gb300 as M
+    s = plt_sys
+    x0, v0 = f32(s.x), f32(s.v)
+    a = make_gpu(s, x=x0, v=v0)
+    a.mts_step(3)
+    b = make_gpu(s, x=x0, v=v0)
+    b.mts_step(3, mode=M.MD_MODE_RESPA, k_m=1, k_p=1)
+    xa, va, _ = a.read_particles()
+    xb, vb, _ = b.read_particles()
+    assert np.abs(xa - xb).max() < 1e-5
+    assert np.abs(va - vb).max() < 1e-3
+
+
+def test_respa_platelet_substeps_track_oracle(plt_sys):
+    """Fixed-k RESPA (k_m = 1, k_p = 4) against the oracle's Table 1 loop."""
+    import paper_2205_14121_gb300 as M
+    s = plt_sys
+    x0, v0 = f32(s.x), f32(s.v)
+    g = make_gpu(s, x=x0, v=v0)
+    g.mts_step(3, mode=M.MD_MODE_RESPA, k_m=1, k_p=4)
+    xg, vg, _ = g.read_particles()
+    p = O.system_params(s)
+    xo, vo, _ = O.run_respa(p, x0, v0, s.tag, X0=f32(s.X0), bonds=s.bonds, r0=f32(s.r0), dt_f=0.01, k_m=1,
+                            k_p=4, n_outer=3)
+    dx = xg - xo
+    L = np.array(s.box)
+    dx -= L * np.round(dx / L)
+    assert np.abs(dx).max() < 1e-4
+    assert np.abs(vg - vo).max() < 5e-3 * np.sqrt((vo ** 2).mean())
+
+
+def test_checkpoint_roundtrip(plt_sys):
+    s = plt_sys
+    g = make_gpu(s)
+    g.mts_step(2)
+    blob = g.get_state()
+    x1, v1, _ = g.read_particles()
+    h = make_gpu(s)
+    h.set_state(blob)
+    x2, v2, _ = h.read_particles()
+    assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
+    g.mts_step(2)
+    h.mts_step(2)
+    xa, _, _ = g.read_particles()
+    xb, _, _ = h.read_particles()
+    assert np.abs(xa - xb).max() < 1e-5
+
+
+def test_full_size_dpd_throughput_system_sampled():
+    """The 1,000,000-particle walled plasma system in the benchmark's launch
+    configuration: forces of 3,000 sampled particles against the oracle."""
+    s = synth.config_dpd_throughput()
+    g = make_gpu(s, step0=1)
+    g.forces()
+    fg = g.read_forces()
+    _, _, x32 = g.read_particles()
+    rng = np.random.default_rng(1)
+    sample = rng.choice(s.n, 3000, replace=False).astype(np.int32)
+    p = O.system_params(s)
+    fo = O.forces_cells(p, f32(x32), f32(s.v), s.tag, n_time=1, dt=0.01, sample=sample)
+    mag = np.sqrt((fo ** 2).sum(1))
+    frms = np.sqrt((mag ** 2).mean())
+    err = np.abs(fg[sample] - fo).max(1)
+    assert np.all(err <= TOL * (mag + frms))
+
+
+def test_philox_matches_curand_and_oracle():
+    """The device Philox4x32-10 equals cuRAND's Philox4_32_10 (a library
+    implementation of the same SC'11 generator) block for block, and the
+    oracle's CPU implementation bit for bit."""
+    from paper_2205_14121_gb300._binding import md_philox
+    rng = np.random.default_rng(3)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:, 1] &= (1 << 30) - 1      # keep 4*counter inside cuRAND's 64-bit offset
+    ctr[:8] = 0
+    ctr[8:16, 0] = np.arange(8)
+    key = np.array([20220528, 0], np.uint32)
+    own = md_philox(ctr, key)
+    lib = md_philox(ctr, key, use_library=True)
+    assert np.array_equal(own, lib)
+    orc = np.array([O.philox4x32_10(c, key) for c in ctr[:512]], dtype=np.uint32)
+    assert np.array_equal(own[:512], orc)
