@@ -99,6 +99,8 @@ def lib():
                                     C.c_double, C.c_int32, C.c_int32, C.c_int32,
                                     C.c_uint32, C.c_double, C.c_int32, dp, dp, dp]
         L.orc_kinetics.argtypes = [P, C.c_int32, dp, dp, ip, C.c_int32, dp, dp, dp]
+        L.orc_run_sts.argtypes = [P, C.c_int32, C.c_int32, dp, dp, ip, ip, dp, ip, dp,
+                                  C.c_double, C.c_int32, C.c_uint32, C.c_double, C.c_int32, dp]
         _lib = L
     return _lib
 
@@ -268,6 +270,27 @@ def run_respa(p, x, v, tag, X0=None, bonds=None, r0=None, ids=None, dt_f=0.01, k
                         idp, tp, X0p, bp, rp, dt_f, k_m, k_p, n_outer, n0, t0, init,
                         ff.ctypes.data_as(dp), fm.ctypes.data_as(dp), fpl.ctypes.data_as(dp))
     return x, v, (ff, fm, fpl)
+
+
+def run_sts(p, x, v, tag, X0=None, bonds=None, r0=None, ids=None, dt=0.01, n_steps=1, n0=0, t0=0.0,
+            force=None):
+    """Single-time-step velocity-Verlet (all forces in one pass).  Returns (x, v, f)."""
+    n = x.shape[0]
+    x = np.array(x, dtype=np.float64, order="C")
+    v = np.array(v, dtype=np.float64, order="C")
+    tag, tp = _i(tag)
+    ids, idp = _i(np.arange(n) if ids is None else ids)
+    X0, X0p = _d(x.copy() if X0 is None else X0)
+    if bonds is None or len(bonds) == 0:
+        bonds = np.zeros((0, 2), np.int32)
+        r0 = np.zeros(0)
+    bonds, bp = _i(bonds)
+    r0, rp = _d(r0)
+    f = np.zeros((n, 3)) if force is None else np.array(force, dtype=np.float64, order="C")
+    dp = C.POINTER(C.c_double)
+    lib().orc_run_sts(C.byref(p), n, bonds.shape[0], x.ctypes.data_as(dp), v.ctypes.data_as(dp), idp, tp, X0p,
+                      bp, rp, dt, n_steps, n0, t0, int(force is None), f.ctypes.data_as(dp))
+    return x, v, f
 
 
 def kinetics(p, x, v, tag, nbins=0):

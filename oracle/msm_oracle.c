@@ -637,13 +637,27 @@ typedef struct {
     const double *r0;
 } orc_state;
 
-/* Wrap / bounce a particle after a drift; Lees-Edwards images move x and v_x. */
+/*
+ * Wrap / bounce a particle after a drift; Lees-Edwards images move x and v_x.
+ * No-slip walls (Sec. 3.1) bounce back: the particle retraces the part of the
+ * drift it spent beyond the wall (time tau = overshoot / v_y) with reversed
+ * velocity.  This equals a continuous-time reflection, so the result does not
+ * depend on how a drift is split into substeps.
+ */
 static void apply_boundaries(const orc_params *p, double *xi, double *vi)
 {
     const double Lx = p->L[0], Ly = p->L[1], Lz = p->L[2];
     if (p->walls) {
-        if (xi[1] < 0.0) { xi[1] = -xi[1]; vi[0] = -vi[0]; vi[1] = -vi[1]; vi[2] = -vi[2]; }
-        else if (xi[1] >= Ly) { xi[1] = 2.0 * Ly - xi[1]; vi[0] = -vi[0]; vi[1] = -vi[1]; vi[2] = -vi[2]; }
+        double wall = -1.0;
+        if (xi[1] < 0.0) wall = 0.0;
+        else if (xi[1] >= Ly) wall = Ly;
+        if (wall >= 0.0) {
+            double tau = vi[1] != 0.0 ? (xi[1] - wall) / vi[1] : 0.0;
+            xi[0] -= 2.0 * vi[0] * tau;
+            xi[2] -= 2.0 * vi[2] * tau;
+            xi[1] = 2.0 * wall - xi[1];
+            vi[0] = -vi[0]; vi[1] = -vi[1]; vi[2] = -vi[2];
+        }
     } else if (p->le) {
         if (xi[1] >= Ly) { xi[1] -= Ly; xi[0] -= p->le_offset; vi[0] -= p->le_rate * Ly; }
         else if (xi[1] < 0.0) { xi[1] += Ly; xi[0] += p->le_offset; vi[0] += p->le_rate * Ly; }
@@ -763,6 +777,37 @@ void orc_run_respa(orc_params *p, int32_t n, int32_t nb, double *x, double *v,
         }
         eval_level(p, &s, &csr, LVL_FLUID, nn + 1, 0, dt_f, dt_m, f_f);
         kick(&s, f_f, 0.5 * dt_f);
+    }
+    free(csr.off); free(csr.nbr); free(csr.r0);
+}
+
+/*
+ * Single time step (STS, the reference run of Sec. 4.1): velocity-Verlet in
+ * which all forces of Eq. 1-4 are evaluated together, at the drifted
+ * positions and the half-kicked velocities:
+ *   v += dt/2 F;  x += dt v;  F = F(x, v) at time index (n+1, 0);  v += dt/2 F.
+ * f: total force [3n] at entry (compute_initial = 1: evaluated first) and exit.
+ */
+void orc_run_sts(orc_params *p, int32_t n, int32_t nb, double *x, double *v,
+                 const int32_t *id, const int32_t *tag, const double *X0,
+                 const int32_t *bonds, const double *r0,
+                 double dt, int32_t n_steps, uint32_t n0, double t0, int32_t compute_initial,
+                 double *f)
+{
+    orc_state s = {n, nb, x, v, id, tag, X0, bonds, r0};
+    bond_csr_t csr;
+    bond_csr_build(n, nb, bonds, r0, &csr);
+    double t = t0;
+    if (p->le) {
+        p->le_offset = fmod(p->le_rate * p->L[1] * t, p->L[0]);
+        if (p->le_offset < 0.0) p->le_offset += p->L[0];
+    }
+    if (compute_initial) eval_level(p, &s, &csr, LVL_FLUID | LVL_IFACE | LVL_PLT, n0, 0, dt, dt, f);
+    for (int32_t k = 0; k < n_steps; ++k) {
+        kick(&s, f, 0.5 * dt);
+        drift(p, &s, dt, &t);
+        eval_level(p, &s, &csr, LVL_FLUID | LVL_IFACE | LVL_PLT, n0 + (uint32_t)k + 1, 0, dt, dt, f);
+        kick(&s, f, 0.5 * dt);
     }
     free(csr.off); free(csr.nbr); free(csr.r0);
 }

@@ -75,10 +75,15 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
             double z = a.zs[k] + a.dt * (double)vv.z;
             const double Lx = a.L[0], Ly = a.L[1], Lz = a.L[2];
             if (a.geom.walls) {
-                if (y < 0.0) {
-                    y = -y; vv.x = -vv.x; vv.y = -vv.y; vv.z = -vv.z;
-                } else if (y >= Ly) {
-                    y = 2.0 * Ly - y; vv.x = -vv.x; vv.y = -vv.y; vv.z = -vv.z;
+                // bounce-back: retrace the overshoot beyond the wall with the
+                // reversed velocity (independent of drift substepping)
+                const double wall = y < 0.0 ? 0.0 : (y >= Ly ? Ly : -1.0);
+                if (wall >= 0.0) {
+                    const double tau = vv.y != 0.0f ? (y - wall) / (double)vv.y : 0.0;
+                    x -= 2.0 * (double)vv.x * tau;
+                    z -= 2.0 * (double)vv.z * tau;
+                    y = 2.0 * wall - y;
+                    vv.x = -vv.x; vv.y = -vv.y; vv.z = -vv.z;
                 }
             } else if (a.geom.le) {
                 const double delta = a.ds->le_offset;

@@ -10,18 +10,27 @@
 // force kernels, one thread per row, read them coalesced.  Row counts beyond
 // the capacity are recorded (overflow bit + longest row) and never written.
 //
-//   MD_LIST_FLUID  rows: every particle; partners j > i, plasma-plasma and
-//                  plasma-wall pairs (Eq. 1)
+//   MD_LIST_FLUID  rows: every particle; owned partners (owns_pair), plasma-
+//                  plasma and plasma-wall pairs (Eq. 1)
 //   MD_LIST_IFACE  rows: platelet particles; partners: every plasma or wall
 //                  particle (Eq. 3)
-//   MD_LIST_LJ     rows: platelet particles; partners j > i on the platelet
+//   MD_LIST_LJ     rows: platelet particles; owned partners on the platelet
 //                  sub-grid, excluding same-platelet pairs closer than
 //                  lj_excl at rest (Eq. 2)
-//   MD_LIST_MORSE  rows: receptor sites; partners j > i on the receptor
+//   MD_LIST_MORSE  rows: receptor sites; owned partners on the receptor
 //                  sub-grid belonging to another platelet (Eq. 4)
 #include "msm_internal.cuh"
 
 namespace {
+
+// Half lists store each unordered pair once, in the row of its owner: the
+// lower index when i + j is even, the higher when odd.  Unlike "j > i" this
+// gives every row about half of its neighbours whatever its place in the
+// sort order, so rows stay short and warps stay balanced.
+__device__ __forceinline__ bool owns_pair(int32_t i, int32_t j)
+{
+    return j != i && ((i < j) == (((i + j) & 1) == 0));
+}
 
 __device__ __forceinline__ int wrapc(int c, int n)
 {
@@ -110,14 +119,14 @@ __global__ void __launch_bounds__(MSM_TPB) k_build(build_args a, const int32_t *
             for_candidates(a.g, a.geom, delta, xi, a.R, a.members, [&](int32_t j) {
                 const int32_t tj = a.tag[j];
                 if (KIND == MD_LIST_FLUID) {
-                    if (j <= i || tj >= 0) return;
+                    if (tj >= 0 || !owns_pair(i, j)) return;
                     if (ti == MD_TAG_WALL && tj == MD_TAG_WALL) return;
                 } else if (KIND == MD_LIST_IFACE) {
                     if (tj >= 0) return;
                 } else if (KIND == MD_LIST_LJ) {
-                    if (j <= i) return;
+                    if (!owns_pair(i, j)) return;
                 } else {  // MORSE
-                    if (j <= i) return;
+                    if (!owns_pair(i, j)) return;
                     if ((ti & ~MD_RECEPTOR_BIT) == (tj & ~MD_RECEPTOR_BIT)) return;
                 }
                 const float4 xj = a.x32[j];

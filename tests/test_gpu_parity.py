@@ -54,7 +54,29 @@ def assert_force_parity(f_gpu, f_orc, tol=TOL):
 
 @pytest.fixture(scope="module")
 def plt_sys():
-    return synth.config_couette_platelet(seed=11, scale=0.6)   # 12^3 box, 5,184 plasma + 720 shell
+    """12^3 Lees-Edwards box, 5,184 plasma + two 400-particle shells 4.0 apart
+    (LJ and receptor pairs between them), shells jittered by 0.02 so that the
+    bonds carry load."""
+    s = synth.platelet_system((12.0, 12.0, 12.0), 5184, 2, 400, synth.scaled_radii(400), shear_rate=0.05,
+                              seed=11, centers=[(4.0, 6.0, 6.0), (8.0, 6.0, 6.0)])
+    rng = np.random.default_rng(21)
+    plt = s.tag >= 0
+    s.x[plt] += 0.02 * rng.standard_normal((plt.sum(), 3))
+    return s
+
+
+@pytest.fixture(scope="module")
+def plt_wall_sys():
+    """The two-shell system in a y-walled channel with a body force (Lees-Edwards
+    images move a plasma particle that crosses y by the offset of the crossing
+    time, which RESPA's once-per-substep fluid drift does not resolve; walls
+    bounce exactly alike)."""
+    s = synth.platelet_system((12.0, 12.0, 12.0), 5184, 2, 400, synth.scaled_radii(400), walls=True,
+                              body_force=0.02, seed=13, centers=[(4.0, 6.0, 6.0), (8.0, 6.0, 6.0)])
+    rng = np.random.default_rng(22)
+    plt = s.tag >= 0
+    s.x[plt] += 0.02 * rng.standard_normal((plt.sum(), 3))
+    return s
 
 
 @pytest.fixture(scope="module")
@@ -70,7 +92,6 @@ def test_neighbor_sets_bit_exact(plt_sys, kind):
     got = g.neighbor_pairs(kind)
     _, _, x32 = g.read_particles()
     cut = [1.3, 1.3, 2.3, 5.3][kind]
-    cut2 = np.float32(np.float32(cut) * 0 + cut * cut)
     ref = O.pairs_f32(x32, s.tag, np.array(s.box, np.float32), kind, np.float32(cut * cut),
                       X0f=s.X0.astype(np.float32), excl2=np.float32(2.5 * 2.5), le=True,
                       delta=le_offset_f32(s, 17))
@@ -78,8 +99,7 @@ def test_neighbor_sets_bit_exact(plt_sys, kind):
     rs = set(map(tuple, ref.tolist()))
     assert len(got) == len(gs), "duplicate pairs in the GPU list"
     assert gs == rs, (len(gs - rs), len(rs - gs))
-    assert len(rs) > 0 or kind == 3
-    del cut2
+    assert len(rs) > 0
 
 
 def test_forces_match_oracle_all_levels(plt_sys):
@@ -137,7 +157,7 @@ def test_sts_trajectory_tracks_oracle(plt_sys):
     g.mts_step(5)
     xg, vg, _ = g.read_particles()
     p = O.system_params(s)
-    xo, vo, _ = O.run_respa(p, x0, v0, s.tag, X0=f32(s.X0), bonds=s.bonds, r0=f32(s.r0), dt_f=0.01, n_outer=5)
+    xo, vo, _ = O.run_sts(p, x0, v0, s.tag, X0=f32(s.X0), bonds=s.bonds, r0=f32(s.r0), dt=0.01, n_steps=5)
     dx = xg - xo
     L = np.array(s.box)
     dx -= L * np.round(dx / L)
@@ -145,10 +165,11 @@ def test_sts_trajectory_tracks_oracle(plt_sys):
     assert np.abs(vg - vo).max() < 5e-3 * np.sqrt((vo ** 2).mean())
 
 
-def test_respa_k1_matches_sts(plt_sys):
-    """RESPA with k_m = k_p = 1 is velocity-Verlet (Table 1 collapses)."""
+def test_respa_k1_is_sts_without_platelets(wall_sys):
+    """With only the fluid level populated, Table 1 with k_m = k_p = 1 is plain
+    velocity-Verlet: the two GPU schedules agree to FP32 atomic-order noise."""
     import paper_2205_14121_gb300 as M
-    s = plt_sys
+    s = wall_sys
     x0, v0 = f32(s.x), f32(s.v)
     a = make_gpu(s, x=x0, v=v0)
     a.mts_step(3)
@@ -156,20 +177,20 @@ def test_respa_k1_matches_sts(plt_sys):
     b.mts_step(3, mode=M.MD_MODE_RESPA, k_m=1, k_p=1)
     xa, va, _ = a.read_particles()
     xb, vb, _ = b.read_particles()
-    assert np.abs(xa - xb).max() < 1e-5
-    assert np.abs(va - vb).max() < 1e-3
+    assert np.abs(xa - xb).max() < 1e-6
+    assert np.abs(va - vb).max() < 1e-4
 
 
-def test_respa_platelet_substeps_track_oracle(plt_sys):
-    """Fixed-k RESPA (k_m = 1, k_p = 4) against the oracle's Table 1 loop."""
+def test_respa_platelet_substeps_track_oracle(plt_wall_sys):
+    """Fixed-k RESPA (k_m = 2, k_p = 4) against the oracle's Table 1 loop."""
     import paper_2205_14121_gb300 as M
-    s = plt_sys
+    s = plt_wall_sys
     x0, v0 = f32(s.x), f32(s.v)
     g = make_gpu(s, x=x0, v=v0)
-    g.mts_step(3, mode=M.MD_MODE_RESPA, k_m=1, k_p=4)
+    g.mts_step(3, mode=M.MD_MODE_RESPA, k_m=2, k_p=4)
     xg, vg, _ = g.read_particles()
     p = O.system_params(s)
-    xo, vo, _ = O.run_respa(p, x0, v0, s.tag, X0=f32(s.X0), bonds=s.bonds, r0=f32(s.r0), dt_f=0.01, k_m=1,
+    xo, vo, _ = O.run_respa(p, x0, v0, s.tag, X0=f32(s.X0), bonds=s.bonds, r0=f32(s.r0), dt_f=0.01, k_m=2,
                             k_p=4, n_outer=3)
     dx = xg - xo
     L = np.array(s.box)

@@ -400,6 +400,26 @@ def test_respa_inner_steps_match_fine_verlet_for_platelet_only():
     assert np.abs(v1 - v2).max() < 1e-9
 
 
+def test_sts_is_respa_k1_with_one_level():
+    """With only the fluid level populated, the single-pass velocity-Verlet and
+    Table 1 at k_m = k_p = 1 perform the same arithmetic (bitwise)."""
+    s = synth.plasma_box(n=3 * 6 ** 3, seed=4, walls=True, body_force=0.02)
+    p = O.system_params(s)
+    x1, v1, _ = O.run_sts(p, s.x, s.v, s.tag, dt=0.01, n_steps=4)
+    x2, v2, _ = O.run_respa(p, s.x, s.v, s.tag, dt_f=0.01, n_outer=4)
+    assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
+
+
+def test_sts_time_reversible():
+    """Single-pass velocity-Verlet is time-reversible for the conservative shell."""
+    s = shell_only()
+    p = O.system_params(s)
+    x1, v1, _ = O.run_sts(p, s.x, s.v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, dt=0.002, n_steps=60)
+    x2, v2, _ = O.run_sts(p, x1, -v1, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, dt=0.002, n_steps=60)
+    assert np.abs(x2 - s.x).max() < 1e-9
+    assert np.abs(v2 + s.v).max() < 1e-8
+
+
 def test_walls_bounce_back():
     """No-slip bounce-back (Sec. 3.1 walls): a particle crossing y = 0 is mirrored
     and its velocity reversed."""
@@ -409,6 +429,21 @@ def test_walls_bounce_back():
     x1, v1, _ = O.run_respa(p, x, v, np.array([-1], np.int32), dt_f=0.01, n_outer=1)
     assert x1[0, 1] == pytest.approx(0.05, abs=1e-12)
     assert np.allclose(v1[0], [-1.0, 10.0, -0.5])
+    # the 0.005 spent beyond the wall is retraced in x and z as well
+    assert x1[0, 0] == pytest.approx(5.0, abs=1e-12)
+    assert x1[0, 2] == pytest.approx(5.0, abs=1e-12)
+
+
+def test_bounce_back_independent_of_substeps():
+    """Table 1 drifts at the innermost level; a walled plasma particle that
+    feels no inner force must end at the same place however the drift is split."""
+    p = O.make_params((10, 10, 10), walls=True, a_ff=0.0, gamma=0.0, sigma=0.0)
+    x = np.array([[5.0, 0.03, 5.0]])
+    v = np.array([[2.0, -7.0, -1.0]])
+    tag = np.array([-1], np.int32)
+    xa, va, _ = O.run_respa(p, x, v, tag, dt_f=0.01, n_outer=1)
+    xb, vb, _ = O.run_respa(p, x, v, tag, dt_f=0.01, k_m=2, k_p=5, n_outer=1)
+    assert np.allclose(xa, xb, atol=1e-14) and np.allclose(va, vb, atol=1e-14)
 
 
 # --------------------------------------------------------------------------
