@@ -184,11 +184,13 @@ int md_read_particles(md_system *sys, double *x, double *v, float *x32);
 #define MD_MODE_RESPA 1  /* k_m interface substeps, k_p platelet substeps each  */
 #define MD_MODE_AI    2  /* per-platelet k from the controller (Table 2)        */
 
+#define MD_SCHED_DIRECT 1  /* launch every kernel from the host (no CUDA graph) */
+
 typedef struct md_mts_schedule {
     int32_t mode;        /* MD_MODE_*                                            */
     int32_t k_m;         /* interface substeps per fluid step (>= 1)             */
     int32_t k_p;         /* platelet substeps per interface step (RESPA)         */
-    int32_t obs_every;   /* record observables every obs_every outer steps (0 = off) */
+    int32_t flags;       /* MD_SCHED_* bits                                      */
 } md_mts_schedule;
 
 /*
@@ -197,7 +199,10 @@ typedef struct md_mts_schedule {
  * forces, k_m interface substeps (half-kick, k_p platelet kick-drift-force-
  * kick substeps, interface forces, half-kick), fluid forces, half-kick.
  * Positions are FP64 masters; the lists are rebuilt on device when the
- * displacement check trips (no host round trip per step).
+ * displacement check trips (no host round trip per step).  After the first
+ * step, the remaining n_outer - 1 steps replay one captured CUDA graph
+ * (a WHILE node over the outer step, IF nodes around the rebuild chain)
+ * unless sched->flags has MD_SCHED_DIRECT or kernel profiling is on.
  * Errors: MD_ENBR_OVERFLOW, MD_EUNSTABLE, MD_ECUDA (checked once at the end).
  */
 int md_mts_step(md_system *sys, int64_t n_outer, const md_mts_schedule *sched);

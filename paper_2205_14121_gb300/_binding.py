@@ -52,7 +52,7 @@ class md_buffers(C.Structure):
 
 
 class md_mts_schedule(C.Structure):
-    _fields_ = [("mode", C.c_int32), ("k_m", C.c_int32), ("k_p", C.c_int32), ("obs_every", C.c_int32)]
+    _fields_ = [("mode", C.c_int32), ("k_m", C.c_int32), ("k_p", C.c_int32), ("flags", C.c_int32)]
 
 
 class md_observables_t(C.Structure):
@@ -269,8 +269,8 @@ class System:
 
     md_read_particles = read_particles
 
-    def mts_step(self, n_outer, mode=MD_MODE_STS, k_m=1, k_p=1):
-        sched = md_mts_schedule(mode, k_m, k_p, 0)
+    def mts_step(self, n_outer, mode=MD_MODE_STS, k_m=1, k_p=1, direct=False):
+        sched = md_mts_schedule(mode, k_m, k_p, 1 if direct else 0)
         self._check(lib().md_mts_step(self.h, int(n_outer), C.byref(sched)), "md_mts_step")
 
     md_mts_step = mts_step

@@ -325,94 +325,228 @@ int ensure_forces(md_system *s)
     return MD_OK;
 }
 
-// One STS step (velocity-Verlet): kick (fused with the previous closing
-// half-kick when not first) + drift + check, rebuild if tripped, forces.
-int sts_step(md_system *s, bool first)
+// Context of a graph capture of the outer step (null: direct launches).
+struct capture_ctx {
+    cudaGraphConditionalHandle loop;
+    std::vector<cudaGraph_t> if_bodies;
+};
+
+// The rebuild chain: gated kernels when launched directly; under capture, a
+// kernel that copies the rebuild flag into a conditional handle and an IF
+// node whose body (captured later) is the ungated chain.
+int enqueue_rebuild(md_system *s, capture_ctx *cap)
 {
-    const md_config &c = s->cfg;
-    const float dt = (float)c.dt;
-    const float hk = first ? 0.5f * dt : dt;
-    const unsigned all = s->n_plt > 0 ? MD_LEVEL_ALL : MD_LEVEL_FLUID;
-    const int64_t n_next = s->host_step + 1;
-    prof_begin(s, MD_PROF_OTHER);
-    CK(launch_set_time(s, n_next, 0, (double)n_next * c.dt), "time");
-    prof_end(s);
-    const float h[3] = {hk, s->n_plt > 0 ? hk : 0.f, s->n_plt > 0 ? hk : 0.f};
-    prof_begin(s, MD_PROF_INTEG);
-    CK(launch_kick_drift(s, h, DRIFT_ALL, c.dt, DRIFT_ALL, all, false), "kick-drift");
-    prof_end(s);
-    prof_begin(s, MD_PROF_BUILD);
-    CK(launch_rebuild(s, s->ctl + CTL_REBUILD), "rebuild");
-    prof_end(s);
-    float4 *out[3] = {s->f[0], s->f[1], s->f[2]};
-    prof_begin(s, MD_PROF_FLUID);
-    CK(launch_forces(s, MD_LEVEL_FLUID, out, false), "fluid forces");
-    prof_end(s);
-    if (s->n_plt > 0) {
-        prof_begin(s, MD_PROF_IFACE);
-        CK(launch_forces(s, MD_LEVEL_IFACE, out, false), "interface forces");
+    if (!cap) {
+        prof_begin(s, MD_PROF_BUILD);
+        CK(launch_rebuild(s, s->ctl + CTL_REBUILD), "rebuild");
         prof_end(s);
-        prof_begin(s, MD_PROF_PLT);
-        CK(launch_forces(s, MD_LEVEL_PLT, out, false), "platelet forces");
+        return MD_OK;
+    }
+    cudaStreamCaptureStatus st;
+    cudaGraph_t capg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(s->stream, &st, nullptr, &capg, &deps, nullptr, &ndeps), "capture info");
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, capg, 0, cudaGraphCondAssignDefault), "conditional handle");
+    CK(launch_cond_rebuild(s, h), "rebuild condition");
+    CK(cudaStreamGetCaptureInfo(s->stream, &st, nullptr, &capg, &deps, nullptr, &ndeps), "capture info");
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, capg, deps, nullptr, ndeps, &p), "IF node");
+    cap->if_bodies.push_back(p.conditional.phGraph_out[0]);
+    CK(cudaStreamUpdateCaptureDependencies(s->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
+       "capture dependencies");
+    return MD_OK;
+}
+
+int enqueue_forces(md_system *s, unsigned levels)
+{
+    float4 *out[3] = {s->f[0], s->f[1], s->f[2]};
+    static const int cls[3] = {MD_PROF_FLUID, MD_PROF_IFACE, MD_PROF_PLT};
+    for (int l = 0; l < 3; ++l) {
+        const unsigned bit = 1u << l;
+        if (!(levels & bit) || (l > 0 && s->n_plt == 0)) continue;
+        prof_begin(s, cls[l]);
+        CK(launch_forces(s, bit, out, false), "forces");
         prof_end(s);
     }
-    s->host_step = n_next;
+    return MD_OK;
+}
+
+int enqueue_kd(md_system *s, const float h[3], int kick_which, double dt, int drift_which, unsigned zero,
+               bool plt_rows)
+{
+    prof_begin(s, MD_PROF_INTEG);
+    CK(launch_kick_drift(s, h, kick_which, dt, drift_which, zero, plt_rows), "kick-drift");
+    prof_end(s);
+    return MD_OK;
+}
+
+int enqueue_time(md_system *s, int dn, int c, double t_off)
+{
+    prof_begin(s, MD_PROF_OTHER);
+    CK(launch_time_rel(s, dn, c, t_off), "time");
+    prof_end(s);
+    return MD_OK;
+}
+
+#define RC(expr)                    \
+    do {                            \
+        int _rc = (expr);           \
+        if (_rc != MD_OK) return _rc; \
+    } while (0)
+
+// One outer step of Table 1 (read symmetrically).  STS: velocity-Verlet with
+// every force at dt_f; the kick fuses the previous step's closing half-kick
+// unless `first`.  RESPA: k_m interface substeps of k_p platelet substeps;
+// plasma feels no inner force, so it drifts once per interface substep while
+// platelets drift every platelet substep.  Step-dependent values come from
+// the device time state, so the same sequence can be captured once and
+// replayed.
+int enqueue_outer_step(md_system *s, int mode, int k_m, int k_p, bool first, capture_ctx *cap)
+{
+    const md_config &c = s->cfg;
+    const bool plt = s->n_plt > 0;
+    prof_begin(s, MD_PROF_OTHER);
+    CK(launch_outer_begin(s, cap ? cap->loop : 0, cap != nullptr), "outer begin");
+    prof_end(s);
+    if (mode == MD_MODE_STS) {
+        const float hk = (float)(first ? 0.5 * c.dt : c.dt);
+        const float h[3] = {hk, plt ? hk : 0.f, plt ? hk : 0.f};
+        RC(enqueue_time(s, 1, 0, c.dt));
+        RC(enqueue_kd(s, h, DRIFT_ALL, c.dt, DRIFT_ALL, plt ? MD_LEVEL_ALL : MD_LEVEL_FLUID, false));
+        RC(enqueue_rebuild(s, cap));
+        RC(enqueue_forces(s, plt ? MD_LEVEL_ALL : MD_LEVEL_FLUID));
+        return MD_OK;
+    }
+    const double dtf = c.dt, dtm = dtf / k_m, dtp = dtm / k_p;
+    for (int ci = 0; ci < k_m; ++ci) {
+        const bool last_c = ci + 1 == k_m;
+        const int dn = last_c ? 1 : 0;
+        const int c_end = last_c ? 0 : ci + 1;
+        const double tc = ci * dtm;
+        RC(enqueue_time(s, dn, c_end, tc + dtm));
+        // A: fluid kick (first substep; fused with the previous outer step's
+        //    closing half-kick) + opening interface half-kick; plasma drift
+        float h[3] = {0.f, 0.f, 0.f};
+        if (ci == 0) h[0] = (float)(first ? 0.5 * dtf : dtf);
+        h[1] = plt ? (float)(0.5 * dtm) : 0.f;
+        const unsigned zero = (plt ? MD_LEVEL_IFACE : 0u) | (ci == 0 ? MD_LEVEL_FLUID : 0u);
+        RC(enqueue_kd(s, h, DRIFT_ALL, dtm, plt ? DRIFT_FLUID : DRIFT_ALL, zero, false));
+        if (plt) {
+            // B: platelet substeps; the kick of substep q fuses the closing
+            //    half-kick of q-1 with its own opening half-kick
+            for (int q = 0; q < k_p; ++q) {
+                RC(enqueue_time(s, dn, c_end, tc + (q + 1) * dtp));
+                const float hq[3] = {0.f, 0.f, (float)(q == 0 ? 0.5 * dtp : dtp)};
+                RC(enqueue_kd(s, hq, DRIFT_PLT, dtp, DRIFT_PLT, MD_LEVEL_PLT, true));
+                RC(enqueue_forces(s, MD_LEVEL_PLT));
+            }
+            const float hc[3] = {0.f, 0.f, (float)(0.5 * dtp)};
+            RC(enqueue_kd(s, hc, DRIFT_PLT, 0.0, -1, 0u, true));
+        }
+        RC(enqueue_rebuild(s, cap));
+        if (plt) {
+            RC(enqueue_forces(s, MD_LEVEL_IFACE));
+            const float hm[3] = {0.f, (float)(0.5 * dtm), 0.f};
+            RC(enqueue_kd(s, hm, DRIFT_ALL, 0.0, -1, 0u, false));
+        }
+    }
+    RC(enqueue_forces(s, MD_LEVEL_FLUID));
     return MD_OK;
 }
 
 int closing_kick(md_system *s, float hf, float hm, float hp)
 {
     const float h[3] = {hf, s->n_plt > 0 ? hm : 0.f, s->n_plt > 0 ? hp : 0.f};
-    CK(launch_kick_drift(s, h, DRIFT_ALL, 0.0, -1, 0u, false), "closing kick");
+    RC(enqueue_kd(s, h, DRIFT_ALL, 0.0, -1, 0u, false));
     return MD_OK;
 }
 
-// One RESPA outer step (Table 1 read symmetrically), k_m interface substeps of
-// k_p platelet substeps each.  Fluid particles feel no inner force, so they
-// drift once per interface substep; platelets drift every platelet substep.
-int respa_step(md_system *s, int k_m, int k_p, bool first)
+void drop_graph(md_system *s)
 {
-    const md_config &c = s->cfg;
-    const double dtf = c.dt, dtm = dtf / k_m, dtp = dtm / k_p;
-    const int64_t n0 = s->host_step;
-    for (int cidx = 0; cidx < k_m; ++cidx) {
-        const double tc = (double)n0 * dtf + (double)cidx * dtm;
-        // interface-substep end time (fluid drift, LE offset)
-        const bool last_c = cidx + 1 == k_m;
-        const int64_t n_end = last_c ? n0 + 1 : n0;
-        const int32_t c_end = last_c ? 0 : cidx + 1;
-        CK(launch_set_time(s, n_end, c_end, tc + dtm), "time");
-        // A: fluid kick (first substep only; fused with the previous outer
-        //    step's closing half-kick) + interface kick, fluid drift
-        float h[3] = {0.f, 0.f, 0.f};
-        if (cidx == 0) h[0] = first ? (float)(0.5 * dtf) : (float)dtf;
-        h[1] = (float)(0.5 * dtm);
-        unsigned zero = MD_LEVEL_IFACE | (cidx == 0 ? MD_LEVEL_FLUID : 0u);
-        CK(launch_kick_drift(s, h, DRIFT_ALL, dtm, DRIFT_FLUID, zero, false), "fluid kick-drift");
-        // B: platelet substeps
-        for (int q = 0; q < k_p; ++q) {
-            CK(launch_set_time(s, n_end, c_end, tc + (q + 1) * dtp), "time");
-            // opening half-kick at q = 0; later substeps fuse the closing
-            // half-kick of q-1 with their opening one
-            const float hq[3] = {0.f, 0.f, q == 0 ? (float)(0.5 * dtp) : (float)dtp};
-            CK(launch_kick_drift(s, hq, DRIFT_PLT, dtp, DRIFT_PLT, MD_LEVEL_PLT, true), "platelet kick-drift");
-            float4 *out[3] = {s->f[0], s->f[1], s->f[2]};
-            CK(launch_forces(s, MD_LEVEL_PLT, out, false), "platelet forces");
-        }
-        // closing platelet half-kick before the interface forces read v
-        const float hc[3] = {0.f, 0.f, (float)(0.5 * dtp)};
-        CK(launch_kick_drift(s, hc, DRIFT_PLT, 0.0, -1, 0u, true), "platelet closing kick");
-        // rebuild if any particle moved too far
-        CK(launch_rebuild(s, s->ctl + CTL_REBUILD), "rebuild");
-        float4 *out[3] = {s->f[0], s->f[1], s->f[2]};
-        CK(launch_forces(s, MD_LEVEL_IFACE, out, false), "interface forces");
-        // closing interface half-kick (before the fluid forces read v)
-        const float hm[3] = {0.f, (float)(0.5 * dtm), 0.f};
-        CK(launch_kick_drift(s, hm, DRIFT_ALL, 0.0, -1, 0u, false), "interface closing kick");
+    if (s->step_exec) cudaGraphExecDestroy(s->step_exec);
+    if (s->step_graph) cudaGraphDestroy(s->step_graph);
+    s->step_exec = nullptr;
+    s->step_graph = nullptr;
+    for (int k = 0; k < 4; ++k) s->graph_key[k] = -1;
+}
+
+// Capture WHILE(steps_left) { outer step } once per schedule shape.
+int build_step_graph(md_system *s, int mode, int k_m, int k_p)
+{
+    const int key[4] = {mode, k_m, k_p, (int)s->cfg_k_m};
+    bool same = s->step_exec != nullptr;
+    for (int k = 0; k < 4; ++k) same = same && s->graph_key[k] == key[k];
+    if (same) return MD_OK;
+    drop_graph(s);
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0), "graph create");
+    capture_ctx cap;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cap.loop, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = cap.loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(s, e, "WHILE node");
     }
-    float4 *out[3] = {s->f[0], s->f[1], s->f[2]};
-    CK(launch_forces(s, MD_LEVEL_FLUID, out, false), "fluid forces");
-    s->host_step = n0 + 1;
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    cudaStream_t cs = nullptr;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+    cudaStream_t saved = s->stream;
+    const bool prof = s->prof_on;
+    s->prof_on = false;
+    s->stream = cs;
+    const int64_t l0 = s->nlaunch;
+    int rc = MD_OK;
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = enqueue_outer_step(s, mode, k_m, k_p, false, &cap);
+        cudaGraph_t out = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &out);
+        if (rc == MD_OK && e2 != cudaSuccess) rc = cuda_fail(s, e2, "end capture");
+    } else {
+        rc = cuda_fail(s, e, "begin capture");
+    }
+    const int64_t l1 = s->nlaunch;
+    for (size_t k = 0; rc == MD_OK && k < cap.if_bodies.size(); ++k) {
+        e = cudaStreamBeginCaptureToGraph(cs, cap.if_bodies[k], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { rc = cuda_fail(s, e, "begin capture (rebuild)"); break; }
+        cudaError_t e1 = launch_rebuild(s, nullptr);
+        cudaGraph_t out = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &out);
+        if (e1 != cudaSuccess) rc = cuda_fail(s, e1, "rebuild capture");
+        else if (e2 != cudaSuccess) rc = cuda_fail(s, e2, "end capture (rebuild)");
+    }
+    const int64_t l2 = s->nlaunch;
+    s->stream = saved;
+    s->prof_on = prof;
+    s->nlaunch = l0;
+    cudaStreamDestroy(cs);
+    if (rc == MD_OK) {
+        e = cudaGraphInstantiate(&s->step_exec, g, 0);
+        if (e != cudaSuccess) rc = cuda_fail(s, e, "graph instantiate");
+    }
+    if (rc != MD_OK) {
+        cudaGraphDestroy(g);
+        s->step_exec = nullptr;
+        cudaGetLastError();
+        return rc;
+    }
+    s->step_graph = g;
+    for (int k = 0; k < 4; ++k) s->graph_key[k] = key[k];
+    s->graph_body_launches = l1 - l0;
+    s->graph_chain_launches = cap.if_bodies.empty() ? 0 : (l2 - l1) / (int64_t)cap.if_bodies.size();
     return MD_OK;
 }
 
@@ -531,6 +665,9 @@ void md_destroy(md_system *s)
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
     else cudaDeviceSynchronize();
+    drop_graph(s);
+    for (auto &r : s->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : s->ev_pool) cudaEventDestroy(e);
     if (s->h_ctl) cudaFreeHost(s->h_ctl);
     if (s->h_ds) cudaFreeHost(s->h_ds);
     delete s;
@@ -580,6 +717,8 @@ int md_set_particles(md_system *s, const double *x, const double *v, const int32
     md_dstate *h = s->h_ds;
     memset(h, 0, sizeof *h);
     h->step = step0;
+    h->base = step0;
+    h->done = step0;
     h->time = (double)step0 * s->cfg.dt;
     h->le_offset = host_le_offset(s, h->time);
     h->le_offset_f = (float)h->le_offset;
@@ -706,22 +845,39 @@ int md_mts_step(md_system *s, int64_t n_outer, const md_mts_schedule *sched)
     int rc = ensure_forces(s);
     if (rc) return rc;
     const md_config &c = s->cfg;
-    if (mode == MD_MODE_STS) {
-        for (int64_t it = 0; it < n_outer; ++it) {
-            rc = sts_step(s, it == 0);
-            if (rc) return rc;
+    rc = enqueue_outer_step(s, mode, k_m, k_p, true, nullptr);
+    if (rc) return rc;
+    const int64_t rest = n_outer - 1;
+    if (rest > 0) {
+        bool use_graph = !s->prof_on && !s->graph_failed && !(sched->flags & MD_SCHED_DIRECT);
+        if (use_graph && build_step_graph(s, mode, k_m, k_p) != MD_OK) {
+            s->graph_failed = true;   // keep going with direct launches
+            use_graph = false;
         }
+        if (use_graph) {
+            rc = sync_ctl(s);
+            if (rc) return rc;
+            const int64_t builds0 = s->h_ds->n_builds;
+            CK(launch_set_loop(s, rest), "loop count");
+            CK(cudaGraphLaunch(s->step_exec, s->stream), "graph launch");
+            rc = sync_ctl(s);
+            if (rc) return rc;
+            s->nlaunch += rest * s->graph_body_launches + (s->h_ds->n_builds - builds0) * s->graph_chain_launches;
+        } else {
+            for (int64_t it = 0; it < rest; ++it) {
+                rc = enqueue_outer_step(s, mode, k_m, k_p, false, nullptr);
+                if (rc) return rc;
+            }
+        }
+    }
+    if (mode == MD_MODE_STS) {
         const float hh = (float)(0.5 * c.dt);
         rc = closing_kick(s, hh, hh, hh);
-        if (rc) return rc;
     } else {
-        for (int64_t it = 0; it < n_outer; ++it) {
-            rc = respa_step(s, k_m, k_p, it == 0);
-            if (rc) return rc;
-        }
         rc = closing_kick(s, (float)(0.5 * c.dt), 0.f, 0.f);
-        if (rc) return rc;
     }
+    if (rc) return rc;
+    s->host_step += n_outer;
     return check_flags(s);
 }
 

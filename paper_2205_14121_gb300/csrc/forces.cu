@@ -71,47 +71,107 @@ __device__ __forceinline__ void scatter(float4 *f, int32_t j, float fx, float fy
 }
 
 // K3: DPD pair forces over one list (fluid level or interface level).
+//
+// Two phases per warp of 32 rows.  Phase 1 walks the rows' candidates in
+// lock step, tests r < rc and appends the survivors to a per-warp queue in
+// shared memory (warp ballot + popc gives each hit its slot).  Whenever 32
+// pairs are queued, phase 2 evaluates them one per lane -- Philox, Box-Muller
+// and the force with every lane busy -- adding F_ij to the row's shared
+// accumulator and scattering -F_ij to j.  Rows flush their sums at the end.
+constexpr int DPD_WARPS = MSM_TPB / 32;
+constexpr int DPD_QCAP = 64;
+
+struct dpd_smem {
+    float4 xi[DPD_WARPS][32];          // row positions (w: id)
+    float4 vi[DPD_WARPS][32];          // row velocities (w: tag)
+    float fi[DPD_WARPS][3][32];        // row force accumulators
+    float4 qa[DPD_WARPS][DPD_QCAP];    // queued pairs: dx, dy, dz, image v-shift
+    int4 qb[DPD_WARPS][DPD_QCAP];      // j, source lane, id_j, -
+};
+
+template <bool VIR>
+__device__ __forceinline__ void dpd_eval(const pair_args &a, dpd_smem &sm, int warp, int e, uint32_t nt,
+                                         uint32_t cs, vir6 &w)
+{
+    const float4 q = sm.qa[warp][e];
+    const int4 b = sm.qb[warp][e];
+    const float4 xi = sm.xi[warp][b.y];
+    const float4 vi = sm.vi[warp][b.y];
+    const float4 vj = a.v[b.x];
+    const float r2 = q.x * q.x + q.y * q.y + q.z * q.z;
+    const bool wall = tag_of(vi) == MD_TAG_WALL || tag_of(vj) == MD_TAG_WALL;
+    const float aij = wall ? a.a_wall : a.a_same;
+    const float inv_r = rsqrtf(r2);
+    const float wr = 1.0f - r2 * inv_r * a.inv_rc;
+    const float ex = q.x * inv_r, ey = q.y * inv_r, ez = q.z * inv_r;
+    const float edv = ex * (vi.x - vj.x - q.w) + ey * (vi.y - vj.y) + ez * (vi.z - vj.z);
+    const float zeta = pair_zeta(id_of(xi), (uint32_t)b.z, nt, cs, a.key);
+    const float fc = aij * wr;
+    const float fp = fc - a.gamma * wr * wr * edv + a.sig_isdt * wr * zeta;
+    const float px = fp * ex, py = fp * ey, pz = fp * ez;
+    atomicAdd(&sm.fi[warp][0][b.y], px);
+    atomicAdd(&sm.fi[warp][1][b.y], py);
+    atomicAdd(&sm.fi[warp][2][b.y], pz);
+    scatter(a.f, b.x, -px, -py, -pz);
+    if (VIR) w.add(q.x, q.y, q.z, fc * inv_r);
+}
+
 template <bool VIR>
 __global__ void __launch_bounds__(MSM_TPB) k_dpd(pair_args a)
 {
+    __shared__ dpd_smem sm;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = r < a.rows;
+    const int32_t i = active ? (a.row_idx ? a.row_idx[r] : (int32_t)r) : 0;
+    const int cnt = active ? min(a.nc[r], a.cap) : 0;
+    const float4 xi = active ? a.x32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    sm.xi[warp][lane] = xi;
+    sm.vi[warp][lane] = active ? a.v[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    sm.fi[warp][0][lane] = 0.f;
+    sm.fi[warp][1][lane] = 0.f;
+    sm.fi[warp][2][lane] = 0.f;
+    const uint32_t nt = (uint32_t)a.ds->step, cs = (uint32_t)a.ds->sub;
+    const float delta = a.ds->le_offset_f;
+    const unsigned lt = (1u << lane) - 1u;
     vir6 w = {0, 0, 0, 0, 0, 0};
-    if (r < a.rows) {
-        const int32_t i = a.row_idx ? a.row_idx[r] : (int32_t)r;
-        const int cnt = min(a.nc[r], a.cap);
-        if (cnt > 0) {
-            const float4 xi = a.x32[i];
-            const float4 vi = a.v[i];
-            const uint32_t idi = id_of(xi);
-            const bool wi = tag_of(vi) == MD_TAG_WALL;
-            const uint32_t nt = (uint32_t)a.ds->step, cs = (uint32_t)a.ds->sub;
-            const float delta = a.ds->le_offset_f;
-            float fx = 0.f, fy = 0.f, fz = 0.f;
-            for (int k = 0; k < cnt; ++k) {
-                const int32_t j = a.nl[(int64_t)k * a.rows + r];
-                const float4 xj = a.x32[j];
-                float dx, dy, dz, vsh;
-                min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 >= a.rc2 || r2 == 0.0f) continue;
-                const float4 vj = a.v[j];
-                const float aij = (wi || tag_of(vj) == MD_TAG_WALL) ? a.a_wall : a.a_same;
-                const float inv_r = rsqrtf(r2);
-                const float rr = r2 * inv_r;
-                const float wr = 1.0f - rr * a.inv_rc;
-                const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
-                const float edv = ex * (vi.x - vj.x - vsh) + ey * (vi.y - vj.y) + ez * (vi.z - vj.z);
-                const float zeta = pair_zeta(idi, id_of(xj), nt, cs, a.key);
-                const float fc = aij * wr;
-                const float fp = fc - a.gamma * wr * wr * edv + a.sig_isdt * wr * zeta;
-                const float px = fp * ex, py = fp * ey, pz = fp * ez;
-                fx += px; fy += py; fz += pz;
-                scatter(a.f, j, -px, -py, -pz);
-                if (VIR) w.add(dx, dy, dz, fc * inv_r);
+    const int kmax = __reduce_max_sync(0xffffffffu, cnt);
+    int qn = 0;
+    __syncwarp();
+    for (int k = 0; k < kmax; ++k) {
+        bool hit = false;
+        int32_t j = 0;
+        float4 xj;
+        float dx = 0.f, dy = 0.f, dz = 0.f, vsh = 0.f;
+        if (k < cnt) {
+            j = a.nl[(int64_t)k * a.rows + r];
+            xj = a.x32[j];
+            min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            hit = r2 < a.rc2 && r2 > 0.0f;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const int pos = qn + __popc(m & lt);
+            sm.qa[warp][pos] = make_float4(dx, dy, dz, vsh);
+            sm.qb[warp][pos] = make_int4(j, lane, __float_as_int(xj.w), 0);
+        }
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 32) {
+            dpd_eval<VIR>(a, sm, warp, lane, nt, cs, w);
+            __syncwarp();
+            if (lane < qn - 32) {
+                sm.qa[warp][lane] = sm.qa[warp][32 + lane];
+                sm.qb[warp][lane] = sm.qb[warp][32 + lane];
             }
-            scatter(a.f, i, fx, fy, fz);
+            qn -= 32;
+            __syncwarp();
         }
     }
+    if (lane < qn) dpd_eval<VIR>(a, sm, warp, lane, nt, cs, w);
+    __syncwarp();
+    if (active && cnt > 0) scatter(a.f, i, sm.fi[warp][0][lane], sm.fi[warp][1][lane], sm.fi[warp][2][lane]);
     if (VIR) flush_virial(a.vir, w);
 }
 

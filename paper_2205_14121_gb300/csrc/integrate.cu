@@ -70,20 +70,28 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
             vv.z += az;
         }
         if (drift) {
-            double x = a.xs[k] + a.dt * (double)vv.x;
-            double y = a.ys[k] + a.dt * (double)vv.y;
-            double z = a.zs[k] + a.dt * (double)vv.z;
+            // FP64 master update; FP64 instructions are rare on this part, so
+            // the wrap decisions are taken on the rounded FP32 copies (a
+            // double >= L always rounds to a float >= (float)L) and the FP64
+            // arithmetic is redone only for the few particles that wrap.
+            double x = fma(a.dt, (double)vv.x, a.xs[k]);
+            double y = fma(a.dt, (double)vv.y, a.ys[k]);
+            double z = fma(a.dt, (double)vv.z, a.zs[k]);
             const double Lx = a.L[0], Ly = a.L[1], Lz = a.L[2];
+            float xf = (float)x, yf = (float)y, zf = (float)z;
             if (a.geom.walls) {
                 // bounce-back: retrace the overshoot beyond the wall with the
                 // reversed velocity (independent of drift substepping)
-                const double wall = y < 0.0 ? 0.0 : (y >= Ly ? Ly : -1.0);
-                if (wall >= 0.0) {
-                    const double tau = vv.y != 0.0f ? (y - wall) / (double)vv.y : 0.0;
-                    x -= 2.0 * (double)vv.x * tau;
-                    z -= 2.0 * (double)vv.z * tau;
-                    y = 2.0 * wall - y;
-                    vv.x = -vv.x; vv.y = -vv.y; vv.z = -vv.z;
+                if (yf < 0.0f || yf >= a.geom.L[1]) {
+                    const double wall = y < 0.0 ? 0.0 : (y >= Ly ? Ly : -1.0);
+                    if (wall >= 0.0) {
+                        const double tau = vv.y != 0.0f ? (y - wall) / (double)vv.y : 0.0;
+                        x -= 2.0 * (double)vv.x * tau;
+                        z -= 2.0 * (double)vv.z * tau;
+                        y = 2.0 * wall - y;
+                        vv.x = -vv.x; vv.y = -vv.y; vv.z = -vv.z;
+                        xf = (float)x; yf = (float)y; zf = (float)z;
+                    }
                 }
             } else if (a.geom.le) {
                 const double delta = a.ds->le_offset;
@@ -92,19 +100,22 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
                 } else if (y < 0.0) {
                     y += Ly; x += delta; vv.x += (float)a.shear_v;
                 }
-            } else {
-                if (y >= Ly) y -= Ly;
-                else if (y < 0.0) y += Ly;
+                xf = (float)x; yf = (float)y;
+            } else if (yf >= a.geom.L[1] || yf < 0.0f) {
+                y += yf < 0.0f ? Ly : -Ly;
+                yf = (float)y;
             }
-            if (x >= Lx) x -= Lx;
-            else if (x < 0.0) x += Lx;
-            if (x >= Lx) x -= Lx;       // a Lees-Edwards shift can add one more period
-            else if (x < 0.0) x += Lx;
-            if (z >= Lz) z -= Lz;
-            else if (z < 0.0) z += Lz;
+            for (int rep = 0; rep < 2 && (xf >= a.geom.L[0] || xf < 0.0f); ++rep) {
+                x += xf < 0.0f ? Lx : -Lx;   // a Lees-Edwards shift can add one more period
+                xf = (float)x;
+            }
+            if (zf >= a.geom.L[2] || zf < 0.0f) {
+                z += zf < 0.0f ? Lz : -Lz;
+                zf = (float)z;
+            }
             a.xs[k] = x; a.ys[k] = y; a.zs[k] = z;
             float4 xn = a.x32[k];
-            xn.x = (float)x; xn.y = (float)y; xn.z = (float)z;
+            xn.x = xf; xn.y = yf; xn.z = zf;
             a.x32[k] = xn;
             // rebuild check against the positions of the last build
             float dx, dy, dz, vs;
@@ -117,8 +128,9 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
                 thr = 0.5f * (a.skin - dd) - a.margin;
             }
             if (!(d2 <= thr * thr) || thr <= 0.0f) a.ctl[CTL_REBUILD] = 1;
-            const bool bad = !(fabs(x) < 1e30) || !(fabsf(vv.x) + fabsf(vv.y) + fabsf(vv.z) < 1e30f) ||
-                             (a.geom.walls && (y < -a.wall || y > Ly + a.wall));
+            const bool bad = !(fabsf(xf) + fabsf(yf) + fabsf(zf) < 1e30f) ||
+                             !(fabsf(vv.x) + fabsf(vv.y) + fabsf(vv.z) < 1e30f) ||
+                             (a.geom.walls && (yf < -(float)a.wall || yf > a.geom.L[1] + (float)a.wall));
             if (bad) a.ctl[CTL_UNSTABLE] = 1;
         }
         a.v[k] = vv;
@@ -145,6 +157,46 @@ __global__ void k_set_time(md_dstate *ds, int64_t n, int32_t c, double t, double
         if (0.5f * (skin - dd) - margin <= 0.0f) ctl[CTL_REBUILD] = 1;
     }
 }
+
+// Start of an outer step: its base index is the count of steps begun; in a
+// captured loop, also count down and steer the WHILE node.
+__global__ void k_outer_begin(md_dstate *ds, cudaGraphConditionalHandle loop, int use_loop)
+{
+    ds->base = ds->done;
+    ds->done += 1;
+    if (use_loop) {
+        ds->steps_left -= 1;
+        cudaGraphSetConditional(loop, ds->steps_left > 0 ? 1u : 0u);
+    }
+}
+
+// Time index relative to the current outer step: (base + dn, c), time
+// base*dt + t_off; Lees-Edwards offset and its drift check as k_set_time.
+__global__ void k_time_rel(md_dstate *ds, int dn, int c, double t_off, double dt, double rate_Ly, double Lx,
+                           int le, float skin, float margin, int32_t *ctl)
+{
+    const int64_t n = ds->base + dn;
+    const double t = (double)ds->base * dt + t_off;
+    ds->step = n;
+    ds->sub = c;
+    ds->time = t;
+    if (le) {
+        double d = fmod(rate_Ly * t, Lx);
+        if (d < 0.0) d += Lx;
+        ds->le_offset = d;
+        ds->le_offset_f = (float)d;
+        float dd = fabsf(ds->le_offset_f - ds->le_build_f);
+        dd = fminf(dd, (float)Lx - dd);
+        if (0.5f * (skin - dd) - margin <= 0.0f) ctl[CTL_REBUILD] = 1;
+    }
+}
+
+__global__ void k_cond_rebuild(const int32_t *ctl, cudaGraphConditionalHandle h)
+{
+    cudaGraphSetConditional(h, ctl[CTL_REBUILD] ? 1u : 0u);
+}
+
+__global__ void k_set_loop(md_dstate *ds, int64_t n) { ds->steps_left = n; }
 
 __global__ void k_zero_f4(float4 *p, int64_t n)
 {
@@ -211,6 +263,36 @@ cudaError_t launch_set_time(md_system *s, int64_t n, int32_t c, double t)
     const md_config &cf = s->cfg;
     k_set_time<<<1, 1, 0, s->stream>>>(s->ds, n, c, t, cf.shear_rate * cf.box[1], cf.box[0], s->geom.le,
                                        (float)cf.skin, s->margin, s->ctl);
+    MSM_COUNT(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_outer_begin(md_system *s, cudaGraphConditionalHandle loop, bool use_loop)
+{
+    k_outer_begin<<<1, 1, 0, s->stream>>>(s->ds, loop, use_loop ? 1 : 0);
+    MSM_COUNT(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_time_rel(md_system *s, int dn, int c, double t_off)
+{
+    const md_config &cf = s->cfg;
+    k_time_rel<<<1, 1, 0, s->stream>>>(s->ds, dn, c, t_off, cf.dt, cf.shear_rate * cf.box[1], cf.box[0], s->geom.le,
+                                       (float)cf.skin, s->margin, s->ctl);
+    MSM_COUNT(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cond_rebuild(md_system *s, cudaGraphConditionalHandle h)
+{
+    k_cond_rebuild<<<1, 1, 0, s->stream>>>(s->ctl, h);
+    MSM_COUNT(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_loop(md_system *s, int64_t n)
+{
+    k_set_loop<<<1, 1, 0, s->stream>>>(s->ds, n);
     MSM_COUNT(s, 1);
     return cudaGetLastError();
 }

@@ -37,6 +37,8 @@ struct md_dstate {
     float   le_build_f;  // offset at the last list build
     int64_t n_builds;
     int64_t steps_left;  // countdown of a captured loop
+    int64_t base;        // fluid steps completed when the current outer step began
+    int64_t done;        // outer steps begun (next base)
 };
 
 struct md_grid {
@@ -133,6 +135,14 @@ struct md_system {
     int prof_cls = -1;
     cudaEvent_t prof_a = nullptr;
     int64_t prof_mark = 0;
+
+    // captured outer step: WHILE(steps_left) { step with IF(rebuild) nodes }
+    cudaGraphExec_t step_exec = nullptr;
+    cudaGraph_t step_graph = nullptr;
+    int graph_key[4] = {-1, -1, -1, -1};
+    int64_t graph_body_launches = 0;     // kernels per body iteration
+    int64_t graph_chain_launches = 0;    // kernels per taken rebuild
+    bool graph_failed = false;
 };
 
 // kernel accounting helpers (diag.cu)
@@ -253,6 +263,10 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
 cudaError_t launch_kick_drift(md_system *s, const float h[3], int kick_which, double dt, int drift_which,
                               unsigned zero_levels, bool plt_rows);
 cudaError_t launch_set_time(md_system *s, int64_t n, int32_t c, double t);
+cudaError_t launch_outer_begin(md_system *s, cudaGraphConditionalHandle loop, bool use_loop);
+cudaError_t launch_time_rel(md_system *s, int dn, int c, double t_off);
+cudaError_t launch_cond_rebuild(md_system *s, cudaGraphConditionalHandle h);
+cudaError_t launch_set_loop(md_system *s, int64_t n);
 cudaError_t launch_zero_forces(md_system *s, unsigned levels);
 // reduce.cu
 cudaError_t launch_kinetics(md_system *s);
