@@ -77,7 +77,7 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
     s.n_plt = c.n_plt_particles;
     s.n_rec = c.n_receptors;
     s.nb = c.n_bonds;
-    s.cap[MD_LIST_FLUID] = default_cap(c.cap_fluid, 48);
+    s.cap[MD_LIST_FLUID] = default_cap(c.cap_fluid, 64);
     s.cap[MD_LIST_IFACE] = default_cap(c.cap_iface, 64);
     s.cap[MD_LIST_LJ] = default_cap(c.cap_lj, 128);
     s.cap[MD_LIST_MORSE] = default_cap(c.cap_morse, 256);
@@ -176,10 +176,13 @@ __global__ void k_import_x(int64_t n, const double *__restrict__ aos, double *xs
 }
 
 __global__ void k_import_v(int64_t n, const double *__restrict__ aos, const int32_t *__restrict__ tag, float4 *v,
-                           int32_t *tag_s, int32_t *pos_of_id)
+                           int32_t *tag_s, int32_t *pos_of_id, float4 *x32, float4 *xb)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
+    const float w = __int_as_float((int)pack_w((uint32_t)k, tag[k]));
+    x32[k].w = w;
+    xb[k].w = w;
     v[k] = make_float4((float)aos[3 * k], (float)aos[3 * k + 1], (float)aos[3 * k + 2], __int_as_float(tag[k]));
     tag_s[k] = tag[k];
     pos_of_id[k] = (int32_t)k;
@@ -204,7 +207,7 @@ __global__ void k_export_x(int64_t n, const double *xs, const double *ys, const 
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const int64_t id = __float_as_int(x32[k].w);
+    const int64_t id = id_of(x32[k]);
     aos[3 * id] = xs[k]; aos[3 * id + 1] = ys[k]; aos[3 * id + 2] = zs[k];
 }
 
@@ -212,7 +215,7 @@ __global__ void k_export_f4(int64_t n, const float4 *src, const float4 *x32, dou
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const int64_t id = __float_as_int(x32[k].w);
+    const int64_t id = id_of(x32[k]);
     const float4 p = src[k];
     aos[3 * id] = p.x; aos[3 * id + 1] = p.y; aos[3 * id + 2] = p.z;
 }
@@ -222,7 +225,7 @@ __global__ void k_export_x32(int64_t n, const float4 *x32, float *aos)
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const float4 p = x32[k];
-    const int64_t id = __float_as_int(p.w);
+    const int64_t id = id_of(p);
     aos[3 * id] = p.x; aos[3 * id + 1] = p.y; aos[3 * id + 2] = p.z;
 }
 
@@ -231,7 +234,7 @@ __global__ void k_export_forces(int64_t n, const float4 *f0, const float4 *f1, c
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const int64_t id = __float_as_int(x32[k].w);
+    const int64_t id = id_of(x32[k]);
     double fx = 0, fy = 0, fz = 0;
     if (f0) { const float4 p = f0[k]; fx += p.x; fy += p.y; fz += p.z; if (tag[k] != MD_TAG_WALL) fx += g; }
     if (f1) { const float4 p = f1[k]; fx += p.x; fy += p.y; fz += p.z; }
@@ -705,7 +708,8 @@ int md_set_particles(md_system *s, const double *x, const double *v, const int32
     CK(cudaGetLastError(), "import x");
     CK(cudaMemcpyAsync(s->alt_tag, tag, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st), "upload tag");
     CK(cudaMemcpyAsync(s->alt64, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload v");
-    k_import_v<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->alt64, s->alt_tag, s->v, s->tag_s, s->pos_of_id);
+    k_import_v<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->alt64, s->alt_tag, s->v, s->tag_s, s->pos_of_id, s->x32,
+                                                   s->xb);
     CK(cudaGetLastError(), "import v");
     if (s->X0) {
         CK(cudaMemcpyAsync(s->alt64, X0 ? X0 : x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload X0");
@@ -935,6 +939,7 @@ int md_neighbor_pairs(md_system *s, int32_t kind, int32_t *pairs, int64_t cap, i
     auto id_of_h = [&](int64_t k) {
         int32_t id;
         memcpy(&id, &x32h[(size_t)(4 * k + 3)], sizeof id);
+        id &= (int32_t)MSM_ID_MASK;
         return id;
     };
     int64_t total = 0;
@@ -1020,6 +1025,7 @@ int md_set_state(md_system *s, const void *blob, size_t nbytes)
     for (int64_t k = 0; k < n; ++k) {
         int32_t id;
         memcpy(&id, &x32h[(size_t)(4 * k + 3)], sizeof id);
+        id &= (int32_t)MSM_ID_MASK;
         tag[(size_t)id] = tag_sorted[(size_t)k];
     }
     std::vector<double> X0;

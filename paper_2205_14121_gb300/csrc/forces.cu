@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_dpd(pair_args a)
         if (hit) {
             const int pos = qn + __popc(m & lt);
             sm.qa[warp][pos] = make_float4(dx, dy, dz, vsh);
-            sm.qb[warp][pos] = make_int4(j, lane, __float_as_int(xj.w), 0);
+            sm.qb[warp][pos] = make_int4(j, lane, (int)id_of(xj), 0);
         }
         qn += __popc(m);
         __syncwarp();

@@ -157,7 +157,17 @@ enum { RED_WORDS = 16, RED_BLOCKS_MAX = 1024 };
 // device helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int tag_of(float4 v) { return __float_as_int(v.w); }
-__device__ __forceinline__ uint32_t id_of(float4 x) { return (uint32_t)__float_as_int(x.w); }
+// x32.w holds the particle id in bits 0-29 and its class in bits 30-31
+// (0 plasma, 1 wall, 2 platelet), so list builds need no tag load.
+#define MSM_ID_MASK 0x3FFFFFFFu
+enum { CLS_FLUID = 0, CLS_WALL = 1, CLS_PLT = 2 };
+__device__ __host__ __forceinline__ uint32_t pack_w(uint32_t id, int32_t tag)
+{
+    const uint32_t cls = tag >= 0 ? CLS_PLT : (tag == MD_TAG_WALL ? CLS_WALL : CLS_FLUID);
+    return (id & MSM_ID_MASK) | (cls << 30);
+}
+__device__ __forceinline__ uint32_t id_of(float4 x) { return (uint32_t)__float_as_int(x.w) & MSM_ID_MASK; }
+__device__ __forceinline__ int class_of(float4 x) { return (int)((uint32_t)__float_as_int(x.w) >> 30); }
 
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the two multiply-xor
 // S-boxes with the Weyl key schedule.

@@ -6,31 +6,26 @@
 // computed from the minimum-image separation of min_image_f32(); a CPU
 // evaluation of the same operation sequence yields the identical pair set.
 //
+// Half lists keep each unordered pair once, in the row of the particle that
+// comes first in the grid's cell-sorted order; a row therefore only scans
+// cells whose index is not below its own, half of the neighbourhood.
+//
 // Lists are ELL, column-major (entry k of row r at k*rows + r) so that the
 // force kernels, one thread per row, read them coalesced.  Row counts beyond
 // the capacity are recorded (overflow bit + longest row) and never written.
 //
-//   MD_LIST_FLUID  rows: every particle; owned partners (owns_pair), plasma-
-//                  plasma and plasma-wall pairs (Eq. 1)
+//   MD_LIST_FLUID  rows: every particle (cell-sorted); later plasma/wall
+//                  partners, plasma-plasma and plasma-wall pairs (Eq. 1)
 //   MD_LIST_IFACE  rows: platelet particles; partners: every plasma or wall
 //                  particle (Eq. 3)
-//   MD_LIST_LJ     rows: platelet particles; owned partners on the platelet
-//                  sub-grid, excluding same-platelet pairs closer than
-//                  lj_excl at rest (Eq. 2)
-//   MD_LIST_MORSE  rows: receptor sites; owned partners on the receptor
-//                  sub-grid belonging to another platelet (Eq. 4)
+//   MD_LIST_LJ     rows: platelet particles in platelet sub-grid order; later
+//                  platelet particles, excluding same-platelet pairs closer
+//                  than lj_excl at rest (Eq. 2)
+//   MD_LIST_MORSE  rows: receptor sites in receptor sub-grid order; later
+//                  receptors of another platelet (Eq. 4)
 #include "msm_internal.cuh"
 
 namespace {
-
-// Half lists store each unordered pair once, in the row of its owner: the
-// lower index when i + j is even, the higher when odd.  Unlike "j > i" this
-// gives every row about half of its neighbours whatever its place in the
-// sort order, so rows stay short and warps stay balanced.
-__device__ __forceinline__ bool owns_pair(int32_t i, int32_t j)
-{
-    return j != i && ((i < j) == (((i + j) & 1) == 0));
-}
 
 __device__ __forceinline__ int wrapc(int c, int n)
 {
@@ -38,12 +33,15 @@ __device__ __forceinline__ int wrapc(int c, int n)
     return c < 0 ? c + n : c;
 }
 
-// Visit every member of the cells within reach R of xi; LE rows that cross
-// the y boundary are shifted by the image offset.
-template <class F>
+// Visit (member position s, particle index) of every member of the cells
+// within reach R of xi; Lees-Edwards rows that cross the y boundary are
+// shifted by the image offset.  half: skip cells with a lower index than
+// xi's own cell.
+template <bool HALF, class F>
 __device__ __forceinline__ void for_candidates(const md_grid &g, const md_geom &geom, float delta, float4 xi,
                                                float R, const int32_t *__restrict__ members, F fn)
 {
+    const int64_t own = cell_index(g, cell_coord(g, 0, xi.x), cell_coord(g, 1, xi.y), cell_coord(g, 2, xi.z));
     int zlo = __float2int_rd((xi.z - g.lo[2] - R) * g.inv_h[2]);
     int zhi = __float2int_rd((xi.z - g.lo[2] + R) * g.inv_h[2]);
     if (zhi - zlo + 1 > g.nc[2]) zhi = zlo + g.nc[2] - 1;
@@ -69,13 +67,15 @@ __device__ __forceinline__ void for_candidates(const md_grid &g, const md_geom &
                     if (geom.le) sx = -delta;
                 }
             }
+            if (HALF && cell_index(g, g.nc[0] - 1, wy, wz) < own) continue;   // whole row below own cell
             int xlo = __float2int_rd((xi.x + sx - g.lo[0] - R) * g.inv_h[0]);
             int xhi = __float2int_rd((xi.x + sx - g.lo[0] + R) * g.inv_h[0]);
             if (xhi - xlo + 1 > g.nc[0]) xhi = xlo + g.nc[0] - 1;
             for (int cx = xlo; cx <= xhi; ++cx) {
                 const int64_t c = cell_index(g, wrapc(cx, g.nc[0]), wy, wz);
+                if (HALF && c < own) continue;
                 const int32_t b = g.start[c], e = g.start[c + 1];
-                for (int32_t s = b; s < e; ++s) fn(members ? members[s] : s);
+                for (int32_t s = b; s < e; ++s) fn(s, members ? members[s] : s);
             }
         }
     }
@@ -95,7 +95,6 @@ struct build_args {
     float R, cut2, excl2;
     int32_t *nl, *nc;
     int cap;
-    int kind;
     int32_t *ctl;
 };
 
@@ -103,41 +102,42 @@ template <int KIND>
 __global__ void __launch_bounds__(MSM_TPB) k_build(build_args a, const int32_t *gate)
 {
     if (gate_closed(gate)) return;
+    constexpr bool HALF = KIND != MD_LIST_IFACE;
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = r < a.rows;
     int cnt = 0;
     if (active) {
         const int32_t i = a.row_idx ? a.row_idx[r] : (int32_t)r;
-        const int32_t ti = a.tag[i];
         const float4 xi = a.x32[i];
+        const int ci = class_of(xi);
         const float delta = a.ds->le_offset_f;
-        const bool owns = KIND == MD_LIST_FLUID ? (ti < 0) : true;
-        if (owns) {
+        if (KIND != MD_LIST_FLUID || ci != CLS_PLT) {
+            int32_t ti = 0;
             float4 x0i = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (KIND == MD_LIST_LJ) x0i = a.X0[__float_as_int(xi.w)];
+            if (KIND == MD_LIST_LJ || KIND == MD_LIST_MORSE) ti = a.tag[i] & ~MD_RECEPTOR_BIT;
+            if (KIND == MD_LIST_LJ) x0i = a.X0[id_of(xi)];
             const int64_t rows = a.rows;
-            for_candidates(a.g, a.geom, delta, xi, a.R, a.members, [&](int32_t j) {
-                const int32_t tj = a.tag[j];
-                if (KIND == MD_LIST_FLUID) {
-                    if (tj >= 0 || !owns_pair(i, j)) return;
-                    if (ti == MD_TAG_WALL && tj == MD_TAG_WALL) return;
-                } else if (KIND == MD_LIST_IFACE) {
-                    if (tj >= 0) return;
-                } else if (KIND == MD_LIST_LJ) {
-                    if (!owns_pair(i, j)) return;
-                } else {  // MORSE
-                    if (!owns_pair(i, j)) return;
-                    if ((ti & ~MD_RECEPTOR_BIT) == (tj & ~MD_RECEPTOR_BIT)) return;
-                }
+            for_candidates<HALF>(a.g, a.geom, delta, xi, a.R, a.members, [&](int32_t s, int32_t j) {
+                if (HALF && s <= (int32_t)r) return;
                 const float4 xj = a.x32[j];
+                const int cj = class_of(xj);
+                if (KIND == MD_LIST_FLUID) {
+                    if (cj == CLS_PLT || (ci == CLS_WALL && cj == CLS_WALL)) return;
+                } else if (KIND == MD_LIST_IFACE) {
+                    if (cj == CLS_PLT) return;
+                }
                 float dx, dy, dz, vs;
                 min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vs);
                 if (!(r2_f32(dx, dy, dz) < a.cut2)) return;
-                if (KIND == MD_LIST_LJ && (ti & ~MD_RECEPTOR_BIT) == (tj & ~MD_RECEPTOR_BIT)) {
-                    const float4 x0j = a.X0[__float_as_int(xj.w)];
-                    const float ex = __fsub_rn(x0i.x, x0j.x), ey = __fsub_rn(x0i.y, x0j.y),
-                                ez = __fsub_rn(x0i.z, x0j.z);
-                    if (r2_f32(ex, ey, ez) < a.excl2) return;
+                if (KIND == MD_LIST_LJ || KIND == MD_LIST_MORSE) {
+                    const bool same = (a.tag[j] & ~MD_RECEPTOR_BIT) == ti;
+                    if (KIND == MD_LIST_MORSE && same) return;
+                    if (KIND == MD_LIST_LJ && same) {
+                        const float4 x0j = a.X0[id_of(xj)];
+                        const float ex = __fsub_rn(x0i.x, x0j.x), ey = __fsub_rn(x0i.y, x0j.y),
+                                    ez = __fsub_rn(x0i.z, x0j.z);
+                        if (r2_f32(ex, ey, ez) < a.excl2) return;
+                    }
                 }
                 if (cnt < a.cap) a.nl[(int64_t)cnt * rows + r] = j;
                 ++cnt;
@@ -146,9 +146,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_build(build_args a, const int32_t *
     }
     // every lane of the warp reaches the row bookkeeping (shuffle needs all)
     if (active) a.nc[r] = cnt;
-    int m = active ? cnt : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int m = __reduce_max_sync(0xffffffffu, active ? cnt : 0);
     if ((threadIdx.x & 31) == 0 && m > 0) {
         atomicMax(&a.ctl[CTL_MAXROW + KIND], m);
         if (m > a.cap) atomicOr(&a.ctl[CTL_OVERFLOW], 1 << KIND);
@@ -182,17 +180,16 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
     a.nl = s->nl[MD_LIST_FLUID];
     a.nc = s->nc[MD_LIST_FLUID];
     a.cap = s->cap[MD_LIST_FLUID];
-    a.kind = MD_LIST_FLUID;
     k_build<MD_LIST_FLUID><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
 
     if (s->n_plt > 0) {
+        // interface: platelet rows (platelet sub-grid order) against the main grid
         a.rows = s->n_plt;
         a.row_idx = s->plt_sorted;
         a.cut2 = s->cut2[MD_LIST_IFACE];
         a.nl = s->nl[MD_LIST_IFACE];
         a.nc = s->nc[MD_LIST_IFACE];
         a.cap = s->cap[MD_LIST_IFACE];
-        a.kind = MD_LIST_IFACE;
         k_build<MD_LIST_IFACE><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
 
         a.g = s->gplt;
@@ -202,7 +199,6 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
         a.nl = s->nl[MD_LIST_LJ];
         a.nc = s->nc[MD_LIST_LJ];
         a.cap = s->cap[MD_LIST_LJ];
-        a.kind = MD_LIST_LJ;
         k_build<MD_LIST_LJ><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
 
         if (s->n_rec > 0) {
@@ -215,7 +211,6 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
             a.nl = s->nl[MD_LIST_MORSE];
             a.nc = s->nc[MD_LIST_MORSE];
             a.cap = s->cap[MD_LIST_MORSE];
-            a.kind = MD_LIST_MORSE;
             k_build<MD_LIST_MORSE><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
         }
     }

@@ -185,7 +185,7 @@ __global__ void k_copyback(copyback_args a, const int32_t *gate)
     a.v[k] = a.altv[k];
     a.tag[k] = a.alt_tag[k];
     for (int l = 0; l < a.nf; ++l) a.f[l][k] = a.altf[l][k];
-    a.pos_of_id[__float_as_int(x.w)] = (int32_t)k;
+    a.pos_of_id[id_of(x)] = (int32_t)k;
 }
 
 __global__ void k_remap_bonds(int64_t nb, const int32_t *__restrict__ bond_id, const int32_t *__restrict__ pos_of_id,
