@@ -79,7 +79,7 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
     s.nb = c.n_bonds;
     s.cap[MD_LIST_FLUID] = default_cap(c.cap_fluid, 64);
     s.cap[MD_LIST_IFACE] = default_cap(c.cap_iface, 64);
-    s.cap[MD_LIST_LJ] = default_cap(c.cap_lj, 128);
+    s.cap[MD_LIST_LJ] = default_cap(c.cap_lj, 256);
     s.cap[MD_LIST_MORSE] = default_cap(c.cap_morse, 256);
     if (!setup_grid(c, c.rc + c.skin, s.gmain, err)) return false;
     const bool plt = s.n_plt > 0;

@@ -138,14 +138,21 @@ __global__ void __launch_bounds__(MSM_TPB) k_dpd(pair_args a)
     const int kmax = __reduce_max_sync(0xffffffffu, cnt);
     int qn = 0;
     __syncwarp();
+    // software pipeline: the index of candidate k+2 and the position of k+1
+    // are in flight while candidate k is tested
+    const int32_t *nlr = a.nl + r;
+    int32_t j1 = cnt > 0 ? nlr[0] : 0;
+    int32_t j2 = cnt > 1 ? nlr[a.rows] : 0;
+    float4 x1 = cnt > 0 ? a.x32[j1] : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int k = 0; k < kmax; ++k) {
+        const int32_t j = j1;
+        const float4 xj = x1;
+        j1 = j2;
+        if (k + 1 < cnt) x1 = a.x32[j1];
+        if (k + 2 < cnt) j2 = nlr[(int64_t)(k + 2) * a.rows];
         bool hit = false;
-        int32_t j = 0;
-        float4 xj;
         float dx = 0.f, dy = 0.f, dz = 0.f, vsh = 0.f;
         if (k < cnt) {
-            j = a.nl[(int64_t)k * a.rows + r];
-            xj = a.x32[j];
             min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
             const float r2 = dx * dx + dy * dy + dz * dz;
             hit = r2 < a.rc2 && r2 > 0.0f;
