@@ -1,0 +1,123 @@
+"""Pins of the FP64 controller oracle (Table 2): GRU forward against
+torch.nn.GRU, every backward against central finite differences, Adam against
+torch.optim.Adam, the filters against closed forms."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ai as A
+
+
+def small_params(seed=1, f_in=3, h=5, latent=4):
+    return A.init_params(seed=seed, f_in=f_in, h=h, latent=latent, head_layers=(6, 4, 3), n_classes=5)
+
+
+def test_moving_average_closed_form():
+    x = np.arange(10.0)[:, None] * np.ones((1, 2))
+    y = A.moving_average(x, 5)
+    assert np.allclose(y[4:, 0], np.arange(4, 10) - 2.0)
+    assert np.allclose(y[:4, 0], [0.0, 0.5, 1.0, 1.5])
+
+
+def test_haar_keeps_constants_and_pair_averages_a_ramp():
+    c = np.full((16, 3), 2.5)
+    assert np.allclose(A.haar_denoise(c), c)
+    ramp = np.arange(16.0)[:, None]
+    y = A.haar_denoise(ramp)
+    pair_mean = (ramp[0::2] + ramp[1::2]) / 2
+    assert np.allclose(y[0::2], pair_mean) and np.allclose(y[1::2], pair_mean)
+
+
+def test_denoise_reduces_noise():
+    rng = np.random.default_rng(0)
+    t = np.linspace(0, 4 * np.pi, 128)
+    clean = np.stack([np.sin(t), np.cos(0.5 * t)], axis=1)
+    noisy = clean + 0.3 * rng.standard_normal(clean.shape)
+    err_noisy = np.mean((noisy - clean) ** 2)
+    err_den = np.mean((A.denoise(noisy) - clean) ** 2)
+    assert err_den < 0.5 * err_noisy
+
+
+def test_gru_forward_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(2)
+    layer = A._gru_layer(rng, 3, 5)
+    xs = rng.standard_normal((7, 4, 3))
+    hs, _ = A.gru_forward(layer, xs)
+    g = torch.nn.GRU(3, 5).double()
+    with torch.no_grad():
+        g.weight_ih_l0.copy_(torch.from_numpy(layer["W_ih"]))
+        g.weight_hh_l0.copy_(torch.from_numpy(layer["W_hh"]))
+        g.bias_ih_l0.copy_(torch.from_numpy(layer["b_ih"]))
+        g.bias_hh_l0.copy_(torch.from_numpy(layer["b_hh"]))
+        out, _ = g(torch.from_numpy(xs))
+    assert np.allclose(hs, out.numpy(), rtol=0, atol=1e-13)
+
+
+def _fd_check(loss_fn, params, grads, names, eps=1e-6, rtol=1e-6, samples=6, seed=0):
+    rng = np.random.default_rng(seed)
+    flat = dict(A.flatten(params))
+    gflat = dict(A.flatten(grads))
+    for name in names:
+        arr = flat[name]
+        g = gflat[name]
+        for _ in range(samples):
+            idx = tuple(rng.integers(0, s) for s in arr.shape)
+            old = arr[idx]
+            arr[idx] = old + eps
+            lp = loss_fn()
+            arr[idx] = old - eps
+            lm = loss_fn()
+            arr[idx] = old
+            fd = (lp - lm) / (2 * eps)
+            assert g[idx] == pytest.approx(fd, rel=rtol, abs=1e-9), (name, idx, g[idx], fd)
+
+
+def test_autoencoder_backward_matches_finite_differences():
+    p = small_params()
+    x = np.random.default_rng(3).standard_normal((2, 6, 3))
+    _, g = A.ae_loss_and_grads(p, x)
+    names = [n for n, _ in A.flatten({k: p[k] for k in ("enc1", "enc2", "lat", "dec1", "dec2", "out")})]
+    _fd_check(lambda: A.ae_loss_and_grads(p, x)[0],
+              {k: p[k] for k in ("enc1", "enc2", "lat", "dec1", "dec2", "out")}, g, names)
+
+
+def test_heads_backward_matches_finite_differences():
+    p = small_params()
+    rng = np.random.default_rng(4)
+    zl = rng.standard_normal((8, 4))
+    kc = rng.integers(0, 5, 8)
+    lh = rng.standard_normal(8)
+    _, g, _ = A.heads_loss_and_grads(p, zl, kc, lh)
+    names = [n for n, _ in A.flatten({"khead": p["khead"], "lhead": p["lhead"]})]
+    _fd_check(lambda: A.heads_loss_and_grads(p, zl, kc, lh)[0], {"khead": p["khead"], "lhead": p["lhead"]}, g,
+              names)
+
+
+def test_adam_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    w = rng.standard_normal((4, 3))
+    p = {"w": w.copy()}
+    opt = A.Adam(p, lr=1e-2)
+    tw = torch.nn.Parameter(torch.from_numpy(w.copy()))
+    topt = torch.optim.Adam([tw], lr=1e-2)
+    for it in range(5):
+        g = rng.standard_normal((4, 3))
+        opt.step(p, {"w": g})
+        topt.zero_grad()
+        tw.grad = torch.from_numpy(g.copy())
+        topt.step()
+    assert np.allclose(p["w"], tw.detach().numpy(), rtol=0, atol=1e-12)
+
+
+def test_predict_trust_bound():
+    p = small_params()
+    rng = np.random.default_rng(6)
+    raw = rng.standard_normal((3, 8, 3))
+    out = A.predict(p, raw, 0.0, 1.0, rec_threshold=np.inf, p_min=0.0)
+    assert out["trusted"].all() and set(out["k"]) <= set(A.K_SET)
+    out = A.predict(p, raw, 0.0, 1.0, rec_threshold=-1.0, p_min=0.0)
+    assert not out["trusted"].any()
+    assert np.all((out["hold"] >= 100) & (out["hold"] <= 2000))
