@@ -84,11 +84,12 @@ constexpr int DPD_QCAP = 64;
 struct dpd_smem {
     float4 xi[DPD_WARPS][32];          // row positions (w: id)
     float4 vi[DPD_WARPS][32];          // row velocities (w: tag)
-    float fi[DPD_WARPS][3][32];        // row force accumulators
+    float4 qf[DPD_WARPS][32];          // F_ij of the batch just evaluated
     float4 qa[DPD_WARPS][DPD_QCAP];    // queued pairs: dx, dy, dz, image v-shift
     int4 qb[DPD_WARPS][DPD_QCAP];      // j, source lane, id_j, -
 };
 
+// Evaluate queue entry e (one lane each): F_ij into qf[e], -F_ij scattered to j.
 template <bool VIR>
 __device__ __forceinline__ void dpd_eval(const pair_args &a, dpd_smem &sm, int warp, int e, uint32_t nt,
                                          uint32_t cs, vir6 &w)
@@ -109,15 +110,25 @@ __device__ __forceinline__ void dpd_eval(const pair_args &a, dpd_smem &sm, int w
     const float fc = aij * wr;
     const float fp = fc - a.gamma * wr * wr * edv + a.sig_isdt * wr * zeta;
     const float px = fp * ex, py = fp * ey, pz = fp * ez;
-    atomicAdd(&sm.fi[warp][0][b.y], px);
-    atomicAdd(&sm.fi[warp][1][b.y], py);
-    atomicAdd(&sm.fi[warp][2][b.y], pz);
+    sm.qf[warp][e] = make_float4(px, py, pz, 0.f);
     scatter(a.f, b.x, -px, -py, -pz);
     if (VIR) w.add(q.x, q.y, q.z, fc * inv_r);
 }
 
+// Row lane adds the forces of its own queue slots (bits of `mine`).
+__device__ __forceinline__ void dpd_collect(const dpd_smem &sm, int warp, uint32_t mine, float &fx, float &fy,
+                                            float &fz)
+{
+    while (mine) {
+        const int e = __ffs(mine) - 1;
+        mine &= mine - 1;
+        const float4 p = sm.qf[warp][e];
+        fx += p.x; fy += p.y; fz += p.z;
+    }
+}
+
 template <bool VIR>
-__global__ void __launch_bounds__(MSM_TPB) k_dpd(pair_args a)
+__global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
 {
     __shared__ dpd_smem sm;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -128,13 +139,12 @@ __global__ void __launch_bounds__(MSM_TPB) k_dpd(pair_args a)
     const float4 xi = active ? a.x32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     sm.xi[warp][lane] = xi;
     sm.vi[warp][lane] = active ? a.v[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    sm.fi[warp][0][lane] = 0.f;
-    sm.fi[warp][1][lane] = 0.f;
-    sm.fi[warp][2][lane] = 0.f;
     const uint32_t nt = (uint32_t)a.ds->step, cs = (uint32_t)a.ds->sub;
     const float delta = a.ds->le_offset_f;
     const unsigned lt = (1u << lane) - 1u;
     vir6 w = {0, 0, 0, 0, 0, 0};
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    uint64_t mine = 0;                   // queue slots holding this row's pairs
     const int kmax = __reduce_max_sync(0xffffffffu, cnt);
     int qn = 0;
     __syncwarp();
@@ -162,12 +172,15 @@ __global__ void __launch_bounds__(MSM_TPB) k_dpd(pair_args a)
             const int pos = qn + __popc(m & lt);
             sm.qa[warp][pos] = make_float4(dx, dy, dz, vsh);
             sm.qb[warp][pos] = make_int4(j, lane, (int)id_of(xj), 0);
+            mine |= 1ull << pos;
         }
         qn += __popc(m);
         __syncwarp();
         if (qn >= 32) {
             dpd_eval<VIR>(a, sm, warp, lane, nt, cs, w);
             __syncwarp();
+            dpd_collect(sm, warp, (uint32_t)mine, fx, fy, fz);
+            mine >>= 32;
             if (lane < qn - 32) {
                 sm.qa[warp][lane] = sm.qa[warp][32 + lane];
                 sm.qb[warp][lane] = sm.qb[warp][32 + lane];
@@ -178,7 +191,8 @@ __global__ void __launch_bounds__(MSM_TPB) k_dpd(pair_args a)
     }
     if (lane < qn) dpd_eval<VIR>(a, sm, warp, lane, nt, cs, w);
     __syncwarp();
-    if (active && cnt > 0) scatter(a.f, i, sm.fi[warp][0][lane], sm.fi[warp][1][lane], sm.fi[warp][2][lane]);
+    dpd_collect(sm, warp, (uint32_t)mine, fx, fy, fz);
+    if (active && cnt > 0) scatter(a.f, i, fx, fy, fz);
     if (VIR) flush_virial(a.vir, w);
 }
 

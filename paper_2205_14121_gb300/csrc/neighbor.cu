@@ -27,10 +27,18 @@
 
 namespace {
 
+// Periodic cell wrap; the integer division only runs for the few cells
+// outside the grid.
 __device__ __forceinline__ int wrapc(int c, int n)
 {
+    if (c >= 0 && c < n) return c;
     c %= n;
     return c < 0 ? c + n : c;
+}
+
+__device__ __forceinline__ int cell_index32(const md_grid &g, int cx, int cy, int cz)
+{
+    return (cz * g.nc[1] + cy) * g.nc[0] + cx;
 }
 
 // Visit (member position s, particle index) of every member of the cells
@@ -39,9 +47,9 @@ __device__ __forceinline__ int wrapc(int c, int n)
 // xi's own cell.
 template <bool HALF, class F>
 __device__ __forceinline__ void for_candidates(const md_grid &g, const md_geom &geom, float delta, float4 xi,
-                                               float R, const int32_t *__restrict__ members, F fn)
+                                               float R, const int32_t *__restrict__ members, int32_t r, F fn)
 {
-    const int64_t own = cell_index(g, cell_coord(g, 0, xi.x), cell_coord(g, 1, xi.y), cell_coord(g, 2, xi.z));
+    const int own = cell_index32(g, cell_coord(g, 0, xi.x), cell_coord(g, 1, xi.y), cell_coord(g, 2, xi.z));
     int zlo = __float2int_rd((xi.z - g.lo[2] - R) * g.inv_h[2]);
     int zhi = __float2int_rd((xi.z - g.lo[2] + R) * g.inv_h[2]);
     if (zhi - zlo + 1 > g.nc[2]) zhi = zlo + g.nc[2] - 1;
@@ -67,14 +75,17 @@ __device__ __forceinline__ void for_candidates(const md_grid &g, const md_geom &
                     if (geom.le) sx = -delta;
                 }
             }
-            if (HALF && cell_index(g, g.nc[0] - 1, wy, wz) < own) continue;   // whole row below own cell
+            const int rowc = cell_index32(g, 0, wy, wz);
+            if (HALF && rowc + g.nc[0] - 1 < own) continue;   // whole row below own cell
             int xlo = __float2int_rd((xi.x + sx - g.lo[0] - R) * g.inv_h[0]);
             int xhi = __float2int_rd((xi.x + sx - g.lo[0] + R) * g.inv_h[0]);
             if (xhi - xlo + 1 > g.nc[0]) xhi = xlo + g.nc[0] - 1;
             for (int cx = xlo; cx <= xhi; ++cx) {
-                const int64_t c = cell_index(g, wrapc(cx, g.nc[0]), wy, wz);
+                const int c = rowc + wrapc(cx, g.nc[0]);
                 if (HALF && c < own) continue;
-                const int32_t b = g.start[c], e = g.start[c + 1];
+                int32_t b = g.start[c];
+                const int32_t e = g.start[c + 1];
+                if (HALF && b <= r) b = r + 1;    // own cell: later members only
                 for (int32_t s = b; s < e; ++s) fn(s, members ? members[s] : s);
             }
         }
@@ -117,8 +128,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_build(build_args a, const int32_t *
             if (KIND == MD_LIST_LJ || KIND == MD_LIST_MORSE) ti = a.tag[i] & ~MD_RECEPTOR_BIT;
             if (KIND == MD_LIST_LJ) x0i = a.X0[id_of(xi)];
             const int64_t rows = a.rows;
-            for_candidates<HALF>(a.g, a.geom, delta, xi, a.R, a.members, [&](int32_t s, int32_t j) {
-                if (HALF && s <= (int32_t)r) return;
+            for_candidates<HALF>(a.g, a.geom, delta, xi, a.R, a.members, (int32_t)r, [&](int32_t s, int32_t j) {
                 const float4 xj = a.x32[j];
                 const int cj = class_of(xj);
                 if (KIND == MD_LIST_FLUID) {
