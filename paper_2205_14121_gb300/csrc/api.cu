@@ -82,6 +82,10 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
     s.cap[MD_LIST_LJ] = default_cap(c.cap_lj, 256);
     s.cap[MD_LIST_MORSE] = default_cap(c.cap_morse, 256);
     if (!setup_grid(c, c.rc + c.skin, s.gmain, err)) return false;
+    if ((c.flags & MD_CFG_LEES_EDWARDS) && s.gmain.nc[1] < 3) {
+        err = "Lees-Edwards images need at least three list cells along y";
+        return false;
+    }
     const bool plt = s.n_plt > 0;
     if (plt) {
         if (!setup_grid(c, c.lj_rc + c.skin, s.gplt, err)) return false;

@@ -102,6 +102,19 @@ def test_neighbor_sets_bit_exact(plt_sys, kind):
     assert len(rs) > 0
 
 
+def test_plasma_list_bit_exact_with_walls(wall_sys):
+    """Plasma list in a walled box (no periodic y): bit-exact set equality."""
+    s = wall_sys
+    g = make_gpu(s, step0=3)
+    g.neighbor_build(force=True)
+    got = g.neighbor_pairs(0)
+    _, _, x32 = g.read_particles()
+    ref = O.pairs_f32(x32, s.tag, np.array(s.box, np.float32), 0, np.float32(1.3 * 1.3), walls=True)
+    gs = set(map(tuple, got.tolist()))
+    assert len(got) == len(gs)
+    assert gs == set(map(tuple, ref.tolist()))
+
+
 def test_forces_match_oracle_all_levels(plt_sys):
     s = plt_sys
     import paper_2205_14121_gb300 as M
