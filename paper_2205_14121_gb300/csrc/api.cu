@@ -952,7 +952,7 @@ int md_neighbor_pairs(md_system *s, int32_t kind, int32_t *pairs, int64_t cap, i
         const int32_t idi = id_of_h(i);
         const int cnt = nc[(size_t)r] < cp ? nc[(size_t)r] : cp;
         for (int k = 0; k < cnt; ++k) {
-            const int32_t idj = id_of_h(nl[(size_t)((int64_t)k * rows + r)]);
+            const int32_t idj = id_of_h(nl[(size_t)(r * cp + k)]);
             if (pairs && total < cap) {
                 pairs[2 * total] = idi < idj ? idi : idj;
                 pairs[2 * total + 1] = idi < idj ? idj : idi;

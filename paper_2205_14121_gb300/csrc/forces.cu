@@ -9,10 +9,10 @@
 //  K5  LJ 12-6 (Eq. 2) on MD_LIST_LJ and the printed-form Morse plus the
 //      receptor term f_A (1 - r/r0) (Eq. 2, Eq. 4) on MD_LIST_MORSE.
 //
-// One thread per list row: partner j's contribution is scattered with one
-// vector atomic (red.global.add.v4.f32), the row's own sum is added once at
-// the end.  The conservative virial (pressure, Sec. 4.2) is accumulated in
-// FP32 per thread and reduced in FP64 when requested.
+// Partner j's contribution is scattered with one vector atomic
+// (red.global.add.v4.f32); a row's own sum is added once at the end.  The
+// conservative virial (pressure, Sec. 4.2) is accumulated in FP32 per thread
+// and reduced in FP64 when requested.
 #include "msm_internal.cuh"
 
 namespace {
@@ -70,60 +70,70 @@ __device__ __forceinline__ void scatter(float4 *f, int32_t j, float fx, float fy
     atomicAdd(&f[j], make_float4(fx, fy, fz, 0.0f));
 }
 
+// ---------------------------------------------------------------------------
 // K3: DPD pair forces over one list (fluid level or interface level).
 //
-// Two phases per warp of 32 rows.  Phase 1 walks the rows' candidates in
-// lock step, tests r < rc and appends the survivors to a per-warp queue in
-// shared memory (warp ballot + popc gives each hit its slot).  Whenever 32
-// pairs are queued, phase 2 evaluates them one per lane -- Philox, Box-Muller
-// and the force with every lane busy -- adding F_ij to the row's shared
-// accumulator and scattering -F_ij to j.  Rows flush their sums at the end.
+// A warp owns 32 consecutive rows and streams their concatenated candidate
+// lists 32 entries at a time, so every lane has work whatever the row
+// lengths (the row of flat entry f is found by a shuffle binary search over
+// the rows' prefix offsets).  Candidates inside rc are appended to a per-warp
+// queue in shared memory (ballot + popc give the slots); whenever 32 pairs
+// are queued each lane evaluates one -- Philox, Box-Muller and Eq. 1 -- and
+// scatters -F_ij to j.  Queue entries keep their row order, so the row sums
+// are a segmented shuffle reduction over each batch.
+// ---------------------------------------------------------------------------
 constexpr int DPD_WARPS = MSM_TPB / 32;
 constexpr int DPD_QCAP = 64;
 
 struct dpd_smem {
     float4 xi[DPD_WARPS][32];          // row positions (w: id)
     float4 vi[DPD_WARPS][32];          // row velocities (w: tag)
-    float4 qf[DPD_WARPS][32];          // F_ij of the batch just evaluated
+    float4 fi[DPD_WARPS][32];          // row force sums
     float4 qa[DPD_WARPS][DPD_QCAP];    // queued pairs: dx, dy, dz, image v-shift
-    int4 qb[DPD_WARPS][DPD_QCAP];      // j, source lane, id_j, -
+    int4 qb[DPD_WARPS][DPD_QCAP];      // j, source row (lane), id_j, -
 };
 
-// Evaluate queue entry e (one lane each): F_ij into qf[e], -F_ij scattered to j.
 template <bool VIR>
-__device__ __forceinline__ void dpd_eval(const pair_args &a, dpd_smem &sm, int warp, int e, uint32_t nt,
-                                         uint32_t cs, vir6 &w)
+__device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int warp, int lane, bool valid,
+                                          uint32_t nt, uint32_t cs, vir6 &w)
 {
-    const float4 q = sm.qa[warp][e];
-    const int4 b = sm.qb[warp][e];
-    const float4 xi = sm.xi[warp][b.y];
-    const float4 vi = sm.vi[warp][b.y];
-    const float4 vj = a.v[b.x];
-    const float r2 = q.x * q.x + q.y * q.y + q.z * q.z;
-    const bool wall = tag_of(vi) == MD_TAG_WALL || tag_of(vj) == MD_TAG_WALL;
-    const float aij = wall ? a.a_wall : a.a_same;
-    const float inv_r = rsqrtf(r2);
-    const float wr = 1.0f - r2 * inv_r * a.inv_rc;
-    const float ex = q.x * inv_r, ey = q.y * inv_r, ez = q.z * inv_r;
-    const float edv = ex * (vi.x - vj.x - q.w) + ey * (vi.y - vj.y) + ez * (vi.z - vj.z);
-    const float zeta = pair_zeta(id_of(xi), (uint32_t)b.z, nt, cs, a.key);
-    const float fc = aij * wr;
-    const float fp = fc - a.gamma * wr * wr * edv + a.sig_isdt * wr * zeta;
-    const float px = fp * ex, py = fp * ey, pz = fp * ez;
-    sm.qf[warp][e] = make_float4(px, py, pz, 0.f);
-    scatter(a.f, b.x, -px, -py, -pz);
-    if (VIR) w.add(q.x, q.y, q.z, fc * inv_r);
-}
-
-// Row lane adds the forces of its own queue slots (bits of `mine`).
-__device__ __forceinline__ void dpd_collect(const dpd_smem &sm, int warp, uint32_t mine, float &fx, float &fy,
-                                            float &fz)
-{
-    while (mine) {
-        const int e = __ffs(mine) - 1;
-        mine &= mine - 1;
-        const float4 p = sm.qf[warp][e];
-        fx += p.x; fy += p.y; fz += p.z;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    int src = -1;
+    if (valid) {
+        const float4 q = sm.qa[warp][lane];
+        const int4 b = sm.qb[warp][lane];
+        src = b.y;
+        const float4 xi = sm.xi[warp][src];
+        const float4 vi = sm.vi[warp][src];
+        const float4 vj = a.v[b.x];
+        const float r2 = q.x * q.x + q.y * q.y + q.z * q.z;
+        const bool wall = tag_of(vi) == MD_TAG_WALL || tag_of(vj) == MD_TAG_WALL;
+        const float aij = wall ? a.a_wall : a.a_same;
+        const float inv_r = rsqrtf(r2);
+        const float wr = 1.0f - r2 * inv_r * a.inv_rc;
+        const float ex = q.x * inv_r, ey = q.y * inv_r, ez = q.z * inv_r;
+        const float edv = ex * (vi.x - vj.x - q.w) + ey * (vi.y - vj.y) + ez * (vi.z - vj.z);
+        const float zeta = pair_zeta(id_of(xi), (uint32_t)b.z, nt, cs, a.key);
+        const float fc = aij * wr;
+        const float fp = fc - a.gamma * wr * wr * edv + a.sig_isdt * wr * zeta;
+        px = fp * ex; py = fp * ey; pz = fp * ez;
+        scatter(a.f, b.x, -px, -py, -pz);
+        if (VIR) w.add(q.x, q.y, q.z, fc * inv_r);
+    }
+    // segmented sum over runs of equal src (entries are in row order)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float ox = __shfl_down_sync(0xffffffffu, px, o);
+        const float oy = __shfl_down_sync(0xffffffffu, py, o);
+        const float oz = __shfl_down_sync(0xffffffffu, pz, o);
+        const int os = __shfl_down_sync(0xffffffffu, src, o);
+        if (lane + o < 32 && os == src) { px += ox; py += oy; pz += oz; }
+    }
+    const int prev = __shfl_up_sync(0xffffffffu, src, 1);
+    if (valid && (lane == 0 || prev != src)) {     // head of a run holds its total
+        float4 t = sm.fi[warp][src];
+        t.x += px; t.y += py; t.z += pz;
+        sm.fi[warp][src] = t;
     }
 }
 
@@ -133,37 +143,48 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
     __shared__ dpd_smem sm;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r0 = r - lane;
     const bool active = r < a.rows;
     const int32_t i = active ? (a.row_idx ? a.row_idx[r] : (int32_t)r) : 0;
     const int cnt = active ? min(a.nc[r], a.cap) : 0;
     const float4 xi = active ? a.x32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     sm.xi[warp][lane] = xi;
     sm.vi[warp][lane] = active ? a.v[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    sm.fi[warp][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t nt = (uint32_t)a.ds->step, cs = (uint32_t)a.ds->sub;
     const float delta = a.ds->le_offset_f;
     const unsigned lt = (1u << lane) - 1u;
     vir6 w = {0, 0, 0, 0, 0, 0};
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    uint64_t mine = 0;                   // queue slots holding this row's pairs
-    const int kmax = __reduce_max_sync(0xffffffffu, cnt);
+    // exclusive prefix of the row lengths: row L owns flat entries [pre_L, pre_L + cnt_L)
+    int pre = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 31);
+    pre -= cnt;
     int qn = 0;
     __syncwarp();
-    // software pipeline: the index of candidate k+2 and the position of k+1
-    // are in flight while candidate k is tested
-    const int32_t *nlr = a.nl + r;
-    int32_t j1 = cnt > 0 ? nlr[0] : 0;
-    int32_t j2 = cnt > 1 ? nlr[a.rows] : 0;
-    float4 x1 = cnt > 0 ? a.x32[j1] : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int k = 0; k < kmax; ++k) {
-        const int32_t j = j1;
-        const float4 xj = x1;
-        j1 = j2;
-        if (k + 1 < cnt) x1 = a.x32[j1];
-        if (k + 2 < cnt) j2 = nlr[(int64_t)(k + 2) * a.rows];
+    for (int base = 0; base < total; base += 32) {
+        const int f = base + lane;
+        const bool valid = f < total;
+        // row of flat entry f: the last lane whose prefix is <= f
+        int row = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int p = __shfl_sync(0xffffffffu, pre, row + step);
+            if (p <= f) row += step;
+        }
+        const int k = f - __shfl_sync(0xffffffffu, pre, row);
         bool hit = false;
+        int32_t j = 0;
+        float4 xj = make_float4(0.f, 0.f, 0.f, 0.f);
         float dx = 0.f, dy = 0.f, dz = 0.f, vsh = 0.f;
-        if (k < cnt) {
-            min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
+        if (valid) {
+            j = a.nl[(r0 + row) * a.cap + k];
+            xj = a.x32[j];
+            min_image_f32(a.geom, delta, sm.xi[warp][row], xj, dx, dy, dz, vsh);
             const float r2 = dx * dx + dy * dy + dz * dz;
             hit = r2 < a.rc2 && r2 > 0.0f;
         }
@@ -171,16 +192,13 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
         if (hit) {
             const int pos = qn + __popc(m & lt);
             sm.qa[warp][pos] = make_float4(dx, dy, dz, vsh);
-            sm.qb[warp][pos] = make_int4(j, lane, (int)id_of(xj), 0);
-            mine |= 1ull << pos;
+            sm.qb[warp][pos] = make_int4(j, row, (int)id_of(xj), 0);
         }
         qn += __popc(m);
         __syncwarp();
         if (qn >= 32) {
-            dpd_eval<VIR>(a, sm, warp, lane, nt, cs, w);
+            dpd_batch<VIR>(a, sm, warp, lane, true, nt, cs, w);
             __syncwarp();
-            dpd_collect(sm, warp, (uint32_t)mine, fx, fy, fz);
-            mine >>= 32;
             if (lane < qn - 32) {
                 sm.qa[warp][lane] = sm.qa[warp][32 + lane];
                 sm.qb[warp][lane] = sm.qb[warp][32 + lane];
@@ -189,10 +207,12 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
             __syncwarp();
         }
     }
-    if (lane < qn) dpd_eval<VIR>(a, sm, warp, lane, nt, cs, w);
+    if (qn > 0) dpd_batch<VIR>(a, sm, warp, lane, lane < qn, nt, cs, w);
     __syncwarp();
-    dpd_collect(sm, warp, (uint32_t)mine, fx, fy, fz);
-    if (active && cnt > 0) scatter(a.f, i, fx, fy, fz);
+    if (active && cnt > 0) {
+        const float4 t = sm.fi[warp][lane];
+        scatter(a.f, i, t.x, t.y, t.z);
+    }
     if (VIR) flush_virial(a.vir, w);
 }
 
@@ -210,7 +230,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_lj(pair_args a)
             const float delta = a.ds->le_offset_f;
             float fx = 0.f, fy = 0.f, fz = 0.f;
             for (int k = 0; k < cnt; ++k) {
-                const int32_t j = a.nl[(int64_t)k * a.rows + r];
+                const int32_t j = a.nl[r * a.cap + k];
                 const float4 xj = a.x32[j];
                 float dx, dy, dz, vsh;
                 min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
@@ -245,7 +265,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_morse(pair_args a)
             const float delta = a.ds->le_offset_f;
             float fx = 0.f, fy = 0.f, fz = 0.f;
             for (int k = 0; k < cnt; ++k) {
-                const int32_t j = a.nl[(int64_t)k * a.rows + r];
+                const int32_t j = a.nl[r * a.cap + k];
                 const float4 xj = a.x32[j];
                 float dx, dy, dz, vsh;
                 min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);

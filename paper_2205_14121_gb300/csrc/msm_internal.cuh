@@ -86,7 +86,7 @@ struct md_system {
     int32_t *plt_idx, *plt_sorted, *plt_cell, *plt_slot;
     int32_t *rec_idx, *rec_sorted, *rec_cell, *rec_slot;
 
-    // lists (ELL, column-major: entry k of row r at k*rows + r)
+    // lists (row-major ELL: entry k of row r at r*cap + k)
     int32_t *nl[4], *nc[4];
 
     // bonds

@@ -10,9 +10,10 @@
 // comes first in the grid's cell-sorted order; a row therefore only scans
 // cells whose index is not below its own, half of the neighbourhood.
 //
-// Lists are ELL, column-major (entry k of row r at k*rows + r) so that the
-// force kernels, one thread per row, read them coalesced.  Row counts beyond
-// the capacity are recorded (overflow bit + longest row) and never written.
+// Lists are row-major ELL (entry k of row r at r*cap + k): a row's entries
+// are contiguous, so a warp that streams the concatenated rows of 32
+// consecutive particles reads them nearly coalesced.  Row counts beyond the
+// capacity are recorded (overflow bit + longest row) and never written.
 //
 //   MD_LIST_FLUID  rows: every particle (cell-sorted); later plasma/wall
 //                  partners, plasma-plasma and plasma-wall pairs (Eq. 1)
@@ -41,6 +42,18 @@ __device__ __forceinline__ int cell_index32(const md_grid &g, int cx, int cy, in
     return (cz * g.nc[1] + cy) * g.nc[0] + cx;
 }
 
+// Cells [lo, hi] within reach R of coordinate x along one axis, clamped to
+// [-2, n+1] and to at most n cells, so that a non-finite or escaped position
+// (reported by the integrator's unstable flag) still gives a bounded scan.
+__device__ __forceinline__ void cell_span(float x, float lo0, float R, float inv_h, int n, int &lo, int &hi)
+{
+    lo = __float2int_rd((x - lo0 - R) * inv_h);
+    hi = __float2int_rd((x - lo0 + R) * inv_h);
+    lo = min(max(lo, -2), n + 1);
+    hi = min(max(hi, -2), n + 1);
+    if (hi - lo + 1 > n) hi = lo + n - 1;
+}
+
 // Visit (member position s, particle index) of every member of the cells
 // within reach R of xi; Lees-Edwards rows that cross the y boundary are
 // shifted by the image offset.  half: skip cells with a lower index than
@@ -50,16 +63,12 @@ __device__ __forceinline__ void for_candidates(const md_grid &g, const md_geom &
                                                float R, const int32_t *__restrict__ members, int32_t r, F fn)
 {
     const int own = cell_index32(g, cell_coord(g, 0, xi.x), cell_coord(g, 1, xi.y), cell_coord(g, 2, xi.z));
-    int zlo = __float2int_rd((xi.z - g.lo[2] - R) * g.inv_h[2]);
-    int zhi = __float2int_rd((xi.z - g.lo[2] + R) * g.inv_h[2]);
-    if (zhi - zlo + 1 > g.nc[2]) zhi = zlo + g.nc[2] - 1;
-    int ylo = __float2int_rd((xi.y - g.lo[1] - R) * g.inv_h[1]);
-    int yhi = __float2int_rd((xi.y - g.lo[1] + R) * g.inv_h[1]);
+    int zlo, zhi, ylo, yhi;
+    cell_span(xi.z, g.lo[2], R, g.inv_h[2], g.nc[2], zlo, zhi);
+    cell_span(xi.y, g.lo[1], R, g.inv_h[1], g.nc[1], ylo, yhi);
     if (geom.walls) {
         ylo = max(ylo, 0);
         yhi = min(yhi, g.nc[1] - 1);
-    } else if (yhi - ylo + 1 > g.nc[1]) {
-        yhi = ylo + g.nc[1] - 1;
     }
     for (int cz = zlo; cz <= zhi; ++cz) {
         const int wz = wrapc(cz, g.nc[2]);
@@ -77,9 +86,8 @@ __device__ __forceinline__ void for_candidates(const md_grid &g, const md_geom &
             }
             const int rowc = cell_index32(g, 0, wy, wz);
             if (HALF && rowc + g.nc[0] - 1 < own) continue;   // whole row below own cell
-            int xlo = __float2int_rd((xi.x + sx - g.lo[0] - R) * g.inv_h[0]);
-            int xhi = __float2int_rd((xi.x + sx - g.lo[0] + R) * g.inv_h[0]);
-            if (xhi - xlo + 1 > g.nc[0]) xhi = xlo + g.nc[0] - 1;
+            int xlo, xhi;
+            cell_span(xi.x + sx, g.lo[0], R, g.inv_h[0], g.nc[0], xlo, xhi);
             for (int cx = xlo; cx <= xhi; ++cx) {
                 const int c = rowc + wrapc(cx, g.nc[0]);
                 if (HALF && c < own) continue;
@@ -149,7 +157,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_build(build_args a, const int32_t *
                         if (r2_f32(ex, ey, ez) < a.excl2) return;
                     }
                 }
-                if (cnt < a.cap) a.nl[(int64_t)cnt * rows + r] = j;
+                if (cnt < a.cap) a.nl[r * a.cap + cnt] = j;
                 ++cnt;
             });
         }
@@ -248,7 +256,7 @@ __global__ void __launch_bounds__(BC_WARPS * 32) k_build_fluid_cells(build_args 
                     const unsigned m = __ballot_sync(0xffffffffu, hit);
                     if (hit) {
                         const int k = cnt + __popc(m & lt);
-                        if (k < a.cap) a.nl[(int64_t)k * rows + i] = j;
+                        if (k < a.cap) a.nl[(int64_t)i * a.cap + k] = j;
                     }
                     cnt += __popc(m);
                 }
