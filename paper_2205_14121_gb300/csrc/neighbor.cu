@@ -171,153 +171,6 @@ __global__ void __launch_bounds__(MSM_TPB) k_build(build_args a, const int32_t *
     }
 }
 
-// ---------------------------------------------------------------------------
-// Plasma list, one warp per home cell.  The warp stages the positions of the
-// home cell and of its neighbour cells with a higher index (the forward half
-// of the stencil) in shared memory, then walks its home particles one at a
-// time: the 32 lanes test 32 staged candidates at once and the hits are
-// compacted into the row with a warp ballot.
-// ---------------------------------------------------------------------------
-constexpr int BC_WARPS = 4;
-constexpr int BC_CAND = 256;
-constexpr int BC_HOME = 64;
-
-struct bc_smem {
-    float4 cx[BC_WARPS][BC_CAND];
-    int32_t cj[BC_WARPS][BC_CAND];
-    int32_t cnt[BC_WARPS][BC_HOME];
-};
-
-// Distinct periodic neighbours of coordinate c along an edge of n cells.
-__device__ __forceinline__ int stencil_axis(int c, int n, bool periodic, int out[3])
-{
-    if (!periodic) {
-        int m = 0;
-        for (int d = -1; d <= 1; ++d)
-            if (c + d >= 0 && c + d < n) out[m++] = c + d;
-        return m;
-    }
-    if (n >= 3) {
-        out[0] = c == 0 ? n - 1 : c - 1;
-        out[1] = c;
-        out[2] = c == n - 1 ? 0 : c + 1;
-        return 3;
-    }
-    for (int d = 0; d < n; ++d) out[d] = d;
-    return n;
-}
-
-__global__ void __launch_bounds__(BC_WARPS * 32) k_build_fluid_cells(build_args a, const int32_t *gate)
-{
-    if (gate_closed(gate)) return;
-    __shared__ bc_smem sm;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const md_grid &g = a.g;
-    const int c = blockIdx.x * BC_WARPS + warp;
-    if (c >= g.ncell) return;                     // warp-uniform; no block barrier is used
-    const int hb = g.start[c], he = g.start[c + 1];
-    if (hb == he) return;
-    const unsigned lt = (1u << lane) - 1u;
-    const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
-    const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
-    const float delta = a.ds->le_offset_f;
-    const int64_t rows = a.rows;
-    int zs[3], ys[3], xs3[3];
-    const int nzs = stencil_axis(cz, nz, true, zs);
-    const int nys = stencil_axis(cy, ny, !a.geom.walls, ys);
-    const int nxs = stencil_axis(cx, nx, true, xs3);
-
-    for (int h0 = hb; h0 < he; h0 += BC_HOME) {
-        const int h1 = min(he, h0 + BC_HOME);
-        for (int t = lane; t < h1 - h0; t += 32) sm.cnt[warp][t] = 0;
-        __syncwarp();
-        int nst = 0;
-        auto process = [&]() {
-            __syncwarp();
-            for (int i = h0; i < h1; ++i) {
-                const float4 xi = a.x32[i];
-                const int ci = class_of(xi);
-                if (ci == CLS_PLT) continue;
-                int cnt = sm.cnt[warp][i - h0];
-                for (int t0 = 0; t0 < nst; t0 += 32) {
-                    const int t = t0 + lane;
-                    bool hit = false;
-                    int32_t j = 0;
-                    if (t < nst) {
-                        j = sm.cj[warp][t];
-                        const float4 xj = sm.cx[warp][t];
-                        const int cj = class_of(xj);
-                        if (j > i && cj != CLS_PLT && !(ci == CLS_WALL && cj == CLS_WALL)) {
-                            float dx, dy, dz, vs;
-                            min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vs);
-                            hit = r2_f32(dx, dy, dz) < a.cut2;
-                        }
-                    }
-                    const unsigned m = __ballot_sync(0xffffffffu, hit);
-                    if (hit) {
-                        const int k = cnt + __popc(m & lt);
-                        if (k < a.cap) a.nl[(int64_t)i * a.cap + k] = j;
-                    }
-                    cnt += __popc(m);
-                }
-                if (lane == 0) sm.cnt[warp][i - h0] = cnt;
-                __syncwarp();
-            }
-            nst = 0;
-        };
-        auto stage = [&](int cc) {
-            const int cb = g.start[cc], ce = g.start[cc + 1];
-            for (int p = cb; p < ce;) {
-                const int room = BC_CAND - nst;
-                if (room == 0) { process(); continue; }
-                const int m = min(ce - p, room);
-                __syncwarp();
-                for (int t = lane; t < m; t += 32) {
-                    sm.cx[warp][nst + t] = a.x32[p + t];
-                    sm.cj[warp][nst + t] = p + t;
-                }
-                nst += m;
-                p += m;
-            }
-        };
-        for (int iz = 0; iz < nzs; ++iz) {
-            for (int iy = 0; iy < nys; ++iy) {
-                const int wy = ys[iy];
-                const int rowc = (zs[iz] * ny + wy) * nx;
-                const bool crossing = a.geom.le && ((cy == 0 && wy == ny - 1 && ny > 1) ||
-                                                    (cy == ny - 1 && wy == 0 && ny > 1));
-                if (!crossing) {
-                    for (int ix = 0; ix < nxs; ++ix) {
-                        const int cc = rowc + xs3[ix];
-                        if (cc >= c) stage(cc);
-                    }
-                } else {
-                    // images across the Lees-Edwards boundary sit delta away in x
-                    const float sx = (cy == ny - 1) ? -delta : delta;
-                    const float x0 = g.lo[0] + cx * g.h[0];
-                    int xlo = __float2int_rd((x0 + sx - g.lo[0] - a.R) * g.inv_h[0]);
-                    int xhi = __float2int_rd((x0 + g.h[0] + sx - g.lo[0] + a.R) * g.inv_h[0]);
-                    if (xhi - xlo + 1 > nx) xhi = xlo + nx - 1;
-                    for (int xx = xlo; xx <= xhi; ++xx) {
-                        const int cc = rowc + wrapc(xx, nx);
-                        if (cc >= c) stage(cc);
-                    }
-                }
-            }
-        }
-        process();
-        for (int t = lane; t < h1 - h0; t += 32) a.nc[h0 + t] = sm.cnt[warp][t];
-        int mx = 0;
-        for (int t = lane; t < h1 - h0; t += 32) mx = max(mx, sm.cnt[warp][t]);
-        mx = __reduce_max_sync(0xffffffffu, mx);
-        if (lane == 0 && mx > 0) {
-            atomicMax(&a.ctl[CTL_MAXROW + MD_LIST_FLUID], mx);
-            if (mx > a.cap) atomicOr(&a.ctl[CTL_OVERFLOW], 1 << MD_LIST_FLUID);
-        }
-        __syncwarp();
-    }
-}
-
 inline unsigned blocks_for(int64_t n) { return (unsigned)(n > 0 ? (n + MSM_TPB - 1) / MSM_TPB : 1); }
 
 }  // namespace
@@ -345,7 +198,7 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
     a.nl = s->nl[MD_LIST_FLUID];
     a.nc = s->nc[MD_LIST_FLUID];
     a.cap = s->cap[MD_LIST_FLUID];
-    k_build_fluid_cells<<<(unsigned)((a.g.ncell + BC_WARPS - 1) / BC_WARPS), BC_WARPS * 32, 0, s->stream>>>(a, gate);
+    k_build<MD_LIST_FLUID><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
 
     if (s->n_plt > 0) {
         // interface: platelet rows (platelet sub-grid order) against the main grid
