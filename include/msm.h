@@ -230,6 +230,29 @@ typedef struct md_observables_t {
 int md_observables(md_system *sys, md_observables_t *out);
 
 /*
+ * Per-platelet measurements of the current state (the time series the
+ * controller reads, Sec. 3.3 / Table 1 "compute and dump platelet physical
+ * properties"), reduced in FP64 on the device, written to HOST
+ * out[n_platelets][12]:
+ *   0-2 centre-of-mass velocity; 3-5 angular velocity I^-1 L about the
+ *   centre of mass; 6-8 principal values (ascending) of the force-moment
+ *   stress -1/2 sum (r F^T + F r^T); 9 largest bond strain |r - r0|/r0;
+ *   10 receptor contacts with other platelets closer than 1.5 morse_r0;
+ *   11 mean speed of the plasma within 2 of the centre of mass.
+ * Errors: MD_EINVAL (no platelets), MD_ECUDA.
+ */
+int md_platelet_features(md_system *sys, double *out);
+
+/*
+ * Append the current measurements to the device ring of the last 128
+ * records per platelet (no host copy), and read that ring back: HOST
+ * out[n_platelets][128][12], oldest retained record first; *count gets the
+ * number of records appended so far (records beyond 128 overwrite the oldest).
+ */
+int md_record_features(md_system *sys);
+int md_read_feature_ring(md_system *sys, float *out, int64_t *count);
+
+/*
  * Neighbour pairs of list kind `kind` as particle ids (a < b), written to
  * HOST pairs[2*cap]; *count gets the total.  For parity checks of K2.
  * Synchronises the stream.

@@ -126,6 +126,11 @@ def lib():
     L.md_profile_enable.argtypes = [vp, C.c_int]
     L.md_profile_read.argtypes = [vp, C.POINTER(md_profile_t), C.c_int]
     L.md_philox.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), i64, C.POINTER(C.c_uint32), C.c_int]
+    L.md_platelet_features.argtypes = [vp, dp]
+    L.md_record_features.argtypes = [vp]
+    L.md_read_feature_ring.argtypes = [vp, fp, C.POINTER(C.c_int64)]
+    for name in ("md_platelet_features", "md_record_features", "md_read_feature_ring"):
+        getattr(L, name).restype = C.c_int
     for name in ("md_config_defaults", "md_workspace_size", "md_init", "md_set_particles", "md_set_bonds",
                  "md_neighbor_build", "md_forces", "md_read_forces", "md_read_particles", "md_mts_step",
                  "md_observables", "md_neighbor_pairs", "md_get_state", "md_set_state", "md_profile_enable",
@@ -308,6 +313,29 @@ class System:
         self._check(lib().md_set_state(self.h, buf, len(blob)), "md_set_state")
 
     md_set_state = set_state
+
+    def platelet_features(self):
+        P = self.cfg.n_platelets
+        out = np.zeros((P, 12))
+        self._check(lib().md_platelet_features(self.h, _dp(out)), "md_platelet_features")
+        return out
+
+    md_platelet_features = platelet_features
+
+    def record_features(self):
+        self._check(lib().md_record_features(self.h), "md_record_features")
+
+    md_record_features = record_features
+
+    def read_feature_ring(self):
+        P = self.cfg.n_platelets
+        out = np.zeros((P, 128, 12), np.float32)
+        cnt = C.c_int64()
+        self._check(lib().md_read_feature_ring(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), C.byref(cnt)),
+                    "md_read_feature_ring")
+        return out[:, :min(cnt.value, 128)], cnt.value
+
+    md_read_feature_ring = read_feature_ring
 
     def profile_enable(self, on=True):
         self._check(lib().md_profile_enable(self.h, int(on)), "md_profile_enable")

@@ -152,6 +152,15 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
         s.bond_ij = cv.take<int32_t>(2 * s.nb);
         s.bond_r0 = cv.take<float>(s.nb);
     }
+    if (plt) {
+        const int64_t P = c.n_platelets > 0 ? c.n_platelets : 1;
+        s.plt_off = cv.take<int32_t>(P + 1);
+        s.plt_ids = cv.take<int32_t>(s.n_plt);
+        s.bond_off = cv.take<int32_t>(P + 1);
+        s.plt_contacts = cv.take<int32_t>(P);
+        s.feat = cv.take<double>(12 * P);
+        s.ring = cv.take<float>(P * (int64_t)s.ring_T * 12);
+    }
     s.red_blocks = (int)((n + MSM_TPB - 1) / MSM_TPB);
     if (s.red_blocks > RED_BLOCKS_MAX) s.red_blocks = RED_BLOCKS_MAX;
     s.red_part = cv.take<double>((int64_t)s.red_blocks * RED_WORDS);
@@ -706,7 +715,33 @@ int md_set_particles(md_system *s, const double *x, const double *v, const int32
     }
     if (np != s->n_plt || nr != s->n_rec)
         return set_error(s, MD_EINVAL, "md_set_particles: platelet/receptor counts differ from the configuration");
+    if (npl > (s->n_plt > 0 ? s->cfg.n_platelets : 0))
+        return set_error(s, MD_EINVAL, "md_set_particles: platelet id beyond cfg.n_platelets");
     cudaStream_t st = s->stream;
+    s->h_tag.assign(tag, tag + n);
+    if (s->n_plt > 0) {
+        // member lists per platelet (ids ascending)
+        const int P = s->cfg.n_platelets;
+        std::vector<int32_t> off((size_t)P + 1, 0), ids((size_t)s->n_plt);
+        for (int64_t k = 0; k < n; ++k)
+            if (tag[k] >= 0) off[(size_t)(tag[k] & ~MD_RECEPTOR_BIT) + 1]++;
+        for (int p = 0; p < P; ++p) off[(size_t)p + 1] += off[(size_t)p];
+        std::vector<int32_t> fill(off.begin(), off.end() - 1);
+        for (int64_t k = 0; k < n; ++k)
+            if (tag[k] >= 0) ids[(size_t)fill[(size_t)(tag[k] & ~MD_RECEPTOR_BIT)]++] = (int32_t)k;
+        for (int p = 0; p < P; ++p)
+            if (off[(size_t)p + 1] == off[(size_t)p])
+                return set_error(s, MD_EINVAL, "md_set_particles: a platelet id has no particles");
+        CK(cudaMemcpyAsync(s->plt_off, off.data(), sizeof(int32_t) * (P + 1), cudaMemcpyHostToDevice, st), "plt off");
+        CK(cudaMemcpyAsync(s->plt_ids, ids.data(), sizeof(int32_t) * s->n_plt, cudaMemcpyHostToDevice, st), "ids");
+        CK(cudaStreamSynchronize(st), "sync");
+        if (s->nb == 0) {
+            std::vector<int32_t> z((size_t)P + 1, 0);
+            CK(cudaMemcpyAsync(s->bond_off, z.data(), sizeof(int32_t) * (P + 1), cudaMemcpyHostToDevice, st), "bo");
+            CK(cudaStreamSynchronize(st), "sync");
+        }
+        s->ring_count = 0;
+    }
     CK(cudaMemcpyAsync(s->alt64, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload x");
     k_import_x<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->alt64, s->xs, s->ys, s->zs, s->x32, s->xb);
     CK(cudaGetLastError(), "import x");
@@ -749,14 +784,35 @@ int md_set_bonds(md_system *s, const int32_t *ij, const double *r0, int64_t nb)
     if (nb != s->nb) return set_error(s, MD_EINVAL, "md_set_bonds: count differs from the configuration");
     if (nb == 0) return MD_OK;
     if (!ij || !r0) return set_error(s, MD_EINVAL, "md_set_bonds: null argument");
-    std::vector<float> r0f((size_t)nb);
+    if ((int64_t)s->h_tag.size() != s->n) return set_error(s, MD_EINVAL, "md_set_bonds: set particles first");
+    const int P = s->cfg.n_platelets;
+    std::vector<int32_t> off((size_t)(P > 0 ? P : 0) + 1, 0);
     for (int64_t b = 0; b < nb; ++b) {
-        if (ij[2 * b] < 0 || ij[2 * b] >= s->n || ij[2 * b + 1] < 0 || ij[2 * b + 1] >= s->n)
+        const int32_t i = ij[2 * b], j = ij[2 * b + 1];
+        if (i < 0 || i >= s->n || j < 0 || j >= s->n)
             return set_error(s, MD_EINVAL, "md_set_bonds: particle id out of range");
-        r0f[(size_t)b] = (float)r0[b];
+        const int32_t ti = s->h_tag[(size_t)i], tj = s->h_tag[(size_t)j];
+        if (ti < 0 || tj < 0 || (ti & ~MD_RECEPTOR_BIT) != (tj & ~MD_RECEPTOR_BIT))
+            return set_error(s, MD_EINVAL, "md_set_bonds: a bond must join two particles of one platelet");
+        off[(size_t)(ti & ~MD_RECEPTOR_BIT) + 1]++;
     }
-    CK(cudaMemcpyAsync(s->bond_id, ij, sizeof(int32_t) * 2 * nb, cudaMemcpyHostToDevice, s->stream), "upload bonds");
+    for (int p = 0; p < P; ++p) off[(size_t)p + 1] += off[(size_t)p];
+    // store the bonds grouped by platelet (the bond kernel is order-independent)
+    std::vector<int32_t> ijs((size_t)(2 * nb));
+    std::vector<float> r0f((size_t)nb);
+    std::vector<int32_t> fill(off.begin(), off.end() - 1);
+    for (int64_t b = 0; b < nb; ++b) {
+        const int32_t p = s->h_tag[(size_t)ij[2 * b]] & ~MD_RECEPTOR_BIT;
+        const int32_t q = fill[(size_t)p]++;
+        ijs[(size_t)(2 * q)] = ij[2 * b];
+        ijs[(size_t)(2 * q + 1)] = ij[2 * b + 1];
+        r0f[(size_t)q] = (float)r0[b];
+    }
+    CK(cudaMemcpyAsync(s->bond_id, ijs.data(), sizeof(int32_t) * 2 * nb, cudaMemcpyHostToDevice, s->stream),
+       "upload bonds");
     CK(cudaMemcpyAsync(s->bond_r0, r0f.data(), sizeof(float) * nb, cudaMemcpyHostToDevice, s->stream), "upload r0");
+    CK(cudaMemcpyAsync(s->bond_off, off.data(), sizeof(int32_t) * (P + 1), cudaMemcpyHostToDevice, s->stream),
+       "upload bond offsets");
     CK(cudaStreamSynchronize(s->stream), "set_bonds sync");
     s->have_bonds = true;
     s->lists_stale = true;   // the remap of bond ends happens in the rebuild
@@ -913,6 +969,51 @@ int md_observables(md_system *s, md_observables_t *o)
     o->pressure = (kt[0] + kt[4] + kt[8] + vir[0] + vir[4] + vir[8]) / (3.0 * V);
     o->n_builds = s->h_ds->n_builds;
     for (int k = 0; k < 4; ++k) o->max_rows[k] = s->h_ctl[CTL_MAXROW + k];
+    return MD_OK;
+}
+
+int md_platelet_features(md_system *s, double *out)
+{
+    if (!s || !out) return MD_EINVAL;
+    if (s->n_plt == 0) return set_error(s, MD_EINVAL, "md_platelet_features: no platelets");
+    int rc = ensure_forces(s);
+    if (rc) return rc;
+    CK(launch_features(s, s->feat), "features");
+    CK(cudaMemcpyAsync(out, s->feat, sizeof(double) * 12 * s->cfg.n_platelets, cudaMemcpyDeviceToHost, s->stream),
+       "download features");
+    CK(cudaStreamSynchronize(s->stream), "sync");
+    return MD_OK;
+}
+
+int md_record_features(md_system *s)
+{
+    if (!s) return MD_EINVAL;
+    if (s->n_plt == 0) return set_error(s, MD_EINVAL, "md_record_features: no platelets");
+    int rc = ensure_forces(s);
+    if (rc) return rc;
+    CK(launch_features(s, s->feat), "features");
+    CK(launch_feature_ring(s, s->feat, (int)(s->ring_count % s->ring_T)), "feature ring");
+    s->ring_count += 1;
+    return MD_OK;
+}
+
+int md_read_feature_ring(md_system *s, float *out, int64_t *count)
+{
+    if (!s || !out || !count) return MD_EINVAL;
+    if (s->n_plt == 0) return set_error(s, MD_EINVAL, "md_read_feature_ring: no platelets");
+    const int P = s->cfg.n_platelets, T = s->ring_T;
+    std::vector<float> raw((size_t)P * T * 12);
+    CK(cudaMemcpyAsync(raw.data(), s->ring, sizeof(float) * raw.size(), cudaMemcpyDeviceToHost, s->stream), "ring");
+    CK(cudaStreamSynchronize(s->stream), "sync");
+    // chronological order: the oldest retained record first
+    const int64_t n = s->ring_count < T ? s->ring_count : T;
+    const int64_t first = s->ring_count - n;
+    for (int p = 0; p < P; ++p)
+        for (int64_t t = 0; t < n; ++t) {
+            const int64_t slot = (first + t) % T;
+            memcpy(out + ((int64_t)p * T + t) * 12, raw.data() + ((int64_t)p * T + slot) * 12, 12 * sizeof(float));
+        }
+    *count = s->ring_count;
     return MD_OK;
 }
 

@@ -1,0 +1,292 @@
+// K8: per-platelet measurements (Sec. 3.3: angular velocity, kinetic state,
+// flow speed at the centre of mass) reduced in FP64, one block per platelet:
+//
+//  0-2  centre-of-mass velocity V
+//  3-5  angular velocity w = I^-1 L (L, I about the centre of mass)
+//  6-8  principal values (ascending) of S = -1/2 sum_i (r_i F_i^T + F_i r_i^T)
+//  9    largest bond strain |r - r0| / r0
+//  10   receptor contacts with other platelets closer than 1.5 r0 (Morse r0)
+//  11   mean speed of the plasma within 2 of the centre of mass
+//
+// Positions enter through their FP32 copies (minimum image about the first
+// member), velocities and forces as stored; every sum is FP64.
+#include "msm_internal.cuh"
+
+namespace {
+
+constexpr int FT_TPB = 256;
+
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int k = 0; k < FT_TPB / 32; ++k) s += sh[k];
+    return s;
+}
+
+__device__ __forceinline__ double block_max(double v, double *sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = sh[0];
+    for (int k = 1; k < FT_TPB / 32; ++k) s = fmax(s, sh[k]);
+    return s;
+}
+
+__device__ __forceinline__ double dimg(double d, double L, bool periodic)
+{
+    return periodic ? d - L * nearbyint(d / L) : d;
+}
+
+// Eigenvalues of a symmetric 3x3 matrix (trigonometric closed form, Smith 1961), ascending.
+__device__ void sym3_eigvals(const double a[6], double out[3])
+{
+    // a: xx, yy, zz, xy, xz, yz
+    const double p1 = a[3] * a[3] + a[4] * a[4] + a[5] * a[5];
+    const double q = (a[0] + a[1] + a[2]) / 3.0;
+    if (p1 <= 1e-300 * (1.0 + q * q)) {
+        double e[3] = {a[0], a[1], a[2]};
+        for (int i = 0; i < 3; ++i)
+            for (int j = i + 1; j < 3; ++j)
+                if (e[j] < e[i]) { const double t = e[i]; e[i] = e[j]; e[j] = t; }
+        out[0] = e[0]; out[1] = e[1]; out[2] = e[2];
+        return;
+    }
+    const double p2 = (a[0] - q) * (a[0] - q) + (a[1] - q) * (a[1] - q) + (a[2] - q) * (a[2] - q) + 2.0 * p1;
+    const double p = sqrt(p2 / 6.0);
+    const double b0 = (a[0] - q) / p, b1 = (a[1] - q) / p, b2 = (a[2] - q) / p;
+    const double b3 = a[3] / p, b4 = a[4] / p, b5 = a[5] / p;
+    const double detb = b0 * (b1 * b2 - b5 * b5) - b3 * (b3 * b2 - b5 * b4) + b4 * (b3 * b5 - b1 * b4);
+    double rr = detb / 2.0;
+    rr = rr <= -1.0 ? -1.0 : (rr >= 1.0 ? 1.0 : rr);
+    const double phi = acos(rr) / 3.0;
+    const double e1 = q + 2.0 * p * cos(phi);
+    const double e3 = q + 2.0 * p * cos(phi + 2.0943951023931954923);
+    const double e2 = 3.0 * q - e1 - e3;
+    out[0] = e3; out[1] = e2; out[2] = e1;
+}
+
+struct feat_args {
+    int P;
+    const int32_t *plt_off, *plt_ids;      // members of platelet p: ids plt_ids[plt_off[p] .. plt_off[p+1])
+    const int32_t *bond_off;               // bonds of platelet p: [bond_off[p], bond_off[p+1]) (platelet order)
+    const int32_t *bond_ij;
+    const float *bond_r0;
+    const int32_t *pos_of_id;
+    const float4 *x32, *v, *f0, *f1, *f2;
+    const int32_t *tag;
+    const int32_t *contacts;               // per platelet, from k_contacts
+    md_grid g;
+    md_geom geom;
+    double L[3];
+    float g_body;
+    double flow_r2, skin;
+    double *out;                           // [P][12]
+};
+
+__global__ void __launch_bounds__(FT_TPB) k_features(feat_args a)
+{
+    __shared__ double sh[FT_TPB / 32];
+    __shared__ double res[32];
+    const int p = blockIdx.x;
+    if (p >= a.P) return;
+    const int b = a.plt_off[p], e = a.plt_off[p + 1];
+    const int nm = e - b;
+    const bool py = !a.geom.walls;
+    const float4 ref = a.x32[a.pos_of_id[a.plt_ids[b]]];
+    // pass 1: mean offset from the reference member, mean velocity
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int m = b + threadIdx.x; m < e; m += FT_TPB) {
+        const int k = a.pos_of_id[a.plt_ids[m]];
+        const float4 xk = a.x32[k];
+        const float4 vk = a.v[k];
+        s[0] += dimg((double)xk.x - ref.x, a.L[0], true);
+        s[1] += dimg((double)xk.y - ref.y, a.L[1], py);
+        s[2] += dimg((double)xk.z - ref.z, a.L[2], true);
+        s[3] += vk.x; s[4] += vk.y; s[5] += vk.z;
+    }
+    double mean[6];
+    for (int q = 0; q < 6; ++q) mean[q] = block_sum(s[q], sh) / nm;
+    // pass 2: angular momentum, inertia, force moment about the centre of mass
+    double t[15];
+    for (int q = 0; q < 15; ++q) t[q] = 0.0;
+    double smax = 0.0;
+    for (int m = b + threadIdx.x; m < e; m += FT_TPB) {
+        const int k = a.pos_of_id[a.plt_ids[m]];
+        const float4 xk = a.x32[k];
+        const float4 vk = a.v[k];
+        const double rx = dimg((double)xk.x - ref.x, a.L[0], true) - mean[0];
+        const double ry = dimg((double)xk.y - ref.y, a.L[1], py) - mean[1];
+        const double rz = dimg((double)xk.z - ref.z, a.L[2], true) - mean[2];
+        const double ux = vk.x - mean[3], uy = vk.y - mean[4], uz = vk.z - mean[5];
+        double fx = 0, fy = 0, fz = 0;
+        if (a.f0) { const float4 q = a.f0[k]; fx += q.x; fy += q.y; fz += q.z; if (a.tag[k] != MD_TAG_WALL) fx += a.g_body; }
+        if (a.f1) { const float4 q = a.f1[k]; fx += q.x; fy += q.y; fz += q.z; }
+        if (a.f2) { const float4 q = a.f2[k]; fx += q.x; fy += q.y; fz += q.z; }
+        t[0] += ry * uz - rz * uy; t[1] += rz * ux - rx * uz; t[2] += rx * uy - ry * ux;   // L
+        const double r2 = rx * rx + ry * ry + rz * rz;
+        t[3] += r2 - rx * rx; t[4] += r2 - ry * ry; t[5] += r2 - rz * rz;                  // I diag
+        t[6] -= rx * ry; t[7] -= rx * rz; t[8] -= ry * rz;                                  // I off-diag
+        t[9] -= rx * fx; t[10] -= ry * fy; t[11] -= rz * fz;                                // S diag
+        t[12] -= 0.5 * (rx * fy + fx * ry); t[13] -= 0.5 * (rx * fz + fx * rz); t[14] -= 0.5 * (ry * fz + fy * rz);
+    }
+    for (int bb = a.bond_off[p] + threadIdx.x; bb < a.bond_off[p + 1]; bb += FT_TPB) {
+        const float4 xi = a.x32[a.bond_ij[2 * bb]], xj = a.x32[a.bond_ij[2 * bb + 1]];
+        const double dx = dimg((double)xi.x - xj.x, a.L[0], true);
+        const double dy = dimg((double)xi.y - xj.y, a.L[1], py);
+        const double dz = dimg((double)xi.z - xj.z, a.L[2], true);
+        const double r0 = a.bond_r0[bb];
+        smax = fmax(smax, fabs(sqrt(dx * dx + dy * dy + dz * dz) - r0) / r0);
+    }
+    double tot[15];
+    for (int q = 0; q < 15; ++q) tot[q] = block_sum(t[q], sh);
+    smax = block_max(smax, sh);
+    // plasma speed near the centre of mass (cells within reach of it)
+    const double cx = ref.x + mean[0], cy = ref.y + mean[1], cz = ref.z + mean[2];
+    const md_grid &g = a.g;
+    // cells are those of the last list build: particles have moved by < skin/2 since
+    const double rr = sqrt(a.flow_r2) + a.skin;
+    const int reach[3] = {(int)ceil(rr / g.h[0]), (int)ceil(rr / g.h[1]), (int)ceil(rr / g.h[2])};
+    const int c0[3] = {(int)floor((cx - g.lo[0]) / g.h[0]), (int)floor((cy - g.lo[1]) / g.h[1]),
+                       (int)floor((cz - g.lo[2]) / g.h[2])};
+    const int span[3] = {min(2 * reach[0] + 1, g.nc[0]), min(2 * reach[1] + 1, g.nc[1]), min(2 * reach[2] + 1, g.nc[2])};
+    const int ncand = span[0] * span[1] * span[2];
+    double fs = 0.0, fn = 0.0;
+    for (int q = threadIdx.x; q < ncand; q += FT_TPB) {
+        const int ox = q % span[0], oy = (q / span[0]) % span[1], oz = q / (span[0] * span[1]);
+        int ix = c0[0] - reach[0] + ox, iy = c0[1] - reach[1] + oy, iz = c0[2] - reach[2] + oz;
+        ix = ((ix % g.nc[0]) + g.nc[0]) % g.nc[0];
+        iz = ((iz % g.nc[2]) + g.nc[2]) % g.nc[2];
+        if (py) iy = ((iy % g.nc[1]) + g.nc[1]) % g.nc[1];
+        else if (iy < 0 || iy >= g.nc[1]) continue;
+        const int64_t c = ((int64_t)iz * g.nc[1] + iy) * g.nc[0] + ix;
+        for (int32_t k = g.start[c]; k < g.start[c + 1]; ++k) {
+            const float4 xk = a.x32[k];
+            if (class_of(xk) != CLS_FLUID) continue;
+            const double dx = dimg((double)xk.x - cx, a.L[0], true);
+            const double dy = dimg((double)xk.y - cy, a.L[1], py);
+            const double dz = dimg((double)xk.z - cz, a.L[2], true);
+            if (dx * dx + dy * dy + dz * dz < a.flow_r2) {
+                const float4 vk = a.v[k];
+                fs += sqrt((double)vk.x * vk.x + (double)vk.y * vk.y + (double)vk.z * vk.z);
+                fn += 1.0;
+            }
+        }
+    }
+    fs = block_sum(fs, sh);
+    fn = block_sum(fn, sh);
+    if (threadIdx.x == 0) {
+        double *o = a.out + 12 * (int64_t)p;
+        o[0] = mean[3]; o[1] = mean[4]; o[2] = mean[5];
+        // w = I^-1 L by Cramer's rule
+        const double I00 = tot[3], I11 = tot[4], I22 = tot[5], I01 = tot[6], I02 = tot[7], I12 = tot[8];
+        const double c00 = I11 * I22 - I12 * I12, c01 = I02 * I12 - I01 * I22, c02 = I01 * I12 - I02 * I11;
+        const double c11 = I00 * I22 - I02 * I02, c12 = I01 * I02 - I00 * I12, c22 = I00 * I11 - I01 * I01;
+        const double det = I00 * c00 + I01 * c01 + I02 * c02;
+        const double Lx = tot[0], Ly = tot[1], Lz = tot[2];
+        if (det != 0.0) {
+            o[3] = (c00 * Lx + c01 * Ly + c02 * Lz) / det;
+            o[4] = (c01 * Lx + c11 * Ly + c12 * Lz) / det;
+            o[5] = (c02 * Lx + c12 * Ly + c22 * Lz) / det;
+        } else {
+            o[3] = o[4] = o[5] = 0.0;
+        }
+        const double S[6] = {tot[9], tot[10], tot[11], tot[12], tot[13], tot[14]};
+        double ev[3];
+        sym3_eigvals(S, ev);
+        o[6] = ev[0]; o[7] = ev[1]; o[8] = ev[2];
+        o[9] = smax;
+        o[10] = a.contacts ? (double)a.contacts[p] : 0.0;
+        o[11] = fn > 0.0 ? fs / fn : 0.0;
+    }
+    (void)res;
+}
+
+// Receptor contacts: Morse-list pairs closer than r_c, counted for both platelets.
+__global__ void k_contacts(int64_t rows, const int32_t *row_idx, const int32_t *nl, const int32_t *nc, int cap,
+                           const float4 *x32, const int32_t *tag, md_geom geom, const md_dstate *ds, float rc2,
+                           int32_t *contacts)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int32_t i = row_idx[r];
+    const int cnt = min(nc[r], cap);
+    const float4 xi = x32[i];
+    const int pi = tag[i] & ~MD_RECEPTOR_BIT;
+    for (int k = 0; k < cnt; ++k) {
+        const int32_t j = nl[r * cap + k];
+        float dx, dy, dz, vs;
+        min_image_f32(geom, ds->le_offset_f, xi, x32[j], dx, dy, dz, vs);
+        if (dx * dx + dy * dy + dz * dz < rc2) {
+            atomicAdd(&contacts[pi], 1);
+            atomicAdd(&contacts[tag[j] & ~MD_RECEPTOR_BIT], 1);
+        }
+    }
+}
+
+__global__ void k_feature_ring(const double *feat, int P, float *ring, int T, int slot)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P * 12) return;
+    const int p = q / 12, c = q % 12;
+    ring[((int64_t)p * T + slot) * 12 + c] = (float)feat[q];
+}
+
+}  // namespace
+
+cudaError_t launch_features(md_system *s, double *out_dev)
+{
+    const int P = s->cfg.n_platelets;
+    if (P <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(s->plt_contacts, 0, sizeof(int32_t) * P, s->stream);
+    if (e != cudaSuccess) return e;
+    if (s->n_rec > 0) {
+        const float rc = (float)(1.5 * s->cfg.morse_r0);
+        k_contacts<<<(unsigned)((s->n_rec + 255) / 256), 256, 0, s->stream>>>(
+            s->n_rec, s->rec_sorted, s->nl[MD_LIST_MORSE], s->nc[MD_LIST_MORSE], s->cap[MD_LIST_MORSE], s->x32,
+            s->tag_s, s->geom, s->ds, rc * rc, s->plt_contacts);
+        MSM_COUNT(s, 1);
+    }
+    feat_args a;
+    a.P = P;
+    a.plt_off = s->plt_off;
+    a.plt_ids = s->plt_ids;
+    a.bond_off = s->bond_off;
+    a.bond_ij = s->bond_ij;
+    a.bond_r0 = s->bond_r0;
+    a.pos_of_id = s->pos_of_id;
+    a.x32 = s->x32;
+    a.v = s->v;
+    a.f0 = s->f[0];
+    a.f1 = s->f[1];
+    a.f2 = s->f[2];
+    a.tag = s->tag_s;
+    a.contacts = s->plt_contacts;
+    a.g = s->gmain;
+    a.geom = s->geom;
+    for (int d = 0; d < 3; ++d) a.L[d] = s->cfg.box[d];
+    a.g_body = (float)s->cfg.body_force;
+    a.flow_r2 = 4.0;
+    a.skin = s->cfg.skin;
+    a.out = out_dev;
+    k_features<<<P, FT_TPB, 0, s->stream>>>(a);
+    MSM_COUNT(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_feature_ring(md_system *s, const double *feat, int slot)
+{
+    const int P = s->cfg.n_platelets;
+    k_feature_ring<<<(P * 12 + 255) / 256, 256, 0, s->stream>>>(feat, P, s->ring, s->ring_T, slot);
+    MSM_COUNT(s, 1);
+    return cudaGetLastError();
+}

@@ -89,9 +89,19 @@ struct md_system {
     // lists (row-major ELL: entry k of row r at r*cap + k)
     int32_t *nl[4], *nc[4];
 
-    // bonds
+    // bonds (stored grouped by platelet: bonds of p are [bond_off[p], bond_off[p+1]))
     int32_t *bond_id, *bond_ij;
     float *bond_r0;
+
+    // per-platelet measurements (K8)
+    int32_t *plt_off, *plt_ids;  // member ids of platelet p: plt_ids[plt_off[p] .. plt_off[p+1])
+    int32_t *bond_off;
+    int32_t *plt_contacts;
+    double *feat;                // [P][12]
+    float *ring;                 // [P][ring_T][12] time series of the measurements
+    int ring_T = 128;
+    int64_t ring_count = 0;
+    std::vector<int32_t> h_tag;  // tags in id order (host copy)
 
     // scan scratch
     int32_t *scan_sums;
@@ -296,6 +306,9 @@ cudaError_t launch_set_loop(md_system *s, int64_t n);
 cudaError_t launch_zero_forces(md_system *s, unsigned levels);
 // reduce.cu
 cudaError_t launch_kinetics(md_system *s);
+// features.cu
+cudaError_t launch_features(md_system *s, double *out_dev);
+cudaError_t launch_feature_ring(md_system *s, const double *feat, int slot);
 // api.cu helpers
 int set_error(md_system *s, int code, const char *msg);
 int cuda_fail(md_system *s, cudaError_t e, const char *where);

@@ -232,6 +232,33 @@ def test_graph_replay_matches_direct_launches(plt_wall_sys, mode, k_m, k_p):
     assert np.abs(dx).max() < 1e-3   # chaotic growth of FP32 atomic-order noise over 25 steps
 
 
+@pytest.mark.parametrize("which", ["le", "walls"])
+def test_platelet_features_match_oracle(plt_sys, plt_wall_sys, which):
+    """K8 per-platelet measurements (FP64 device reductions) against the oracle on
+    the GPU's own FP32 snapshot and forces."""
+    from oracle import features as OF
+    s = plt_sys if which == "le" else plt_wall_sys
+    g = make_gpu(s, step0=2)
+    g.mts_step(3)
+    feat = g.platelet_features()
+    _, v, x32 = g.read_particles()
+    f = g.read_forces()
+    ref = OF.platelet_features(f32(x32), f32(v), f, s.tag, s.bonds, f32(s.r0), np.array(s.box, np.float32),
+                               walls=s.walls)
+    assert feat.shape == ref.shape == (2, 12)
+    cols = [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 11]
+    scale = np.abs(ref[:, cols]).max(0) + 1e-12
+    assert np.all(np.abs(feat[:, cols] - ref[:, cols]) <= 1e-6 * scale + 1e-9), (feat, ref)
+    assert np.all(np.abs(feat[:, 10] - ref[:, 10]) <= 1)   # pairs on the 1.5 r0 boundary may flip (FP32 test)
+    # ring buffer: chronological records
+    g.record_features()
+    g.mts_step(1)
+    g.record_features()
+    ring, cnt = g.read_feature_ring()
+    assert cnt == 2 and ring.shape == (2, 2, 12)
+    assert np.allclose(ring[:, 0], feat.astype(np.float32))
+
+
 def test_checkpoint_roundtrip(plt_sys):
     s = plt_sys
     g = make_gpu(s)
