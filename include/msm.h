@@ -259,6 +259,83 @@ int md_read_feature_ring(md_system *sys, float *out, int64_t *count);
  */
 int md_neighbor_pairs(md_system *sys, int32_t kind, int32_t *pairs, int64_t cap, int64_t *count);
 
+/* ---- learned step-size controller (Sec. 3.3, Table 2) --------------------- */
+/*
+ * Inference pipeline of Table 2 on the device: raw windows [B][T][F] of the
+ * per-platelet measurements -> denoise (causal moving average over 5 steps,
+ * one-level Haar transform with the soft threshold median|d|/0.6745 *
+ * sqrt(2 ln T), inverse) -> per-feature normalisation -> GRU autoencoder
+ * (2-layer encoder, hidden 64; latent = linear map of the last hidden state;
+ * 2-layer decoder fed the repeated latent; linear read-out) -> two FCN heads
+ * on the latent (ReLU hidden layers head_hidden[0..2]): logits over the step
+ * ratios k in {1, 2, 5, 10, 20} and log of the hold length.
+ * GRU cell: r = s(W_ir x + b_ir + W_hr h + b_hr), z = s(W_iz x + b_iz + W_hz h
+ * + b_hz), n = tanh(W_in x + b_in + r (W_hn h + b_hn)), h' = (1-z) n + z h.
+ * Matrix products run on the tensor cores in BF16 with FP32 accumulation;
+ * parameters, activations and optimiser state are FP32.
+ *
+ * Flat FP32 parameter layout (md_ai_param_count entries), in order:
+ *   enc1 {W_ih[3H][F], W_hh[3H][H], b_ih[3H], b_hh[3H]}, enc2 {W_ih[3H][H], ...},
+ *   lat {W[L][H], b[L]}, dec1 {W_ih[3H][L], ...}, dec2 {W_ih[3H][H], ...},
+ *   out {W[F][H], b[F]}, k-head {W0[h0][L], b0, W1[h1][h0], b1, W2[h2][h1], b2,
+ *   W3[C][h2], b3}, hold head {same with 1 output}.
+ */
+#define MD_AI_HOST   0   /* argument arrays live in host memory   */
+#define MD_AI_DEVICE 1   /* ... in device memory                  */
+#define MD_AI_TRAIN_AE    1
+#define MD_AI_TRAIN_HEADS 2
+
+typedef struct md_ai_config {
+    int32_t T;              /* window length (even, <= 256)              */
+    int32_t F;              /* measurements per step                     */
+    int32_t hidden;         /* GRU hidden size (64)                      */
+    int32_t latent;         /* latent size                               */
+    int32_t n_classes;      /* step-ratio classes                        */
+    int32_t head_hidden[3]; /* FCN hidden widths                         */
+    int32_t batch_max;      /* largest batch of windows                  */
+} md_ai_config;
+
+typedef struct md_ai md_ai;
+
+int md_ai_config_defaults(md_ai_config *cfg);          /* T 128, F 12, H 64, L 16, C 5, (32,16,8), B 256 */
+int md_ai_param_count(const md_ai_config *cfg, int64_t *n);
+int md_ai_workspace_size(const md_ai_config *cfg, size_t *bytes);
+/* Create over a caller-owned device workspace (>= md_ai_workspace_size). */
+int md_ai_init(const md_ai_config *cfg, void *workspace, size_t bytes, void *cuda_stream, md_ai **out);
+void md_ai_destroy(md_ai *ai);
+const char *md_ai_last_error(const md_ai *ai);
+/* Parameters (HOST, flat layout above); setting them resets the Adam state. */
+int md_ai_set_params(md_ai *ai, const float *params, int64_t n);
+int md_ai_get_params(md_ai *ai, float *params, int64_t n);
+/* Per-feature normalisation applied after denoising (HOST mean[F], std[F]). */
+int md_ai_set_norm(md_ai *ai, const float *mean, const float *stdv);
+/*
+ * Table 2 steps 1-4 for B raw windows (raw in host or device memory per
+ * `where`): out (HOST) [B][C + 2] = class probabilities, predicted log hold,
+ * reconstruction error (mean square over the window).  Errors: MD_EINVAL,
+ * MD_ENOTRAINED (no parameters), MD_ECUDA.
+ */
+int md_ai_predict(md_ai *ai, const float *raw, int32_t B, int32_t where, float *out);
+/*
+ * Autoencoder on already denoised, normalised HOST windows x[B][T][F]:
+ * latent (HOST [B][L], may be NULL) and reconstruction (HOST, time-major
+ * [T][B][F], may be NULL).
+ */
+int md_ai_encode(md_ai *ai, const float *x, int32_t B, float *latent, float *recon);
+/*
+ * Loss and gradient (HOST grads[n_params], may be NULL; flat layout) on a
+ * batch of denoised, normalised HOST windows: what = MD_AI_TRAIN_AE
+ * (reconstruction MSE over B*T*F; head gradients are zero) or
+ * MD_AI_TRAIN_HEADS (mean over the batch of the softmax cross-entropy of
+ * k_class[B] plus the squared error of log_hold[B]; autoencoder gradients are
+ * zero).  md_ai_train_step also applies one Adam step (b1 0.9, b2 0.999,
+ * eps 1e-8) with learning rate lr to that part.
+ */
+int md_ai_grads(md_ai *ai, const float *x, const int32_t *k_class, const float *log_hold, int32_t B, int32_t what,
+                float *grads, float *loss);
+int md_ai_train_step(md_ai *ai, const float *x, const int32_t *k_class, const float *log_hold, int32_t B,
+                     int32_t what, float lr, float *loss);
+
 /* ---- diagnostics ---------------------------------------------------------- */
 #define MD_PROF_FLUID   0  /* K3 plasma-plasma / plasma-wall DPD pass          */
 #define MD_PROF_IFACE   1  /* K3 interface DPD pass                            */

@@ -1,0 +1,208 @@
+"""Binding of the learned step-size controller (Table 2) in libmsm.
+
+Argument marshalling only: denoising, the GRU autoencoder, the heads, the
+losses, backpropagation and Adam all run in libmsm's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from ._binding import MdError, lib
+
+K_SET = (1, 2, 5, 10, 20)
+AI_HOST, AI_DEVICE = 0, 1
+TRAIN_AE, TRAIN_HEADS = 1, 2
+
+
+class md_ai_config(C.Structure):
+    _fields_ = [("T", C.c_int32), ("F", C.c_int32), ("hidden", C.c_int32), ("latent", C.c_int32),
+                ("n_classes", C.c_int32), ("head_hidden", C.c_int32 * 3), ("batch_max", C.c_int32)]
+
+
+_bound = False
+
+
+def _bind():
+    global _bound
+    if _bound:
+        return lib()
+    L = lib()
+    vp, fp, ip = C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int32)
+    cfgp = C.POINTER(md_ai_config)
+    L.md_ai_config_defaults.argtypes = [cfgp]
+    L.md_ai_param_count.argtypes = [cfgp, C.POINTER(C.c_int64)]
+    L.md_ai_workspace_size.argtypes = [cfgp, C.POINTER(C.c_size_t)]
+    L.md_ai_init.argtypes = [cfgp, vp, C.c_size_t, vp, C.POINTER(vp)]
+    L.md_ai_destroy.argtypes = [vp]
+    L.md_ai_destroy.restype = None
+    L.md_ai_last_error.argtypes = [vp]
+    L.md_ai_last_error.restype = C.c_char_p
+    L.md_ai_set_params.argtypes = [vp, fp, C.c_int64]
+    L.md_ai_get_params.argtypes = [vp, fp, C.c_int64]
+    L.md_ai_set_norm.argtypes = [vp, fp, fp]
+    L.md_ai_predict.argtypes = [vp, vp, C.c_int32, C.c_int32, fp]
+    L.md_ai_encode.argtypes = [vp, fp, C.c_int32, fp, fp]
+    L.md_ai_grads.argtypes = [vp, fp, ip, fp, C.c_int32, C.c_int32, fp, fp]
+    L.md_ai_train_step.argtypes = [vp, fp, ip, fp, C.c_int32, C.c_int32, C.c_float, fp]
+    for n in ("md_ai_config_defaults", "md_ai_param_count", "md_ai_workspace_size", "md_ai_init", "md_ai_set_params",
+              "md_ai_get_params", "md_ai_set_norm", "md_ai_predict", "md_ai_encode", "md_ai_grads",
+              "md_ai_train_step"):
+        getattr(L, n).restype = C.c_int
+    _bound = True
+    return L
+
+
+def default_config(batch_max=256, T=128, F=12, latent=16, head_hidden=(32, 16, 8), n_classes=5):
+    c = md_ai_config()
+    _bind().md_ai_config_defaults(C.byref(c))
+    c.T, c.F, c.latent, c.n_classes, c.batch_max = T, F, latent, n_classes, batch_max
+    for k in range(3):
+        c.head_hidden[k] = head_hidden[k]
+    return c
+
+
+def param_layout(cfg):
+    """(name, shape) of every parameter block in the flat layout of msm.h."""
+    H, F, L, Cn = cfg.hidden, cfg.F, cfg.latent, cfg.n_classes
+    hh = list(cfg.head_hidden)
+    out = []
+
+    def gru(name, nin):
+        out.extend([(f"{name}.W_ih", (3 * H, nin)), (f"{name}.W_hh", (3 * H, H)), (f"{name}.b_ih", (3 * H,)),
+                    (f"{name}.b_hh", (3 * H,))])
+
+    gru("enc1", F)
+    gru("enc2", H)
+    out.extend([("lat.W", (L, H)), ("lat.b", (L,))])
+    gru("dec1", L)
+    gru("dec2", H)
+    out.extend([("out.W", (F, H)), ("out.b", (F,))])
+    for head, last in (("khead", Cn), ("lhead", 1)):
+        dims = [L] + hh + [last]
+        for l in range(4):
+            out.extend([(f"{head}.{l}.W", (dims[l + 1], dims[l])), (f"{head}.{l}.b", (dims[l + 1],))])
+    return out
+
+
+def flatten(params_by_name, cfg):
+    """Concatenate named arrays (dict name -> array) in the flat layout."""
+    parts = []
+    for name, shape in param_layout(cfg):
+        a = np.asarray(params_by_name[name], np.float32)
+        assert a.shape == tuple(shape), (name, a.shape, shape)
+        parts.append(a.ravel())
+    return np.concatenate(parts)
+
+
+def unflatten(vec, cfg):
+    out, o = {}, 0
+    for name, shape in param_layout(cfg):
+        n = int(np.prod(shape))
+        out[name] = np.asarray(vec[o:o + n]).reshape(shape)
+        o += n
+    return out
+
+
+class Controller:
+    """The Table 2 pipeline over a torch-allocated device workspace."""
+
+    def __init__(self, cfg=None, stream=None):
+        import torch
+        L = _bind()
+        self.cfg = cfg if cfg is not None else default_config()
+        n = C.c_int64()
+        nb = C.c_size_t()
+        if L.md_ai_param_count(C.byref(self.cfg), C.byref(n)) or L.md_ai_workspace_size(C.byref(self.cfg),
+                                                                                        C.byref(nb)):
+            raise MdError(-1, "invalid controller configuration")
+        self.n_params = n.value
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        rc = L.md_ai_init(C.byref(self.cfg), C.c_void_p(self.workspace.data_ptr()), nb.value,
+                          C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc:
+            raise MdError(rc, "md_ai_init")
+        self.h = h
+
+    def _check(self, rc, what):
+        if rc:
+            raise MdError(rc, f"{what}: {_bind().md_ai_last_error(self.h).decode()}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            _bind().md_ai_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _f(a):
+        a = np.ascontiguousarray(a, np.float32)
+        return a, a.ctypes.data_as(C.POINTER(C.c_float))
+
+    def set_params(self, vec):
+        vec, p = self._f(vec)
+        self._check(_bind().md_ai_set_params(self.h, p, vec.size), "md_ai_set_params")
+
+    def get_params(self):
+        out = np.zeros(self.n_params, np.float32)
+        self._check(_bind().md_ai_get_params(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), self.n_params),
+                    "md_ai_get_params")
+        return out
+
+    def set_norm(self, mean, std):
+        m, mp = self._f(mean)
+        s, sp = self._f(std)
+        self._check(_bind().md_ai_set_norm(self.h, mp, sp), "md_ai_set_norm")
+
+    def predict(self, raw):
+        raw, rp = self._f(raw)
+        B = raw.shape[0]
+        out = np.zeros((B, self.cfg.n_classes + 2), np.float32)
+        self._check(_bind().md_ai_predict(self.h, C.cast(rp, C.c_void_p), B, AI_HOST,
+                                          out.ctypes.data_as(C.POINTER(C.c_float))), "md_ai_predict")
+        probs = out[:, :self.cfg.n_classes]
+        return dict(prob=probs, cls=probs.argmax(1), k=np.array(K_SET)[probs.argmax(1)],
+                    log_hold=out[:, self.cfg.n_classes], rec_err=out[:, self.cfg.n_classes + 1])
+
+    def encode(self, x):
+        x, xp = self._f(x)
+        B = x.shape[0]
+        z = np.zeros((B, self.cfg.latent), np.float32)
+        y = np.zeros((self.cfg.T, B, self.cfg.F), np.float32)
+        self._check(_bind().md_ai_encode(self.h, xp, B, z.ctypes.data_as(C.POINTER(C.c_float)),
+                                         y.ctypes.data_as(C.POINTER(C.c_float))), "md_ai_encode")
+        return z, np.transpose(y, (1, 0, 2))
+
+    def _labels(self, k_class, log_hold, B):
+        if k_class is None:
+            return None, None, None, None
+        kc = np.ascontiguousarray(k_class, np.int32)
+        lh = np.ascontiguousarray(log_hold, np.float32)
+        return kc, lh, kc.ctypes.data_as(C.POINTER(C.c_int32)), lh.ctypes.data_as(C.POINTER(C.c_float))
+
+    def grads(self, x, what, k_class=None, log_hold=None):
+        x, xp = self._f(x)
+        B = x.shape[0]
+        kc, lh, kp, lp = self._labels(k_class, log_hold, B)
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_float()
+        self._check(_bind().md_ai_grads(self.h, xp, kp, lp, B, what, g.ctypes.data_as(C.POINTER(C.c_float)),
+                                        C.byref(loss)), "md_ai_grads")
+        return loss.value, g
+
+    def train_step(self, x, what, lr, k_class=None, log_hold=None):
+        x, xp = self._f(x)
+        B = x.shape[0]
+        kc, lh, kp, lp = self._labels(k_class, log_hold, B)
+        loss = C.c_float()
+        self._check(_bind().md_ai_train_step(self.h, xp, kp, lp, B, what, float(lr), C.byref(loss)),
+                    "md_ai_train_step")
+        return loss.value

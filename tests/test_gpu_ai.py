@@ -1,0 +1,149 @@
+"""The GPU controller (libmsm, BF16 tensor-core GEMMs with FP32 accumulation)
+against the FP64 oracle of Table 2.
+
+Tolerances follow from BF16 operand rounding (8-bit significand, relative
+2^-9 per operand): outputs within 3 % of their scale, gradients with cosine
+similarity >= 0.99 and norm within 5 % per parameter block, Adam updates
+exact to FP32 rounding given the same gradient.
+"""
+import numpy as np
+import pytest
+
+from oracle import ai as A
+
+pytestmark = pytest.mark.gpu
+
+
+def named(p):
+    out = {}
+    for k in ("enc1", "enc2", "dec1", "dec2"):
+        for q in ("W_ih", "W_hh", "b_ih", "b_hh"):
+            out[f"{k}.{q}"] = p[k][q]
+    for k in ("lat", "out"):
+        out[f"{k}.W"], out[f"{k}.b"] = p[k]["W"], p[k]["b"]
+    for h in ("khead", "lhead"):
+        for l, layer in enumerate(p[h]):
+            out[f"{h}.{l}.W"], out[f"{h}.{l}.b"] = layer["W"], layer["b"]
+    return out
+
+
+@pytest.fixture(scope="module")
+def setup():
+    from paper_2205_14121_gb300 import controller as Ctl
+    cfg = Ctl.default_config(batch_max=32)
+    ctl = Ctl.Controller(cfg)
+    p = A.init_params(seed=3)
+    ctl.set_params(Ctl.flatten(named(p), cfg))
+    return Ctl, cfg, ctl, p
+
+
+def windows(B, seed, T=128, F=12):
+    rng = np.random.default_rng(seed)
+    t = np.arange(T)[None, :, None]
+    base = np.sin(0.05 * t * (1 + rng.random((B, 1, F)))) + 0.3 * rng.standard_normal((B, T, F))
+    return base
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / (np.abs(b).max() + 1e-12)
+
+
+def test_autoencoder_forward_matches_oracle(setup):
+    Ctl, cfg, ctl, p = setup
+    x = windows(20, 1)
+    z, y = ctl.encode(x.astype(np.float32))
+    zo, _ = A.encode(p, x)
+    yo, _ = A.decode(p, zo, x.shape[1])
+    assert rel(z, zo) < 3e-2
+    assert rel(y, yo) < 3e-2
+
+
+def test_predict_pipeline_matches_oracle(setup):
+    """Denoise + normalise + AE + heads (Table 2 steps 1-4)."""
+    Ctl, cfg, ctl, p = setup
+    raw = 2.0 + windows(12, 2)
+    mean = np.full(12, 2.0)
+    std = np.full(12, 0.7)
+    ctl.set_norm(mean, std)
+    out = ctl.predict(raw.astype(np.float32))
+    x = (A.denoise(raw) - mean) / std
+    zo, _ = A.encode(p, x)
+    yo, _ = A.decode(p, zo, x.shape[1])
+    logits, _ = A.mlp_forward(p["khead"], zo)
+    lh, _ = A.mlp_forward(p["lhead"], zo)
+    pr = A.softmax(logits)
+    assert np.abs(out["prob"] - pr).max() < 2e-2
+    assert rel(out["log_hold"], lh[:, 0]) < 3e-2
+    rec = np.mean((yo - x) ** 2, axis=(1, 2))
+    assert rel(out["rec_err"], rec) < 5e-2
+
+
+def _blocks(vec, cfg, Ctl):
+    return Ctl.unflatten(vec, cfg)
+
+
+@pytest.mark.parametrize("what", ["ae", "heads"])
+def test_gradients_match_oracle(setup, what):
+    Ctl, cfg, ctl, p = setup
+    x = windows(16, 3)
+    rng = np.random.default_rng(4)
+    kc = rng.integers(0, 5, 16)
+    lh = rng.standard_normal(16)
+    if what == "ae":
+        loss_o, go = A.ae_loss_and_grads(p, x)
+        loss_g, gg = ctl.grads(x.astype(np.float32), Ctl.TRAIN_AE)
+        names = [n for n, _ in Ctl.param_layout(cfg) if not n.startswith(("khead", "lhead"))]
+    else:
+        zo, _ = A.encode(p, x)
+        loss_o, go, _ = A.heads_loss_and_grads(p, zo, kc, lh)
+        loss_g, gg = ctl.grads(x.astype(np.float32), Ctl.TRAIN_HEADS, k_class=kc, log_hold=lh)
+        names = [n for n, _ in Ctl.param_layout(cfg) if n.startswith(("khead", "lhead"))]
+    assert loss_g == pytest.approx(loss_o, rel=3e-2)
+    gn = named({**{k: go[k] if k in go else A.zeros_like(p[k]) for k in p}})
+    gb = _blocks(gg, cfg, Ctl)
+    for n in names:
+        a = gb[n].ravel().astype(np.float64)
+        b = gn[n].ravel()
+        nb = np.linalg.norm(b)
+        if nb < 1e-10:
+            assert np.linalg.norm(a) < 1e-6
+            continue
+        cos = a @ b / (np.linalg.norm(a) * nb)
+        assert cos > 0.99, (n, cos)
+        assert abs(np.linalg.norm(a) / nb - 1) < 5e-2, (n, np.linalg.norm(a) / nb)
+
+
+def test_adam_step_matches_oracle_update(setup):
+    """One train step = the GPU gradient + Adam (Kingma & Ba) on the AE part."""
+    Ctl, cfg, ctl, p = setup
+    p0 = ctl.get_params()
+    x = windows(8, 5).astype(np.float32)
+    _, g = ctl.grads(x, Ctl.TRAIN_AE)
+    ctl.train_step(x, Ctl.TRAIN_AE, lr=1e-3)
+    p1 = ctl.get_params()
+    ref = {"w": p0.astype(np.float64).copy()}
+    opt = A.Adam(ref, lr=1e-3)
+    gm = g.astype(np.float64)
+    n_ae = sum(int(np.prod(s)) for n, s in Ctl.param_layout(cfg) if not n.startswith(("khead", "lhead")))
+    gm[n_ae:] = 0.0
+    opt.step(ref, {"w": gm})
+    assert np.abs(p1 - ref["w"]).max() < 1e-6
+    ctl.set_params(p0)
+
+
+def test_training_reduces_losses(setup):
+    Ctl, cfg, ctl, p = setup
+    p0 = ctl.get_params()
+    x = windows(32, 6).astype(np.float32)
+    rng = np.random.default_rng(7)
+    kc = (x[:, :, 0].std(1) > np.median(x[:, :, 0].std(1))).astype(np.int32) * 3   # learnable labels
+    lh = np.log(200.0 + 100 * rng.random(32))
+    l0 = ctl.train_step(x, Ctl.TRAIN_AE, 3e-3)
+    for _ in range(40):
+        l1 = ctl.train_step(x, Ctl.TRAIN_AE, 3e-3)
+    assert l1 < 0.7 * l0
+    h0 = ctl.train_step(x, Ctl.TRAIN_HEADS, 3e-3, k_class=kc, log_hold=lh)
+    for _ in range(60):
+        h1 = ctl.train_step(x, Ctl.TRAIN_HEADS, 3e-3, k_class=kc, log_hold=lh)
+    assert h1 < 0.5 * h0
+    ctl.set_params(p0)
