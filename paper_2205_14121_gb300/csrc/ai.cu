@@ -729,7 +729,7 @@ int stage_windows(md_ai *m, const float *x, int B, int where, bool raw)
     }
     if (raw) {
         if (T > 256 || (T & 1)) { m->err = "window length must be even and <= 256"; return MD_EINVAL; }
-        k_denoise<<<nblk((int64_t)B * F), 128, 0, m->st>>>(src, B, T, F, m->has_norm ? m->mean : nullptr,
+        k_denoise<<<nblk((int64_t)B * F, 128), 128, 0, m->st>>>(src, B, T, F, m->has_norm ? m->mean : nullptr,
                                                             m->has_norm ? m->stdv : nullptr, m->X);
     } else {
         k_to_time_major<<<nblk(cnt), 256, 0, m->st>>>(src, B, T, F, m->X);
@@ -849,7 +849,7 @@ int md_ai_predict(md_ai *m, const float *raw, int32_t B, int32_t where, float *o
     if (rc) return rc;
     rc = heads_forward(m, B);
     if (rc) return rc;
-    k_heads_loss<<<nblk(B), 128, 0, m->st>>>(m->logits, m->c.n_classes, m->lh, nullptr, nullptr, B, 0.f, nullptr,
+    k_heads_loss<<<nblk(B, 128), 128, 0, m->st>>>(m->logits, m->c.n_classes, m->lh, nullptr, nullptr, B, 0.f, nullptr,
                                              nullptr, nullptr, m->probs);
     AK(cudaGetLastError(), "softmax");
     const int C = m->c.n_classes;
@@ -905,7 +905,7 @@ int md_ai_grads(md_ai *m, const float *x, const int32_t *k_class, const float *l
         AK(cudaMemcpyAsync(m->cls, k_class, sizeof(int32_t) * B, cudaMemcpyHostToDevice, m->st), "labels");
         AK(cudaMemcpyAsync(m->lht, log_hold, sizeof(float) * B, cudaMemcpyHostToDevice, m->st), "labels");
         AK(cudaMemsetAsync(m->loss + 1, 0, sizeof(float), m->st), "zero loss");
-        k_heads_loss<<<nblk(B), 128, 0, m->st>>>(m->logits, m->c.n_classes, m->lh, m->cls, m->lht, B, 1.f, m->dlog,
+        k_heads_loss<<<nblk(B, 128), 128, 0, m->st>>>(m->logits, m->c.n_classes, m->lh, m->cls, m->lht, B, 1.f, m->dlog,
                                                  m->dlh, m->loss + 1, m->probs);
         AK(cudaGetLastError(), "heads loss");
         rc = heads_backward(m, B);
