@@ -182,7 +182,7 @@ int md_read_particles(md_system *sys, double *x, double *v, float *x32);
 /* ---- multiple time stepping (Table 1) ----------------------------------- */
 #define MD_MODE_STS   0  /* single time step: every force every dt_f           */
 #define MD_MODE_RESPA 1  /* k_m interface substeps, k_p platelet substeps each  */
-#define MD_MODE_AI    2  /* per-platelet k from the controller (Table 2)        */
+#define MD_MODE_AI    2  /* per-platelet k (md_set_platelet_levels), Table 2    */
 
 #define MD_SCHED_DIRECT 1  /* launch every kernel from the host (no CUDA graph) */
 
@@ -206,6 +206,24 @@ typedef struct md_mts_schedule {
  * Errors: MD_ENBR_OVERFLOW, MD_EUNSTABLE, MD_ECUDA (checked once at the end).
  */
 int md_mts_step(md_system *sys, int64_t n_outer, const md_mts_schedule *sched);
+
+/*
+ * AI-MTS step ratios (Sec. 3.3, Table 2): k[P] (HOST, P = cfg.n_platelets)
+ * platelet substeps per interface step for each platelet, as the controller
+ * predicts them (classes {1, 2, 5, 10, 20}).  MD_MODE_AI then runs the
+ * platelet level on the fine grid of K = lcm(k) substeps of dt_m / K:
+ * platelet p is due every K / k_p substeps, when it kicks with its last
+ * platelet-level force (a half kick at its first substep, two fused half
+ * kicks afterwards), drifts dt_m / k_p and has that force re-evaluated
+ * (bonds, LJ and Morse on its own particles; partners not due are read at
+ * their current positions); every platelet closes the interface step with a
+ * half kick.  With all k_p equal this is MD_MODE_RESPA with that k_p.
+ * Each k_p >= 1 and K <= MD_AI_K_LCM_MAX.  Copies synchronously; the values
+ * may change between md_mts_step calls (a new K recaptures the step graph).
+ * Errors: MD_EINVAL (no platelets, k out of range), MD_ECUDA.
+ */
+#define MD_AI_K_LCM_MAX 64
+int md_set_platelet_levels(md_system *sys, const int32_t *k);
 
 /* Observables (Sec. 4.2), FP64, reduced on the device. */
 typedef struct md_observables_t {

@@ -101,6 +101,9 @@ def lib():
         L.orc_kinetics.argtypes = [P, C.c_int32, dp, dp, ip, C.c_int32, dp, dp, dp]
         L.orc_run_sts.argtypes = [P, C.c_int32, C.c_int32, dp, dp, ip, ip, dp, ip, dp,
                                   C.c_double, C.c_int32, C.c_uint32, C.c_double, C.c_int32, dp]
+        L.orc_run_ai_respa.argtypes = [P, C.c_int32, C.c_int32, dp, dp, ip, ip, dp, ip, dp, ip, C.c_int32,
+                                       C.c_double, C.c_int32, C.c_int32, C.c_uint32, C.c_double, C.c_int32,
+                                       dp, dp, dp]
         _lib = L
     return _lib
 
@@ -269,6 +272,38 @@ def run_respa(p, x, v, tag, X0=None, bonds=None, r0=None, ids=None, dt_f=0.01, k
     lib().orc_run_respa(C.byref(p), n, bonds.shape[0], x.ctypes.data_as(dp), v.ctypes.data_as(dp),
                         idp, tp, X0p, bp, rp, dt_f, k_m, k_p, n_outer, n0, t0, init,
                         ff.ctypes.data_as(dp), fm.ctypes.data_as(dp), fpl.ctypes.data_as(dp))
+    return x, v, (ff, fm, fpl)
+
+
+def run_ai_respa(p, x, v, tag, plt_k, X0=None, bonds=None, r0=None, ids=None, dt_f=0.01, k_m=1, n_outer=1,
+                 n0=0, t0=0.0, forces=None):
+    """AI-MTS: Table 1 with per-platelet step ratios plt_k[P].  Returns (x, v, forces)."""
+    import math
+    n = x.shape[0]
+    x = np.array(x, dtype=np.float64, order="C")
+    v = np.array(v, dtype=np.float64, order="C")
+    tag, tp = _i(tag)
+    ids, idp = _i(np.arange(n) if ids is None else ids)
+    X0, X0p = _d(x.copy() if X0 is None else X0)
+    if bonds is None or len(bonds) == 0:
+        bonds = np.zeros((0, 2), np.int32)
+        r0 = np.zeros(0)
+    bonds, bp = _i(bonds)
+    r0, rp = _d(r0)
+    pk, pkp = _i(plt_k)
+    K = 1
+    for k in pk:
+        K = K * int(k) // math.gcd(K, int(k))
+    if forces is None:
+        ff, fm, fpl = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+        init = 1
+    else:
+        ff, fm, fpl = (np.array(a, dtype=np.float64, order="C") for a in forces)
+        init = 0
+    dp = C.POINTER(C.c_double)
+    lib().orc_run_ai_respa(C.byref(p), n, bonds.shape[0], x.ctypes.data_as(dp), v.ctypes.data_as(dp), idp, tp,
+                           X0p, bp, rp, pkp, K, dt_f, k_m, n_outer, n0, t0, init, ff.ctypes.data_as(dp),
+                           fm.ctypes.data_as(dp), fpl.ctypes.data_as(dp))
     return x, v, (ff, fm, fpl)
 
 

@@ -782,6 +782,88 @@ void orc_run_respa(orc_params *p, int32_t n, int32_t nb, double *x, double *v,
 }
 
 /*
+ * AI-MTS (Sec. 3.3): Table 1 with a per-platelet step ratio.  Platelet p
+ * takes k_p substeps of dt_m / k_p per interface step; on the fine grid of
+ * K = lcm(k_p) substeps it is due every K / k_p substeps.  Plasma and walls
+ * feel no platelet-level force and drift every fine substep.  At a due
+ * substep a platelet's particles kick with their last platelet-level force
+ * (half at the first substep, full afterwards -- two fused half kicks),
+ * drift by dt_m / k_p, and their platelet-level force is re-evaluated (the
+ * full force on each due particle, partners due or not); particles not due
+ * keep their last force.  The interface step ends with the closing half kick
+ * of every platelet particle.  plt_k[P] holds the ratios; K is their lcm.
+ */
+void orc_run_ai_respa(orc_params *p, int32_t n, int32_t nb, double *x, double *v,
+                      const int32_t *id, const int32_t *tag, const double *X0,
+                      const int32_t *bonds, const double *r0, const int32_t *plt_k, int32_t K,
+                      double dt_f, int32_t k_m, int32_t n_outer, uint32_t n0, double t0,
+                      int32_t compute_initial, double *f_f, double *f_m, double *f_p)
+{
+    orc_state s = {n, nb, x, v, id, tag, X0, bonds, r0};
+    bond_csr_t csr;
+    bond_csr_build(n, nb, bonds, r0, &csr);
+    double *fnew = (double *)malloc((size_t)3 * (n > 0 ? n : 1) * sizeof(double));
+    const double dt_m = dt_f / k_m, dts = dt_m / K;
+    double t = t0;
+    if (p->le) {
+        p->le_offset = fmod(p->le_rate * p->L[1] * t, p->L[0]);
+        if (p->le_offset < 0.0) p->le_offset += p->L[0];
+    }
+    if (compute_initial) {
+        eval_level(p, &s, &csr, LVL_FLUID, n0, 0, dt_f, dt_m, f_f);
+        eval_level(p, &s, &csr, LVL_IFACE, n0, 0, dt_f, dt_m, f_m);
+        eval_level(p, &s, &csr, LVL_PLT, n0, 0, dt_f, dt_m, f_p);
+    }
+    for (int32_t so = 0; so < n_outer; ++so) {
+        uint32_t nn = n0 + (uint32_t)so;
+        kick(&s, f_f, 0.5 * dt_f);
+        for (int32_t c = 0; c < k_m; ++c) {
+            kick(&s, f_m, 0.5 * dt_m);
+            for (int32_t q = 0; q < K; ++q) {
+                t += dts;
+                if (p->le) {
+                    p->le_offset = fmod(p->le_rate * p->L[1] * t, p->L[0]);
+                    if (p->le_offset < 0.0) p->le_offset += p->L[0];
+                }
+                for (int32_t i = 0; i < n; ++i) {
+                    if (tag[i] == TAG_WALL) continue;
+                    double dt_i = dts;
+                    if (tag[i] >= 0) {
+                        const int32_t kp = plt_k[tag[i] & ~REC_BIT];
+                        if (q % (K / kp) != 0) continue;
+                        dt_i = dt_m / kp;
+                        const double h = (q == 0 ? 0.5 : 1.0) * dt_i;
+                        for (int k = 0; k < 3; ++k) v[3 * i + k] += h * f_p[3 * i + k];
+                    }
+                    for (int k = 0; k < 3; ++k) x[3 * i + k] += dt_i * v[3 * i + k];
+                    apply_boundaries(p, x + 3 * i, v + 3 * i);
+                }
+                eval_level(p, &s, &csr, LVL_PLT, 0, 0, dt_f, dt_m, fnew);
+                for (int32_t i = 0; i < n; ++i) {
+                    if (tag[i] < 0) continue;
+                    const int32_t kp = plt_k[tag[i] & ~REC_BIT];
+                    if (q % (K / kp) != 0) continue;
+                    for (int k = 0; k < 3; ++k) f_p[3 * i + k] = fnew[3 * i + k];
+                }
+            }
+            for (int32_t i = 0; i < n; ++i) {
+                if (tag[i] < 0) continue;
+                const double h = 0.5 * dt_m / plt_k[tag[i] & ~REC_BIT];
+                for (int k = 0; k < 3; ++k) v[3 * i + k] += h * f_p[3 * i + k];
+            }
+            uint32_t nt = (c + 1 == k_m) ? nn + 1 : nn;
+            uint32_t cs = (c + 1 == k_m) ? 0u : (uint32_t)(c + 1);
+            eval_level(p, &s, &csr, LVL_IFACE, nt, cs, dt_f, dt_m, f_m);
+            kick(&s, f_m, 0.5 * dt_m);
+        }
+        eval_level(p, &s, &csr, LVL_FLUID, nn + 1, 0, dt_f, dt_m, f_f);
+        kick(&s, f_f, 0.5 * dt_f);
+    }
+    free(fnew);
+    free(csr.off); free(csr.nbr); free(csr.r0);
+}
+
+/*
  * Single time step (STS, the reference run of Sec. 4.1): velocity-Verlet in
  * which all forces of Eq. 1-4 are evaluated together, at the drifted
  * positions and the half-kicked velocities:

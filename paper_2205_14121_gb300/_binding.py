@@ -119,6 +119,7 @@ def lib():
     L.md_read_forces.argtypes = [vp, u32, dp]
     L.md_read_particles.argtypes = [vp, dp, dp, fp]
     L.md_mts_step.argtypes = [vp, i64, C.POINTER(md_mts_schedule)]
+    L.md_set_platelet_levels.argtypes = [vp, ip]
     L.md_observables.argtypes = [vp, C.POINTER(md_observables_t)]
     L.md_neighbor_pairs.argtypes = [vp, i32, ip, i64, C.POINTER(C.c_int64)]
     L.md_get_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
@@ -133,6 +134,7 @@ def lib():
         getattr(L, name).restype = C.c_int
     for name in ("md_config_defaults", "md_workspace_size", "md_init", "md_set_particles", "md_set_bonds",
                  "md_neighbor_build", "md_forces", "md_read_forces", "md_read_particles", "md_mts_step",
+                 "md_set_platelet_levels",
                  "md_observables", "md_neighbor_pairs", "md_get_state", "md_set_state", "md_profile_enable",
                  "md_profile_read", "md_philox"):
         getattr(L, name).restype = C.c_int
@@ -279,6 +281,14 @@ class System:
         self._check(lib().md_mts_step(self.h, int(n_outer), C.byref(sched)), "md_mts_step")
 
     md_mts_step = mts_step
+
+    def set_platelet_levels(self, k):
+        """Per-platelet step ratios k_p for MD_MODE_AI (Sec. 3.3)."""
+        k = np.ascontiguousarray(k, dtype=np.int32)
+        self._check(lib().md_set_platelet_levels(self.h, k.ctypes.data_as(C.POINTER(C.c_int32))),
+                    "md_set_platelet_levels")
+
+    md_set_platelet_levels = set_platelet_levels
 
     def observables(self):
         o = md_observables_t()

@@ -160,6 +160,7 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
         s.plt_contacts = cv.take<int32_t>(P);
         s.feat = cv.take<double>(12 * P);
         s.ring = cv.take<float>(P * (int64_t)s.ring_T * 12);
+        s.plt_k = cv.take<int32_t>(P);
     }
     s.red_blocks = (int)((n + MSM_TPB - 1) / MSM_TPB);
     if (s.red_blocks > RED_BLOCKS_MAX) s.red_blocks = RED_BLOCKS_MAX;
@@ -454,7 +455,31 @@ int enqueue_outer_step(md_system *s, int mode, int k_m, int k_p, bool first, cap
         h[1] = plt ? (float)(0.5 * dtm) : 0.f;
         const unsigned zero = (plt ? MD_LEVEL_IFACE : 0u) | (ci == 0 ? MD_LEVEL_FLUID : 0u);
         RC(enqueue_kd(s, h, DRIFT_ALL, dtm, plt ? DRIFT_FLUID : DRIFT_ALL, zero, false));
-        if (plt) {
+        if (plt && mode == MD_MODE_AI) {
+            // B (AI-MTS): K = lcm(k_p) fine substeps of dt_m / K; platelet p
+            //    is due every K/k_p of them and then kicks, drifts dt_m / k_p
+            //    and refreshes its platelet-level force; the kernels take the
+            //    per-platelet step sizes from plt_k on the device.
+            const int K = s->plt_K;
+            const double dts = dtm / K;
+            s->due_on = true;
+            s->due_dtm = dtm;
+            int rc = MD_OK;
+            for (int q = 0; q < K && rc == MD_OK; ++q) {
+                s->due_q = q;
+                rc = enqueue_time(s, dn, c_end, tc + (q + 1) * dts);
+                const float hq[3] = {0.f, 0.f, 1.f};   // replaced per platelet
+                if (rc == MD_OK) rc = enqueue_kd(s, hq, DRIFT_PLT, dts, DRIFT_PLT, MD_LEVEL_PLT, true);
+                if (rc == MD_OK) rc = enqueue_forces(s, MD_LEVEL_PLT);
+            }
+            s->due_closing = true;
+            const float hc[3] = {0.f, 0.f, 1.f};
+            if (rc == MD_OK) rc = enqueue_kd(s, hc, DRIFT_PLT, 0.0, -1, 0u, true);
+            s->due_on = false;
+            s->due_closing = false;
+            s->due_q = 0;
+            if (rc != MD_OK) return rc;
+        } else if (plt) {
             // B: platelet substeps; the kick of substep q fuses the closing
             //    half-kick of q-1 with its own opening half-kick
             for (int q = 0; q < k_p; ++q) {
@@ -820,6 +845,28 @@ int md_set_bonds(md_system *s, const int32_t *ij, const double *r0, int64_t nb)
     return MD_OK;
 }
 
+int md_set_platelet_levels(md_system *s, const int32_t *k)
+{
+    if (!s || !k) return set_error(s, MD_EINVAL, "md_set_platelet_levels: null argument");
+    if (s->n_plt == 0 || !s->plt_k) return set_error(s, MD_EINVAL, "md_set_platelet_levels: no platelets");
+    const int P = s->cfg.n_platelets;
+    int64_t K = 1;
+    for (int p = 0; p < P; ++p) {
+        if (k[p] < 1 || k[p] > MD_AI_K_LCM_MAX)
+            return set_error(s, MD_EINVAL, "md_set_platelet_levels: k out of range");
+        int64_t a = K, b = k[p];
+        while (b) { const int64_t t = a % b; a = b; b = t; }
+        K = K / a * k[p];
+        if (K > MD_AI_K_LCM_MAX) return set_error(s, MD_EINVAL, "md_set_platelet_levels: lcm(k) too large");
+    }
+    CK(cudaMemcpyAsync(s->plt_k, k, sizeof(int32_t) * P, cudaMemcpyHostToDevice, s->stream), "upload k");
+    CK(cudaStreamSynchronize(s->stream), "levels sync");
+    s->h_plt_k.assign(k, k + P);
+    s->plt_K = (int)K;
+    s->have_levels = true;
+    return MD_OK;
+}
+
 int md_neighbor_build(md_system *s, uint32_t list_mask, int force)
 {
     if (!s || !s->have_particles) return set_error(s, MD_EINVAL, "md_neighbor_build: no particles");
@@ -899,7 +946,11 @@ int md_mts_step(md_system *s, int64_t n_outer, const md_mts_schedule *sched)
     int k_m = sched->k_m > 0 ? sched->k_m : 1;
     int k_p = sched->k_p > 0 ? sched->k_p : 1;
     if (mode == MD_MODE_STS) { k_m = 1; k_p = 1; }
-    else if (mode != MD_MODE_RESPA) return set_error(s, MD_EINVAL, "md_mts_step: unsupported mode");
+    else if (mode == MD_MODE_AI) {
+        if (s->n_plt == 0) return set_error(s, MD_EINVAL, "md_mts_step: AI-MTS needs platelets");
+        if (!s->have_levels) return set_error(s, MD_EINVAL, "md_mts_step: platelet levels not set");
+        k_p = s->plt_K;   // the fine grid; part of the captured graph's shape
+    } else if (mode != MD_MODE_RESPA) return set_error(s, MD_EINVAL, "md_mts_step: unsupported mode");
     if (s->cfg_k_m != k_m) {
         // the interface noise amplitude depends on dt_m: recompute those forces
         s->cfg_k_m = k_m;

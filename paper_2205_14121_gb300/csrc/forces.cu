@@ -33,7 +33,16 @@ struct pair_args {
     float lj_eps24, lj_sig2, lj_rc2;
     float m_Da_r0, m_alpha, m_inv_r0, m_rc2, f_A;
     double *vir;
+    // AI-MTS: only pairs with a due end are evaluated, and only due ends receive
+    // the force (a platelet keeps its last force until its next substep)
+    md_due due;
+    const int32_t *tag;
 };
+
+__device__ __forceinline__ bool due_of(const pair_args &a, int32_t i)
+{
+    return a.due.plt_k ? platelet_due(a.due, a.tag[i]) : true;
+}
 
 struct vir6 {
     float xx, yy, zz, xy, xz, yz;
@@ -228,9 +237,12 @@ __global__ void __launch_bounds__(MSM_TPB) k_lj(pair_args a)
         if (cnt > 0) {
             const float4 xi = a.x32[i];
             const float delta = a.ds->le_offset_f;
+            const bool di = due_of(a, i);
             float fx = 0.f, fy = 0.f, fz = 0.f;
             for (int k = 0; k < cnt; ++k) {
                 const int32_t j = a.nl[r * a.cap + k];
+                const bool dj = due_of(a, j);
+                if (!di && !dj) continue;
                 const float4 xj = a.x32[j];
                 float dx, dy, dz, vsh;
                 min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
@@ -241,11 +253,11 @@ __global__ void __launch_bounds__(MSM_TPB) k_lj(pair_args a)
                 const float s6 = s2 * s2 * s2;
                 const float fr = a.lj_eps24 * (2.0f * s6 * s6 - s6) * inv_r2;
                 const float px = fr * dx, py = fr * dy, pz = fr * dz;
-                fx += px; fy += py; fz += pz;
-                scatter(a.f, j, -px, -py, -pz);
+                if (di) { fx += px; fy += py; fz += pz; }
+                if (dj) scatter(a.f, j, -px, -py, -pz);
                 if (VIR) w.add(dx, dy, dz, fr);
             }
-            scatter(a.f, i, fx, fy, fz);
+            if (di) scatter(a.f, i, fx, fy, fz);
         }
     }
     if (VIR) flush_virial(a.vir, w);
@@ -263,9 +275,12 @@ __global__ void __launch_bounds__(MSM_TPB) k_morse(pair_args a)
         if (cnt > 0) {
             const float4 xi = a.x32[i];
             const float delta = a.ds->le_offset_f;
+            const bool di = due_of(a, i);
             float fx = 0.f, fy = 0.f, fz = 0.f;
             for (int k = 0; k < cnt; ++k) {
                 const int32_t j = a.nl[r * a.cap + k];
+                const bool dj = due_of(a, j);
+                if (!di && !dj) continue;
                 const float4 xj = a.x32[j];
                 float dx, dy, dz, vsh;
                 min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
@@ -277,11 +292,11 @@ __global__ void __launch_bounds__(MSM_TPB) k_morse(pair_args a)
                 const float fm = a.m_Da_r0 * (expf(t) - expf(0.5f * t)) + a.f_A * (1.0f - rr * a.m_inv_r0);
                 const float s = fm * inv_r;
                 const float px = s * dx, py = s * dy, pz = s * dz;
-                fx += px; fy += py; fz += pz;
-                scatter(a.f, j, -px, -py, -pz);
+                if (di) { fx += px; fy += py; fz += pz; }
+                if (dj) scatter(a.f, j, -px, -py, -pz);
                 if (VIR) w.add(dx, dy, dz, s);
             }
-            scatter(a.f, i, fx, fy, fz);
+            if (di) scatter(a.f, i, fx, fy, fz);
         }
     }
     if (VIR) flush_virial(a.vir, w);
@@ -291,11 +306,13 @@ __global__ void __launch_bounds__(MSM_TPB) k_morse(pair_args a)
 template <bool VIR>
 __global__ void __launch_bounds__(MSM_TPB) k_bonds(int64_t nb, const int32_t *__restrict__ ij,
                                                   const float *__restrict__ r0, float kb2, const float4 *__restrict__ x32,
-                                                  float4 *f, md_geom geom, const md_dstate *ds, double *vir)
+                                                  float4 *f, md_geom geom, const md_dstate *ds, double *vir, md_due due,
+                                                  const int32_t *tag)
 {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     vir6 w = {0, 0, 0, 0, 0, 0};
-    if (b < nb) {
+    // both ends belong to one platelet: skip the bonds of platelets not due
+    if (b < nb && (!due.plt_k || platelet_due(due, tag[ij[2 * b]]))) {
         const int32_t i = ij[2 * b], j = ij[2 * b + 1];
         float dx, dy, dz, vsh;
         min_image_f32(geom, ds->le_offset_f, x32[i], x32[j], dx, dy, dz, vsh);
@@ -339,6 +356,10 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
     a.m_rc2 = (float)(c.morse_rc * c.morse_rc);
     a.f_A = (float)c.f_A;
     a.vir = s->vir_acc;
+    a.tag = s->tag_s;
+    a.due.plt_k = s->due_on ? s->plt_k : nullptr;
+    a.due.q = s->due_q;
+    a.due.K = s->plt_K;
     const int km = s->cfg_k_m > 0 ? s->cfg_k_m : 1;
 
     if (level_mask & MD_LEVEL_FLUID) {
@@ -374,11 +395,11 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
             if (virial)
                 k_bonds<true><<<blocks_for(s->nb), MSM_TPB, 0, s->stream>>>(s->nb, s->bond_ij, s->bond_r0,
                                                                            (float)(2.0 * c.k_bond), s->x32, out[2],
-                                                                           s->geom, s->ds, s->vir_acc);
+                                                                           s->geom, s->ds, s->vir_acc, a.due, s->tag_s);
             else
                 k_bonds<false><<<blocks_for(s->nb), MSM_TPB, 0, s->stream>>>(s->nb, s->bond_ij, s->bond_r0,
                                                                             (float)(2.0 * c.k_bond), s->x32, out[2],
-                                                                            s->geom, s->ds, s->vir_acc);
+                                                                            s->geom, s->ds, s->vir_acc, a.due, s->tag_s);
         }
         a.rows = s->n_plt;
         a.row_idx = s->plt_sorted;

@@ -103,6 +103,17 @@ struct md_system {
     int64_t ring_count = 0;
     std::vector<int32_t> h_tag;  // tags in id order (host copy)
 
+    // per-platelet step ratios (AI-MTS): platelet p takes k_p substeps per
+    // interface step on a fine grid of K = lcm(k_p) substeps
+    int32_t *plt_k = nullptr;    // device [P]
+    std::vector<int32_t> h_plt_k;
+    int plt_K = 1;
+    // schedule of the platelet launches being enqueued (AI-MTS substep q of K;
+    // plt_k null outside AI-MTS), read by launch_kick_drift / launch_forces
+    int due_q = 0;
+    bool due_on = false, due_closing = false;
+    double due_dtm = 0.0;
+
     // scan scratch
     int32_t *scan_sums;
     int64_t scan_cap;
@@ -128,6 +139,7 @@ struct md_system {
     bool forces_stale = true;
     bool have_particles = false;
     bool have_bonds = false;
+    bool have_levels = false;
     int64_t host_step = 0;
     int32_t host_sub = 0;
     unsigned forces_levels = 0;  // levels whose buffers hold current forces
@@ -283,6 +295,20 @@ __device__ __forceinline__ int64_t cell_index(const md_grid &g, int cx, int cy, 
 }
 
 __device__ __forceinline__ bool gate_closed(const int32_t *gate) { return gate && *gate == 0; }
+
+// AI-MTS substep schedule: on the fine grid of K substeps per interface
+// step, platelet p (ratio k_p) is due every K/k_p substeps.
+struct md_due {
+    const int32_t *plt_k;   // null: every platelet is due (fixed-k RESPA)
+    int q, K;
+};
+
+__device__ __forceinline__ bool platelet_due(const md_due &d, int32_t tag)
+{
+    if (!d.plt_k) return true;
+    const int kp = d.plt_k[tag & ~MD_RECEPTOR_BIT];
+    return (d.q % (d.K / kp)) == 0;
+}
 
 // ---------------------------------------------------------------------------
 // host-side launchers (one translation unit each)

@@ -232,6 +232,83 @@ def test_graph_replay_matches_direct_launches(plt_wall_sys, mode, k_m, k_p):
     assert np.abs(dx).max() < 1e-3   # chaotic growth of FP32 atomic-order noise over 25 steps
 
 
+def test_ai_mts_mixed_ratios_track_oracle(plt_wall_sys):
+    """AI-MTS (Sec. 3.3) with per-platelet ratios k = (2, 5) on the fine grid
+    K = 10 against the oracle's per-platelet loop; same bound as fixed-k RESPA."""
+    import paper_2205_14121_gb300 as M
+    s = plt_wall_sys
+    x0, v0 = f32(s.x), f32(s.v)
+    g = make_gpu(s, x=x0, v=v0)
+    g.set_platelet_levels([2, 5])
+    g.mts_step(3, mode=M.MD_MODE_AI, k_m=2)
+    xg, vg, _ = g.read_particles()
+    p = O.system_params(s)
+    xo, vo, _ = O.run_ai_respa(p, x0, v0, s.tag, [2, 5], X0=f32(s.X0), bonds=s.bonds, r0=f32(s.r0), dt_f=0.01,
+                               k_m=2, n_outer=3)
+    dx = xg - xo
+    L = np.array(s.box)
+    dx -= L * np.round(dx / L)
+    assert np.abs(dx).max() < 1e-4
+    assert np.abs(vg - vo).max() < 5e-3 * np.sqrt((vo ** 2).mean())
+    # the two platelets really moved on different grids: k = (5, 2) differs
+    h = make_gpu(s, x=x0, v=v0)
+    h.set_platelet_levels([5, 2])
+    h.mts_step(3, mode=M.MD_MODE_AI, k_m=2)
+    xh, _, _ = h.read_particles()
+    plt = s.tag >= 0
+    d2 = xh[plt] - xg[plt]
+    d2 -= L * np.round(d2 / L)
+    assert np.abs(d2).max() > 1e-6
+
+
+def test_ai_mts_equal_ratios_match_respa_on_gpu(plt_wall_sys):
+    """With every k_p = 4 the AI-MTS kernels take the fixed-k RESPA steps."""
+    import paper_2205_14121_gb300 as M
+    s = plt_wall_sys
+    x0, v0 = f32(s.x), f32(s.v)
+    a = make_gpu(s, x=x0, v=v0)
+    a.set_platelet_levels([4, 4])
+    a.mts_step(4, mode=M.MD_MODE_AI, k_m=2)
+    b = make_gpu(s, x=x0, v=v0)
+    b.mts_step(4, mode=M.MD_MODE_RESPA, k_m=2, k_p=4)
+    xa, va, _ = a.read_particles()
+    xb, vb, _ = b.read_particles()
+    dx = xa - xb
+    dx -= np.array(s.box) * np.round(dx / np.array(s.box))
+    assert np.abs(dx).max() < 1e-4
+    assert np.abs(va - vb).max() < 1e-2
+
+
+def test_ai_mts_graph_replay_and_level_validation(plt_wall_sys):
+    """Graph replay of the AI-MTS step equals direct launches; a new ratio set
+    with another lcm recaptures; bad ratios are rejected."""
+    import paper_2205_14121_gb300 as M
+    s = plt_wall_sys
+    x0, v0 = f32(s.x), f32(s.v)
+    a = make_gpu(s, x=x0, v=v0)
+    with pytest.raises(M.MdError):
+        a.mts_step(2, mode=M.MD_MODE_AI)          # no ratios yet
+    for bad in ([0, 1], [1, 65], [7, 11]):
+        with pytest.raises(M.MdError):
+            a.set_platelet_levels(bad)
+    b = make_gpu(s, x=x0, v=v0)
+    for g in (a, b):
+        g.set_platelet_levels([1, 2])
+    a.mts_step(10, mode=M.MD_MODE_AI, k_m=1)
+    b.mts_step(10, mode=M.MD_MODE_AI, k_m=1, direct=True)
+    for g in (a, b):
+        g.set_platelet_levels([10, 20])
+    a.mts_step(10, mode=M.MD_MODE_AI, k_m=1)
+    b.mts_step(10, mode=M.MD_MODE_AI, k_m=1, direct=True)
+    oa, ob = a.observables(), b.observables()
+    assert oa["step"] == ob["step"] == 20 and oa["n_builds"] == ob["n_builds"]
+    xa, _, _ = a.read_particles()
+    xb, _, _ = b.read_particles()
+    dx = xa - xb
+    dx -= np.array(s.box) * np.round(dx / np.array(s.box))
+    assert np.abs(dx).max() < 1e-3
+
+
 @pytest.mark.parametrize("which", ["le", "walls"])
 def test_platelet_features_match_oracle(plt_sys, plt_wall_sys, which):
     """K8 per-platelet measurements (FP64 device reductions) against the oracle on

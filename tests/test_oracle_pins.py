@@ -525,3 +525,50 @@ def test_couette_linear_profile_under_lees_edwards():
     pred = slope * yc + icpt
     r2 = 1 - ((prof - pred) ** 2).sum() / ((prof - prof.mean()) ** 2).sum()
     assert r2 > 0.98
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.3 -- AI-MTS: per-platelet step ratios
+# --------------------------------------------------------------------------
+
+def two_isolated_shells(n_shell=200, seed=17):
+    """Two platelets 14 apart in a 30^3 box (beyond every platelet-level cutoff),
+    no plasma: the levels do not couple them."""
+    s = synth.platelet_system((30.0, 30.0, 30.0), 0, 2, n_shell, synth.scaled_radii(n_shell), seed=seed,
+                              centers=[(8.0, 15.0, 15.0), (22.0, 15.0, 15.0)])
+    rng = np.random.default_rng(seed)
+    s.x += 0.03 * rng.standard_normal(s.x.shape)
+    return s
+
+
+def test_ai_mts_equal_ratios_is_fixed_k_respa():
+    """Sec. 3.3: when the controller gives every platelet the same k, AI-MTS is
+    Table 1's RESPA with k_p = k (plasma, walls and interface levels included)."""
+    s = synth.platelet_system((8.0, 8.0, 8.0), 1200, 2, 120, synth.scaled_radii(120), walls=True,
+                              body_force=0.02, seed=5, centers=[(2.7, 4.0, 4.0), (5.4, 4.0, 4.0)])
+    p = O.system_params(s)
+    xa, va, _ = O.run_respa(p, s.x, s.v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, dt_f=0.01, k_m=2, k_p=3,
+                            n_outer=3)
+    xb, vb, _ = O.run_ai_respa(p, s.x, s.v, s.tag, [3, 3], X0=s.X0, bonds=s.bonds, r0=s.r0, dt_f=0.01, k_m=2,
+                               n_outer=3)
+    assert np.abs(xa - xb).max() < 1e-11
+    assert np.abs(va - vb).max() < 1e-9
+
+
+def test_ai_mts_isolated_platelets_follow_their_own_ratio():
+    """Sec. 3.3: each platelet moves with its own k.  Two platelets that share no
+    force each follow the fixed-k RESPA trajectory of their own ratio."""
+    s = two_isolated_shells()
+    p = O.system_params(s)
+    kw = dict(X0=s.X0, bonds=s.bonds, r0=s.r0, dt_f=0.004, k_m=2, n_outer=4)
+    xa, va, _ = O.run_ai_respa(p, s.x, s.v, s.tag, [2, 5], **kw)
+    p0 = s.tag == 0
+    p1 = s.tag == 1
+    for k, sel in ((2, p0), (5, p1)):
+        xr, vr, _ = O.run_respa(p, s.x, s.v, s.tag, k_p=k, **kw)
+        assert np.abs(xa[sel] - xr[sel]).max() < 1e-11
+        assert np.abs(va[sel] - vr[sel]).max() < 1e-9
+    # and the two ratios give visibly different trajectories
+    x1, _, _ = O.run_respa(p, s.x, s.v, s.tag, k_p=1, **kw)
+    assert np.abs(xa[p1] - x1[p1]).max() > 1e-9
+
