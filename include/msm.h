@@ -38,6 +38,7 @@ extern "C" {
 #define MD_EUNSTABLE     (-5)   /* NaN/Inf state or a particle left the box */
 #define MD_ETIMEOUT      (-6)   /* a bounded device wait gave up            */
 #define MD_ENOTRAINED    (-7)   /* the controller has no weights loaded     */
+#define MD_ETOOLARGE     (-8)   /* n beyond a fixed static scratch capacity */
 
 /* ---- force levels (Table 1 component splitting) ------------------------- */
 #define MD_LEVEL_FLUID 1u  /* plasma-plasma and plasma-wall DPD + body force */
@@ -387,6 +388,33 @@ int md_profile_read(md_system *sys, md_profile_t *out, int reset);
  * MD_ECUDA.
  */
 int md_philox(const uint32_t *ctr, const uint32_t key[2], int64_t n, uint32_t *out, int use_library);
+
+/*
+ * md_philox without any allocation.  The paper has no counterpart: this is a
+ * service entry point of the library, for callers that cannot allocate device
+ * memory -- a process whose device memory is held by a caching pool
+ * allocator (a cudaMalloc there fails or forces the pool to give memory
+ * back), or a caller working beside other streams, for which cudaFree's
+ * implicit device-wide synchronisation would stall the work in flight.
+ * Same arguments, blocks and errors as md_philox; the device staging
+ * buffers are a file-scope static __device__ array of 2 * MD_PHILOX_STATIC_MAX
+ * uint4 (512 KiB, 256-byte aligned, part of the library's module image)
+ * instead of cudaMalloc'd scratch.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.
+ *  - n > MD_PHILOX_STATIC_MAX returns MD_ETOOLARGE before any CUDA call.
+ *  - The array's device address is looked up (cudaGetSymbolAddress) once per
+ *    device, at the first call made with that device current; make that
+ *    first call before any stream capture begins on the device.
+ *  - The array keeps the last call's counters and outputs.  Nothing in it
+ *    has to start at zero: a call copies its n counters in before the kernel
+ *    reads them, and the kernel writes the n outputs before they are copied
+ *    out.
+ *  - Every call on a device shares the one array, so overlapping calls (from
+ *    several host threads) race on it: the caller serialises them.
+ * Runs on the legacy default stream with synchronous copies, as md_philox.
+ */
+#define MD_PHILOX_STATIC_MAX 16384
+int md_philox_static(const uint32_t *ctr, const uint32_t key[2], int64_t n, uint32_t *out, int use_library);
 
 /*
  * Checkpoint: md_get_state writes the full dynamical state (positions,

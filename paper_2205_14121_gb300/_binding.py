@@ -22,7 +22,8 @@ MD_MODE_STS, MD_MODE_RESPA, MD_MODE_AI = 0, 1, 2
 RECEPTOR_BIT = 1 << 30
 
 ERRORS = {-1: "MD_EINVAL", -2: "MD_ENOMEM", -3: "MD_ECUDA", -4: "MD_ENBR_OVERFLOW", -5: "MD_EUNSTABLE",
-          -6: "MD_ETIMEOUT", -7: "MD_ENOTRAINED"}
+          -6: "MD_ETIMEOUT", -7: "MD_ENOTRAINED", -8: "MD_ETOOLARGE"}
+MD_PHILOX_STATIC_MAX = 16384
 
 
 class MdError(RuntimeError):
@@ -88,6 +89,21 @@ def md_philox(ctr, key, use_library=False):
     return out
 
 
+def md_philox_static(ctr, key, use_library=False):
+    """md_philox with the library's static device scratch (no allocation);
+    at most MD_PHILOX_STATIC_MAX blocks per call."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(2)
+    out = np.zeros_like(ctr)
+    u32p = C.POINTER(C.c_uint32)
+    rc = lib().md_philox_static(ctr.ctypes.data_as(u32p), key.ctypes.data_as(u32p), ctr.shape[0],
+                                out.ctypes.data_as(u32p), int(use_library))
+    if rc:
+        raise MdError(rc, f"md_philox_static: {ctr.shape[0]} blocks (static scratch holds "
+                          f"{MD_PHILOX_STATIC_MAX})")
+    return out
+
+
 def library_path():
     return os.path.join(HERE, "_lib", "libmsm.so")
 
@@ -127,6 +143,7 @@ def lib():
     L.md_profile_enable.argtypes = [vp, C.c_int]
     L.md_profile_read.argtypes = [vp, C.POINTER(md_profile_t), C.c_int]
     L.md_philox.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), i64, C.POINTER(C.c_uint32), C.c_int]
+    L.md_philox_static.argtypes = L.md_philox.argtypes
     L.md_platelet_features.argtypes = [vp, dp]
     L.md_record_features.argtypes = [vp]
     L.md_read_feature_ring.argtypes = [vp, fp, C.POINTER(C.c_int64)]
@@ -136,7 +153,7 @@ def lib():
                  "md_neighbor_build", "md_forces", "md_read_forces", "md_read_particles", "md_mts_step",
                  "md_set_platelet_levels",
                  "md_observables", "md_neighbor_pairs", "md_get_state", "md_set_state", "md_profile_enable",
-                 "md_profile_read", "md_philox"):
+                 "md_profile_read", "md_philox", "md_philox_static"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -3,6 +3,8 @@
 // cuRAND's generator for cross-checking.
 #include <curand_kernel.h>
 
+#include <mutex>
+
 #include "msm_internal.cuh"
 
 namespace {
@@ -67,6 +69,16 @@ void prof_end(md_system *s)
     s->prof_cls = -1;
 }
 
+// Staging buffers of md_philox_static: counters in [0, MAX), outputs in
+// [MAX, 2 MAX).  Keeps the last call's contents; calls on one device share it.
+static __device__ __align__(256) uint4 philox_scratch[2 * MD_PHILOX_STATIC_MAX];
+
+namespace {
+constexpr int SCRATCH_DEVICES = 64;
+std::mutex scratch_mu;
+uint4 *scratch_addr[SCRATCH_DEVICES] = {};   // device address per device ordinal
+}  // namespace
+
 extern "C" {
 
 int md_profile_enable(md_system *s, int enable)
@@ -123,6 +135,44 @@ int md_philox(const uint32_t *ctr, const uint32_t key[2], int64_t n, uint32_t *o
     if (e == cudaSuccess) e = cudaMemcpy(out, d_out, sizeof(uint4) * n, cudaMemcpyDeviceToHost);
     if (d_ctr) cudaFree(d_ctr);
     if (d_out) cudaFree(d_out);
+    return e == cudaSuccess ? MD_OK : MD_ECUDA;
+}
+
+int md_philox_static(const uint32_t *ctr, const uint32_t key[2], int64_t n, uint32_t *out, int use_library)
+{
+    if (n < 0 || (n > 0 && (!ctr || !key || !out))) return MD_EINVAL;
+    if (n > MD_PHILOX_STATIC_MAX) return MD_ETOOLARGE;
+    if (n == 0) return MD_OK;
+    if (use_library)
+        for (int64_t k = 0; k < n; ++k)
+            if (ctr[4 * k + 1] >= (1u << 30)) return MD_EINVAL;  // 4*counter must fit the 64-bit offset
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return MD_ECUDA;
+    if (dev < 0 || dev >= SCRATCH_DEVICES) return MD_EINVAL;
+    uint4 *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(scratch_mu);
+        if (!scratch_addr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, philox_scratch);
+            if (e != cudaSuccess) return MD_ECUDA;
+            scratch_addr[dev] = (uint4 *)p;
+        }
+        base = scratch_addr[dev];
+    }
+    uint4 *d_ctr = base, *d_out = base + MD_PHILOX_STATIC_MAX;
+    e = cudaMemcpy(d_ctr, ctr, sizeof(uint4) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const unsigned blocks = (unsigned)((n + 255) / 256);
+        if (use_library)
+            k_philox_curand<<<blocks, 256>>>(n, d_ctr, (unsigned long long)key[0] | ((unsigned long long)key[1] << 32),
+                                             d_out);
+        else
+            k_philox_own<<<blocks, 256>>>(n, d_ctr, make_uint2(key[0], key[1]), d_out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, d_out, sizeof(uint4) * n, cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? MD_OK : MD_ECUDA;
 }
 
