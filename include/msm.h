@@ -169,7 +169,8 @@ int md_forces(md_system *sys, uint32_t level_mask, uint32_t flags);
 
 /*
  * Copy the sum of the level forces in level_mask to HOST f[n*3] (FP64, id
- * order).  Synchronises the stream.  Errors: MD_EINVAL, MD_ECUDA.
+ * order); stale forces (new particles, or after an AI-MTS call) are
+ * recomputed first.  Synchronises the stream.  Errors: MD_EINVAL, MD_ECUDA.
  */
 int md_read_forces(md_system *sys, uint32_t level_mask, double *f);
 
@@ -211,17 +212,19 @@ int md_mts_step(md_system *sys, int64_t n_outer, const md_mts_schedule *sched);
 /*
  * AI-MTS step ratios (Sec. 3.3, Table 2): k[P] (HOST, P = cfg.n_platelets)
  * platelet substeps per interface step for each platelet, as the controller
- * predicts them (classes {1, 2, 5, 10, 20}).  MD_MODE_AI then runs the
- * platelet level on the fine grid of K = lcm(k) substeps of dt_m / K:
- * platelet p is due every K / k_p substeps, when it kicks with its last
- * platelet-level force (a half kick at its first substep, two fused half
- * kicks afterwards), drifts dt_m / k_p and has that force re-evaluated
- * (bonds, LJ and Morse on its own particles; partners not due are read at
- * their current positions); every platelet closes the interface step with a
- * half kick.  With all k_p equal this is MD_MODE_RESPA with that k_p.
- * Each k_p >= 1 and K <= MD_AI_K_LCM_MAX.  Copies synchronously; the values
- * may change between md_mts_step calls (a new K recaptures the step graph).
- * Errors: MD_EINVAL (no platelets, k out of range), MD_ECUDA.
+ * predicts them (classes {1, 2, 5, 10, 20}).  MD_MODE_AI then cuts each
+ * interface step into K = lcm(k) substeps of dt_m / K in which every
+ * platelet particle drifts.  Each platelet-level term -- a bond, an LJ or a
+ * Morse pair -- lives on the grid of the finer of its two platelets,
+ * c = max(k_i, k_j), and is integrated there by velocity-Verlet with step
+ * dt_m / c: half kicks at the ends of the interface step, full kicks at its
+ * interior points K/c, 2K/c, ...  Both ends of a pair get the same impulse at
+ * the same time, so momentum is conserved, and with all k_p equal this is
+ * MD_MODE_RESPA with that k_p.  During an AI-MTS call the platelet force
+ * buffer holds impulses; plain forces are recomputed by the next call that
+ * needs them.  Each k_p >= 1 and K <= MD_AI_K_LCM_MAX.  Copies synchronously;
+ * the ratios may change between md_mts_step calls (a new K recaptures the
+ * step graph).  Errors: MD_EINVAL (no platelets, k out of range), MD_ECUDA.
  */
 #define MD_AI_K_LCM_MAX 64
 int md_set_platelet_levels(md_system *sys, const int32_t *k);

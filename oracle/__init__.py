@@ -42,6 +42,7 @@ class Params(C.Structure):
         ("m_rc", C.c_double), ("f_A", C.c_double),
         ("k_b", C.c_double),
         ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32),
+        ("plt_k", C.POINTER(C.c_int32)), ("lvl_k", C.c_int32),
     ]
 
 
@@ -101,7 +102,7 @@ def lib():
         L.orc_kinetics.argtypes = [P, C.c_int32, dp, dp, ip, C.c_int32, dp, dp, dp]
         L.orc_run_sts.argtypes = [P, C.c_int32, C.c_int32, dp, dp, ip, ip, dp, ip, dp,
                                   C.c_double, C.c_int32, C.c_uint32, C.c_double, C.c_int32, dp]
-        L.orc_run_ai_respa.argtypes = [P, C.c_int32, C.c_int32, dp, dp, ip, ip, dp, ip, dp, ip, C.c_int32,
+        L.orc_run_ai_respa.argtypes = [P, C.c_int32, C.c_int32, dp, dp, ip, ip, dp, ip, dp, ip, C.c_int32, C.c_int32,
                                        C.c_double, C.c_int32, C.c_int32, C.c_uint32, C.c_double, C.c_int32,
                                        dp, dp, dp]
         _lib = L
@@ -277,7 +278,8 @@ def run_respa(p, x, v, tag, X0=None, bonds=None, r0=None, ids=None, dt_f=0.01, k
 
 def run_ai_respa(p, x, v, tag, plt_k, X0=None, bonds=None, r0=None, ids=None, dt_f=0.01, k_m=1, n_outer=1,
                  n0=0, t0=0.0, forces=None):
-    """AI-MTS: Table 1 with per-platelet step ratios plt_k[P].  Returns (x, v, forces)."""
+    """AI-MTS: Table 1 with per-platelet step ratios plt_k[P].  Returns (x, v, (f_f, f_m, J)),
+    J the platelet-level impulse of the last evaluation point (every term due)."""
     import math
     n = x.shape[0]
     x = np.array(x, dtype=np.float64, order="C")
@@ -302,7 +304,7 @@ def run_ai_respa(p, x, v, tag, plt_k, X0=None, bonds=None, r0=None, ids=None, dt
         init = 0
     dp = C.POINTER(C.c_double)
     lib().orc_run_ai_respa(C.byref(p), n, bonds.shape[0], x.ctypes.data_as(dp), v.ctypes.data_as(dp), idp, tp,
-                           X0p, bp, rp, pkp, K, dt_f, k_m, n_outer, n0, t0, init, ff.ctypes.data_as(dp),
+                           X0p, bp, rp, pkp, len(pk), K, dt_f, k_m, n_outer, n0, t0, init, ff.ctypes.data_as(dp),
                            fm.ctypes.data_as(dp), fpl.ctypes.data_as(dp))
     return x, v, (ff, fm, fpl)
 

@@ -50,7 +50,19 @@ typedef struct {
     double m_D, m_alpha, m_r0, m_rc, f_A;
     double k_b;
     uint32_t seed_lo, seed_hi;
+    /* AI-MTS term selection (NULL: every term): with plt_k[P] set, a
+     * platelet-level term counts only if the finer of its two platelets'
+     * ratios, max(k_i, k_j), equals lvl_k */
+    const int32_t *plt_k;
+    int32_t lvl_k;
 } orc_params;
+
+static int term_selected(const orc_params *p, int32_t ti, int32_t tj)
+{
+    if (!p->plt_k) return 1;
+    int32_t ki = p->plt_k[ti & ~REC_BIT], kj = p->plt_k[tj & ~REC_BIT];
+    return (ki > kj ? ki : kj) == p->lvl_k;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (SC'11) and the Gaussian                                    */
@@ -259,6 +271,7 @@ static int pair_force(const pair_ctx *c, int32_t i, int32_t j, double *F, double
     }
     /* platelet-platelet: LJ (Eq. 2) with the rest-distance exclusion, Morse +
      * receptor term between receptors of different platelets (Eq. 4) */
+    if (!term_selected(p, ti, tj)) return 0;
     int32_t pi = ti & ~REC_BIT, pj = tj & ~REC_BIT;
     double fsum = 0.0, usum = 0.0;
     int lj_on = 1;
@@ -351,6 +364,7 @@ void orc_forces_brute(const orc_params *p, int32_t n, const double *x, const dou
         for (int32_t b = 0; b < nb; ++b) {
             int32_t i = bonds[2 * b], j = bonds[2 * b + 1];
             double F[3], u, rij[3];
+            if (!term_selected(p, tag[i], tag[j])) continue;
             bond_force(p, x, i, j, r0[b], F, &u, rij);
             for (int k = 0; k < 3; ++k) { f[3 * i + k] += F[k]; f[3 * j + k] -= F[k]; }
             acc.epot += u;
@@ -515,6 +529,7 @@ void orc_forces_cells(const orc_params *p, int32_t n, const double *x, const dou
             if ((level_mask & LVL_PLT) && bond_off) {
                 for (int32_t b = bond_off[i]; b < bond_off[i + 1]; ++b) {
                     double F[3], u, rij[3];
+                    if (!term_selected(p, tag[i], tag[bond_nbr[b]])) continue;
                     bond_force(p, x, i, bond_nbr[b], bond_r0[b], F, &u, rij);
                     fi[0] += F[0]; fi[1] += F[1]; fi[2] += F[2];
                 }
@@ -782,27 +797,45 @@ void orc_run_respa(orc_params *p, int32_t n, int32_t nb, double *x, double *v,
 }
 
 /*
- * AI-MTS (Sec. 3.3): Table 1 with a per-platelet step ratio.  Platelet p
- * takes k_p substeps of dt_m / k_p per interface step; on the fine grid of
- * K = lcm(k_p) substeps it is due every K / k_p substeps.  Plasma and walls
- * feel no platelet-level force and drift every fine substep.  At a due
- * substep a platelet's particles kick with their last platelet-level force
- * (half at the first substep, full afterwards -- two fused half kicks),
- * drift by dt_m / k_p, and their platelet-level force is re-evaluated (the
- * full force on each due particle, partners due or not); particles not due
- * keep their last force.  The interface step ends with the closing half kick
- * of every platelet particle.  plt_k[P] holds the ratios; K is their lcm.
+ * AI-MTS (Sec. 3.3): Table 1 with a step ratio k_p per platelet (plt_k[P]).
+ * The interface step is cut into K = lcm(k_p) fine substeps dts = dt_m / K,
+ * and every mobile particle drifts by dts in each of them.  A platelet-level
+ * term (a bond, an LJ or a Morse pair) belongs to the grid of the finer of
+ * its two platelets, c = max(k_i, k_j), and is integrated by velocity-Verlet
+ * with the step dt_m / c on that grid: a half kick at the start of the
+ * interface step, a full kick (closing + opening) at each interior point
+ * K/c, 2K/c, ..., and a half kick at the end.  The kicks of the terms due at
+ * one point are summed as the impulse J = sum_c (dt_m / c) F^(c).  With all
+ * k_p equal this is the RESPA loop above.  f_p holds J of the last point
+ * (all terms due) instead of a force.
  */
+static void eval_impulse(orc_params *p, const orc_state *s, const bond_csr_t *csr, const int32_t *plt_k,
+                         int32_t P, int32_t K, int32_t qe, double dt_m, double *tmp, double *J)
+{
+    memset(J, 0, (size_t)3 * s->n * sizeof(double));
+    for (int32_t c = 1; c <= K; ++c) {
+        if (K % c != 0 || qe % (K / c) != 0) continue;
+        int used = 0;
+        for (int32_t q = 0; q < P; ++q) used |= plt_k[q] == c;
+        if (!used) continue;
+        p->plt_k = plt_k;
+        p->lvl_k = c;
+        eval_level(p, s, csr, LVL_PLT, 0, 0, 1.0, dt_m, tmp);
+        p->plt_k = NULL;
+        for (int64_t k = 0; k < 3 * (int64_t)s->n; ++k) J[k] += dt_m / c * tmp[k];
+    }
+}
+
 void orc_run_ai_respa(orc_params *p, int32_t n, int32_t nb, double *x, double *v,
                       const int32_t *id, const int32_t *tag, const double *X0,
-                      const int32_t *bonds, const double *r0, const int32_t *plt_k, int32_t K,
+                      const int32_t *bonds, const double *r0, const int32_t *plt_k, int32_t P, int32_t K,
                       double dt_f, int32_t k_m, int32_t n_outer, uint32_t n0, double t0,
                       int32_t compute_initial, double *f_f, double *f_m, double *f_p)
 {
     orc_state s = {n, nb, x, v, id, tag, X0, bonds, r0};
     bond_csr_t csr;
     bond_csr_build(n, nb, bonds, r0, &csr);
-    double *fnew = (double *)malloc((size_t)3 * (n > 0 ? n : 1) * sizeof(double));
+    double *tmp = (double *)malloc((size_t)3 * (n > 0 ? n : 1) * sizeof(double));
     const double dt_m = dt_f / k_m, dts = dt_m / K;
     double t = t0;
     if (p->le) {
@@ -812,7 +845,7 @@ void orc_run_ai_respa(orc_params *p, int32_t n, int32_t nb, double *x, double *v
     if (compute_initial) {
         eval_level(p, &s, &csr, LVL_FLUID, n0, 0, dt_f, dt_m, f_f);
         eval_level(p, &s, &csr, LVL_IFACE, n0, 0, dt_f, dt_m, f_m);
-        eval_level(p, &s, &csr, LVL_PLT, n0, 0, dt_f, dt_m, f_p);
+        eval_impulse(p, &s, &csr, plt_k, P, K, K, dt_m, tmp, f_p);
     }
     for (int32_t so = 0; so < n_outer; ++so) {
         uint32_t nn = n0 + (uint32_t)so;
@@ -820,37 +853,11 @@ void orc_run_ai_respa(orc_params *p, int32_t n, int32_t nb, double *x, double *v
         for (int32_t c = 0; c < k_m; ++c) {
             kick(&s, f_m, 0.5 * dt_m);
             for (int32_t q = 0; q < K; ++q) {
-                t += dts;
-                if (p->le) {
-                    p->le_offset = fmod(p->le_rate * p->L[1] * t, p->L[0]);
-                    if (p->le_offset < 0.0) p->le_offset += p->L[0];
-                }
-                for (int32_t i = 0; i < n; ++i) {
-                    if (tag[i] == TAG_WALL) continue;
-                    double dt_i = dts;
-                    if (tag[i] >= 0) {
-                        const int32_t kp = plt_k[tag[i] & ~REC_BIT];
-                        if (q % (K / kp) != 0) continue;
-                        dt_i = dt_m / kp;
-                        const double h = (q == 0 ? 0.5 : 1.0) * dt_i;
-                        for (int k = 0; k < 3; ++k) v[3 * i + k] += h * f_p[3 * i + k];
-                    }
-                    for (int k = 0; k < 3; ++k) x[3 * i + k] += dt_i * v[3 * i + k];
-                    apply_boundaries(p, x + 3 * i, v + 3 * i);
-                }
-                eval_level(p, &s, &csr, LVL_PLT, 0, 0, dt_f, dt_m, fnew);
-                for (int32_t i = 0; i < n; ++i) {
-                    if (tag[i] < 0) continue;
-                    const int32_t kp = plt_k[tag[i] & ~REC_BIT];
-                    if (q % (K / kp) != 0) continue;
-                    for (int k = 0; k < 3; ++k) f_p[3 * i + k] = fnew[3 * i + k];
-                }
+                kick(&s, f_p, q == 0 ? 0.5 : 1.0);
+                drift(p, &s, dts, &t);
+                eval_impulse(p, &s, &csr, plt_k, P, K, q + 1, dt_m, tmp, f_p);
             }
-            for (int32_t i = 0; i < n; ++i) {
-                if (tag[i] < 0) continue;
-                const double h = 0.5 * dt_m / plt_k[tag[i] & ~REC_BIT];
-                for (int k = 0; k < 3; ++k) v[3 * i + k] += h * f_p[3 * i + k];
-            }
+            kick(&s, f_p, 0.5);
             uint32_t nt = (c + 1 == k_m) ? nn + 1 : nn;
             uint32_t cs = (c + 1 == k_m) ? 0u : (uint32_t)(c + 1);
             eval_level(p, &s, &csr, LVL_IFACE, nt, cs, dt_f, dt_m, f_m);
@@ -859,7 +866,7 @@ void orc_run_ai_respa(orc_params *p, int32_t n, int32_t nb, double *x, double *v
         eval_level(p, &s, &csr, LVL_FLUID, nn + 1, 0, dt_f, dt_m, f_f);
         kick(&s, f_f, 0.5 * dt_f);
     }
-    free(fnew);
+    free(tmp);
     free(csr.off); free(csr.nbr); free(csr.r0);
 }
 

@@ -456,29 +456,26 @@ int enqueue_outer_step(md_system *s, int mode, int k_m, int k_p, bool first, cap
         const unsigned zero = (plt ? MD_LEVEL_IFACE : 0u) | (ci == 0 ? MD_LEVEL_FLUID : 0u);
         RC(enqueue_kd(s, h, DRIFT_ALL, dtm, plt ? DRIFT_FLUID : DRIFT_ALL, zero, false));
         if (plt && mode == MD_MODE_AI) {
-            // B (AI-MTS): K = lcm(k_p) fine substeps of dt_m / K; platelet p
-            //    is due every K/k_p of them and then kicks, drifts dt_m / k_p
-            //    and refreshes its platelet-level force; the kernels take the
-            //    per-platelet step sizes from plt_k on the device.
+            // B (AI-MTS): every platelet particle drifts on the fine grid of
+            //    K = lcm(k) substeps of dt_m / K; the platelet buffer holds
+            //    impulses, so substep q kicks by 1/2 (q = 0) or 1 (fused
+            //    closing + opening) of the terms due at its start, and the
+            //    terms due at its end are evaluated after the drift.
             const int K = s->plt_K;
             const double dts = dtm / K;
-            s->due_on = true;
-            s->due_dtm = dtm;
-            int rc = MD_OK;
-            for (int q = 0; q < K && rc == MD_OK; ++q) {
-                s->due_q = q;
-                rc = enqueue_time(s, dn, c_end, tc + (q + 1) * dts);
-                const float hq[3] = {0.f, 0.f, 1.f};   // replaced per platelet
-                if (rc == MD_OK) rc = enqueue_kd(s, hq, DRIFT_PLT, dts, DRIFT_PLT, MD_LEVEL_PLT, true);
-                if (rc == MD_OK) rc = enqueue_forces(s, MD_LEVEL_PLT);
+            for (int q = 0; q < K; ++q) {
+                RC(enqueue_time(s, dn, c_end, tc + (q + 1) * dts));
+                const float hq[3] = {0.f, 0.f, q == 0 ? 0.5f : 1.0f};
+                RC(enqueue_kd(s, hq, DRIFT_PLT, dts, DRIFT_PLT, MD_LEVEL_PLT, true));
+                s->due_on = true;
+                s->due_q = q + 1;
+                s->due_dtm = dtm;
+                const int rc = enqueue_forces(s, MD_LEVEL_PLT);
+                s->due_on = false;
+                if (rc != MD_OK) return rc;
             }
-            s->due_closing = true;
-            const float hc[3] = {0.f, 0.f, 1.f};
-            if (rc == MD_OK) rc = enqueue_kd(s, hc, DRIFT_PLT, 0.0, -1, 0u, true);
-            s->due_on = false;
-            s->due_closing = false;
-            s->due_q = 0;
-            if (rc != MD_OK) return rc;
+            const float hc[3] = {0.f, 0.f, 0.5f};
+            RC(enqueue_kd(s, hc, DRIFT_PLT, 0.0, -1, 0u, true));
         } else if (plt) {
             // B: platelet substeps; the kick of substep q fuses the closing
             //    half-kick of q-1 with its own opening half-kick
@@ -898,6 +895,8 @@ int md_forces(md_system *s, uint32_t level_mask, uint32_t flags)
 int md_read_forces(md_system *s, uint32_t level_mask, double *f)
 {
     if (!s || !f) return MD_EINVAL;
+    const int rc = ensure_forces(s);
+    if (rc) return rc;
     const int64_t n = s->n;
     const float4 *f0 = (level_mask & MD_LEVEL_FLUID) ? s->f[0] : nullptr;
     const float4 *f1 = (level_mask & MD_LEVEL_IFACE) ? s->f[1] : nullptr;
@@ -960,6 +959,17 @@ int md_mts_step(md_system *s, int64_t n_outer, const md_mts_schedule *sched)
     int rc = ensure_forces(s);
     if (rc) return rc;
     const md_config &c = s->cfg;
+    if (mode == MD_MODE_AI) {
+        // the platelet buffer switches to impulses: every term due (qe = K)
+        CK(cudaMemsetAsync(s->f[2], 0, sizeof(float4) * s->n, s->stream), "zero platelet level");
+        s->due_on = true;
+        s->due_q = s->plt_K;
+        s->due_dtm = c.dt / k_m;
+        rc = enqueue_forces(s, MD_LEVEL_PLT);
+        s->due_on = false;
+        if (rc) return rc;
+        s->forces_stale = true;   // plain forces again at the next call that needs them
+    }
     rc = enqueue_outer_step(s, mode, k_m, k_p, true, nullptr);
     if (rc) return rc;
     const int64_t rest = n_outer - 1;

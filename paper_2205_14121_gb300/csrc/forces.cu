@@ -33,16 +33,10 @@ struct pair_args {
     float lj_eps24, lj_sig2, lj_rc2;
     float m_Da_r0, m_alpha, m_inv_r0, m_rc2, f_A;
     double *vir;
-    // AI-MTS: only pairs with a due end are evaluated, and only due ends receive
-    // the force (a platelet keeps its last force until its next substep)
+    // AI-MTS: platelet-level pairs scaled to impulses, or skipped, per term_scale
     md_due due;
     const int32_t *tag;
 };
-
-__device__ __forceinline__ bool due_of(const pair_args &a, int32_t i)
-{
-    return a.due.plt_k ? platelet_due(a.due, a.tag[i]) : true;
-}
 
 struct vir6 {
     float xx, yy, zz, xy, xz, yz;
@@ -237,12 +231,12 @@ __global__ void __launch_bounds__(MSM_TPB) k_lj(pair_args a)
         if (cnt > 0) {
             const float4 xi = a.x32[i];
             const float delta = a.ds->le_offset_f;
-            const bool di = due_of(a, i);
+            const int32_t ti = a.due.plt_k ? a.tag[i] : 0;
             float fx = 0.f, fy = 0.f, fz = 0.f;
             for (int k = 0; k < cnt; ++k) {
                 const int32_t j = a.nl[r * a.cap + k];
-                const bool dj = due_of(a, j);
-                if (!di && !dj) continue;
+                const float sc = a.due.plt_k ? term_scale(a.due, ti, a.tag[j]) : 1.0f;
+                if (sc == 0.0f) continue;
                 const float4 xj = a.x32[j];
                 float dx, dy, dz, vsh;
                 min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
@@ -251,13 +245,13 @@ __global__ void __launch_bounds__(MSM_TPB) k_lj(pair_args a)
                 const float inv_r2 = 1.0f / r2;
                 const float s2 = a.lj_sig2 * inv_r2;
                 const float s6 = s2 * s2 * s2;
-                const float fr = a.lj_eps24 * (2.0f * s6 * s6 - s6) * inv_r2;
+                const float fr = a.lj_eps24 * (2.0f * s6 * s6 - s6) * inv_r2 * sc;
                 const float px = fr * dx, py = fr * dy, pz = fr * dz;
-                if (di) { fx += px; fy += py; fz += pz; }
-                if (dj) scatter(a.f, j, -px, -py, -pz);
+                fx += px; fy += py; fz += pz;
+                scatter(a.f, j, -px, -py, -pz);
                 if (VIR) w.add(dx, dy, dz, fr);
             }
-            if (di) scatter(a.f, i, fx, fy, fz);
+            scatter(a.f, i, fx, fy, fz);
         }
     }
     if (VIR) flush_virial(a.vir, w);
@@ -275,12 +269,12 @@ __global__ void __launch_bounds__(MSM_TPB) k_morse(pair_args a)
         if (cnt > 0) {
             const float4 xi = a.x32[i];
             const float delta = a.ds->le_offset_f;
-            const bool di = due_of(a, i);
+            const int32_t ti = a.due.plt_k ? a.tag[i] : 0;
             float fx = 0.f, fy = 0.f, fz = 0.f;
             for (int k = 0; k < cnt; ++k) {
                 const int32_t j = a.nl[r * a.cap + k];
-                const bool dj = due_of(a, j);
-                if (!di && !dj) continue;
+                const float sc = a.due.plt_k ? term_scale(a.due, ti, a.tag[j]) : 1.0f;
+                if (sc == 0.0f) continue;
                 const float4 xj = a.x32[j];
                 float dx, dy, dz, vsh;
                 min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
@@ -290,13 +284,13 @@ __global__ void __launch_bounds__(MSM_TPB) k_morse(pair_args a)
                 const float rr = r2 * inv_r;
                 const float t = a.m_alpha * (1.0f - rr * a.m_inv_r0);
                 const float fm = a.m_Da_r0 * (expf(t) - expf(0.5f * t)) + a.f_A * (1.0f - rr * a.m_inv_r0);
-                const float s = fm * inv_r;
+                const float s = fm * inv_r * sc;
                 const float px = s * dx, py = s * dy, pz = s * dz;
-                if (di) { fx += px; fy += py; fz += pz; }
-                if (dj) scatter(a.f, j, -px, -py, -pz);
+                fx += px; fy += py; fz += pz;
+                scatter(a.f, j, -px, -py, -pz);
                 if (VIR) w.add(dx, dy, dz, s);
             }
-            if (di) scatter(a.f, i, fx, fy, fz);
+            scatter(a.f, i, fx, fy, fz);
         }
     }
     if (VIR) flush_virial(a.vir, w);
@@ -311,8 +305,9 @@ __global__ void __launch_bounds__(MSM_TPB) k_bonds(int64_t nb, const int32_t *__
 {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     vir6 w = {0, 0, 0, 0, 0, 0};
-    // both ends belong to one platelet: skip the bonds of platelets not due
-    if (b < nb && (!due.plt_k || platelet_due(due, tag[ij[2 * b]]))) {
+    // both ends belong to one platelet: the bond lives on that platelet's grid
+    const float sc = (b < nb && due.plt_k) ? term_scale(due, tag[ij[2 * b]], tag[ij[2 * b]]) : 1.0f;
+    if (b < nb && sc != 0.0f) {
         const int32_t i = ij[2 * b], j = ij[2 * b + 1];
         float dx, dy, dz, vsh;
         min_image_f32(geom, ds->le_offset_f, x32[i], x32[j], dx, dy, dz, vsh);
@@ -320,7 +315,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_bonds(int64_t nb, const int32_t *__
         if (r2 > 0.0f) {
             const float inv_r = rsqrtf(r2);
             const float rr = r2 * inv_r;
-            const float s = -kb2 * (rr - r0[b]) * inv_r;
+            const float s = -kb2 * (rr - r0[b]) * inv_r * sc;
             scatter(f, i, s * dx, s * dy, s * dz);
             scatter(f, j, -s * dx, -s * dy, -s * dz);
             if (VIR) w.add(dx, dy, dz, s);
@@ -358,8 +353,9 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
     a.vir = s->vir_acc;
     a.tag = s->tag_s;
     a.due.plt_k = s->due_on ? s->plt_k : nullptr;
-    a.due.q = s->due_q;
+    a.due.qe = s->due_q;
     a.due.K = s->plt_K;
+    a.due.dtm = (float)s->due_dtm;
     const int km = s->cfg_k_m > 0 ? s->cfg_k_m : 1;
 
     if (level_mask & MD_LEVEL_FLUID) {

@@ -37,10 +37,6 @@ struct kd_args {
     md_geom geom;
     const md_dstate *ds;
     int32_t *ctl;
-    // AI-MTS: platelets kick / drift / clear with their own substep dt_m / k_p
-    md_due due;
-    double dtm;
-    int closing;
 };
 
 __device__ __forceinline__ bool selected(int which, int32_t t)
@@ -57,34 +53,16 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
     if (r >= a.n) return;
     const int64_t k = a.idx ? a.idx[r] : r;
     const int32_t t = a.tag[k];
-    bool kick = selected(a.kick_which, t);
-    bool drift = selected(a.drift_which, t);
-    float h[3] = {a.h[0], a.h[1], a.h[2]};
-    double dt = a.dt;
-    unsigned zero_levels = a.zero_levels;
-    if (a.due.plt_k && t >= 0) {
-        // platelet p moves on its own grid: dt_p = dt_m / k_p, due every K/k_p fine substeps
-        const int kp = a.due.plt_k[t & ~MD_RECEPTOR_BIT];
-        const double dtp = a.dtm / kp;
-        if (a.closing) {
-            h[2] = (float)(0.5 * dtp);
-        } else {
-            const bool due = (a.due.q % (a.due.K / kp)) == 0;
-            h[2] = due ? (float)((a.due.q == 0 ? 0.5 : 1.0) * dtp) : 0.f;
-            dt = dtp;
-            drift = drift && due;
-            kick = kick && due;
-            if (!due) zero_levels &= ~MD_LEVEL_PLT;
-        }
-    }
+    const bool kick = selected(a.kick_which, t);
+    const bool drift = selected(a.drift_which, t);
     if (kick || drift) {
         float4 vv = a.v[k];
         if (kick) {
             float ax = 0.f, ay = 0.f, az = 0.f;
             for (int l = 0; l < a.nf; ++l) {
-                if (h[l] == 0.0f) continue;
+                if (a.h[l] == 0.0f) continue;
                 const float4 fl = a.f[l][k];
-                ax += h[l] * fl.x; ay += h[l] * fl.y; az += h[l] * fl.z;
+                ax += a.h[l] * fl.x; ay += a.h[l] * fl.y; az += a.h[l] * fl.z;
             }
             ax += a.h[0] * a.g;
             vv.x += ax;
@@ -96,9 +74,9 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
             // the wrap decisions are taken on the rounded FP32 copies (a
             // double >= L always rounds to a float >= (float)L) and the FP64
             // arithmetic is redone only for the few particles that wrap.
-            double x = fma(dt, (double)vv.x, a.xs[k]);
-            double y = fma(dt, (double)vv.y, a.ys[k]);
-            double z = fma(dt, (double)vv.z, a.zs[k]);
+            double x = fma(a.dt, (double)vv.x, a.xs[k]);
+            double y = fma(a.dt, (double)vv.y, a.ys[k]);
+            double z = fma(a.dt, (double)vv.z, a.zs[k]);
             const double Lx = a.L[0], Ly = a.L[1], Lz = a.L[2];
             float xf = (float)x, yf = (float)y, zf = (float)z;
             if (a.geom.walls) {
@@ -158,7 +136,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
         a.v[k] = vv;
     }
     for (int l = 0; l < a.nf; ++l)
-        if (zero_levels & (1u << l)) a.f[l][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (a.zero_levels & (1u << l)) a.f[l][k] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Set the device time index (n, c) and the time n dt + c dt_m + q dt_p;
@@ -253,11 +231,6 @@ kd_args base_args(md_system *s)
     a.kick_which = -1;
     a.drift_which = -1;
     a.zero_levels = 0;
-    a.due.plt_k = s->due_on ? s->plt_k : nullptr;
-    a.due.q = s->due_q;
-    a.due.K = s->plt_K;
-    a.dtm = s->due_dtm;
-    a.closing = s->due_closing ? 1 : 0;
     return a;
 }
 

@@ -108,10 +108,10 @@ struct md_system {
     int32_t *plt_k = nullptr;    // device [P]
     std::vector<int32_t> h_plt_k;
     int plt_K = 1;
-    // schedule of the platelet launches being enqueued (AI-MTS substep q of K;
-    // plt_k null outside AI-MTS), read by launch_kick_drift / launch_forces
+    // AI-MTS evaluation point of the next platelet-level launch_forces (due_on
+    // false: plain forces)
     int due_q = 0;
-    bool due_on = false, due_closing = false;
+    bool due_on = false;
     double due_dtm = 0.0;
 
     // scan scratch
@@ -296,18 +296,22 @@ __device__ __forceinline__ int64_t cell_index(const md_grid &g, int cx, int cy, 
 
 __device__ __forceinline__ bool gate_closed(const int32_t *gate) { return gate && *gate == 0; }
 
-// AI-MTS substep schedule: on the fine grid of K substeps per interface
-// step, platelet p (ratio k_p) is due every K/k_p substeps.
+// AI-MTS (Sec. 3.3): every platelet-level term (a bond, an LJ or a Morse pair)
+// lives on the grid of the finer of its platelets, c = max(k_i, k_j), of the
+// K = lcm(k) substeps per interface step.  At evaluation point qe (1..K) the
+// term is due when qe is a multiple of K/c, and it is stored as the impulse
+// (dt_m / c) F it applies; terms not due contribute nothing.
 struct md_due {
-    const int32_t *plt_k;   // null: every platelet is due (fixed-k RESPA)
-    int q, K;
+    const int32_t *plt_k;   // null: plain forces (STS, fixed-k RESPA)
+    int qe, K;
+    float dtm;
 };
 
-__device__ __forceinline__ bool platelet_due(const md_due &d, int32_t tag)
+__device__ __forceinline__ float term_scale(const md_due &d, int32_t ti, int32_t tj)
 {
-    if (!d.plt_k) return true;
-    const int kp = d.plt_k[tag & ~MD_RECEPTOR_BIT];
-    return (d.q % (d.K / kp)) == 0;
+    if (!d.plt_k) return 1.0f;
+    const int c = max(d.plt_k[ti & ~MD_RECEPTOR_BIT], d.plt_k[tj & ~MD_RECEPTOR_BIT]);
+    return (d.qe % (d.K / c)) == 0 ? d.dtm / (float)c : 0.0f;
 }
 
 // ---------------------------------------------------------------------------
