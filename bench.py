@@ -169,6 +169,20 @@ def ncu_traffic(workload_name):
     return None
 
 
+def whole_job_rate(units_local, seconds_local, world, device="cpu"):
+    """Replicas: units processed by all ranks / the slowest rank's time.
+    Returns (units_total, seconds_max); collective only when world > 1."""
+    if world <= 1:
+        return float(units_local), float(seconds_local)
+    import torch
+    import torch.distributed as dist
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -253,13 +267,11 @@ def main():
         barrier()
     ms = ev0.elapsed_time(ev1)
     prof_plain = g.profile_read(reset=True)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    sec = ms / 1e3
-    value = ns_per_day(args.steps, sec, wl["dt"]) * world
-    ps = n * args.steps / sec * world
+    # whole job: every rank's particle-steps over the slowest rank's time
+    units, sec = whole_job_rate(n * args.steps, ms / 1e3, world, device="cuda")
+    ms = sec * 1e3
+    ps = units / sec
+    value = ns_per_day(args.steps, sec, wl["dt"]) * (units / (n * args.steps))
 
     # ---- roofline pass: same K steps with per-class CUDA events ----------
     g.profile_enable(True)
