@@ -1,12 +1,18 @@
 #!/usr/bin/env python
 """Throughput benchmark of the DPD-CGMD engine on synthetic systems.
 
-Default workload (N = 1): the DPD-only throughput system -- 1,000,000 plasma
-particles at rho = 3 in a 69.336^3 box with frozen walls in y and a
-Poiseuille body force g = 0.02, velocity-Verlet at dt = 0.01 (one reduced time
-unit = 166.4 ns, so a step is 1.664 ns), Verlet skin 0.3.  One "step" is one
-fluid step of the whole hot path: kick-drift + rebuild check, (conditional)
-cell sort + list build, DPD pair forces.
+Default workload (N = 1): the platelet channel -- 8,040,000 plasma particles
+at rho = 3 in a 400 x 100 x 67 channel with frozen walls in y and a
+Poiseuille body force (wall shear rate 0.05), plus 16 platelets of 10,000
+coarse-grained particles (8,360,800 particles).  The timed arm is AI-MTS:
+outer steps of dt_f = 0.01 (one reduced time unit = 166.4 ns, so 1.664 ns per
+step), one interface substep, per-platelet step ratios from the trained
+controller (fixed k = 10 when no trained parameters are present).  Beside it,
+the same system under fine-step STS (velocity-Verlet with dt = 0.001 for
+every particle, the reference of Sec. 4.1) and under fixed-k RESPA (k = 10).
+
+``--workload dpd1m``: the DPD-only throughput system (1,000,000 plasma
+particles in a 69.336^3 box, walls, g = 0.02, STS dt = 0.01, skin 0.3).
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 instead, on a bounded sample of the same workload.
@@ -28,30 +34,39 @@ sys.path.insert(0, ROOT)
 
 NS_PER_TAU = 166.4          # 1 tau = 166.4 ns (dt_f = 0.01 tau = 1.664 ns)
 METRIC = "simulated ns/day & particle-steps/s, AI-MTS vs fine-step STS on 1 GB300"
-L2_BYTES = 126 * 2 ** 20
 FALLBACK_HBM_GBS = 6800.0
+CONTROLLER = os.path.join(ROOT, "paper_2205_14121_gb300", "data", "controller.npz")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
-    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=150)
     ap.add_argument("--impl", default="msm", choices=["msm", "reference"])
-    ap.add_argument("--workload", default="dpd1m", choices=["dpd1m"])
+    ap.add_argument("--workload", default="channel", choices=["channel", "dpd1m"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-compare", action="store_true", help="skip the fine-STS and fixed-k arms")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--direct", action="store_true",
                     help="launch every kernel from the host instead of replaying the captured graph "
                          "(profilers cannot see kernels inside conditional graphs)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def workload(name, seed):
     import synth
     if name == "dpd1m":
-        s = synth.config_dpd_throughput(seed=seed)
-        return s, dict(dt=0.01, skin=0.3, mode="sts")
+        return synth.config_dpd_throughput(seed=seed), dict(
+            dt=0.01, skin=0.3,
+            desc="dpd-only throughput: 1,000,000 plasma particles, rho=3, 69.336^3 box, walls in y, g=0.02, "
+                 "STS velocity-Verlet dt=0.01, skin 0.3")
+    if name == "channel":
+        return synth.config_channel_platelets(seed=seed), dict(
+            dt=0.01, skin=0.3,
+            desc="platelet channel: 8,040,000 plasma at rho=3 in 400x100x67, y walls, Poiseuille g for wall "
+                 "shear rate 0.05, 16 platelets x 10,000 CG particles (5% receptors); AI-MTS dt_f=0.01, k_m=1, "
+                 "per-platelet k from the controller vs fine-step STS dt=0.001; skin 0.3")
     raise ValueError(name)
 
 
@@ -66,22 +81,61 @@ def cpu_count():
         return os.cpu_count() or 1
 
 
-def oracle_sample(seed, target_s=10.0, max_steps=200):
-    """The FP64 oracle (as it stands) on a 65,536-particle sample of the same
-    workload (same density, walls, body force, dt): particle-steps/s."""
-    import oracle as O
-    import synth
-    s = synth.plasma_box(n=65536, walls=True, body_force=0.02, seed=seed)
-    p = O.system_params(s)
-    x, v, f = O.run_respa(p, s.x, s.v, s.tag, dt_f=0.01, n_outer=1)
+def whole_job_rate(units_local, seconds_local, world, device="cpu"):
+    """Replicas: units processed by all ranks / the slowest rank's time.
+    Returns (units_total, seconds_max); collective only when world > 1."""
+    if world <= 1:
+        return float(units_local), float(seconds_local)
+    import torch
+    import torch.distributed as dist
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
+class OracleSample:
+    """The FP64 oracle (as it stands) on a bounded sample of the workload."""
+
+    def __init__(self, name, seed):
+        import oracle as O
+        import synth
+        self.O = O
+        if name == "dpd1m":
+            s = synth.plasma_box(n=65536, walls=True, body_force=0.02, seed=seed)
+            self.what = "STS steps"
+            self.kw = dict(dt_f=0.01)
+            self.fn = O.run_respa
+            self.extra = ()
+        else:
+            # a 20 x 10 x 8 section of the channel with one 600-particle platelet, AI-MTS with k = 10
+            g = synth.poiseuille_g(0.05, synth.ETA_DPD, 3.0, 10.0)
+            s = synth.platelet_system((20.0, 10.0, 8.0), 4800, 1, 600, synth.scaled_radii(600), walls=True,
+                                      body_force=g, seed=seed, centers=[(10.0, 5.0, 4.0)])
+            self.what = "AI-MTS outer steps (k = 10)"
+            self.kw = dict(X0=s.X0, bonds=s.bonds, r0=s.r0, dt_f=0.01, k_m=1)
+            self.fn = O.run_ai_respa
+            self.extra = ([10],)
+        self.s = s
+        self.p = O.system_params(s)
+        self.x, self.v, self.f = self.fn(self.p, s.x, s.v, s.tag, *self.extra, n_outer=1, **self.kw)
+        self.n0 = 1
+
+    def step(self):
+        self.x, self.v, self.f = self.fn(self.p, self.x, self.v, self.s.tag, *self.extra, n_outer=1, n0=self.n0,
+                                         t0=self.n0 * 0.01, forces=self.f, **self.kw)
+        self.n0 += 1
+
+
+def oracle_rate(name, seed, target_s=10.0, max_steps=200):
+    o = OracleSample(name, seed)
     steps, t0 = 0, time.perf_counter()
-    n0 = 1
     while steps < max_steps and time.perf_counter() - t0 < target_s:
-        x, v, f = O.run_respa(p, x, v, s.tag, dt_f=0.01, n_outer=1, n0=n0, t0=n0 * 0.01, forces=f)
+        o.step()
         steps += 1
-        n0 += 1
     el = time.perf_counter() - t0
-    return s.n * steps / el, steps, s.n, el
+    return o.s.n * steps / el, steps, o.s.n, el, o.what
 
 
 class ClockSampler:
@@ -169,53 +223,52 @@ def ncu_traffic(workload_name):
     return None
 
 
-def whole_job_rate(units_local, seconds_local, world, device="cpu"):
-    """Replicas: units processed by all ranks / the slowest rank's time.
-    Returns (units_total, seconds_max); collective only when world > 1."""
-    if world <= 1:
-        return float(units_local), float(seconds_local)
-    import torch
-    import torch.distributed as dist
-    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
-    t = torch.tensor([float(seconds_local)], dtype=torch.float64, device=device)
-    dist.all_reduce(u, op=dist.ReduceOp.SUM)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(u.item()), float(t.item())
-
-
 def run_reference(args, rank, world):
+    """The oracle, as it stands, timed step by step on the host cores."""
     if rank != 0:
         return
-    s_ps, steps, n, el = None, 0, 0, 0.0
+    s, wl = workload(args.workload, seed=20220528)
+    n_full = s.n
+    del s
+    o = OracleSample(args.workload, 20220528)
     per_step = []
-    import oracle as O
-    import synth
-    s = synth.plasma_box(n=65536, walls=True, body_force=0.02, seed=20220528)
-    p = O.system_params(s)
-    x, v, f = O.run_respa(p, s.x, s.v, s.tag, dt_f=0.01, n_outer=1)
-    n0 = 1
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        x, v, f = O.run_respa(p, x, v, s.tag, dt_f=0.01, n_outer=1, n0=n0, t0=n0 * 0.01, forces=f)
-        n0 += 1
+        o.step()
         if it >= args.warmup:
             per_step.append(time.perf_counter() - t0)
     el = float(np.sum(per_step))
-    s_ps = s.n * args.steps / el
-    # the sample's particle-steps/s, expressed for the full workload's particle count
-    n_full = workload(args.workload, seed=20220528)[0].n
-    value = s_ps / n_full * 0.01 * NS_PER_TAU * 86400.0
+    n_s = o.s.n
+    s_ps = n_s * args.steps / el
+    value = s_ps / n_full * wl["dt"] * NS_PER_TAU * 86400.0
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "particle_steps_per_s": s_ps,
-            "config": {"workload": "dpd-only throughput, 65,536-particle sample (rho=3, walls, g=0.02, dt=0.01)",
-                       "sample_of": args.workload},
+            "config": {"workload": f"FP64 oracle on a {n_s}-particle sample: {o.what}", "sample_of": wl["desc"]},
             "cpu_baseline": {"value": value, "unit": "ns/day", "cores": cpu_count(), "kind": "oracle",
-                             "sample": f"{args.steps} STS steps of a {s.n}-particle sample, scaled to "
+                             "sample": f"{args.steps} {o.what} of a {n_s}-particle sample, scaled to "
                                        f"{n_full} particles by particle-steps/s"},
             "e2e": {"value": value, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def make_system(M, s, dt, skin, seed):
+    return M.System(s.box, s.x, s.v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, walls=s.walls, wall=s.wall,
+                    shear_rate=s.shear_rate, body_force=s.body_force, dt=dt, skin=skin, seed=seed)
+
+
+def timed(g, step, n, barrier):
+    """CUDA-event time (ms) of `step(n)` on g's stream, barriers on both sides."""
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(g.stream)
+    step(n)
+    ev1.record(g.stream)
+    barrier()
+    return ev0.elapsed_time(ev1)
 
 
 def main():
@@ -231,55 +284,78 @@ def main():
     import torch.distributed as dist
 
     import paper_2205_14121_gb300 as M
-    from paper_2205_14121_gb300 import build as B
+    from paper_2205_14121_gb300 import ai_mts as A
+    from paper_2205_14121_gb300 import build as Bld
 
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
-    B.build()
-
-    s, wl = workload(args.workload, seed=20220528 + rank)
-    n = s.n
-    g = M.System(s.box, s.x, s.v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, walls=s.walls, wall=s.wall,
-                 shear_rate=s.shear_rate, body_force=s.body_force, dt=wl["dt"], skin=wl["skin"])
-    stream = g.stream
-
-    # warm-up (first list build, first forces, clocks)
-    g.mts_step(args.warmup, direct=args.direct)
-    torch.cuda.synchronize()
+    Bld.build()
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
+    seed = 20220528 + rank
+    s, wl = workload(args.workload, seed=seed)
+    n = s.n
+    g = make_system(M, s, wl["dt"], wl["skin"], seed)
+
+    mode_info = {}
+    decisions = []
+    ctl = None
+    if args.workload == "channel":
+        if os.path.exists(CONTROLLER):
+            ctl, trust = A.load_controller(CONTROLLER)
+            mode_info["controller"] = os.path.relpath(CONTROLLER, ROOT)
+        else:
+            trust = A.TrustBound()
+            mode_info["controller"] = "absent: fixed k = 10 for every platelet"
+
+        def step(k):
+            if ctl is None:
+                g.set_platelet_levels(np.full(g.cfg.n_platelets, trust.fallback_k, np.int32))
+                g.mts_step(k, mode=M.MD_MODE_AI, k_m=1, direct=args.direct, record=True)
+            else:
+                A.run_ai_mts(g, ctl, k, k_m=1, trust=trust, log=decisions)
+        mode_info["mode"] = "AI-MTS"
+    else:
+        def step(k):
+            g.mts_step(k, direct=args.direct)
+        mode_info["mode"] = "STS"
+
+    # warm-up (first list build, first forces, graph capture, a full feature window)
+    step(args.warmup)
+    torch.cuda.synchronize()
+    decisions.clear()
+
     # ---- timed region --------------------------------------------------
     g.profile_read(reset=True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
     clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
     with ClockSampler(clk_path) as clk:
-        barrier()
-        ev0.record(stream)
-        g.mts_step(args.steps, direct=args.direct)
-        ev1.record(stream)
-        barrier()
-    ms = ev0.elapsed_time(ev1)
+        ms = timed(g, step, args.steps, barrier)
     prof_plain = g.profile_read(reset=True)
-    # whole job: every rank's particle-steps over the slowest rank's time
     units, sec = whole_job_rate(n * args.steps, ms / 1e3, world, device="cuda")
     ms = sec * 1e3
     ps = units / sec
     value = ns_per_day(args.steps, sec, wl["dt"]) * (units / (n * args.steps))
+    if ctl is not None:
+        ks = [k for d in decisions for k in d["k"]]
+        mode_info["decisions"] = len(decisions)
+        mode_info["mean_k"] = float(np.mean(ks)) if ks else None
+        mode_info["fallback_fraction"] = (float(np.mean([u for d in decisions for u in d["unsure"]]))
+                                          if decisions else None)
 
-    # ---- roofline pass: same K steps with per-class CUDA events ----------
+    # ---- roofline pass: per-class CUDA events on the launching stream -----
     g.profile_enable(True)
-    g.mts_step(args.steps)
+    n_prof = min(args.steps, 100)
+    step(n_prof)
     prof = g.profile_read(reset=True)
     g.profile_enable(False)
     obs = g.observables()
-    n_half = len(g.neighbor_pairs(M.MD_LIST_FLUID)) / n
+    n_half = g.neighbor_count(M.MD_LIST_FLUID) / n
     fl_launch = prof["launches"]["fluid_dpd"]
     fl_ms = prof["ms"]["fluid_dpd"] / max(fl_launch, 1)
     bytes_per_particle = 16 + 16 + 4 * n_half + 16      # x32 + v + list + f
@@ -297,21 +373,47 @@ def main():
         t0 = time.perf_counter()
         for k in range(args.e2e_steps):
             g.set_particles(xh, vh, th, s.X0, step0=k)
-            g.mts_step(1)
+            if args.workload == "channel":
+                g.set_platelet_levels(np.full(g.cfg.n_platelets, 10, np.int32))
+                g.mts_step(1, mode=M.MD_MODE_AI, k_m=1)
+            else:
+                g.mts_step(1)
             g.observables()
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         e2e = {"value": ns_per_day(args.e2e_steps, el, wl["dt"]) * world, "unit": "ns/day",
                "h2d_bytes_per_step": int(xh.nbytes + vh.nbytes + th.nbytes),
                "d2h_bytes_per_step": 3 * (16 * 4 + 64) + 16 * 8 + 9 * 8,
-               "note": "per step: state upload, forced list rebuild + forces, one step, observables"}
+               "note": "per step: state upload, forced list rebuild + forces, one outer step, observables"}
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+
+    # ---- comparison arms on the same system ------------------------------
+    compare = {}
+    if args.workload == "channel" and not args.no_compare:
+        arms = [("fine_sts", 0.001, lambda h, k: h.mts_step(k, direct=args.direct)),
+                ("respa_k10", 0.01, lambda h, k: h.mts_step(k, mode=M.MD_MODE_RESPA, k_m=1, k_p=10,
+                                                             direct=args.direct))]
+        for name, dt, fn in arms:
+            h = make_system(M, s, dt, wl["skin"], seed)
+            fn(h, args.warmup)
+            t_ms = timed(h, lambda k: fn(h, k), args.steps, barrier)
+            u2, s2 = whole_job_rate(n * args.steps, t_ms / 1e3, world, device="cuda")
+            compare[name] = {"ns_per_day": ns_per_day(args.steps, s2, dt) * (u2 / (n * args.steps)),
+                             "ms_per_step": s2 * 1e3 / args.steps, "dt": dt,
+                             "particle_steps_per_s": u2 / s2}
+            h.close()
+            del h
+            torch.cuda.empty_cache()
+        compare["speedup_ai_mts_vs_fine_sts"] = value / compare["fine_sts"]["ns_per_day"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ps_cpu, st_cpu, n_cpu, el_cpu = oracle_sample(seed=20220528)
+        ps_cpu, st_cpu, n_cpu, el_cpu, what = oracle_rate(args.workload, seed=20220528)
         cpu = {"value": ps_cpu / n * wl["dt"] * NS_PER_TAU * 86400.0, "unit": "ns/day", "cores": cpu_count(),
                "kind": "oracle", "particle_steps_per_s": ps_cpu,
-               "sample": f"{st_cpu} STS steps of a {n_cpu}-particle sample of the same workload ({el_cpu:.1f} s), "
+               "sample": f"{st_cpu} {what} of a {n_cpu}-particle sample of the same workload ({el_cpu:.1f} s), "
                          f"scaled to {n} particles by particle-steps/s"}
 
     if rank != 0:
@@ -324,10 +426,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "particle_steps_per_s": ps,
-        "config": {"workload": "dpd-only throughput: 1,000,000 plasma particles, rho=3, 69.336^3 box, walls in y, "
-                               "g=0.02, STS velocity-Verlet dt=0.01, skin 0.3",
-                   "n_particles": n, "mode": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (about 2e8 B touched per step vs 1.3e8 B L2); no flush"},
+        "config": {"workload": wl["desc"], "n_particles": n, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (a force pass reads more than 129 MB); no flush", **mode_info},
+        "compare": compare or None,
         "roofline": {"bound": "hbm", "kernel": "k_dpd (fluid level pair forces)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": peak_kind,
@@ -336,12 +437,11 @@ def main():
         "e2e": e2e,
         "gpu_launches": prof_plain["total_launches"],
         "clocks": clocks,
-        "kernel_ms_per_step": {k: v / max(args.steps, 1) for k, v in prof["ms"].items()},
+        "kernel_ms_per_step": {k: v / max(n_prof, 1) for k, v in prof["ms"].items()},
         "n_builds": obs["n_builds"],
         "temperature": obs["temperature"],
     }
     print(json.dumps(line), flush=True)
-    g.close()
     if world > 1:
         dist.destroy_process_group()
 

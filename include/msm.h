@@ -187,6 +187,8 @@ int md_read_particles(md_system *sys, double *x, double *v, float *x32);
 #define MD_MODE_AI    2  /* per-platelet k (md_set_platelet_levels), Table 2    */
 
 #define MD_SCHED_DIRECT 1  /* launch every kernel from the host (no CUDA graph) */
+#define MD_SCHED_RECORD 2  /* append the per-platelet measurements after every
+                              outer step to the feature ring (md_record_features) */
 
 typedef struct md_mts_schedule {
     int32_t mode;        /* MD_MODE_*                                            */
@@ -276,8 +278,8 @@ int md_read_feature_ring(md_system *sys, float *out, int64_t *count);
 
 /*
  * Neighbour pairs of list kind `kind` as particle ids (a < b), written to
- * HOST pairs[2*cap]; *count gets the total.  For parity checks of K2.
- * Synchronises the stream.
+ * HOST pairs[2*cap]; *count gets the total (pairs = NULL: the count alone,
+ * from the row counts).  For parity checks of K2.  Synchronises the stream.
  */
 int md_neighbor_pairs(md_system *sys, int32_t kind, int32_t *pairs, int64_t cap, int64_t *count);
 
@@ -338,6 +340,13 @@ int md_ai_set_norm(md_ai *ai, const float *mean, const float *stdv);
  * MD_ENOTRAINED (no parameters), MD_ECUDA.
  */
 int md_ai_predict(md_ai *ai, const float *raw, int32_t B, int32_t where, float *out);
+/*
+ * Table 2 steps 1-2 only: raw windows (host or device per `where`) ->
+ * denoised, normalised HOST windows out[B][T][F], the input of md_ai_encode,
+ * md_ai_grads and md_ai_train_step (no parameters needed; the identity
+ * normalisation until md_ai_set_norm).  Errors: MD_EINVAL, MD_ECUDA.
+ */
+int md_ai_prepare(md_ai *ai, const float *raw, int32_t B, int32_t where, float *out);
 /*
  * Autoencoder on already denoised, normalised HOST windows x[B][T][F]:
  * latent (HOST [B][L], may be NULL) and reconstruction (HOST, time-major

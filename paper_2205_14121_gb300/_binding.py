@@ -293,8 +293,8 @@ class System:
 
     md_read_particles = read_particles
 
-    def mts_step(self, n_outer, mode=MD_MODE_STS, k_m=1, k_p=1, direct=False):
-        sched = md_mts_schedule(mode, k_m, k_p, 1 if direct else 0)
+    def mts_step(self, n_outer, mode=MD_MODE_STS, k_m=1, k_p=1, direct=False, record=False):
+        sched = md_mts_schedule(mode, k_m, k_p, (1 if direct else 0) | (2 if record else 0))
         self._check(lib().md_mts_step(self.h, int(n_outer), C.byref(sched)), "md_mts_step")
 
     md_mts_step = mts_step
@@ -325,6 +325,12 @@ class System:
         return out[:cnt.value]
 
     md_neighbor_pairs = neighbor_pairs
+
+    def neighbor_count(self, kind):
+        """Number of pairs in list `kind` (row counts only, no pair download)."""
+        cnt = C.c_int64()
+        self._check(lib().md_neighbor_pairs(self.h, kind, None, 0, C.byref(cnt)), "md_neighbor_pairs")
+        return cnt.value
 
     def get_state(self):
         nb = C.c_size_t()

@@ -1,0 +1,285 @@
+"""AI-MTS (Sec. 3.3, Table 2): the controller-driven time stepping loop and
+the pipeline that trains the controller on trajectories of this code.
+
+Every step of the simulation and of the network runs in libmsm (md_mts_step,
+the per-platelet measurements, md_ai_*); this module only sequences those
+calls and keeps the bookkeeping: which windows were recorded, which step
+ratio each one earned, when to ask the controller again.
+
+Labels ("trial and error" made a procedure): from the state at the end of a
+window, fixed-k continuations are run for every k of the class set and
+compared with the finest one (k = 20) over the next `horizon` outer steps;
+the label is the coarsest k (the largest platelet step dt_m / k) whose mean
+principal stresses stay within 3% and whose mean centre-of-mass velocity
+stays within 1% of the finest run (the tolerances of Sec. 4.2).  The hold
+label is how long that label stays unchanged along the trajectory, clipped to
+[100, 2000] steps.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _binding as B
+from .controller import K_SET, TRAIN_AE, TRAIN_HEADS, Controller, default_config, param_layout
+
+GATE_STRESS = 0.03
+GATE_VCOM = 0.01
+HOLD_RANGE = (100.0, 2000.0)
+F_VCOM = slice(0, 3)       # measurement columns: centre-of-mass velocity
+F_STRESS = slice(6, 9)     # principal stresses
+F_STRAIN = 9               # largest bond strain
+
+
+@dataclass
+class TrustBound:
+    """Fallback to a fixed ratio when the controller is unsure (Table 2)."""
+    p_min: float = 0.6           # smallest accepted top class probability
+    rec_max: float = math.inf    # largest accepted reconstruction error
+    strain_max: float = 0.2      # largest accepted bond strain in the window
+    fallback_k: int = 10
+
+
+def init_params(cfg, seed=0):
+    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, shape in param_layout(cfg):
+        if name.endswith(".W") or ".W_" in name:
+            bound = 1.0 / math.sqrt(shape[-1])
+            parts.append(rng.uniform(-bound, bound, size=shape).astype(np.float32).ravel())
+        else:
+            parts.append(np.zeros(int(np.prod(shape)), np.float32))
+    return np.concatenate(parts)
+
+
+def decide(pred, windows, trust):
+    """Per-platelet ratio and hold from one prediction, with the trust bound."""
+    k = np.asarray(pred["k"], np.int32).copy()
+    unsure = ((pred["prob"].max(1) < trust.p_min) | (pred["rec_err"] > trust.rec_max)
+              | (windows[:, :, F_STRAIN].max(1) > trust.strain_max))
+    k[unsure] = trust.fallback_k
+    hold = np.clip(np.exp(pred["log_hold"]), *HOLD_RANGE)
+    return k, hold, unsure
+
+
+def run_ai_mts(system, controller, n_steps, k_m=1, trust=None, T=128, log=None):
+    """Advance n_steps outer steps under AI-MTS: the measurements of every step
+    go to the feature ring inside the step graph; once a full window exists
+    the controller sets each platelet's ratio, and is asked again after the
+    shortest predicted hold."""
+    trust = trust or TrustBound()
+    P = system.cfg.n_platelets
+    system.set_platelet_levels(np.full(P, trust.fallback_k, np.int32))
+    done = 0
+    while done < n_steps:
+        windows, count = system.read_feature_ring()
+        if count >= T:
+            pred = controller.predict(windows)
+            k, hold, unsure = decide(pred, windows, trust)
+            system.set_platelet_levels(k)
+            run = int(hold.min())
+            if log is not None:
+                log.append(dict(step=done, k=k.tolist(), hold=hold.tolist(), unsure=unsure.tolist()))
+        else:
+            run = T - count
+        run = max(1, min(run, n_steps - done))
+        system.mts_step(run, mode=B.MD_MODE_AI, k_m=k_m, record=True)
+        done += run
+    return log
+
+
+# ---------------------------------------------------------------------------
+# training data
+# ---------------------------------------------------------------------------
+
+def training_system(seed, box=(32.0, 16.0, 16.0), n_shell=600, shear_rate=0.05):
+    """A walled channel with four platelets: two close to each other near the
+    lower wall (contacting, fast dynamics) and two in the flow."""
+    import synth
+    rng = np.random.default_rng(seed)
+    Lx, Ly, Lz = box
+    radii = synth.scaled_radii(n_shell)
+    a, b = radii[0], radii[1]
+    x0 = rng.uniform(a + 1.0, Lx - 3 * a - 3.0)
+    gap = rng.uniform(0.6, 1.6)
+    centers = [(x0, b + 1.2, Lz / 2), (x0 + 2 * a + gap, b + 1.2 + rng.uniform(-0.3, 0.3), Lz / 2),
+               (rng.uniform(a + 1, Lx - a - 1), Ly / 2 + rng.uniform(1.0, 3.0), rng.uniform(b + 1, Lz - b - 1)),
+               (rng.uniform(a + 1, Lx - a - 1), Ly - b - 2.0, rng.uniform(b + 1, Lz - b - 1))]
+    n_pl = int(round(3.0 * Lx * Ly * Lz))
+    g = synth.poiseuille_g(shear_rate, synth.ETA_DPD, 3.0, Ly)
+    return synth.platelet_system(box, n_pl, 4, n_shell, radii, walls=True, body_force=g, seed=seed,
+                                 centers=centers)
+
+
+def make_system(s, **kw):
+    return B.System(s.box, s.x, s.v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, walls=s.walls, wall=s.wall,
+                    shear_rate=s.shear_rate, body_force=s.body_force, **kw)
+
+
+def _means(records):
+    return records[:, :, F_STRESS].mean(1), records[:, :, F_VCOM].mean(1)
+
+
+def continuation_errors(system, horizon, k_m=1):
+    """Relative errors [P][len(K_SET)] of each fixed-k continuation from the
+    current state against the finest, for the mean principal stresses and
+    the mean centre-of-mass velocity over `horizon` outer steps.  The state
+    is restored afterwards."""
+    blob = system.get_state()
+    means = {}
+    for k in K_SET:
+        system.set_state(blob)
+        system.mts_step(horizon, mode=B.MD_MODE_RESPA, k_m=k_m, k_p=k, record=True)
+        rec, _ = system.read_feature_ring()
+        means[k] = _means(rec[:, -horizon:])
+    system.set_state(blob)
+    s_ref, v_ref = means[K_SET[-1]]
+    v_scale = np.linalg.norm(v_ref, axis=1) + 0.05
+    s_scale = np.linalg.norm(s_ref, axis=1) + 1e-6
+    es = np.stack([np.linalg.norm(means[k][0] - s_ref, axis=1) / s_scale for k in K_SET], 1)
+    ev = np.stack([np.linalg.norm(means[k][1] - v_ref, axis=1) / v_scale for k in K_SET], 1)
+    return es, ev
+
+
+def label_from_errors(es, ev):
+    """Class of the coarsest k within both tolerances (the finest when none is)."""
+    ok = (es <= GATE_STRESS) & (ev <= GATE_VCOM)
+    ok[:, -1] = True
+    return ok.argmax(1).astype(np.int32)
+
+
+def hold_labels(classes, stride):
+    """Steps for which each window's label stays unchanged along the
+    trajectory: classes [W][P] -> hold [W][P]."""
+    W, P = classes.shape
+    hold = np.zeros((W, P))
+    for p in range(P):
+        run = 0
+        for w in range(W - 1, -1, -1):
+            run = run + 1 if (w + 1 < W and classes[w + 1, p] == classes[w, p]) else 1
+            hold[w, p] = run * stride
+    return np.clip(hold, *HOLD_RANGE)
+
+
+@dataclass
+class Dataset:
+    windows: list = field(default_factory=list)    # [P][T][F] raw windows
+    classes: list = field(default_factory=list)    # [P]
+    holds: list = field(default_factory=list)      # [P]
+    err_s: list = field(default_factory=list)      # [P][len(K_SET)]
+    err_v: list = field(default_factory=list)
+
+    def arrays(self):
+        cat = lambda xs: np.concatenate(xs, 0)
+        return (cat(self.windows).astype(np.float32), cat(self.classes), cat(self.holds), cat(self.err_s),
+                cat(self.err_v))
+
+
+def generate(seeds, n_windows=8, warmup=50, horizon=50, k_m=1, k_record=10, T=128, n_shell=600, progress=None):
+    """Windows of per-platelet measurements under fixed-k RESPA (k_record),
+    each labelled from the continuations at its end."""
+    data = Dataset()
+    for seed in seeds:
+        sys = make_system(training_system(seed, n_shell=n_shell), seed=int(seed))
+        sys.mts_step(warmup, mode=B.MD_MODE_RESPA, k_m=k_m, k_p=k_record)
+        wins, cls, es_all, ev_all = [], [], [], []
+        for w in range(n_windows):
+            blob = sys.get_state()
+            sys.set_state(blob)                      # restart the ring at this window
+            sys.mts_step(T, mode=B.MD_MODE_RESPA, k_m=k_m, k_p=k_record, record=True)
+            win, cnt = sys.read_feature_ring()
+            es, ev = continuation_errors(sys, horizon, k_m=k_m)
+            wins.append(win)
+            cls.append(label_from_errors(es, ev))
+            es_all.append(es)
+            ev_all.append(ev)
+        classes = np.stack(cls)
+        holds = hold_labels(classes, T)
+        for w in range(n_windows):
+            data.windows.append(wins[w])
+            data.classes.append(classes[w])
+            data.holds.append(holds[w])
+            data.err_s.append(es_all[w])
+            data.err_v.append(ev_all[w])
+        sys.close()
+        if progress:
+            progress(seed, classes)
+    return data
+
+
+# ---------------------------------------------------------------------------
+# training
+# ---------------------------------------------------------------------------
+
+def _batches(n, size, rng):
+    idx = rng.permutation(n)
+    for b in range(0, n, size):
+        yield idx[b:b + size]
+
+
+def train(windows, classes, holds, epochs_ae=40, epochs_heads=80, batch=128, lr_ae=2e-3, lr_heads=3e-3, seed=0,
+          progress=None):
+    """Autoencoder first (reconstruction), then the heads on its latent
+    (Sec. 3.3 trains them separately).  Returns (controller, artefacts)."""
+    cfg = default_config(batch_max=batch)
+    ctl = Controller(cfg)
+    ctl.set_params(init_params(cfg, seed))
+    n = windows.shape[0]
+    den = np.concatenate([ctl.prepare(windows[b:b + batch]) for b in range(0, n, batch)])
+    mean = den.reshape(-1, cfg.F).mean(0)
+    std = den.reshape(-1, cfg.F).std(0) + 1e-6
+    ctl.set_norm(mean, std)
+    x = np.concatenate([ctl.prepare(windows[b:b + batch]) for b in range(0, n, batch)])
+    rng = np.random.default_rng(seed)
+    hist = {"ae": [], "heads": []}
+    for ep in range(epochs_ae):
+        losses = [ctl.train_step(x[i], TRAIN_AE, lr_ae) for i in _batches(n, batch, rng)]
+        hist["ae"].append(float(np.mean(losses)))
+        if progress:
+            progress("ae", ep, hist["ae"][-1])
+    log_hold = np.log(holds).astype(np.float32)
+    for ep in range(epochs_heads):
+        losses = [ctl.train_step(x[i], TRAIN_HEADS, lr_heads, k_class=classes[i], log_hold=log_hold[i])
+                  for i in _batches(n, batch, rng)]
+        hist["heads"].append(float(np.mean(losses)))
+        if progress:
+            progress("heads", ep, hist["heads"][-1])
+    rec = np.concatenate([ctl.predict(windows[b:b + batch])["rec_err"] for b in range(0, n, batch)])
+    art = dict(params=ctl.get_params(), mean=mean.astype(np.float32), std=std.astype(np.float32),
+               rec_p99=np.float32(np.percentile(rec, 99)), history=hist)
+    return ctl, art
+
+
+def load_controller(path, batch=256):
+    """Controller with the parameters and normalisation saved by `save`."""
+    d = np.load(path)
+    ctl = Controller(default_config(batch_max=batch))
+    ctl.set_params(d["params"])
+    ctl.set_norm(d["mean"], d["std"])
+    return ctl, TrustBound(rec_max=float(d["rec_p99"]))
+
+
+def save(path, art):
+    np.savez(path, params=art["params"], mean=art["mean"], std=art["std"], rec_p99=art["rec_p99"])
+
+
+def evaluate(ctl, windows, err_s, err_v, trust, batch=128):
+    """Policies on labelled windows: the violation rate of the tolerances and
+    the mean step ratio (cost of the platelet level) of the controller and of
+    every fixed ratio."""
+    n = windows.shape[0]
+    ks = []
+    for b in range(0, n, batch):
+        pred = ctl.predict(windows[b:b + batch])
+        k, _, _ = decide(pred, windows[b:b + batch], trust)
+        ks.append(k)
+    k = np.concatenate(ks)
+    col = np.searchsorted(np.array(K_SET), k)
+    viol = lambda c: float(np.mean((err_s[np.arange(n), c] > GATE_STRESS) | (err_v[np.arange(n), c] > GATE_VCOM)))
+    out = {"controller": {"violations": viol(col), "mean_k": float(k.mean())}}
+    for j, kk in enumerate(K_SET):
+        out[f"fixed_k{kk}"] = {"violations": viol(np.full(n, j)), "mean_k": float(kk)}
+    return out

@@ -44,10 +44,11 @@ def _bind():
     L.md_ai_set_norm.argtypes = [vp, fp, fp]
     L.md_ai_predict.argtypes = [vp, vp, C.c_int32, C.c_int32, fp]
     L.md_ai_encode.argtypes = [vp, fp, C.c_int32, fp, fp]
+    L.md_ai_prepare.argtypes = [vp, vp, C.c_int32, C.c_int32, fp]
     L.md_ai_grads.argtypes = [vp, fp, ip, fp, C.c_int32, C.c_int32, fp, fp]
     L.md_ai_train_step.argtypes = [vp, fp, ip, fp, C.c_int32, C.c_int32, C.c_float, fp]
     for n in ("md_ai_config_defaults", "md_ai_param_count", "md_ai_workspace_size", "md_ai_init", "md_ai_set_params",
-              "md_ai_get_params", "md_ai_set_norm", "md_ai_predict", "md_ai_encode", "md_ai_grads",
+              "md_ai_get_params", "md_ai_set_norm", "md_ai_predict", "md_ai_encode", "md_ai_grads", "md_ai_prepare",
               "md_ai_train_step"):
         getattr(L, n).restype = C.c_int
     _bound = True
@@ -171,6 +172,15 @@ class Controller:
         probs = out[:, :self.cfg.n_classes]
         return dict(prob=probs, cls=probs.argmax(1), k=np.array(K_SET)[probs.argmax(1)],
                     log_hold=out[:, self.cfg.n_classes], rec_err=out[:, self.cfg.n_classes + 1])
+
+    def prepare(self, raw):
+        """Denoised, normalised windows [B][T][F] (Table 2 steps 1-2, on the device)."""
+        raw, rp = self._f(raw)
+        B = raw.shape[0]
+        out = np.zeros((B, self.cfg.T, self.cfg.F), np.float32)
+        self._check(_bind().md_ai_prepare(self.h, C.cast(rp, C.c_void_p), B, AI_HOST,
+                                          out.ctypes.data_as(C.POINTER(C.c_float))), "md_ai_prepare")
+        return out
 
     def encode(self, x):
         x, xp = self._f(x)

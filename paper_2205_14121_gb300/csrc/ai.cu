@@ -866,6 +866,22 @@ int md_ai_predict(md_ai *m, const float *raw, int32_t B, int32_t where, float *o
     return MD_OK;
 }
 
+int md_ai_prepare(md_ai *m, const float *raw, int32_t B, int32_t where, float *out)
+{
+    if (!m || !raw || !out || B < 1 || B > m->c.batch_max) return MD_EINVAL;
+    int rc = stage_windows(m, raw, B, where, true);
+    if (rc) return rc;
+    const int T = m->c.T, F = m->c.F;
+    std::vector<float> tm((size_t)T * B * F);
+    AK(cudaMemcpyAsync(tm.data(), m->X, sizeof(float) * tm.size(), cudaMemcpyDeviceToHost, m->st), "windows");
+    AK(cudaStreamSynchronize(m->st), "sync");
+    for (int t = 0; t < T; ++t)          // time-major [T][B][F] -> [B][T][F]
+        for (int b = 0; b < B; ++b)
+            for (int f = 0; f < F; ++f)
+                out[((int64_t)b * T + t) * F + f] = tm[((size_t)t * B + b) * F + f];
+    return MD_OK;
+}
+
 int md_ai_encode(md_ai *m, const float *x, int32_t B, float *latent_out, float *recon_out)
 {
     if (!m || !x || B < 1 || B > m->c.batch_max) return MD_EINVAL;

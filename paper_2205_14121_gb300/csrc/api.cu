@@ -81,15 +81,17 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
     s.cap[MD_LIST_IFACE] = default_cap(c.cap_iface, 64);
     s.cap[MD_LIST_LJ] = default_cap(c.cap_lj, 256);
     s.cap[MD_LIST_MORSE] = default_cap(c.cap_morse, 256);
-    if (!setup_grid(c, c.rc + c.skin, s.gmain, err)) return false;
-    if ((c.flags & MD_CFG_LEES_EDWARDS) && s.gmain.nc[1] < 3) {
-        err = "Lees-Edwards images need at least three list cells along y";
+    // list cells at least half the list reach wide: the candidate scan visits
+    // contiguous row ranges trimmed to the reach sphere
+    if (!setup_grid(c, 0.5 * (c.rc + c.skin), s.gmain, err)) return false;
+    if ((c.flags & MD_CFG_LEES_EDWARDS) && s.gmain.nc[1] < 6) {
+        err = "Lees-Edwards images need Ly of at least three list reaches (rc + skin)";
         return false;
     }
     const bool plt = s.n_plt > 0;
     if (plt) {
-        if (!setup_grid(c, c.lj_rc + c.skin, s.gplt, err)) return false;
-        if (s.n_rec > 0 && !setup_grid(c, c.morse_rc + c.skin, s.grec, err)) return false;
+        if (!setup_grid(c, 0.5 * (c.lj_rc + c.skin), s.gplt, err)) return false;
+        if (s.n_rec > 0 && !setup_grid(c, 0.5 * (c.morse_rc + c.skin), s.grec, err)) return false;
     }
     const int64_t n = s.n;
     s.xs = cv.take<double>(n);
@@ -425,7 +427,27 @@ int enqueue_time(md_system *s, int dn, int c, double t_off)
 // platelets drift every platelet substep.  Step-dependent values come from
 // the device time state, so the same sequence can be captured once and
 // replayed.
-int enqueue_outer_step(md_system *s, int mode, int k_m, int k_p, bool first, capture_ctx *cap)
+// Per-platelet measurements of the state at the end of the step appended to
+// the feature ring (inside the step, so a replayed graph records every step).
+// In AI-MTS the platelet buffer holds impulses: the platelet-level forces
+// are evaluated afresh into a sort buffer (free between rebuilds).
+int enqueue_record(md_system *s, int mode)
+{
+    prof_begin(s, MD_PROF_OTHER);
+    const float4 *fp = nullptr;
+    if (mode == MD_MODE_AI) {
+        CK(cudaMemsetAsync(s->altf[2], 0, sizeof(float4) * s->n, s->stream), "zero scratch forces");
+        float4 *out[3] = {nullptr, nullptr, s->altf[2]};
+        CK(launch_forces(s, MD_LEVEL_PLT, out, false), "record forces");
+        fp = s->altf[2];
+    }
+    CK(launch_features(s, s->feat, fp), "features");
+    CK(launch_feature_ring(s, s->feat), "feature ring");
+    prof_end(s);
+    return MD_OK;
+}
+
+int enqueue_outer_step(md_system *s, int mode, int k_m, int k_p, bool first, capture_ctx *cap, bool record)
 {
     const md_config &c = s->cfg;
     const bool plt = s->n_plt > 0;
@@ -439,6 +461,7 @@ int enqueue_outer_step(md_system *s, int mode, int k_m, int k_p, bool first, cap
         RC(enqueue_kd(s, h, DRIFT_ALL, c.dt, DRIFT_ALL, plt ? MD_LEVEL_ALL : MD_LEVEL_FLUID, false));
         RC(enqueue_rebuild(s, cap));
         RC(enqueue_forces(s, plt ? MD_LEVEL_ALL : MD_LEVEL_FLUID));
+        if (record) RC(enqueue_record(s, mode));
         return MD_OK;
     }
     const double dtf = c.dt, dtm = dtf / k_m, dtp = dtm / k_p;
@@ -496,6 +519,7 @@ int enqueue_outer_step(md_system *s, int mode, int k_m, int k_p, bool first, cap
         }
     }
     RC(enqueue_forces(s, MD_LEVEL_FLUID));
+    if (record) RC(enqueue_record(s, mode));
     return MD_OK;
 }
 
@@ -516,9 +540,9 @@ void drop_graph(md_system *s)
 }
 
 // Capture WHILE(steps_left) { outer step } once per schedule shape.
-int build_step_graph(md_system *s, int mode, int k_m, int k_p)
+int build_step_graph(md_system *s, int mode, int k_m, int k_p, bool record)
 {
-    const int key[4] = {mode, k_m, k_p, (int)s->cfg_k_m};
+    const int key[4] = {mode | (record ? 256 : 0), k_m, k_p, (int)s->cfg_k_m};
     bool same = s->step_exec != nullptr;
     for (int k = 0; k < 4; ++k) same = same && s->graph_key[k] == key[k];
     if (same) return MD_OK;
@@ -549,7 +573,7 @@ int build_step_graph(md_system *s, int mode, int k_m, int k_p)
     int rc = MD_OK;
     e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        rc = enqueue_outer_step(s, mode, k_m, k_p, false, &cap);
+        rc = enqueue_outer_step(s, mode, k_m, k_p, false, &cap, record);
         cudaGraph_t out = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &out);
         if (rc == MD_OK && e2 != cudaSuccess) rc = cuda_fail(s, e2, "end capture");
@@ -762,7 +786,6 @@ int md_set_particles(md_system *s, const double *x, const double *v, const int32
             CK(cudaMemcpyAsync(s->bond_off, z.data(), sizeof(int32_t) * (P + 1), cudaMemcpyHostToDevice, st), "bo");
             CK(cudaStreamSynchronize(st), "sync");
         }
-        s->ring_count = 0;
     }
     CK(cudaMemcpyAsync(s->alt64, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload x");
     k_import_x<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->alt64, s->xs, s->ys, s->zs, s->x32, s->xb);
@@ -942,6 +965,8 @@ int md_mts_step(md_system *s, int64_t n_outer, const md_mts_schedule *sched)
     if (s->nb > 0 && !s->have_bonds) return set_error(s, MD_EINVAL, "md_mts_step: bonds not set");
     if (n_outer == 0) return MD_OK;
     const int mode = sched->mode;
+    const bool record = (sched->flags & MD_SCHED_RECORD) != 0;
+    if (record && s->n_plt == 0) return set_error(s, MD_EINVAL, "md_mts_step: recording needs platelets");
     int k_m = sched->k_m > 0 ? sched->k_m : 1;
     int k_p = sched->k_p > 0 ? sched->k_p : 1;
     if (mode == MD_MODE_STS) { k_m = 1; k_p = 1; }
@@ -970,12 +995,12 @@ int md_mts_step(md_system *s, int64_t n_outer, const md_mts_schedule *sched)
         if (rc) return rc;
         s->forces_stale = true;   // plain forces again at the next call that needs them
     }
-    rc = enqueue_outer_step(s, mode, k_m, k_p, true, nullptr);
+    rc = enqueue_outer_step(s, mode, k_m, k_p, true, nullptr, record);
     if (rc) return rc;
     const int64_t rest = n_outer - 1;
     if (rest > 0) {
         bool use_graph = !s->prof_on && !s->graph_failed && !(sched->flags & MD_SCHED_DIRECT);
-        if (use_graph && build_step_graph(s, mode, k_m, k_p) != MD_OK) {
+        if (use_graph && build_step_graph(s, mode, k_m, k_p, record) != MD_OK) {
             s->graph_failed = true;   // keep going with direct launches
             use_graph = false;
         }
@@ -990,7 +1015,7 @@ int md_mts_step(md_system *s, int64_t n_outer, const md_mts_schedule *sched)
             s->nlaunch += rest * s->graph_body_launches + (s->h_ds->n_builds - builds0) * s->graph_chain_launches;
         } else {
             for (int64_t it = 0; it < rest; ++it) {
-                rc = enqueue_outer_step(s, mode, k_m, k_p, false, nullptr);
+                rc = enqueue_outer_step(s, mode, k_m, k_p, false, nullptr, record);
                 if (rc) return rc;
             }
         }
@@ -1053,8 +1078,7 @@ int md_record_features(md_system *s)
     int rc = ensure_forces(s);
     if (rc) return rc;
     CK(launch_features(s, s->feat), "features");
-    CK(launch_feature_ring(s, s->feat, (int)(s->ring_count % s->ring_T)), "feature ring");
-    s->ring_count += 1;
+    CK(launch_feature_ring(s, s->feat), "feature ring");
     return MD_OK;
 }
 
@@ -1065,16 +1089,18 @@ int md_read_feature_ring(md_system *s, float *out, int64_t *count)
     const int P = s->cfg.n_platelets, T = s->ring_T;
     std::vector<float> raw((size_t)P * T * 12);
     CK(cudaMemcpyAsync(raw.data(), s->ring, sizeof(float) * raw.size(), cudaMemcpyDeviceToHost, s->stream), "ring");
-    CK(cudaStreamSynchronize(s->stream), "sync");
+    int rc = sync_ctl(s);
+    if (rc) return rc;
+    const int64_t ring_count = s->h_ds->ring_count;
     // chronological order: the oldest retained record first
-    const int64_t n = s->ring_count < T ? s->ring_count : T;
-    const int64_t first = s->ring_count - n;
+    const int64_t n = ring_count < T ? ring_count : T;
+    const int64_t first = ring_count - n;
     for (int p = 0; p < P; ++p)
         for (int64_t t = 0; t < n; ++t) {
             const int64_t slot = (first + t) % T;
             memcpy(out + ((int64_t)p * T + t) * 12, raw.data() + ((int64_t)p * T + slot) * 12, 12 * sizeof(float));
         }
-    *count = s->ring_count;
+    *count = ring_count;
     return MD_OK;
 }
 
@@ -1091,6 +1117,15 @@ int md_neighbor_pairs(md_system *s, int32_t kind, int32_t *pairs, int64_t cap, i
     *count = 0;
     if (rows == 0 || !s->nl[kind]) return MD_OK;
     const int cp = s->cap[kind];
+    if (!pairs) {   // the count alone: the row counts (every pair is stored once)
+        std::vector<int32_t> nc((size_t)rows);
+        CK(cudaMemcpyAsync(nc.data(), s->nc[kind], sizeof(int32_t) * rows, cudaMemcpyDeviceToHost, s->stream), "nc");
+        CK(cudaStreamSynchronize(s->stream), "sync");
+        int64_t total = 0;
+        for (int64_t r = 0; r < rows; ++r) total += nc[(size_t)r] < cp ? nc[(size_t)r] : cp;
+        *count = total;
+        return MD_OK;
+    }
     std::vector<int32_t> nc((size_t)rows), nl((size_t)(rows * cp)), ridx;
     std::vector<float> x32h((size_t)(4 * s->n));
     cudaStream_t st = s->stream;

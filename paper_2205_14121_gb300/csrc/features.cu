@@ -233,17 +233,22 @@ __global__ void k_contacts(int64_t rows, const int32_t *row_idx, const int32_t *
     }
 }
 
-__global__ void k_feature_ring(const double *feat, int P, float *ring, int T, int slot)
+// One block: every record of this step goes to slot ring_count % T, then the
+// counter advances (device-side, so a captured step graph records in place).
+__global__ void k_feature_ring(const double *feat, int P, float *ring, int T, md_dstate *ds)
 {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= P * 12) return;
-    const int p = q / 12, c = q % 12;
-    ring[((int64_t)p * T + slot) * 12 + c] = (float)feat[q];
+    const int slot = (int)(ds->ring_count % T);
+    for (int q = threadIdx.x; q < P * 12; q += blockDim.x) {
+        const int p = q / 12, c = q % 12;
+        ring[((int64_t)p * T + slot) * 12 + c] = (float)feat[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ds->ring_count += 1;
 }
 
 }  // namespace
 
-cudaError_t launch_features(md_system *s, double *out_dev)
+cudaError_t launch_features(md_system *s, double *out_dev, const float4 *f_plt)
 {
     const int P = s->cfg.n_platelets;
     if (P <= 0) return cudaSuccess;
@@ -268,7 +273,7 @@ cudaError_t launch_features(md_system *s, double *out_dev)
     a.v = s->v;
     a.f0 = s->f[0];
     a.f1 = s->f[1];
-    a.f2 = s->f[2];
+    a.f2 = f_plt ? f_plt : s->f[2];
     a.tag = s->tag_s;
     a.contacts = s->plt_contacts;
     a.g = s->gmain;
@@ -283,10 +288,10 @@ cudaError_t launch_features(md_system *s, double *out_dev)
     return cudaGetLastError();
 }
 
-cudaError_t launch_feature_ring(md_system *s, const double *feat, int slot)
+cudaError_t launch_feature_ring(md_system *s, const double *feat)
 {
     const int P = s->cfg.n_platelets;
-    k_feature_ring<<<(P * 12 + 255) / 256, 256, 0, s->stream>>>(feat, P, s->ring, s->ring_T, slot);
+    k_feature_ring<<<1, 256, 0, s->stream>>>(feat, P, s->ring, s->ring_T, s->ds);
     MSM_COUNT(s, 1);
     return cudaGetLastError();
 }

@@ -39,6 +39,7 @@ struct md_dstate {
     int64_t steps_left;  // countdown of a captured loop
     int64_t base;        // fluid steps completed when the current outer step began
     int64_t done;        // outer steps begun (next base)
+    int64_t ring_count;  // per-platelet feature records appended so far
 };
 
 struct md_grid {
@@ -100,7 +101,6 @@ struct md_system {
     double *feat;                // [P][12]
     float *ring;                 // [P][ring_T][12] time series of the measurements
     int ring_T = 128;
-    int64_t ring_count = 0;
     std::vector<int32_t> h_tag;  // tags in id order (host copy)
 
     // per-platelet step ratios (AI-MTS): platelet p takes k_p substeps per
@@ -337,8 +337,10 @@ cudaError_t launch_zero_forces(md_system *s, unsigned levels);
 // reduce.cu
 cudaError_t launch_kinetics(md_system *s);
 // features.cu
-cudaError_t launch_features(md_system *s, double *out_dev);
-cudaError_t launch_feature_ring(md_system *s, const double *feat, int slot);
+// f_plt: platelet-level forces to use (null: s->f[2])
+cudaError_t launch_features(md_system *s, double *out_dev, const float4 *f_plt = nullptr);
+// append feat to the ring at the device record counter, then advance it
+cudaError_t launch_feature_ring(md_system *s, const double *feat);
 // api.cu helpers
 int set_error(md_system *s, int code, const char *msg);
 int cuda_fail(md_system *s, cudaError_t e, const char *where);

@@ -54,15 +54,30 @@ __device__ __forceinline__ void cell_span(float x, float lo0, float R, float inv
     if (hi - lo + 1 > n) hi = lo + n - 1;
 }
 
+// Distance from x to the slab [c0, c0 + h] along one axis, less a slack that
+// covers the rounding of the cell assignment (positions sit within a few ulp
+// of their cell's nominal bounds).
+__device__ __forceinline__ float slab_gap(float x, float c0, float h)
+{
+    const float gap = fmaxf(fmaxf(c0 - x, x - (c0 + h)), 0.0f);
+    return fmaxf(gap - 1e-4f, 0.0f);
+}
+
 // Visit (member position s, particle index) of every member of the cells
-// within reach R of xi; Lees-Edwards rows that cross the y boundary are
-// shifted by the image offset.  half: skip cells with a lower index than
-// xi's own cell.
+// within reach R of xi.  Cells are at least R/2 wide; each (y, z) row of
+// cells is one or two contiguous member ranges, rows out of reach are
+// skipped and the x extent of a row is trimmed to the sphere of radius R.
+// Lees-Edwards rows that cross the y boundary are shifted by the image
+// offset.  half: skip cells with a lower index than xi's own cell, and in
+// that cell the members up to r.
 template <bool HALF, class F>
 __device__ __forceinline__ void for_candidates(const md_grid &g, const md_geom &geom, float delta, float4 xi,
                                                float R, const int32_t *__restrict__ members, int32_t r, F fn)
 {
-    const int own = cell_index32(g, cell_coord(g, 0, xi.x), cell_coord(g, 1, xi.y), cell_coord(g, 2, xi.z));
+    const int ox = cell_coord(g, 0, xi.x);
+    const int own_row = cell_coord(g, 2, xi.z) * g.nc[1] + cell_coord(g, 1, xi.y);
+    const float R2 = R * R;
+    const int nx = g.nc[0];
     int zlo, zhi, ylo, yhi;
     cell_span(xi.z, g.lo[2], R, g.inv_h[2], g.nc[2], zlo, zhi);
     cell_span(xi.y, g.lo[1], R, g.inv_h[1], g.nc[1], ylo, yhi);
@@ -72,6 +87,7 @@ __device__ __forceinline__ void for_candidates(const md_grid &g, const md_geom &
     }
     for (int cz = zlo; cz <= zhi; ++cz) {
         const int wz = wrapc(cz, g.nc[2]);
+        const float gz = slab_gap(xi.z, g.lo[2] + cz * g.h[2], g.h[2]);
         for (int cy = ylo; cy <= yhi; ++cy) {
             int wy = cy;
             float sx = 0.0f;
@@ -84,17 +100,30 @@ __device__ __forceinline__ void for_candidates(const md_grid &g, const md_geom &
                     if (geom.le) sx = -delta;
                 }
             }
-            const int rowc = cell_index32(g, 0, wy, wz);
-            if (HALF && rowc + g.nc[0] - 1 < own) continue;   // whole row below own cell
+            const int row = wz * g.nc[1] + wy;
+            if (HALF && row < own_row) continue;
+            const float gy = slab_gap(xi.y, g.lo[1] + cy * g.h[1], g.h[1]);
+            const float rem = R2 - (gy * gy + gz * gz);
+            if (rem < 0.0f) continue;
             int xlo, xhi;
-            cell_span(xi.x + sx, g.lo[0], R, g.inv_h[0], g.nc[0], xlo, xhi);
-            for (int cx = xlo; cx <= xhi; ++cx) {
-                const int c = rowc + wrapc(cx, g.nc[0]);
-                if (HALF && c < own) continue;
-                int32_t b = g.start[c];
-                const int32_t e = g.start[c + 1];
-                if (HALF && b <= r) b = r + 1;    // own cell: later members only
-                for (int32_t s = b; s < e; ++s) fn(s, members ? members[s] : s);
+            cell_span(xi.x + sx, g.lo[0], sqrtf(rem) + 1e-4f, g.inv_h[0], nx, xlo, xhi);
+            // the span as at most two runs of wrapped cell indices
+            int a0 = xlo, b0 = xhi, a1 = 0, b1 = -1;
+            if (xhi < 0) { a0 += nx; b0 += nx; }
+            else if (xlo >= nx) { a0 -= nx; b0 -= nx; }
+            else if (xlo < 0) { a0 = xlo + nx; b0 = nx - 1; a1 = 0; b1 = xhi; }
+            else if (xhi >= nx) { a0 = xlo; b0 = nx - 1; a1 = 0; b1 = xhi - nx; }
+            const int rowc = row * nx;
+#pragma unroll 1
+            for (int seg = 0; seg < 2; ++seg) {
+                int a = seg ? a1 : a0;
+                const int b = seg ? b1 : b0;
+                if (HALF && row == own_row) a = max(a, ox);
+                if (a > b) continue;
+                int32_t sb = g.start[rowc + a];
+                const int32_t se = g.start[rowc + b + 1];
+                if (HALF && row == own_row && sb <= r) sb = r + 1;
+                for (int32_t s = sb; s < se; ++s) fn(s, members ? members[s] : s);
             }
         }
     }

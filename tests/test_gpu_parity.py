@@ -336,6 +336,36 @@ def test_platelet_features_match_oracle(plt_sys, plt_wall_sys, which):
     assert np.allclose(ring[:, 0], feat.astype(np.float32))
 
 
+@pytest.mark.parametrize("mode", ["respa", "ai"])
+def test_step_graph_records_features_every_step(plt_wall_sys, mode):
+    """MD_SCHED_RECORD appends the measurements of every outer step from inside
+    the (replayed) step graph: the records equal those of one-step calls
+    followed by md_record_features; in AI-MTS they use plain platelet forces."""
+    import paper_2205_14121_gb300 as M
+    s = plt_wall_sys
+    x0, v0 = f32(s.x), f32(s.v)
+    kw = dict(mode=M.MD_MODE_RESPA, k_m=1, k_p=2) if mode == "respa" else dict(mode=M.MD_MODE_AI, k_m=1)
+    a = make_gpu(s, x=x0, v=v0)
+    b = make_gpu(s, x=x0, v=v0)
+    if mode == "ai":
+        a.set_platelet_levels([2, 2])
+        b.set_platelet_levels([2, 2])
+    a.mts_step(6, record=True, **kw)
+    for _ in range(6):
+        b.mts_step(1, **kw)
+        b.record_features()
+    ra, ca = a.read_feature_ring()
+    rb, cb = b.read_feature_ring()
+    assert ca == cb == 6 and ra.shape == (2, 6, 12)
+    scale = np.abs(rb).max(axis=(0, 1)) + 1e-9
+    assert np.all(np.abs(ra - rb) <= 2e-3 * scale + 1e-6), np.abs(ra - rb).max(axis=(0, 1)) / scale
+    if mode == "ai":   # the same step under fixed-k RESPA records the same measurements
+        c = make_gpu(s, x=x0, v=v0)
+        c.mts_step(6, record=True, mode=M.MD_MODE_RESPA, k_m=1, k_p=2)
+        rc_, _ = c.read_feature_ring()
+        assert np.all(np.abs(ra - rc_) <= 2e-3 * scale + 1e-6)
+
+
 def test_checkpoint_roundtrip(plt_sys):
     s = plt_sys
     g = make_gpu(s)
