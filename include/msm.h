@@ -90,7 +90,8 @@ typedef struct md_config {
     double   morse_D, morse_alpha, morse_r0, morse_rc, f_A; /* Eq. 2 / Eq. 4     */
     double   k_bond;                                       /* Eq. 2 bonds        */
     uint64_t seed;            /* key of the Philox4x32-10 pair noise              */
-    int32_t  cap_fluid, cap_iface, cap_lj, cap_morse; /* list capacities per row  */
+    int32_t  cap_fluid, cap_iface, cap_lj, cap_morse; /* list capacities per row;
+                                                   0: 64, 96, 1024, 256        */
 } md_config;
 
 /* Fill *cfg with the defaults above for n particles in box (no platelets). */

@@ -78,8 +78,8 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
     s.n_rec = c.n_receptors;
     s.nb = c.n_bonds;
     s.cap[MD_LIST_FLUID] = default_cap(c.cap_fluid, 64);
-    s.cap[MD_LIST_IFACE] = default_cap(c.cap_iface, 64);
-    s.cap[MD_LIST_LJ] = default_cap(c.cap_lj, 256);
+    s.cap[MD_LIST_IFACE] = default_cap(c.cap_iface, 96);
+    s.cap[MD_LIST_LJ] = default_cap(c.cap_lj, 1024);   // shells in contact: hundreds of partners
     s.cap[MD_LIST_MORSE] = default_cap(c.cap_morse, 256);
     // list cells at least half the list reach wide: the candidate scan visits
     // contiguous row ranges trimmed to the reach sphere
@@ -441,7 +441,11 @@ int enqueue_record(md_system *s, int mode)
         CK(launch_forces(s, MD_LEVEL_PLT, out, false), "record forces");
         fp = s->altf[2];
     }
-    CK(launch_features(s, s->feat, fp), "features");
+    // the stored velocities still miss the closing half kick(s) that the
+    // next step's opening kick applies: the fluid level, and in STS all levels
+    const float h = (float)(0.5 * s->cfg.dt);
+    const float hk[3] = {h, mode == MD_MODE_STS ? h : 0.f, mode == MD_MODE_STS ? h : 0.f};
+    CK(launch_features(s, s->feat, fp, hk), "features");
     CK(launch_feature_ring(s, s->feat), "feature ring");
     prof_end(s);
     return MD_OK;

@@ -90,8 +90,25 @@ struct feat_args {
     double L[3];
     float g_body;
     double flow_r2, skin;
+    float hk[3];                           // half kicks still pending per level (0: none)
     double *out;                           // [P][12]
 };
+
+// Velocity at the recorded time: the stored one plus the half kicks that a
+// step recording from inside itself has not applied yet (none otherwise).
+__device__ __forceinline__ float4 vel_at(const feat_args &a, int k)
+{
+    float4 v = a.v[k];
+    if ((a.hk[0] == 0.f && a.hk[1] == 0.f && a.hk[2] == 0.f) || a.tag[k] == MD_TAG_WALL) return v;
+    const float4 *fl[3] = {a.f0, a.f1, a.f2};
+    for (int l = 0; l < 3; ++l) {
+        if (a.hk[l] == 0.f || !fl[l]) continue;
+        const float4 q = fl[l][k];
+        v.x += a.hk[l] * q.x; v.y += a.hk[l] * q.y; v.z += a.hk[l] * q.z;
+    }
+    v.x += a.hk[0] * a.g_body;
+    return v;
+}
 
 __global__ void __launch_bounds__(FT_TPB) k_features(feat_args a)
 {
@@ -108,7 +125,7 @@ __global__ void __launch_bounds__(FT_TPB) k_features(feat_args a)
     for (int m = b + threadIdx.x; m < e; m += FT_TPB) {
         const int k = a.pos_of_id[a.plt_ids[m]];
         const float4 xk = a.x32[k];
-        const float4 vk = a.v[k];
+        const float4 vk = vel_at(a, k);
         s[0] += dimg((double)xk.x - ref.x, a.L[0], true);
         s[1] += dimg((double)xk.y - ref.y, a.L[1], py);
         s[2] += dimg((double)xk.z - ref.z, a.L[2], true);
@@ -123,7 +140,7 @@ __global__ void __launch_bounds__(FT_TPB) k_features(feat_args a)
     for (int m = b + threadIdx.x; m < e; m += FT_TPB) {
         const int k = a.pos_of_id[a.plt_ids[m]];
         const float4 xk = a.x32[k];
-        const float4 vk = a.v[k];
+        const float4 vk = vel_at(a, k);
         const double rx = dimg((double)xk.x - ref.x, a.L[0], true) - mean[0];
         const double ry = dimg((double)xk.y - ref.y, a.L[1], py) - mean[1];
         const double rz = dimg((double)xk.z - ref.z, a.L[2], true) - mean[2];
@@ -176,7 +193,7 @@ __global__ void __launch_bounds__(FT_TPB) k_features(feat_args a)
             const double dy = dimg((double)xk.y - cy, a.L[1], py);
             const double dz = dimg((double)xk.z - cz, a.L[2], true);
             if (dx * dx + dy * dy + dz * dz < a.flow_r2) {
-                const float4 vk = a.v[k];
+                const float4 vk = vel_at(a, k);
                 fs += sqrt((double)vk.x * vk.x + (double)vk.y * vk.y + (double)vk.z * vk.z);
                 fn += 1.0;
             }
@@ -248,7 +265,7 @@ __global__ void k_feature_ring(const double *feat, int P, float *ring, int T, md
 
 }  // namespace
 
-cudaError_t launch_features(md_system *s, double *out_dev, const float4 *f_plt)
+cudaError_t launch_features(md_system *s, double *out_dev, const float4 *f_plt, const float *hk)
 {
     const int P = s->cfg.n_platelets;
     if (P <= 0) return cudaSuccess;
@@ -274,6 +291,7 @@ cudaError_t launch_features(md_system *s, double *out_dev, const float4 *f_plt)
     a.f0 = s->f[0];
     a.f1 = s->f[1];
     a.f2 = f_plt ? f_plt : s->f[2];
+    for (int l = 0; l < 3; ++l) a.hk[l] = hk ? hk[l] : 0.0f;
     a.tag = s->tag_s;
     a.contacts = s->plt_contacts;
     a.g = s->gmain;

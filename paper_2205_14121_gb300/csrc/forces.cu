@@ -141,7 +141,7 @@ __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int 
 }
 
 template <bool VIR>
-__global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
+__global__ void __launch_bounds__(MSM_TPB, 4) k_dpd(pair_args a)
 {
     __shared__ dpd_smem sm;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -168,26 +168,34 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
     const int total = __shfl_sync(0xffffffffu, pre, 31);
     pre -= cnt;
     int qn = 0;
-    __syncwarp();
-    for (int base = 0; base < total; base += 32) {
-        const int f = base + lane;
-        const bool valid = f < total;
-        // row of flat entry f: the last lane whose prefix is <= f
-        int row = 0;
+    // row of flat entry f (the last lane whose prefix is <= f) and its list entry
+    auto locate = [&](int f, int &row, int32_t &j) {
+        row = 0;
 #pragma unroll
         for (int step = 16; step > 0; step >>= 1) {
             const int p = __shfl_sync(0xffffffffu, pre, row + step);
             if (p <= f) row += step;
         }
         const int k = f - __shfl_sync(0xffffffffu, pre, row);
+        j = f < total ? a.nl[(r0 + row) * a.cap + k] : 0;
+    };
+    // software pipeline over rounds of 32 entries: the list entries of round
+    // t + 2 and the positions of round t + 1 are in flight while round t is
+    // tested and its queued pairs evaluated
+    int row_c, row_n, row_nn;
+    int32_t j_c, j_n, j_nn;
+    locate(lane, row_c, j_c);
+    float4 xj_c = lane < total ? a.x32[j_c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    locate(32 + lane, row_n, j_n);
+    __syncwarp();
+    for (int base = 0; base < total; base += 32) {
+        const bool valid = base + lane < total;
+        const float4 xj_n = base + 32 + lane < total ? a.x32[j_n] : make_float4(0.f, 0.f, 0.f, 0.f);
+        locate(base + 64 + lane, row_nn, j_nn);
         bool hit = false;
-        int32_t j = 0;
-        float4 xj = make_float4(0.f, 0.f, 0.f, 0.f);
         float dx = 0.f, dy = 0.f, dz = 0.f, vsh = 0.f;
         if (valid) {
-            j = a.nl[(r0 + row) * a.cap + k];
-            xj = a.x32[j];
-            min_image_f32(a.geom, delta, sm.xi[warp][row], xj, dx, dy, dz, vsh);
+            min_image_f32(a.geom, delta, sm.xi[warp][row_c], xj_c, dx, dy, dz, vsh);
             const float r2 = dx * dx + dy * dy + dz * dz;
             hit = r2 < a.rc2 && r2 > 0.0f;
         }
@@ -195,7 +203,7 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
         if (hit) {
             const int pos = qn + __popc(m & lt);
             sm.qa[warp][pos] = make_float4(dx, dy, dz, vsh);
-            sm.qb[warp][pos] = make_int4(j, row, (int)id_of(xj), 0);
+            sm.qb[warp][pos] = make_int4(j_c, row_c, (int)id_of(xj_c), 0);
         }
         qn += __popc(m);
         __syncwarp();
@@ -209,6 +217,8 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
             qn -= 32;
             __syncwarp();
         }
+        row_c = row_n; j_c = j_n; xj_c = xj_n;
+        row_n = row_nn; j_n = j_nn;
     }
     if (qn > 0) dpd_batch<VIR>(a, sm, warp, lane, lane < qn, nt, cs, w);
     __syncwarp();

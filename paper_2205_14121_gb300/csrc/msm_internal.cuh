@@ -337,8 +337,10 @@ cudaError_t launch_zero_forces(md_system *s, unsigned levels);
 // reduce.cu
 cudaError_t launch_kinetics(md_system *s);
 // features.cu
-// f_plt: platelet-level forces to use (null: s->f[2])
-cudaError_t launch_features(md_system *s, double *out_dev, const float4 *f_plt = nullptr);
+// f_plt: platelet-level forces to use (null: s->f[2]); hk: half kicks per
+// level still pending on the stored velocities (null: none)
+cudaError_t launch_features(md_system *s, double *out_dev, const float4 *f_plt = nullptr,
+                            const float *hk = nullptr);
 // append feat to the ring at the device record counter, then advance it
 cudaError_t launch_feature_ring(md_system *s, const double *feat);
 // api.cu helpers
