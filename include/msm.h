@@ -224,8 +224,8 @@ int md_mts_step(md_system *sys, int64_t n_outer, const md_mts_schedule *sched);
  * interior points K/c, 2K/c, ...  Both ends of a pair get the same impulse at
  * the same time, so momentum is conserved, and with all k_p equal this is
  * MD_MODE_RESPA with that k_p.  During an AI-MTS call the platelet force
- * buffer holds impulses; plain forces are recomputed by the next call that
- * needs them.  Each k_p >= 1 and K <= MD_AI_K_LCM_MAX.  Copies synchronously;
+ * buffer holds impulses; the call ends by evaluating the plain platelet
+ * forces of the final state.  Each k_p >= 1 and K <= MD_AI_K_LCM_MAX.  Copies synchronously;
  * the ratios may change between md_mts_step calls (a new K recaptures the
  * step graph).  Errors: MD_EINVAL (no platelets, k out of range), MD_ECUDA.
  */

@@ -104,7 +104,7 @@ def training_system(seed, box=(32.0, 16.0, 16.0), n_shell=600, shear_rate=0.05):
     radii = synth.scaled_radii(n_shell)
     a, b = radii[0], radii[1]
     x0 = rng.uniform(a + 1.0, Lx - 3 * a - 3.0)
-    gap = rng.uniform(0.6, 1.6)
+    gap = rng.uniform(1.0, 1.8)
     centers = [(x0, b + 1.2, Lz / 2), (x0 + 2 * a + gap, b + 1.2 + rng.uniform(-0.3, 0.3), Lz / 2),
                (rng.uniform(a + 1, Lx - a - 1), Ly / 2 + rng.uniform(1.0, 3.0), rng.uniform(b + 1, Lz - b - 1)),
                (rng.uniform(a + 1, Lx - a - 1), Ly - b - 2.0, rng.uniform(b + 1, Lz - b - 1))]

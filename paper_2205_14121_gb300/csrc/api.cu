@@ -997,7 +997,6 @@ int md_mts_step(md_system *s, int64_t n_outer, const md_mts_schedule *sched)
         rc = enqueue_forces(s, MD_LEVEL_PLT);
         s->due_on = false;
         if (rc) return rc;
-        s->forces_stale = true;   // plain forces again at the next call that needs them
     }
     rc = enqueue_outer_step(s, mode, k_m, k_p, true, nullptr, record);
     if (rc) return rc;
@@ -1031,6 +1030,12 @@ int md_mts_step(md_system *s, int64_t n_outer, const md_mts_schedule *sched)
         rc = closing_kick(s, (float)(0.5 * c.dt), 0.f, 0.f);
     }
     if (rc) return rc;
+    if (mode == MD_MODE_AI) {
+        // the platelet buffer held impulses: plain platelet forces of the final state
+        CK(cudaMemsetAsync(s->f[2], 0, sizeof(float4) * s->n, s->stream), "zero platelet level");
+        rc = enqueue_forces(s, MD_LEVEL_PLT);
+        if (rc) return rc;
+    }
     s->host_step += n_outer;
     return check_flags(s);
 }

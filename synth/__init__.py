@@ -152,7 +152,7 @@ class _Occupancy:
 
 def _place_platelets(rng, n_plt, n_shell, radii, lo, hi, centers_fn=None,
                      max_tries=20000, occ=None, periodic_xz=None):
-    """Random non-overlapping placements; returns list of (points, center)."""
+    """Random non-overlapping placements; returns list of (points, center, rotation)."""
     body = spheroid_shell(n_shell, radii)
     occ = occ or _Occupancy(lo, hi)
     out = []
@@ -166,13 +166,14 @@ def _place_platelets(rng, n_plt, n_shell, radii, lo, hi, centers_fn=None,
             c = centers_fn(rng)
         else:
             c = lo + rmax + 1.0 + (np.asarray(hi) - np.asarray(lo) - 2 * rmax - 2.0) * rng.random(3)
-        pts = body @ random_rotation(rng).T + c
+        rot = random_rotation(rng)
+        pts = body @ rot.T + c
         if (pts < np.asarray(lo) + 0.5).any() or (pts > np.asarray(hi) - 0.5).any():
             continue
         if not occ.free(pts):
             continue
         occ.mark(pts)
-        out.append((pts, c))
+        out.append((pts, c, rot))
     return out
 
 
@@ -180,7 +181,7 @@ def _assemble(box, fluid_x, wall_x, plts, rng, n_shell, receptor_frac, kT=1.0):
     nf = fluid_x.shape[0]
     nw = wall_x.shape[0]
     npl = len(plts)
-    xs = [fluid_x, wall_x] + [p for p, _ in plts]
+    xs = [fluid_x, wall_x] + [p[0] for p in plts]
     x = np.concatenate(xs, axis=0) if xs else np.zeros((0, 3))
     n = x.shape[0]
     tag = np.empty(n, dtype=np.int32)
@@ -207,6 +208,39 @@ def _assemble(box, fluid_x, wall_x, plts, rng, n_shell, receptor_frac, kT=1.0):
     bonds = np.concatenate(bonds, axis=0).astype(np.int32) if bonds else np.zeros((0, 2), np.int32)
     r0 = np.concatenate(r0s) if r0s else np.zeros((0,), np.float64)
     return x, v, tag, bonds, r0
+
+
+def _fill_platelets(rng, fx, plts, radii, box, gap, rho=3.0):
+    """Plasma around and inside the shells: positions inside a spheroid or
+    closer than `gap` to its membrane are dropped, and each interior gets
+    rho x (its full volume) positions drawn uniformly in the spheroid shrunk
+    by `gap`.  A plasma particle on top of the dense membrane would start
+    under the summed repulsion of dozens of membrane particles, and a shell
+    without its interior fluid collapses under the outer pressure (it has no
+    bending stiffness); a slightly denser interior keeps it inflated."""
+    from scipy.spatial import cKDTree
+    L = np.asarray(box, dtype=np.float64)
+    a = np.asarray(radii, dtype=np.float64)
+    keep = np.ones(len(fx), dtype=bool)
+    tree = cKDTree(fx % L, boxsize=L)
+    interiors = []
+    for pts, c, rot in plts:
+        near = np.asarray(tree.query_ball_point(np.asarray(c) % L, a.max() + gap), dtype=np.int64)
+        if len(near):
+            d = fx[near] - c
+            d -= L * np.round(d / L)
+            y = d @ rot                                   # body frame
+            inside = ((y / a) ** 2).sum(1) < 1.0
+            dm, _ = cKDTree(pts).query(c + d, distance_upper_bound=gap)
+            keep[near[inside | np.isfinite(dm)]] = False
+        n_in = int(round(rho * 4.0 / 3.0 * np.pi * a.prod()))
+        b = np.maximum(a - gap, 0.05)
+        u = rng.standard_normal((n_in, 3))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        u *= rng.random((n_in, 1)) ** (1.0 / 3.0)
+        interiors.append((u * b) @ rot.T + c)
+    out = np.concatenate([fx[keep]] + interiors, axis=0)
+    return out % L if len(out) else out
 
 
 def wall_layers(rng, box, wall, rho=3.0):
@@ -241,8 +275,11 @@ def plasma_box(n=None, box=None, rho=3.0, walls=False, wall=1.0, body_force=0.0,
 
 def platelet_system(box, n_plasma, n_plt, n_shell, radii, walls=False, wall=1.0,
                     shear_rate=0.0, body_force=0.0, receptor_frac=0.05,
-                    seed=DEFAULT_SEED, centers=None, clusters=None, kT=1.0):
-    """Plasma + spheroid platelet shells (Fig. 1 shapes, synthetic sizes)."""
+                    seed=DEFAULT_SEED, centers=None, clusters=None, kT=1.0, plasma_gap=0.8):
+    """Plasma + spheroid platelet shells (Fig. 1 shapes, synthetic sizes).
+
+    n_plasma plasma positions are drawn uniformly; see _fill_platelets for
+    how the plasma meets the membranes."""
     rng = rng_for(seed)
     box = tuple(float(b) for b in box)
     lo = np.zeros(3)
@@ -252,9 +289,10 @@ def platelet_system(box, n_plasma, n_plt, n_shell, radii, walls=False, wall=1.0,
     if centers is not None:
         body = spheroid_shell(n_shell, radii)
         for c in centers:
-            pts = body @ random_rotation(rng).T + np.asarray(c, dtype=np.float64)
+            rot = random_rotation(rng)
+            pts = body @ rot.T + np.asarray(c, dtype=np.float64)
             occ.mark(pts)
-            plts.append((pts, np.asarray(c)))
+            plts.append((pts, np.asarray(c, dtype=np.float64), rot))
     if clusters:
         for (cx, cy, cz, spread, count) in clusters:
             def cfn(r, cx=cx, cy=cy, cz=cz, spread=spread):
@@ -264,6 +302,8 @@ def platelet_system(box, n_plasma, n_plt, n_shell, radii, walls=False, wall=1.0,
     if rest > 0:
         plts += _place_platelets(rng, rest, n_shell, radii, lo, hi, occ=occ)
     fx = uniform_box(rng, n_plasma, (0, 0, 0), box)
+    if plts and len(fx):
+        fx = _fill_platelets(rng, fx, plts, radii, box, plasma_gap)
     wx = wall_layers(rng, box, wall) if walls else np.zeros((0, 3))
     x, v, tag, bonds, r0 = _assemble(box, fx, wx, plts, rng, n_shell, receptor_frac, kT)
     return System(box=box, x=x, v=v, tag=tag, X0=x.copy(), bonds=bonds, r0=r0,
