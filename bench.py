@@ -212,7 +212,7 @@ def kernel_source_hash():
 def ncu_traffic(workload_name):
     """DRAM bytes per launch of the fluid DPD kernel from a committed ncu
     summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    path = os.path.join(ROOT, "profiles", "k_dpd_traffic.json")
     try:
         d = json.load(open(path))
         e = d.get(workload_name)

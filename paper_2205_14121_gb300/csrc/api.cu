@@ -331,12 +331,14 @@ int eval_forces(md_system *s, unsigned levels, bool virial)
     return MD_OK;
 }
 
+// Lists first, always: forces restored from a checkpoint are current while
+// the lists of the new particle order are not.
 int ensure_forces(md_system *s)
 {
     const unsigned all = s->n_plt > 0 ? MD_LEVEL_ALL : MD_LEVEL_FLUID;
-    if (!s->forces_stale && (s->forces_levels & all) == all) return MD_OK;
     int rc = ensure_lists(s);
     if (rc) return rc;
+    if (!s->forces_stale && (s->forces_levels & all) == all) return MD_OK;
     rc = eval_forces(s, all, false);
     if (rc) return rc;
     s->forces_stale = false;
@@ -817,6 +819,10 @@ int md_set_particles(md_system *s, const double *x, const double *v, const int32
     h->le_build_f = h->le_offset_f;
     CK(cudaMemcpyAsync(s->ds, h, sizeof(md_dstate), cudaMemcpyHostToDevice, st), "upload dstate");
     CK(cudaMemsetAsync(s->ctl, 0, sizeof(int32_t) * CTL_WORDS, st), "reset ctl");
+    // empty rows until the first build (the workspace holds stale contents)
+    const int64_t rows_k[4] = {s->n, s->n_plt, s->n_plt, s->n_rec};
+    for (int k = 0; k < 4; ++k)
+        if (s->nc[k] && rows_k[k] > 0) CK(cudaMemsetAsync(s->nc[k], 0, sizeof(int32_t) * rows_k[k], st), "reset rows");
     CK(cudaStreamSynchronize(st), "set_particles sync");
     s->host_step = step0;
     s->host_sub = 0;

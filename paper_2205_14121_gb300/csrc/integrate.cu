@@ -121,11 +121,15 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
             float dx, dy, dz, vs;
             min_image_f32(a.geom, a.ds->le_offset_f, xn, a.xb[k], dx, dy, dz, vs);
             const float d2 = dx * dx + dy * dy + dz * dz;
-            float thr = a.skin_half - a.margin;
+            // the margin covers platelet particles, which keep drifting in the
+            // inner substeps after this check and before the rebuild point at
+            // the end of the interface substep; plasma does not move in between
+            const float mg = t >= 0 ? a.margin : 0.0f;
+            float thr = a.skin_half - mg;
             if (a.geom.le) {
                 float dd = fabsf(a.ds->le_offset_f - a.ds->le_build_f);
                 dd = fminf(dd, a.geom.L[0] - dd);
-                thr = 0.5f * (a.skin - dd) - a.margin;
+                thr = 0.5f * (a.skin - dd) - mg;
             }
             if (!(d2 <= thr * thr) || thr <= 0.0f) a.ctl[CTL_REBUILD] = 1;
             const bool bad = !(fabsf(xf) + fabsf(yf) + fabsf(zf) < 1e30f) ||

@@ -210,109 +210,6 @@ __global__ void __launch_bounds__(MSM_TPB) k_build(build_args a, const int32_t *
     }
 }
 
-// The plasma / wall list, warp-flattened: every lane first records the
-// member runs of its row's candidates in shared memory, then the warp walks
-// the concatenated candidates of its 32 rows 32 at a time (the owner row of
-// flat entry f is found by a shuffle binary search over the rows' prefix
-// offsets, the run by a search over the owner's run prefix), so all lanes
-// test pairs whatever the row lengths.  Passing pairs are appended to their
-// row through a shared-memory counter (entry order within a row is free).
-// Runs beyond BF_RUNS per row are tested by their own lane afterwards.
-constexpr int BF_WARPS = MSM_TPB / 32;
-constexpr int BF_RUNS = 16;
-
-struct bflat_smem {
-    float4 xi[BF_WARPS][32];
-    int32_t rs[BF_WARPS][BF_RUNS][32];    // run starts, [warp][run][lane]
-    int32_t rc[BF_WARPS][BF_RUNS][32];    // inclusive prefix of run lengths
-    int32_t cnt[BF_WARPS][32];
-};
-
-__device__ __forceinline__ bool fluid_pair(const build_args &a, float4 xi, float delta, int ci, int32_t j)
-{
-    const float4 xj = a.x32[j];
-    const int cj = class_of(xj);
-    if (cj == CLS_PLT || (ci == CLS_WALL && cj == CLS_WALL)) return false;
-    float dx, dy, dz, vs;
-    min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vs);
-    return r2_f32(dx, dy, dz) < a.cut2;
-}
-
-__global__ void __launch_bounds__(MSM_TPB) k_build_fluid(build_args a, const int32_t *gate)
-{
-    if (gate_closed(gate)) return;
-    __shared__ bflat_smem sm;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t r0 = r - lane;
-    const bool active = r < a.rows;
-    const float delta = a.ds->le_offset_f;
-    const float4 xi = active ? a.x32[r] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int ci = class_of(xi);
-    sm.xi[warp][lane] = xi;
-    sm.cnt[warp][lane] = 0;
-    int nrun = 0, tot = 0;
-    if (active && ci != CLS_PLT) {
-        for_ranges<true>(a.g, a.geom, delta, xi, a.R, (int32_t)r, [&](int32_t sb, int32_t se) {
-            if (nrun < BF_RUNS) {
-                tot += se - sb;
-                sm.rs[warp][nrun][lane] = sb;
-                sm.rc[warp][nrun][lane] = tot;
-            }
-            ++nrun;
-        });
-    }
-    // exclusive prefix of the lanes' candidate counts
-    int pre = tot;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, pre, o);
-        if (lane >= o) pre += t;
-    }
-    const int total = __shfl_sync(0xffffffffu, pre, 31);
-    pre -= tot;
-    __syncwarp();
-    for (int base = 0; base < total; base += 32) {
-        const int f = base + lane;
-        int own = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int p = __shfl_sync(0xffffffffu, pre, own + step);
-            if (p <= f) own += step;
-        }
-        const int q = f - __shfl_sync(0xffffffffu, pre, own);
-        if (f < total) {
-            int k = 0;                                   // first run whose prefix exceeds q
-            while (sm.rc[warp][k][own] <= q) ++k;
-            const int32_t j = sm.rs[warp][k][own] + q - (k ? sm.rc[warp][k - 1][own] : 0);
-            const float4 xo = sm.xi[warp][own];
-            if (fluid_pair(a, xo, delta, class_of(xo), j)) {
-                const int pos = atomicAdd(&sm.cnt[warp][own], 1);
-                if (pos < a.cap) a.nl[(r0 + own) * a.cap + pos] = j;
-            }
-        }
-    }
-    __syncwarp();
-    int cnt = sm.cnt[warp][lane];
-    if (nrun > BF_RUNS) {      // runs that did not fit: this lane tests them itself
-        int k = 0;
-        for_ranges<true>(a.g, a.geom, delta, xi, a.R, (int32_t)r, [&](int32_t sb, int32_t se) {
-            if (k++ < BF_RUNS) return;
-            for (int32_t j = sb; j < se; ++j)
-                if (fluid_pair(a, xi, delta, ci, j)) {
-                    if (cnt < a.cap) a.nl[r * a.cap + cnt] = j;
-                    ++cnt;
-                }
-        });
-    }
-    if (active) a.nc[r] = cnt;
-    const int m = __reduce_max_sync(0xffffffffu, active ? cnt : 0);
-    if (lane == 0 && m > 0) {
-        atomicMax(&a.ctl[CTL_MAXROW + MD_LIST_FLUID], m);
-        if (m > a.cap) atomicOr(&a.ctl[CTL_OVERFLOW], 1 << MD_LIST_FLUID);
-    }
-}
-
 inline unsigned blocks_for(int64_t n) { return (unsigned)(n > 0 ? (n + MSM_TPB - 1) / MSM_TPB : 1); }
 
 }  // namespace
@@ -340,7 +237,7 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
     a.nl = s->nl[MD_LIST_FLUID];
     a.nc = s->nc[MD_LIST_FLUID];
     a.cap = s->cap[MD_LIST_FLUID];
-    k_build_fluid<<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
+    k_build<MD_LIST_FLUID><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
 
     if (s->n_plt > 0) {
         // interface: platelet rows (platelet sub-grid order) against the main grid

@@ -213,11 +213,12 @@ def _assemble(box, fluid_x, wall_x, plts, rng, n_shell, receptor_frac, kT=1.0):
 def _fill_platelets(rng, fx, plts, radii, box, gap, rho=3.0):
     """Plasma around and inside the shells: positions inside a spheroid or
     closer than `gap` to its membrane are dropped, and each interior gets
-    rho x (its full volume) positions drawn uniformly in the spheroid shrunk
-    by `gap`.  A plasma particle on top of the dense membrane would start
-    under the summed repulsion of dozens of membrane particles, and a shell
-    without its interior fluid collapses under the outer pressure (it has no
-    bending stiffness); a slightly denser interior keeps it inflated."""
+    1.1 rho x (the volume of the spheroid shrunk by `gap`) positions drawn
+    uniformly in that shrunken spheroid.  A plasma particle on top of the
+    dense membrane would start under the summed repulsion of dozens of
+    membrane particles, and a shell without its interior fluid collapses
+    under the outer pressure (it has no bending stiffness); a slightly denser
+    interior keeps it inflated."""
     from scipy.spatial import cKDTree
     L = np.asarray(box, dtype=np.float64)
     a = np.asarray(radii, dtype=np.float64)
@@ -233,8 +234,8 @@ def _fill_platelets(rng, fx, plts, radii, box, gap, rho=3.0):
             inside = ((y / a) ** 2).sum(1) < 1.0
             dm, _ = cKDTree(pts).query(c + d, distance_upper_bound=gap)
             keep[near[inside | np.isfinite(dm)]] = False
-        n_in = int(round(rho * 4.0 / 3.0 * np.pi * a.prod()))
         b = np.maximum(a - gap, 0.05)
+        n_in = int(round(1.1 * rho * 4.0 / 3.0 * np.pi * b.prod()))
         u = rng.standard_normal((n_in, 3))
         u /= np.linalg.norm(u, axis=1, keepdims=True)
         u *= rng.random((n_in, 1)) ** (1.0 / 3.0)
