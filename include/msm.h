@@ -69,8 +69,11 @@ extern "C" {
  * System configuration.  Defaults follow the paper's model as read for the
  * synthetic systems: Eq. 1 a = 25 (plasma-plasma, plasma-wall), gamma = 4.5,
  * sigma = 3, rc = 1; Eq. 3 interface DPD a_fp = 50; Eq. 2 LJ eps = 1,
- * sigma = 0.8, cut-off 2.5 sigma, k_b = 100; Eq. 2/4 Morse D = 2,
- * alpha = 2, r0 = 1 with cut-off 5.
+ * sigma = 0.8, cut-off 2.5 sigma, between particles of different platelets
+ * (lj_excl = 1e30: a same-platelet pair feels LJ only when its rest distance
+ * is at least lj_excl -- the shells have no bending stiffness, so a fold of
+ * the 0.22-spaced membrane would overlap dozens of LJ cores at once), k_b =
+ * 100; Eq. 2/4 Morse D = 2, alpha = 2, r0 = 1 with cut-off 5.
  */
 typedef struct md_config {
     int64_t  n;               /* particles (plasma + wall + platelet)            */

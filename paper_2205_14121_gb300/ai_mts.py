@@ -95,19 +95,18 @@ def run_ai_mts(system, controller, n_steps, k_m=1, trust=None, T=128, log=None):
 # training data
 # ---------------------------------------------------------------------------
 
-def training_system(seed, box=(32.0, 16.0, 16.0), n_shell=600, shear_rate=0.05):
+def training_system(seed, box=(36.0, 18.0, 16.0), n_shell=2000, shear_rate=0.05):
     """A walled channel with four platelets: two close to each other near the
-    lower wall (contacting, fast dynamics) and two in the flow."""
+    lower wall (in contact range, fast dynamics) and two placed at random in
+    the flow."""
     import synth
     rng = np.random.default_rng(seed)
     Lx, Ly, Lz = box
     radii = synth.scaled_radii(n_shell)
-    a, b = radii[0], radii[1]
+    a = radii[0]
     x0 = rng.uniform(a + 1.0, Lx - 3 * a - 3.0)
     gap = rng.uniform(1.0, 1.8)
-    centers = [(x0, b + 1.2, Lz / 2), (x0 + 2 * a + gap, b + 1.2 + rng.uniform(-0.3, 0.3), Lz / 2),
-               (rng.uniform(a + 1, Lx - a - 1), Ly / 2 + rng.uniform(1.0, 3.0), rng.uniform(b + 1, Lz - b - 1)),
-               (rng.uniform(a + 1, Lx - a - 1), Ly - b - 2.0, rng.uniform(b + 1, Lz - b - 1))]
+    centers = [(x0, a + 1.0, Lz / 2), (x0 + 2 * a + gap, a + 1.0 + rng.uniform(-0.3, 0.3), Lz / 2)]
     n_pl = int(round(3.0 * Lx * Ly * Lz))
     g = synth.poiseuille_g(shear_rate, synth.ETA_DPD, 3.0, Ly)
     return synth.platelet_system(box, n_pl, 4, n_shell, radii, walls=True, body_force=g, seed=seed,
@@ -178,7 +177,7 @@ class Dataset:
                 cat(self.err_v))
 
 
-def generate(seeds, n_windows=8, warmup=50, horizon=50, k_m=1, k_record=10, T=128, n_shell=600, progress=None):
+def generate(seeds, n_windows=8, warmup=50, horizon=50, k_m=1, k_record=10, T=128, n_shell=2000, progress=None):
     """Windows of per-platelet measurements under fixed-k RESPA (k_record),
     each labelled from the continuations at its end."""
     data = Dataset()

@@ -653,7 +653,7 @@ int md_config_defaults(md_config *c)
     c->dt = 0.01;
     c->skin = 0.3;
     c->rc = 1.0; c->a_ff = 25.0; c->a_fw = 25.0; c->a_fp = 50.0; c->gamma = 4.5; c->sigma = 3.0;
-    c->lj_eps = 1.0; c->lj_sigma = 0.8; c->lj_rc = 2.0; c->lj_excl = 2.5;
+    c->lj_eps = 1.0; c->lj_sigma = 0.8; c->lj_rc = 2.0; c->lj_excl = 1e30;   // no LJ within one platelet
     c->morse_D = 2.0; c->morse_alpha = 2.0; c->morse_r0 = 1.0; c->morse_rc = 5.0; c->f_A = 0.0;
     c->k_bond = 100.0;
     c->seed = 20220528ull;

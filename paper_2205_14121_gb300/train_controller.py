@@ -29,7 +29,7 @@ def main(argv=None):
     ap.add_argument("--test-seeds", type=int, default=6)
     ap.add_argument("--windows", type=int, default=8)
     ap.add_argument("--horizon", type=int, default=50)
-    ap.add_argument("--n-shell", type=int, default=600)
+    ap.add_argument("--n-shell", type=int, default=2000)
     ap.add_argument("--epochs-ae", type=int, default=40)
     ap.add_argument("--epochs-heads", type=int, default=80)
     ap.add_argument("--dataset", default=None, help="save / reuse the labelled windows here (.npz)")

@@ -87,7 +87,7 @@ def wall_sys():
 @pytest.mark.parametrize("kind", [0, 1, 2, 3])
 def test_neighbor_sets_bit_exact(plt_sys, kind):
     s = plt_sys
-    g = make_gpu(s, step0=17)
+    g = make_gpu(s, step0=17, lj_excl=2.5)     # an exclusion radius that keeps far-at-rest pairs
     g.neighbor_build(force=True)
     got = g.neighbor_pairs(kind)
     _, _, x32 = g.read_particles()

@@ -217,8 +217,13 @@ def test_receptor_term_fA():
 
 
 def test_lj_rest_distance_exclusion():
-    """Same-platelet pairs closer than 2.5 at rest feel no LJ; far-at-rest pairs do."""
-    p = O.make_params((20, 20, 20), m_D=0.0)
+    """With an exclusion radius of 2.5, same-platelet pairs closer than that at
+    rest feel no LJ and far-at-rest pairs do; the default radius excludes every
+    pair of one platelet."""
+    pd = O.make_params((20, 20, 20), m_D=0.0)
+    x, v, tag, X0 = plt_pair(1.0, rec=False, same=True, X0_far=True)
+    assert np.all(O.forces_brute(pd, x, v, tag, X0=X0)[0] == 0)
+    p = O.make_params((20, 20, 20), m_D=0.0, lj_excl=2.5)
     x, v, tag, X0 = plt_pair(1.0, rec=False, same=True, X0_far=False)
     assert np.all(O.forces_brute(p, x, v, tag, X0=X0)[0] == 0)
     x, v, tag, X0 = plt_pair(1.0, rec=False, same=True, X0_far=True)
