@@ -131,11 +131,22 @@ def continuation_errors(system, horizon, k_m=1):
     means = {}
     for k in K_SET:
         system.set_state(blob)
-        system.mts_step(horizon, mode=B.MD_MODE_RESPA, k_m=k_m, k_p=k, record=True)
+        try:
+            system.mts_step(horizon, mode=B.MD_MODE_RESPA, k_m=k_m, k_p=k, record=True)
+        except B.MdError as e:      # a ratio too coarse for these dynamics
+            if e.code != -5:
+                raise
+            means[k] = None
+            continue
         rec, _ = system.read_feature_ring()
         means[k] = _means(rec[:, -horizon:])
     system.set_state(blob)
+    if means[K_SET[-1]] is None:
+        return None, None
     s_ref, v_ref = means[K_SET[-1]]
+    for k in K_SET:
+        if means[k] is None:
+            means[k] = (np.full_like(s_ref, np.inf), np.full_like(v_ref, np.inf))
     v_scale = np.linalg.norm(v_ref, axis=1) + 0.05
     s_scale = np.linalg.norm(s_ref, axis=1) + 1e-6
     es = np.stack([np.linalg.norm(means[k][0] - s_ref, axis=1) / s_scale for k in K_SET], 1)
@@ -183,27 +194,42 @@ def generate(seeds, n_windows=8, warmup=50, horizon=50, k_m=1, k_record=10, T=12
     data = Dataset()
     for seed in seeds:
         sys = make_system(training_system(seed, n_shell=n_shell), seed=int(seed))
-        sys.mts_step(warmup, mode=B.MD_MODE_RESPA, k_m=k_m, k_p=k_record)
+        try:
+            sys.mts_step(warmup, mode=B.MD_MODE_RESPA, k_m=k_m, k_p=k_record)
+        except B.MdError as e:
+            if e.code != -5:
+                raise
+            sys.close()
+            continue
         wins, cls, es_all, ev_all = [], [], [], []
         for w in range(n_windows):
             blob = sys.get_state()
             sys.set_state(blob)                      # restart the ring at this window
-            sys.mts_step(T, mode=B.MD_MODE_RESPA, k_m=k_m, k_p=k_record, record=True)
+            try:
+                sys.mts_step(T, mode=B.MD_MODE_RESPA, k_m=k_m, k_p=k_record, record=True)
+            except B.MdError as e:
+                if e.code != -5:
+                    raise
+                break                                # this trajectory went unstable
             win, cnt = sys.read_feature_ring()
             es, ev = continuation_errors(sys, horizon, k_m=k_m)
+            if es is None:
+                break
             wins.append(win)
             cls.append(label_from_errors(es, ev))
             es_all.append(es)
             ev_all.append(ev)
+        sys.close()
+        if not cls:
+            continue
         classes = np.stack(cls)
         holds = hold_labels(classes, T)
-        for w in range(n_windows):
+        for w in range(len(cls)):
             data.windows.append(wins[w])
             data.classes.append(classes[w])
             data.holds.append(holds[w])
             data.err_s.append(es_all[w])
             data.err_v.append(ev_all[w])
-        sys.close()
         if progress:
             progress(seed, classes)
     return data

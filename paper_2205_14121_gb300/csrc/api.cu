@@ -163,6 +163,8 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
         s.feat = cv.take<double>(12 * P);
         s.ring = cv.take<float>(P * (int64_t)s.ring_T * 12);
         s.plt_k = cv.take<int32_t>(P);
+        s.plt_bound = cv.take<float4>(P);
+        s.plt_near = cv.take<int32_t>(P);
     }
     s.red_blocks = (int)((n + MSM_TPB - 1) / MSM_TPB);
     if (s.red_blocks > RED_BLOCKS_MAX) s.red_blocks = RED_BLOCKS_MAX;

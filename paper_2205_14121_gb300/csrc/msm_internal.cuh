@@ -98,6 +98,8 @@ struct md_system {
     int32_t *plt_off, *plt_ids;  // member ids of platelet p: plt_ids[plt_off[p] .. plt_off[p+1])
     int32_t *bond_off;
     int32_t *plt_contacts;
+    float4 *plt_bound;           // per platelet at the last build: centre of mass, radius
+    int32_t *plt_near;           // bit 0 / 1: another platelet within LJ / Morse reach
     double *feat;                // [P][12]
     float *ring;                 // [P][ring_T][12] time series of the measurements
     int ring_T = 128;

@@ -154,6 +154,8 @@ struct build_args {
     int32_t *nl, *nc;
     int cap;
     int32_t *ctl;
+    const int32_t *near;        // LJ / Morse kinds: platelets with a neighbour platelet in reach
+    int near_bit;
 };
 
 template <int KIND>
@@ -173,6 +175,13 @@ __global__ void __launch_bounds__(MSM_TPB) k_build(build_args a, const int32_t *
             int32_t ti = 0;
             float4 x0i = make_float4(0.f, 0.f, 0.f, 0.f);
             if (KIND == MD_LIST_LJ || KIND == MD_LIST_MORSE) ti = a.tag[i] & ~MD_RECEPTOR_BIT;
+            // no other platelet within reach of this one's bounding sphere: no
+            // partner can pass (same-platelet pairs need a rest distance of at
+            // least lj_excl, which the caller rules out before using `near`)
+            if ((KIND == MD_LIST_LJ || KIND == MD_LIST_MORSE) && a.near && !(a.near[ti] & a.near_bit)) {
+                if (active) a.nc[r] = 0;
+                goto done;
+            }
             if (KIND == MD_LIST_LJ) x0i = a.X0[id_of(xi)];
             const int64_t rows = a.rows;
             for_candidates<HALF>(a.g, a.geom, delta, xi, a.R, a.members, (int32_t)r, [&](int32_t s, int32_t j) {
@@ -201,12 +210,96 @@ __global__ void __launch_bounds__(MSM_TPB) k_build(build_args a, const int32_t *
             });
         }
     }
+done:
     // every lane of the warp reaches the row bookkeeping (shuffle needs all)
     if (active) a.nc[r] = cnt;
     const int m = __reduce_max_sync(0xffffffffu, active ? cnt : 0);
     if ((threadIdx.x & 31) == 0 && m > 0) {
         atomicMax(&a.ctl[CTL_MAXROW + KIND], m);
         if (m > a.cap) atomicOr(&a.ctl[CTL_OVERFLOW], 1 << KIND);
+    }
+}
+
+// Bounding sphere of every platelet at the build: centre of mass (minimum
+// image offsets from the first member) and the largest member distance from
+// it.  One block per platelet.
+__global__ void __launch_bounds__(256) k_plt_bounds(const int32_t *__restrict__ off, const int32_t *__restrict__ ids,
+                                                    const int32_t *__restrict__ pos_of_id, const float4 *__restrict__ x32,
+                                                    md_geom geom, const md_dstate *ds, float4 *bound,
+                                                    const int32_t *gate)
+{
+    if (gate_closed(gate)) return;
+    __shared__ float red[4][8];
+    const float delta = ds->le_offset_f;
+    const int p = blockIdx.x, b = off[p], e = off[p + 1];
+    const float4 ref = x32[pos_of_id[ids[b]]];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float s[3] = {0.f, 0.f, 0.f};
+    for (int m = b + threadIdx.x; m < e; m += blockDim.x) {
+        const float4 xm = x32[pos_of_id[ids[m]]];
+        float dx, dy, dz, vs;
+        min_image_f32(geom, delta, xm, ref, dx, dy, dz, vs);
+        s[0] += dx; s[1] += dy; s[2] += dz;
+    }
+    for (int k = 0; k < 3; ++k) {
+        float v = s[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][w] = v;
+    }
+    __syncthreads();
+    float c[3];
+    for (int k = 0; k < 3; ++k) {
+        float t = 0.f;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[k][q];
+        c[k] = t / (float)(e - b);
+    }
+    float rmax = 0.f;
+    for (int m = b + threadIdx.x; m < e; m += blockDim.x) {
+        const float4 xm = x32[pos_of_id[ids[m]]];
+        float dx, dy, dz, vs;
+        min_image_f32(geom, delta, xm, ref, dx, dy, dz, vs);
+        dx -= c[0]; dy -= c[1]; dz -= c[2];
+        rmax = fmaxf(rmax, dx * dx + dy * dy + dz * dz);
+    }
+    rmax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(rmax)));   // rmax >= 0
+    __syncthreads();
+    if (lane == 0) red[3][w] = rmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float r2 = 0.f;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r2 = fmaxf(r2, red[3][q]);
+        bound[p] = make_float4(ref.x + c[0], ref.y + c[1], ref.z + c[2], sqrtf(r2));
+    }
+}
+
+// near[p] bit 0 (1): some other platelet's bounding sphere comes within the
+// LJ (Morse) list reach of p's.  Under Lees-Edwards the x separation of a
+// pair across the y boundary is taken as zero (its image offset varies).
+__global__ void k_plt_near(const float4 *__restrict__ bound, int P, md_geom geom, float reach_lj, float reach_m,
+                           int32_t *near, const int32_t *gate)
+{
+    if (gate_closed(gate)) return;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const float4 bp = bound[p];
+        int bits = 0;
+        for (int q = 0; q < P && bits != 3; ++q) {
+            if (q == p) continue;
+            const float4 bq = bound[q];
+            float dx = bp.x - bq.x, dy = bp.y - bq.y, dz = bp.z - bq.z;
+            dz -= geom.L[2] * rintf(dz / geom.L[2]);
+            bool crossed = false;
+            if (!geom.walls) {
+                const float dy0 = dy;
+                dy -= geom.L[1] * rintf(dy / geom.L[1]);
+                crossed = dy != dy0;
+            }
+            dx -= geom.L[0] * rintf(dx / geom.L[0]);
+            if (geom.le && crossed) dx = 0.0f;
+            const float d = sqrtf(dx * dx + dy * dy + dz * dz) - bp.w - bq.w;
+            if (d < reach_lj + 0.5f) bits |= 1;
+            if (d < reach_m + 0.5f) bits |= 2;
+        }
+        near[p] = bits;
     }
 }
 
@@ -226,6 +319,8 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
     a.ds = s->ds;
     a.ctl = s->ctl;
     a.excl2 = s->excl2;
+    a.near = nullptr;
+    a.near_bit = 0;
 
     // plasma / wall list over the main grid
     a.rows = s->n;
@@ -249,6 +344,18 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
         a.cap = s->cap[MD_LIST_IFACE];
         k_build<MD_LIST_IFACE><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
 
+        // platelets far from every other platelet get empty LJ / Morse rows
+        // without a scan (only when no same-platelet pair can feel LJ)
+        const bool prefilter = s->cfg.lj_excl > 1e20;
+        if (prefilter) {
+            const int P = s->cfg.n_platelets;
+            k_plt_bounds<<<P, 256, 0, s->stream>>>(s->plt_off, s->plt_ids, s->pos_of_id, s->x32, s->geom, s->ds,
+                                                  s->plt_bound, gate);
+            k_plt_near<<<1, 256, 0, s->stream>>>(s->plt_bound, P, s->geom, (float)(s->cfg.lj_rc + s->cfg.skin),
+                                                 (float)(s->cfg.morse_rc + s->cfg.skin), s->plt_near, gate);
+        }
+        a.near = prefilter ? s->plt_near : nullptr;
+        a.near_bit = 1;
         a.g = s->gplt;
         a.members = s->plt_sorted;
         a.R = (float)(s->cfg.lj_rc + s->cfg.skin) * margin;
@@ -264,6 +371,7 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
             a.g = s->grec;
             a.members = s->rec_sorted;
             a.R = (float)(s->cfg.morse_rc + s->cfg.skin) * margin;
+            a.near_bit = 2;
             a.cut2 = s->cut2[MD_LIST_MORSE];
             a.nl = s->nl[MD_LIST_MORSE];
             a.nc = s->nc[MD_LIST_MORSE];
@@ -271,6 +379,6 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
             k_build<MD_LIST_MORSE><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
         }
     }
-    MSM_COUNT(s, 1 + (s->n_plt > 0 ? 2 + (s->n_rec > 0 ? 1 : 0) : 0));
+    MSM_COUNT(s, 1 + (s->n_plt > 0 ? 2 + (s->n_rec > 0 ? 1 : 0) + (s->cfg.lj_excl > 1e20 ? 2 : 0) : 0));
     return cudaGetLastError();
 }

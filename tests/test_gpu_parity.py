@@ -84,16 +84,21 @@ def wall_sys():
     return synth.plasma_box(box=(9.0, 8.0, 7.0), walls=True, body_force=0.02, seed=12)
 
 
+@pytest.mark.parametrize("excl", [2.5, None])
 @pytest.mark.parametrize("kind", [0, 1, 2, 3])
-def test_neighbor_sets_bit_exact(plt_sys, kind):
+def test_neighbor_sets_bit_exact(plt_sys, kind, excl):
+    """Every list kind equals the oracle's brute-force FP32 pair set: with an LJ
+    exclusion radius of 2.5 (far-at-rest pairs of one platelet kept) and with
+    the default (no same-platelet LJ; the bounding-sphere prefilter active)."""
     s = plt_sys
-    g = make_gpu(s, step0=17, lj_excl=2.5)     # an exclusion radius that keeps far-at-rest pairs
+    g = make_gpu(s, step0=17, **({} if excl is None else {"lj_excl": excl}))
     g.neighbor_build(force=True)
     got = g.neighbor_pairs(kind)
     _, _, x32 = g.read_particles()
     cut = [1.3, 1.3, 2.3, 5.3][kind]
+    excl2 = np.float32(np.inf) if excl is None else np.float32(excl * excl)
     ref = O.pairs_f32(x32, s.tag, np.array(s.box, np.float32), kind, np.float32(cut * cut),
-                      X0f=s.X0.astype(np.float32), excl2=np.float32(2.5 * 2.5), le=True,
+                      X0f=s.X0.astype(np.float32), excl2=excl2, le=True,
                       delta=le_offset_f32(s, 17))
     gs = set(map(tuple, got.tolist()))
     rs = set(map(tuple, ref.tolist()))
