@@ -134,7 +134,7 @@ def continuation_errors(system, horizon, k_m=1):
         try:
             system.mts_step(horizon, mode=B.MD_MODE_RESPA, k_m=k_m, k_p=k, record=True)
         except B.MdError as e:      # a ratio too coarse for these dynamics
-            if e.code != -5:
+            if e.code not in (-4, -5):
                 raise
             means[k] = None
             continue
@@ -193,11 +193,12 @@ def generate(seeds, n_windows=8, warmup=50, horizon=50, k_m=1, k_record=10, T=12
     each labelled from the continuations at its end."""
     data = Dataset()
     for seed in seeds:
-        sys = make_system(training_system(seed, n_shell=n_shell), seed=int(seed))
+        # platelets in contact: long LJ rows
+        sys = make_system(training_system(seed, n_shell=n_shell), seed=int(seed), caps={"lj": 4096})
         try:
             sys.mts_step(warmup, mode=B.MD_MODE_RESPA, k_m=k_m, k_p=k_record)
         except B.MdError as e:
-            if e.code != -5:
+            if e.code not in (-4, -5):
                 raise
             sys.close()
             continue
@@ -208,7 +209,7 @@ def generate(seeds, n_windows=8, warmup=50, horizon=50, k_m=1, k_record=10, T=12
             try:
                 sys.mts_step(T, mode=B.MD_MODE_RESPA, k_m=k_m, k_p=k_record, record=True)
             except B.MdError as e:
-                if e.code != -5:
+                if e.code not in (-4, -5):
                     raise
                 break                                # this trajectory went unstable
             win, cnt = sys.read_feature_ring()

@@ -164,6 +164,7 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
         s.ring = cv.take<float>(P * (int64_t)s.ring_T * 12);
         s.plt_k = cv.take<int32_t>(P);
         s.plt_bound = cv.take<float4>(P);
+        s.feat_sums = cv.take<double>(25 * P + (P + 1) / 2);
         s.plt_near = cv.take<int32_t>(P);
     }
     s.red_blocks = (int)((n + MSM_TPB - 1) / MSM_TPB);

@@ -1,5 +1,6 @@
 // K8: per-platelet measurements (Sec. 3.3: angular velocity, kinetic state,
-// flow speed at the centre of mass) reduced in FP64, one block per platelet:
+// flow speed at the centre of mass) reduced in FP64 (raw sums over blocks of
+// every platelet, then one block per platelet for the moments):
 //
 //  0-2  centre-of-mass velocity V
 //  3-5  angular velocity w = I^-1 L (L, I about the centre of mass)
@@ -110,67 +111,94 @@ __device__ __forceinline__ float4 vel_at(const feat_args &a, int k)
     return v;
 }
 
-__global__ void __launch_bounds__(FT_TPB) k_features(feat_args a)
+// Minimum image of a separation along one axis (|d| < 1.5 L), no division.
+__device__ __forceinline__ double img64(double d, double L, bool periodic)
 {
-    __shared__ double sh[FT_TPB / 32];
-    __shared__ double res[32];
+    if (!periodic) return d;
+    if (d > 0.5 * L) d -= L;
+    else if (d < -0.5 * L) d += L;
+    return d;
+}
+
+// Raw FP64 sums per platelet, about its first member r_ref (the centre of
+// mass is not known until every block has added its members):
+//   0 n | 1-3 sum r | 4-6 sum v | 7-9 sum r x v | 10-15 sum r_a r_b (xx yy zz
+//   xy xz yz) | 16-18 sum F | 19-24 sum (r_a F_b + F_a r_b) / 2
+constexpr int FS_N = 25;
+
+// Blocks (p, chunk): members and bonds of platelet p strided over the chunks
+// of the y grid dimension; block sums go to the platelet's accumulators by
+// FP64 atomics, the largest bond strain by an integer max on float bits.
+__global__ void __launch_bounds__(FT_TPB) k_feat_sums(feat_args a, double *sums, unsigned *strain)
+{
+    __shared__ double sh[FT_TPB / 32][FS_N];
     const int p = blockIdx.x;
-    if (p >= a.P) return;
     const int b = a.plt_off[p], e = a.plt_off[p + 1];
-    const int nm = e - b;
     const bool py = !a.geom.walls;
     const float4 ref = a.x32[a.pos_of_id[a.plt_ids[b]]];
-    // pass 1: mean offset from the reference member, mean velocity
-    double s[6] = {0, 0, 0, 0, 0, 0};
-    for (int m = b + threadIdx.x; m < e; m += FT_TPB) {
+    double t[FS_N];
+#pragma unroll
+    for (int q = 0; q < FS_N; ++q) t[q] = 0.0;
+    const int stride = gridDim.y * FT_TPB;
+    for (int m = b + blockIdx.y * FT_TPB + threadIdx.x; m < e; m += stride) {
         const int k = a.pos_of_id[a.plt_ids[m]];
         const float4 xk = a.x32[k];
         const float4 vk = vel_at(a, k);
-        s[0] += dimg((double)xk.x - ref.x, a.L[0], true);
-        s[1] += dimg((double)xk.y - ref.y, a.L[1], py);
-        s[2] += dimg((double)xk.z - ref.z, a.L[2], true);
-        s[3] += vk.x; s[4] += vk.y; s[5] += vk.z;
-    }
-    double mean[6];
-    for (int q = 0; q < 6; ++q) mean[q] = block_sum(s[q], sh) / nm;
-    // pass 2: angular momentum, inertia, force moment about the centre of mass
-    double t[15];
-    for (int q = 0; q < 15; ++q) t[q] = 0.0;
-    double smax = 0.0;
-    for (int m = b + threadIdx.x; m < e; m += FT_TPB) {
-        const int k = a.pos_of_id[a.plt_ids[m]];
-        const float4 xk = a.x32[k];
-        const float4 vk = vel_at(a, k);
-        const double rx = dimg((double)xk.x - ref.x, a.L[0], true) - mean[0];
-        const double ry = dimg((double)xk.y - ref.y, a.L[1], py) - mean[1];
-        const double rz = dimg((double)xk.z - ref.z, a.L[2], true) - mean[2];
-        const double ux = vk.x - mean[3], uy = vk.y - mean[4], uz = vk.z - mean[5];
+        const double rx = img64((double)xk.x - ref.x, a.L[0], true), ry = img64((double)xk.y - ref.y, a.L[1], py),
+                     rz = img64((double)xk.z - ref.z, a.L[2], true);
         double fx = 0, fy = 0, fz = 0;
-        if (a.f0) { const float4 q = a.f0[k]; fx += q.x; fy += q.y; fz += q.z; if (a.tag[k] != MD_TAG_WALL) fx += a.g_body; }
+        if (a.f0) { const float4 q = a.f0[k]; fx += q.x; fy += q.y; fz += q.z; fx += a.g_body; }
         if (a.f1) { const float4 q = a.f1[k]; fx += q.x; fy += q.y; fz += q.z; }
         if (a.f2) { const float4 q = a.f2[k]; fx += q.x; fy += q.y; fz += q.z; }
-        t[0] += ry * uz - rz * uy; t[1] += rz * ux - rx * uz; t[2] += rx * uy - ry * ux;   // L
-        const double r2 = rx * rx + ry * ry + rz * rz;
-        t[3] += r2 - rx * rx; t[4] += r2 - ry * ry; t[5] += r2 - rz * rz;                  // I diag
-        t[6] -= rx * ry; t[7] -= rx * rz; t[8] -= ry * rz;                                  // I off-diag
-        t[9] -= rx * fx; t[10] -= ry * fy; t[11] -= rz * fz;                                // S diag
-        t[12] -= 0.5 * (rx * fy + fx * ry); t[13] -= 0.5 * (rx * fz + fx * rz); t[14] -= 0.5 * (ry * fz + fy * rz);
+        t[0] += 1.0;
+        t[1] += rx; t[2] += ry; t[3] += rz;
+        t[4] += vk.x; t[5] += vk.y; t[6] += vk.z;
+        t[7] += ry * vk.z - rz * vk.y; t[8] += rz * vk.x - rx * vk.z; t[9] += rx * vk.y - ry * vk.x;
+        t[10] += rx * rx; t[11] += ry * ry; t[12] += rz * rz; t[13] += rx * ry; t[14] += rx * rz; t[15] += ry * rz;
+        t[16] += fx; t[17] += fy; t[18] += fz;
+        t[19] += rx * fx; t[20] += ry * fy; t[21] += rz * fz;
+        t[22] += 0.5 * (rx * fy + fx * ry); t[23] += 0.5 * (rx * fz + fx * rz); t[24] += 0.5 * (ry * fz + fy * rz);
     }
-    for (int bb = a.bond_off[p] + threadIdx.x; bb < a.bond_off[p + 1]; bb += FT_TPB) {
+    float smax = 0.f;
+    for (int bb = a.bond_off[p] + blockIdx.y * FT_TPB + threadIdx.x; bb < a.bond_off[p + 1]; bb += stride) {
         const float4 xi = a.x32[a.bond_ij[2 * bb]], xj = a.x32[a.bond_ij[2 * bb + 1]];
-        const double dx = dimg((double)xi.x - xj.x, a.L[0], true);
-        const double dy = dimg((double)xi.y - xj.y, a.L[1], py);
-        const double dz = dimg((double)xi.z - xj.z, a.L[2], true);
+        const double dx = img64((double)xi.x - xj.x, a.L[0], true), dy = img64((double)xi.y - xj.y, a.L[1], py),
+                     dz = img64((double)xi.z - xj.z, a.L[2], true);
         const double r0 = a.bond_r0[bb];
-        smax = fmax(smax, fabs(sqrt(dx * dx + dy * dy + dz * dz) - r0) / r0);
+        smax = fmaxf(smax, (float)(fabs(sqrt(dx * dx + dy * dy + dz * dz) - r0) / r0));
     }
-    double tot[15];
-    for (int q = 0; q < 15; ++q) tot[q] = block_sum(t[q], sh);
-    smax = block_max(smax, sh);
-    // plasma speed near the centre of mass (cells within reach of it)
-    const double cx = ref.x + mean[0], cy = ref.y + mean[1], cz = ref.z + mean[2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < FS_N; ++q) {
+        double v = t[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[w][q] = v;
+    }
+    smax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(smax)));   // smax >= 0
+    if (lane == 0 && smax > 0.f) atomicMax(&strain[p], __float_as_uint(smax));
+    __syncthreads();
+    if (threadIdx.x < FS_N) {
+        double v = 0.0;
+        for (int q = 0; q < FT_TPB / 32; ++q) v += sh[q][threadIdx.x];
+        atomicAdd(&sums[(int64_t)p * FS_N + threadIdx.x], v);
+    }
+}
+
+// One block per platelet: moments about the centre of mass from the raw
+// sums, the flow speed around it, the 12 measurements.
+__global__ void __launch_bounds__(FT_TPB) k_feat_final(feat_args a, const double *sums, const unsigned *strain)
+{
+    __shared__ double sh[FT_TPB / 32];
+    const int p = blockIdx.x;
+    const double *S = sums + (int64_t)p * FS_N;
+    const bool py = !a.geom.walls;
+    const double n = S[0];
+    const double rc[3] = {S[1] / n, S[2] / n, S[3] / n}, vc[3] = {S[4] / n, S[5] / n, S[6] / n};
+    const float4 ref = a.x32[a.pos_of_id[a.plt_ids[a.plt_off[p]]]];
+    // plasma speed near the centre of mass (cells of the last list build:
+    // particles have moved by less than skin/2 since)
+    const double cx = ref.x + rc[0], cy = ref.y + rc[1], cz = ref.z + rc[2];
     const md_grid &g = a.g;
-    // cells are those of the last list build: particles have moved by < skin/2 since
     const double rr = sqrt(a.flow_r2) + a.skin;
     const int reach[3] = {(int)ceil(rr / g.h[0]), (int)ceil(rr / g.h[1]), (int)ceil(rr / g.h[2])};
     const int c0[3] = {(int)floor((cx - g.lo[0]) / g.h[0]), (int)floor((cy - g.lo[1]) / g.h[1]),
@@ -189,9 +217,9 @@ __global__ void __launch_bounds__(FT_TPB) k_features(feat_args a)
         for (int32_t k = g.start[c]; k < g.start[c + 1]; ++k) {
             const float4 xk = a.x32[k];
             if (class_of(xk) != CLS_FLUID) continue;
-            const double dx = dimg((double)xk.x - cx, a.L[0], true);
-            const double dy = dimg((double)xk.y - cy, a.L[1], py);
-            const double dz = dimg((double)xk.z - cz, a.L[2], true);
+            const double dx = img64((double)xk.x - cx, a.L[0], true);
+            const double dy = img64((double)xk.y - cy, a.L[1], py);
+            const double dz = img64((double)xk.z - cz, a.L[2], true);
             if (dx * dx + dy * dy + dz * dz < a.flow_r2) {
                 const float4 vk = vel_at(a, k);
                 fs += sqrt((double)vk.x * vk.x + (double)vk.y * vk.y + (double)vk.z * vk.z);
@@ -203,13 +231,18 @@ __global__ void __launch_bounds__(FT_TPB) k_features(feat_args a)
     fn = block_sum(fn, sh);
     if (threadIdx.x == 0) {
         double *o = a.out + 12 * (int64_t)p;
-        o[0] = mean[3]; o[1] = mean[4]; o[2] = mean[5];
-        // w = I^-1 L by Cramer's rule
-        const double I00 = tot[3], I11 = tot[4], I22 = tot[5], I01 = tot[6], I02 = tot[7], I12 = tot[8];
+        o[0] = vc[0]; o[1] = vc[1]; o[2] = vc[2];
+        // about the centre of mass: L = sum r x v - n rc x vc, second moments
+        // M_ab = sum r_a r_b - n rc_a rc_b, I = tr(M) 1 - M
+        const double Lx = S[7] - n * (rc[1] * vc[2] - rc[2] * vc[1]);
+        const double Ly = S[8] - n * (rc[2] * vc[0] - rc[0] * vc[2]);
+        const double Lz = S[9] - n * (rc[0] * vc[1] - rc[1] * vc[0]);
+        const double Mxx = S[10] - n * rc[0] * rc[0], Myy = S[11] - n * rc[1] * rc[1], Mzz = S[12] - n * rc[2] * rc[2];
+        const double Mxy = S[13] - n * rc[0] * rc[1], Mxz = S[14] - n * rc[0] * rc[2], Myz = S[15] - n * rc[1] * rc[2];
+        const double I00 = Myy + Mzz, I11 = Mxx + Mzz, I22 = Mxx + Myy, I01 = -Mxy, I02 = -Mxz, I12 = -Myz;
         const double c00 = I11 * I22 - I12 * I12, c01 = I02 * I12 - I01 * I22, c02 = I01 * I12 - I02 * I11;
         const double c11 = I00 * I22 - I02 * I02, c12 = I01 * I02 - I00 * I12, c22 = I00 * I11 - I01 * I01;
         const double det = I00 * c00 + I01 * c01 + I02 * c02;
-        const double Lx = tot[0], Ly = tot[1], Lz = tot[2];
         if (det != 0.0) {
             o[3] = (c00 * Lx + c01 * Ly + c02 * Lz) / det;
             o[4] = (c01 * Lx + c11 * Ly + c12 * Lz) / det;
@@ -217,15 +250,19 @@ __global__ void __launch_bounds__(FT_TPB) k_features(feat_args a)
         } else {
             o[3] = o[4] = o[5] = 0.0;
         }
-        const double S[6] = {tot[9], tot[10], tot[11], tot[12], tot[13], tot[14]};
+        // S = -1/2 sum (r' F^T + F r'^T), r' = r - rc
+        const double F[3] = {S[16], S[17], S[18]};
+        const double Sm[6] = {-(S[19] - rc[0] * F[0]), -(S[20] - rc[1] * F[1]), -(S[21] - rc[2] * F[2]),
+                              -(S[22] - 0.5 * (rc[0] * F[1] + F[0] * rc[1])),
+                              -(S[23] - 0.5 * (rc[0] * F[2] + F[0] * rc[2])),
+                              -(S[24] - 0.5 * (rc[1] * F[2] + F[1] * rc[2]))};
         double ev[3];
-        sym3_eigvals(S, ev);
+        sym3_eigvals(Sm, ev);
         o[6] = ev[0]; o[7] = ev[1]; o[8] = ev[2];
-        o[9] = smax;
+        o[9] = (double)__uint_as_float(strain[p]);
         o[10] = a.contacts ? (double)a.contacts[p] : 0.0;
         o[11] = fn > 0.0 ? fs / fn : 0.0;
     }
-    (void)res;
 }
 
 // Receptor contacts: Morse-list pairs closer than r_c, counted for both platelets.
@@ -301,8 +338,14 @@ cudaError_t launch_features(md_system *s, double *out_dev, const float4 *f_plt, 
     a.flow_r2 = 4.0;
     a.skin = s->cfg.skin;
     a.out = out_dev;
-    k_features<<<P, FT_TPB, 0, s->stream>>>(a);
-    MSM_COUNT(s, 1);
+    e = cudaMemsetAsync(s->feat_sums, 0, sizeof(double) * FS_N * P + sizeof(unsigned) * P, s->stream);
+    if (e != cudaSuccess) return e;
+    unsigned *strain = (unsigned *)(s->feat_sums + (int64_t)FS_N * P);
+    const int mean_members = (int)((s->n_plt + P - 1) / P);
+    const int chunks = min(64, mean_members / (4 * FT_TPB) + 1);    // blocks per platelet
+    k_feat_sums<<<dim3(P, chunks), FT_TPB, 0, s->stream>>>(a, s->feat_sums, strain);
+    k_feat_final<<<P, FT_TPB, 0, s->stream>>>(a, s->feat_sums, strain);
+    MSM_COUNT(s, 2);
     return cudaGetLastError();
 }
 

@@ -99,6 +99,7 @@ struct md_system {
     int32_t *bond_off;
     int32_t *plt_contacts;
     float4 *plt_bound;           // per platelet at the last build: centre of mass, radius
+    double *feat_sums;           // [P][25] FP64 partial sums of the measurements, then [P] strain bits
     int32_t *plt_near;           // bit 0 / 1: another platelet within LJ / Morse reach
     double *feat;                // [P][12]
     float *ring;                 // [P][ring_T][12] time series of the measurements

@@ -156,6 +156,8 @@ struct build_args {
     int32_t *ctl;
     const int32_t *near;        // LJ / Morse kinds: platelets with a neighbour platelet in reach
     int near_bit;
+    const float4 *bound;        // platelet bounding spheres (row-level test when P is small)
+    int P;
 };
 
 template <int KIND>
@@ -178,9 +180,29 @@ __global__ void __launch_bounds__(MSM_TPB) k_build(build_args a, const int32_t *
             // no other platelet within reach of this one's bounding sphere: no
             // partner can pass (same-platelet pairs need a rest distance of at
             // least lj_excl, which the caller rules out before using `near`)
-            if ((KIND == MD_LIST_LJ || KIND == MD_LIST_MORSE) && a.near && !(a.near[ti] & a.near_bit)) {
-                if (active) a.nc[r] = 0;
-                goto done;
+            if ((KIND == MD_LIST_LJ || KIND == MD_LIST_MORSE) && a.near) {
+                bool reach = (a.near[ti] & a.near_bit) != 0;
+                if (reach && a.P <= 64) {   // this particle itself within reach of another sphere?
+                    reach = false;
+                    for (int q = 0; q < a.P && !reach; ++q) {
+                        if (q == ti) continue;
+                        const float4 bq = a.bound[q];
+                        float dx = xi.x - bq.x, dy = xi.y - bq.y, dz = xi.z - bq.z;
+                        dx -= a.geom.L[0] * rintf(dx / a.geom.L[0]);
+                        dz -= a.geom.L[2] * rintf(dz / a.geom.L[2]);
+                        if (!a.geom.walls) {
+                            const float dy0 = dy;
+                            dy -= a.geom.L[1] * rintf(dy / a.geom.L[1]);
+                            if (a.geom.le && dy != dy0) dx = 0.0f;
+                        }
+                        const float lim = bq.w + a.R + 0.5f;
+                        reach = dx * dx + dy * dy + dz * dz < lim * lim;
+                    }
+                }
+                if (!reach) {
+                    if (active) a.nc[r] = 0;
+                    goto done;
+                }
             }
             if (KIND == MD_LIST_LJ) x0i = a.X0[id_of(xi)];
             const int64_t rows = a.rows;
@@ -356,6 +378,8 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
         }
         a.near = prefilter ? s->plt_near : nullptr;
         a.near_bit = 1;
+        a.bound = s->plt_bound;
+        a.P = s->cfg.n_platelets;
         a.g = s->gplt;
         a.members = s->plt_sorted;
         a.R = (float)(s->cfg.lj_rc + s->cfg.skin) * margin;
