@@ -35,7 +35,10 @@ F_STRAIN = 9               # largest bond strain
 
 @dataclass
 class TrustBound:
-    """Fallback to a fixed ratio when the controller is unsure (Table 2)."""
+    """Fallback to a fixed ratio when the controller is unsure (Table 2): the
+    top class probability is low, or the window lies outside the training
+    data (reconstruction error or bond strain beyond their 99th percentiles
+    over the training windows)."""
     p_min: float = 0.6           # smallest accepted top class probability
     rec_max: float = math.inf    # largest accepted reconstruction error
     strain_max: float = 0.2      # largest accepted bond strain in the window
@@ -275,7 +278,8 @@ def train(windows, classes, holds, epochs_ae=40, epochs_heads=80, batch=128, lr_
             progress("heads", ep, hist["heads"][-1])
     rec = np.concatenate([ctl.predict(windows[b:b + batch])["rec_err"] for b in range(0, n, batch)])
     art = dict(params=ctl.get_params(), mean=mean.astype(np.float32), std=std.astype(np.float32),
-               rec_p99=np.float32(np.percentile(rec, 99)), history=hist)
+               rec_p99=np.float32(np.percentile(rec, 99)),
+               strain_p99=np.float32(np.percentile(windows[:, :, F_STRAIN].max(1), 99)), history=hist)
     return ctl, art
 
 
@@ -285,11 +289,13 @@ def load_controller(path, batch=256):
     ctl = Controller(default_config(batch_max=batch))
     ctl.set_params(d["params"])
     ctl.set_norm(d["mean"], d["std"])
-    return ctl, TrustBound(rec_max=float(d["rec_p99"]))
+    strain = float(d["strain_p99"]) if "strain_p99" in d.files else TrustBound.strain_max
+    return ctl, TrustBound(rec_max=float(d["rec_p99"]), strain_max=strain)
 
 
 def save(path, art):
-    np.savez(path, params=art["params"], mean=art["mean"], std=art["std"], rec_p99=art["rec_p99"])
+    np.savez(path, params=art["params"], mean=art["mean"], std=art["std"], rec_p99=art["rec_p99"],
+             strain_p99=art["strain_p99"])
 
 
 def evaluate(ctl, windows, err_s, err_v, trust, batch=128):

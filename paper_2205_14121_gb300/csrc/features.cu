@@ -342,7 +342,7 @@ cudaError_t launch_features(md_system *s, double *out_dev, const float4 *f_plt, 
     if (e != cudaSuccess) return e;
     unsigned *strain = (unsigned *)(s->feat_sums + (int64_t)FS_N * P);
     const int mean_members = (int)((s->n_plt + P - 1) / P);
-    const int chunks = min(64, mean_members / (4 * FT_TPB) + 1);    // blocks per platelet
+    const int chunks = min(256, mean_members / FT_TPB + 1);    // blocks per platelet: about a member per thread
     k_feat_sums<<<dim3(P, chunks), FT_TPB, 0, s->stream>>>(a, s->feat_sums, strain);
     k_feat_final<<<P, FT_TPB, 0, s->stream>>>(a, s->feat_sums, strain);
     MSM_COUNT(s, 2);

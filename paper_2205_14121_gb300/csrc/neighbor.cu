@@ -242,65 +242,75 @@ done:
     }
 }
 
-// Bounding sphere of every platelet at the build: centre of mass (minimum
-// image offsets from the first member) and the largest member distance from
-// it.  One block per platelet.
-__global__ void __launch_bounds__(256) k_plt_bounds(const int32_t *__restrict__ off, const int32_t *__restrict__ ids,
-                                                    const int32_t *__restrict__ pos_of_id, const float4 *__restrict__ x32,
-                                                    md_geom geom, const md_dstate *ds, float4 *bound,
-                                                    const int32_t *gate)
+// Bounding sphere of every platelet at the build, over blocks (p, chunk):
+// pass 1 sums the member offsets from the first member (minimum image) into
+// bound[p].xyz, pass 2 the largest squared distance from the centre of mass
+// into bound[p].w (float bits; k_plt_near turns both into centre and radius).
+__global__ void __launch_bounds__(256) k_plt_com(const int32_t *__restrict__ off, const int32_t *__restrict__ ids,
+                                                 const int32_t *__restrict__ pos_of_id, const float4 *__restrict__ x32,
+                                                 md_geom geom, const md_dstate *ds, float4 *bound, const int32_t *gate)
 {
     if (gate_closed(gate)) return;
-    __shared__ float red[4][8];
-    const float delta = ds->le_offset_f;
     const int p = blockIdx.x, b = off[p], e = off[p + 1];
     const float4 ref = x32[pos_of_id[ids[b]]];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    float s[3] = {0.f, 0.f, 0.f};
-    for (int m = b + threadIdx.x; m < e; m += blockDim.x) {
-        const float4 xm = x32[pos_of_id[ids[m]]];
+    const float delta = ds->le_offset_f;
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    for (int m = b + blockIdx.y * blockDim.x + threadIdx.x; m < e; m += gridDim.y * blockDim.x) {
         float dx, dy, dz, vs;
-        min_image_f32(geom, delta, xm, ref, dx, dy, dz, vs);
-        s[0] += dx; s[1] += dy; s[2] += dz;
+        min_image_f32(geom, delta, x32[pos_of_id[ids[m]]], ref, dx, dy, dz, vs);
+        sx += dx; sy += dy; sz += dz;
     }
-    for (int k = 0; k < 3; ++k) {
-        float v = s[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[k][w] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
     }
-    __syncthreads();
-    float c[3];
-    for (int k = 0; k < 3; ++k) {
-        float t = 0.f;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[k][q];
-        c[k] = t / (float)(e - b);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&bound[p].x, sx);
+        atomicAdd(&bound[p].y, sy);
+        atomicAdd(&bound[p].z, sz);
     }
-    float rmax = 0.f;
-    for (int m = b + threadIdx.x; m < e; m += blockDim.x) {
-        const float4 xm = x32[pos_of_id[ids[m]]];
+}
+
+__global__ void __launch_bounds__(256) k_plt_radius(const int32_t *__restrict__ off, const int32_t *__restrict__ ids,
+                                                    const int32_t *__restrict__ pos_of_id,
+                                                    const float4 *__restrict__ x32, md_geom geom, const md_dstate *ds,
+                                                    float4 *bound, const int32_t *gate)
+{
+    if (gate_closed(gate)) return;
+    const int p = blockIdx.x, b = off[p], e = off[p + 1];
+    const float4 ref = x32[pos_of_id[ids[b]]];
+    const float delta = ds->le_offset_f;
+    const float inv_n = 1.0f / (float)(e - b);
+    const float cx = bound[p].x * inv_n, cy = bound[p].y * inv_n, cz = bound[p].z * inv_n;
+    float r2 = 0.f;
+    for (int m = b + blockIdx.y * blockDim.x + threadIdx.x; m < e; m += gridDim.y * blockDim.x) {
         float dx, dy, dz, vs;
-        min_image_f32(geom, delta, xm, ref, dx, dy, dz, vs);
-        dx -= c[0]; dy -= c[1]; dz -= c[2];
-        rmax = fmaxf(rmax, dx * dx + dy * dy + dz * dz);
+        min_image_f32(geom, delta, x32[pos_of_id[ids[m]]], ref, dx, dy, dz, vs);
+        dx -= cx; dy -= cy; dz -= cz;
+        r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
     }
-    rmax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(rmax)));   // rmax >= 0
-    __syncthreads();
-    if (lane == 0) red[3][w] = rmax;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float r2 = 0.f;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r2 = fmaxf(r2, red[3][q]);
-        bound[p] = make_float4(ref.x + c[0], ref.y + c[1], ref.z + c[2], sqrtf(r2));
-    }
+    r2 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(r2)));   // r2 >= 0
+    if ((threadIdx.x & 31) == 0) atomicMax((unsigned *)&bound[p].w, __float_as_uint(r2));
 }
 
 // near[p] bit 0 (1): some other platelet's bounding sphere comes within the
 // LJ (Morse) list reach of p's.  Under Lees-Edwards the x separation of a
 // pair across the y boundary is taken as zero (its image offset varies).
-__global__ void k_plt_near(const float4 *__restrict__ bound, int P, md_geom geom, float reach_lj, float reach_m,
-                           int32_t *near, const int32_t *gate)
+__global__ void k_plt_near(const int32_t *__restrict__ off, const int32_t *__restrict__ ids,
+                           const int32_t *__restrict__ pos_of_id, const float4 *__restrict__ x32, float4 *bound, int P,
+                           md_geom geom, float reach_lj, float reach_m, int32_t *near, const int32_t *gate)
 {
     if (gate_closed(gate)) return;
+    // sums and squared radii -> centre of mass and radius
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const float4 ref = x32[pos_of_id[ids[off[p]]]];
+        const float4 a = bound[p];
+        const float inv_n = 1.0f / (float)(off[p + 1] - off[p]);
+        bound[p] = make_float4(ref.x + a.x * inv_n, ref.y + a.y * inv_n, ref.z + a.z * inv_n,
+                               sqrtf(__uint_as_float(__float_as_uint(a.w))));
+    }
+    __syncthreads();
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
         const float4 bp = bound[p];
         int bits = 0;
@@ -371,9 +381,16 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
         const bool prefilter = s->cfg.lj_excl > 1e20;
         if (prefilter) {
             const int P = s->cfg.n_platelets;
-            k_plt_bounds<<<P, 256, 0, s->stream>>>(s->plt_off, s->plt_ids, s->pos_of_id, s->x32, s->geom, s->ds,
-                                                  s->plt_bound, gate);
-            k_plt_near<<<1, 256, 0, s->stream>>>(s->plt_bound, P, s->geom, (float)(s->cfg.lj_rc + s->cfg.skin),
+            const int64_t per = s->n_plt / P / 256 + 1;
+            const int chunks = (int)(per < 256 ? per : 256);
+            cudaError_t e = cudaMemsetAsync(s->plt_bound, 0, sizeof(float4) * P, s->stream);
+            if (e != cudaSuccess) return e;
+            k_plt_com<<<dim3(P, chunks), 256, 0, s->stream>>>(s->plt_off, s->plt_ids, s->pos_of_id, s->x32, s->geom,
+                                                               s->ds, s->plt_bound, gate);
+            k_plt_radius<<<dim3(P, chunks), 256, 0, s->stream>>>(s->plt_off, s->plt_ids, s->pos_of_id, s->x32,
+                                                                  s->geom, s->ds, s->plt_bound, gate);
+            k_plt_near<<<1, 256, 0, s->stream>>>(s->plt_off, s->plt_ids, s->pos_of_id, s->x32, s->plt_bound, P,
+                                                 s->geom, (float)(s->cfg.lj_rc + s->cfg.skin),
                                                  (float)(s->cfg.morse_rc + s->cfg.skin), s->plt_near, gate);
         }
         a.near = prefilter ? s->plt_near : nullptr;
@@ -403,6 +420,6 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
             k_build<MD_LIST_MORSE><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
         }
     }
-    MSM_COUNT(s, 1 + (s->n_plt > 0 ? 2 + (s->n_rec > 0 ? 1 : 0) + (s->cfg.lj_excl > 1e20 ? 2 : 0) : 0));
+    MSM_COUNT(s, 1 + (s->n_plt > 0 ? 2 + (s->n_rec > 0 ? 1 : 0) + (s->cfg.lj_excl > 1e20 ? 3 : 0) : 0));
     return cudaGetLastError();
 }

@@ -69,17 +69,19 @@ def main(argv=None):
 
     ctl, art = A.train(w_tr, c_tr, h_tr, epochs_ae=args.epochs_ae, epochs_heads=args.epochs_heads, progress=prog)
     t_train = time.time() - t0 - t_data
-    trust = A.TrustBound(rec_max=float(art["rec_p99"]))
+    trust = A.TrustBound(rec_max=float(art["rec_p99"]), strain_max=float(art["strain_p99"]))
     ev_train = A.evaluate(ctl, w_tr, es_tr, ev_tr, trust)
     ev_test = A.evaluate(ctl, w_te, es_te, ev_te, trust)
     pred_te = np.concatenate([ctl.predict(w_te[b:b + 128])["cls"] for b in range(0, len(c_te), 128)])
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     A.save(args.out, art)
+    np.savez(os.path.splitext(args.out)[0] + "_heldout.npz", w=w_te, c=c_te, h=h_te, es=es_te, ev=ev_te)
     summary = dict(train_windows=int(len(c_tr)), test_windows=int(len(c_te)),
                    class_counts_train=np.bincount(c_tr, minlength=5).tolist(),
                    class_counts_test=np.bincount(c_te, minlength=5).tolist(),
                    test_class_accuracy=float(np.mean(pred_te == c_te)),
                    eval_train=ev_train, eval_test=ev_test, rec_p99=float(art["rec_p99"]),
+                   strain_p99=float(art["strain_p99"]),
                    loss_ae=art["history"]["ae"][-1], loss_heads=art["history"]["heads"][-1],
                    seconds_data=t_data, seconds_train=t_train,
                    horizon=args.horizon, windows_per_trajectory=args.windows, n_shell=args.n_shell)
