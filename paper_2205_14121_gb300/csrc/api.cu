@@ -166,6 +166,7 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
         s.plt_bound = cv.take<float4>(P);
         s.feat_sums = cv.take<double>(25 * P + (P + 1) / 2);
         s.plt_near = cv.take<int32_t>(P);
+        s.cell_pid = cv.take<int2>(s.gplt.ncell > s.grec.ncell ? s.gplt.ncell : s.grec.ncell);
     }
     s.red_blocks = (int)((n + MSM_TPB - 1) / MSM_TPB);
     if (s.red_blocks > RED_BLOCKS_MAX) s.red_blocks = RED_BLOCKS_MAX;
@@ -353,16 +354,17 @@ int ensure_forces(md_system *s)
 struct capture_ctx {
     cudaGraphConditionalHandle loop;
     std::vector<cudaGraph_t> if_bodies;
+    std::vector<unsigned> if_carry;
 };
 
 // The rebuild chain: gated kernels when launched directly; under capture, a
 // kernel that copies the rebuild flag into a conditional handle and an IF
 // node whose body (captured later) is the ungated chain.
-int enqueue_rebuild(md_system *s, capture_ctx *cap)
+int enqueue_rebuild(md_system *s, capture_ctx *cap, unsigned carry)
 {
     if (!cap) {
         prof_begin(s, MD_PROF_BUILD);
-        CK(launch_rebuild(s, s->ctl + CTL_REBUILD), "rebuild");
+        CK(launch_rebuild(s, s->ctl + CTL_REBUILD, carry), "rebuild");
         prof_end(s);
         return MD_OK;
     }
@@ -383,6 +385,7 @@ int enqueue_rebuild(md_system *s, capture_ctx *cap)
     cudaGraphNode_t node;
     CK(cudaGraphAddNode(&node, capg, deps, nullptr, ndeps, &p), "IF node");
     cap->if_bodies.push_back(p.conditional.phGraph_out[0]);
+    cap->if_carry.push_back(carry);
     CK(cudaStreamUpdateCaptureDependencies(s->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
        "capture dependencies");
     return MD_OK;
@@ -468,7 +471,7 @@ int enqueue_outer_step(md_system *s, int mode, int k_m, int k_p, bool first, cap
         const float h[3] = {hk, plt ? hk : 0.f, plt ? hk : 0.f};
         RC(enqueue_time(s, 1, 0, c.dt));
         RC(enqueue_kd(s, h, DRIFT_ALL, c.dt, DRIFT_ALL, plt ? MD_LEVEL_ALL : MD_LEVEL_FLUID, false));
-        RC(enqueue_rebuild(s, cap));
+        RC(enqueue_rebuild(s, cap, 0u));   // every level was cleared by the kick-drift
         RC(enqueue_forces(s, plt ? MD_LEVEL_ALL : MD_LEVEL_FLUID));
         if (record) RC(enqueue_record(s, mode));
         return MD_OK;
@@ -520,7 +523,9 @@ int enqueue_outer_step(md_system *s, int mode, int k_m, int k_p, bool first, cap
             const float hc[3] = {0.f, 0.f, (float)(0.5 * dtp)};
             RC(enqueue_kd(s, hc, DRIFT_PLT, 0.0, -1, 0u, true));
         }
-        RC(enqueue_rebuild(s, cap));
+        // the fluid level is cleared at the first substep and the interface
+        // level at every one: only the platelet level holds values here
+        RC(enqueue_rebuild(s, cap, plt ? MD_LEVEL_PLT : 0u));
         if (plt) {
             RC(enqueue_forces(s, MD_LEVEL_IFACE));
             const float hm[3] = {0.f, (float)(0.5 * dtm), 0.f};
@@ -593,7 +598,7 @@ int build_step_graph(md_system *s, int mode, int k_m, int k_p, bool record)
     for (size_t k = 0; rc == MD_OK && k < cap.if_bodies.size(); ++k) {
         e = cudaStreamBeginCaptureToGraph(cs, cap.if_bodies[k], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) { rc = cuda_fail(s, e, "begin capture (rebuild)"); break; }
-        cudaError_t e1 = launch_rebuild(s, nullptr);
+        cudaError_t e1 = launch_rebuild(s, nullptr, cap.if_carry[k]);
         cudaGraph_t out = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &out);
         if (e1 != cudaSuccess) rc = cuda_fail(s, e1, "rebuild capture");

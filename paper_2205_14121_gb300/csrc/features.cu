@@ -162,10 +162,12 @@ __global__ void __launch_bounds__(FT_TPB) k_feat_sums(feat_args a, double *sums,
     float smax = 0.f;
     for (int bb = a.bond_off[p] + blockIdx.y * FT_TPB + threadIdx.x; bb < a.bond_off[p + 1]; bb += stride) {
         const float4 xi = a.x32[a.bond_ij[2 * bb]], xj = a.x32[a.bond_ij[2 * bb + 1]];
-        const double dx = img64((double)xi.x - xj.x, a.L[0], true), dy = img64((double)xi.y - xj.y, a.L[1], py),
-                     dz = img64((double)xi.z - xj.z, a.L[2], true);
-        const double r0 = a.bond_r0[bb];
-        smax = fmaxf(smax, (float)(fabs(sqrt(dx * dx + dy * dy + dz * dz) - r0) / r0));
+        // the largest strain needs no FP64 arithmetic: the exact separation rounded to FP32
+        const float dx = (float)img64((double)xi.x - xj.x, a.L[0], true);
+        const float dy = (float)img64((double)xi.y - xj.y, a.L[1], py);
+        const float dz = (float)img64((double)xi.z - xj.z, a.L[2], true);
+        const float r0 = a.bond_r0[bb];
+        smax = fmaxf(smax, fabsf(sqrtf(dx * dx + dy * dy + dz * dz) - r0) / r0);
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(FT_TPB) k_feat_final(feat_args a, const double
             const double dz = img64((double)xk.z - cz, a.L[2], true);
             if (dx * dx + dy * dy + dz * dz < a.flow_r2) {
                 const float4 vk = vel_at(a, k);
-                fs += sqrt((double)vk.x * vk.x + (double)vk.y * vk.y + (double)vk.z * vk.z);
+                fs += (double)sqrtf(vk.x * vk.x + vk.y * vk.y + vk.z * vk.z);
                 fn += 1.0;
             }
         }

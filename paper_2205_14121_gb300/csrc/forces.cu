@@ -141,7 +141,7 @@ __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int 
 }
 
 template <bool VIR>
-__global__ void __launch_bounds__(MSM_TPB, 4) k_dpd(pair_args a)
+__global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
 {
     __shared__ dpd_smem sm;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -101,6 +101,7 @@ struct md_system {
     float4 *plt_bound;           // per platelet at the last build: centre of mass, radius
     double *feat_sums;           // [P][25] FP64 partial sums of the measurements, then [P] strain bits
     int32_t *plt_near;           // bit 0 / 1: another platelet within LJ / Morse reach
+    int2 *cell_pid;              // per platelet (receptor) sub-grid cell: lowest, highest platelet id
     double *feat;                // [P][12]
     float *ring;                 // [P][ring_T][12] time series of the measurements
     int ring_T = 128;
@@ -321,7 +322,9 @@ __device__ __forceinline__ float term_scale(const md_due &d, int32_t ti, int32_t
 // host-side launchers (one translation unit each)
 // ---------------------------------------------------------------------------
 // sort.cu
-cudaError_t launch_rebuild(md_system *s, const int32_t *gate);
+// carry: force levels whose values survive the re-sort (the others are zero
+// at that point and stay so)
+cudaError_t launch_rebuild(md_system *s, const int32_t *gate, unsigned carry = MD_LEVEL_ALL);
 cudaError_t launch_scan(md_system *s, const int32_t *in, int32_t *out, int64_t count, int32_t *total_out,
                         const int32_t *gate);
 // neighbor.cu

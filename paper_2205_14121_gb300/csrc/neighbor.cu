@@ -70,9 +70,9 @@ __device__ __forceinline__ float slab_gap(float x, float c0, float h)
 // Lees-Edwards rows that cross the y boundary are shifted by the image
 // offset.  half: skip cells with a lower index than xi's own cell, and in
 // that cell the members up to r.
-template <bool HALF, class E>
+template <bool HALF, class E, class K>
 __device__ __forceinline__ void for_ranges(const md_grid &g, const md_geom &geom, float delta, float4 xi, float R,
-                                           int32_t r, E emit)
+                                           int32_t r, E emit, K skip_cell)
 {
     const int ox = cell_coord(g, 0, xi.x);
     const int own_row = cell_coord(g, 2, xi.z) * g.nc[1] + cell_coord(g, 1, xi.y);
@@ -120,23 +120,33 @@ __device__ __forceinline__ void for_ranges(const md_grid &g, const md_geom &geom
                 const int b = seg ? b1 : b0;
                 if (HALF && row == own_row) a = max(a, ox);
                 if (a > b) continue;
-                int32_t sb = g.start[rowc + a];
-                const int32_t se = g.start[rowc + b + 1];
-                if (HALF && row == own_row && sb <= r) sb = r + 1;
-                if (sb < se) emit(sb, se);
+                // cells that cannot hold a partner are cut out of the run
+                while (a <= b && skip_cell(rowc + a)) ++a;
+                int bb = b;
+                while (bb >= a && skip_cell(rowc + bb)) --bb;
+                for (int c = a; c <= bb;) {
+                    int d = c;
+                    while (d < bb && !skip_cell(rowc + d + 1)) ++d;
+                    int32_t sb = g.start[rowc + c];
+                    const int32_t se = g.start[rowc + d + 1];
+                    if (HALF && row == own_row && sb <= r) sb = r + 1;
+                    if (sb < se) emit(sb, se);
+                    c = d + 1;
+                    while (c <= bb && skip_cell(rowc + c)) ++c;
+                }
             }
         }
     }
 }
 
 // Visit (member position s, particle index) of every candidate of xi.
-template <bool HALF, class F>
+template <bool HALF, class F, class K>
 __device__ __forceinline__ void for_candidates(const md_grid &g, const md_geom &geom, float delta, float4 xi,
-                                               float R, const int32_t *__restrict__ members, int32_t r, F fn)
+                                               float R, const int32_t *__restrict__ members, int32_t r, F fn, K skip)
 {
     for_ranges<HALF>(g, geom, delta, xi, R, r, [&](int32_t sb, int32_t se) {
         for (int32_t s = sb; s < se; ++s) fn(s, members ? members[s] : s);
-    });
+    }, skip);
 }
 
 struct build_args {
@@ -158,6 +168,7 @@ struct build_args {
     int near_bit;
     const float4 *bound;        // platelet bounding spheres (row-level test when P is small)
     int P;
+    const int2 *cell_pid;       // LJ / Morse sub-grids: lowest and highest platelet id per cell
 };
 
 template <int KIND>
@@ -206,6 +217,14 @@ __global__ void __launch_bounds__(MSM_TPB) k_build(build_args a, const int32_t *
             }
             if (KIND == MD_LIST_LJ) x0i = a.X0[id_of(xi)];
             const int64_t rows = a.rows;
+            // LJ / Morse without same-platelet pairs: cells holding only this
+            // platelet's particles hold no partner
+            const int2 *cp = (KIND == MD_LIST_LJ || KIND == MD_LIST_MORSE) && a.near ? a.cell_pid : nullptr;
+            auto skip = [&](int c) {
+                if (!cp) return false;
+                const int2 q = cp[c];
+                return q.x == ti && q.y == ti;
+            };
             for_candidates<HALF>(a.g, a.geom, delta, xi, a.R, a.members, (int32_t)r, [&](int32_t s, int32_t j) {
                 const float4 xj = a.x32[j];
                 const int cj = class_of(xj);
@@ -229,7 +248,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_build(build_args a, const int32_t *
                 }
                 if (cnt < a.cap) a.nl[r * a.cap + cnt] = j;
                 ++cnt;
-            });
+            }, skip);
         }
     }
 done:
@@ -335,6 +354,23 @@ __global__ void k_plt_near(const int32_t *__restrict__ off, const int32_t *__res
     }
 }
 
+// Lowest and highest platelet id among the members of every sub-grid cell
+// (empty cells: (INT_MAX, -1)).
+__global__ void k_cell_pid(int64_t ncell, const int32_t *__restrict__ start, const int32_t *__restrict__ members,
+                           const int32_t *__restrict__ tag, int2 *out, const int32_t *gate)
+{
+    if (gate_closed(gate)) return;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int lo = 0x7fffffff, hi = -1;
+    for (int32_t s = start[c]; s < start[c + 1]; ++s) {
+        const int p = tag[members[s]] & ~MD_RECEPTOR_BIT;
+        lo = min(lo, p);
+        hi = max(hi, p);
+    }
+    out[c] = make_int2(lo, hi);
+}
+
 inline unsigned blocks_for(int64_t n) { return (unsigned)(n > 0 ? (n + MSM_TPB - 1) / MSM_TPB : 1); }
 
 }  // namespace
@@ -353,6 +389,9 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
     a.excl2 = s->excl2;
     a.near = nullptr;
     a.near_bit = 0;
+    a.bound = nullptr;
+    a.P = 0;
+    a.cell_pid = nullptr;
 
     // plasma / wall list over the main grid
     a.rows = s->n;
@@ -397,6 +436,10 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
         a.near_bit = 1;
         a.bound = s->plt_bound;
         a.P = s->cfg.n_platelets;
+        if (prefilter)
+            k_cell_pid<<<blocks_for(s->gplt.ncell), MSM_TPB, 0, s->stream>>>(s->gplt.ncell, s->gplt.start, s->plt_sorted,
+                                                                            s->tag_s, s->cell_pid, gate);
+        a.cell_pid = s->cell_pid;
         a.g = s->gplt;
         a.members = s->plt_sorted;
         a.R = (float)(s->cfg.lj_rc + s->cfg.skin) * margin;
@@ -413,6 +456,10 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
             a.members = s->rec_sorted;
             a.R = (float)(s->cfg.morse_rc + s->cfg.skin) * margin;
             a.near_bit = 2;
+            if (prefilter)
+                k_cell_pid<<<blocks_for(s->grec.ncell), MSM_TPB, 0, s->stream>>>(s->grec.ncell, s->grec.start,
+                                                                                s->rec_sorted, s->tag_s, s->cell_pid,
+                                                                                gate);
             a.cut2 = s->cut2[MD_LIST_MORSE];
             a.nl = s->nl[MD_LIST_MORSE];
             a.nc = s->nc[MD_LIST_MORSE];
@@ -420,6 +467,6 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
             k_build<MD_LIST_MORSE><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
         }
     }
-    MSM_COUNT(s, 1 + (s->n_plt > 0 ? 2 + (s->n_rec > 0 ? 1 : 0) + (s->cfg.lj_excl > 1e20 ? 3 : 0) : 0));
+    MSM_COUNT(s, 1 + (s->n_plt > 0 ? 2 + (s->n_rec > 0 ? 1 : 0) + (s->cfg.lj_excl > 1e20 ? 4 + (s->n_rec > 0 ? 1 : 0) : 0) : 0));
     return cudaGetLastError();
 }

@@ -142,6 +142,7 @@ struct gather_args {
     float4 *altx, *altv, *altf[3];
     int32_t *alt_tag;
     int nf;
+    unsigned carry;
 };
 
 __global__ void k_gather(gather_args a, const int32_t *gate)
@@ -156,7 +157,8 @@ __global__ void k_gather(gather_args a, const int32_t *gate)
     a.altx[k] = a.x32[i];
     a.altv[k] = a.v[i];
     a.alt_tag[k] = a.tag[i];
-    for (int l = 0; l < a.nf; ++l) a.altf[l][k] = a.f[l][i];
+    for (int l = 0; l < a.nf; ++l)
+        if (a.carry & (1u << l)) a.altf[l][k] = a.f[l][i];
 }
 
 struct copyback_args {
@@ -169,6 +171,7 @@ struct copyback_args {
     const float4 *altx, *altv, *altf[3];
     const int32_t *alt_tag;
     int nf;
+    unsigned carry;
 };
 
 __global__ void k_copyback(copyback_args a, const int32_t *gate)
@@ -184,7 +187,8 @@ __global__ void k_copyback(copyback_args a, const int32_t *gate)
     a.xb[k] = x;
     a.v[k] = a.altv[k];
     a.tag[k] = a.alt_tag[k];
-    for (int l = 0; l < a.nf; ++l) a.f[l][k] = a.altf[l][k];
+    for (int l = 0; l < a.nf; ++l)
+        if (a.carry & (1u << l)) a.f[l][k] = a.altf[l][k];
     a.pos_of_id[id_of(x)] = (int32_t)k;
 }
 
@@ -266,7 +270,7 @@ cudaError_t launch_scan(md_system *s, const int32_t *in, int32_t *out, int64_t c
 }
 
 // The whole rebuild chain: bin + sort + reorder + sub-grids + every list.
-cudaError_t launch_rebuild(md_system *s, const int32_t *gate)
+cudaError_t launch_rebuild(md_system *s, const int32_t *gate, unsigned carry)
 {
     const int64_t n = s->n;
     cudaStream_t st = s->stream;
@@ -285,6 +289,7 @@ cudaError_t launch_rebuild(md_system *s, const int32_t *gate)
     ga.alt64 = s->alt64; ga.altx = s->altx; ga.altv = s->altv; ga.alt_tag = s->alt_tag;
     for (int l = 0; l < 3; ++l) { ga.f[l] = s->f[l]; ga.altf[l] = s->altf[l]; }
     ga.nf = nf;
+    ga.carry = carry;
     k_gather<<<blocks_for(n), MSM_TPB, 0, st>>>(ga, gate);
     copyback_args ca;
     ca.n = n; ca.xs = s->xs; ca.ys = s->ys; ca.zs = s->zs; ca.x32 = s->x32; ca.v = s->v; ca.xb = s->xb;
@@ -292,6 +297,7 @@ cudaError_t launch_rebuild(md_system *s, const int32_t *gate)
     ca.alt64 = s->alt64; ca.altx = s->altx; ca.altv = s->altv; ca.alt_tag = s->alt_tag;
     for (int l = 0; l < 3; ++l) { ca.f[l] = s->f[l]; ca.altf[l] = s->altf[l]; }
     ca.nf = nf;
+    ca.carry = carry;
     k_copyback<<<blocks_for(n), MSM_TPB, 0, st>>>(ca, gate);
     if (s->nb > 0)
         k_remap_bonds<<<blocks_for(2 * s->nb), MSM_TPB, 0, st>>>(s->nb, s->bond_id, s->pos_of_id, s->bond_ij, gate);
