@@ -258,6 +258,16 @@ typedef struct md_observables_t {
 int md_observables(md_system *sys, md_observables_t *out);
 
 /*
+ * Flow profile across the channel (Sec. 4.2, Fig. 4): nbins equal slabs of y
+ * in [0, Ly) (positions below 0 or above Ly count in the edge slabs); HOST
+ * out[2*nbins] = mean v_x of the plasma particles of each slab (out[b], 0 for
+ * an empty slab), then their number density (out[nbins + b], particles per
+ * unit volume).  FP64 sums on the device; velocities as stored (synchronised
+ * after md_mts_step).  Errors: MD_EINVAL (nbins outside [1, 256]), MD_ECUDA.
+ */
+int md_flow_profile(md_system *sys, int32_t nbins, double *out);
+
+/*
  * Per-platelet measurements of the current state (the time series the
  * controller reads, Sec. 3.3 / Table 1 "compute and dump platelet physical
  * properties"), reduced in FP64 on the device, written to HOST

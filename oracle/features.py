@@ -76,3 +76,18 @@ def platelet_features(x, v, f, tag, bonds, r0, box, walls=False, morse_r0=1.0, f
         near = np.linalg.norm(d, axis=1) < flow_radius
         out[p, 11] = float(np.linalg.norm(v[fl][near], axis=1).mean()) if near.any() else 0.0
     return out
+
+
+def flow_profile(x, v, tag, box, nbins=20):
+    """Sec. 4.2 (Fig. 4): the flow across the channel -- nbins equal slabs of y
+    in [0, Ly), positions outside counted in the edge slabs; per slab the mean
+    v_x of its plasma particles (0 when empty) and their number density."""
+    x = np.asarray(x, np.float64)
+    v = np.asarray(v, np.float64)
+    plasma = np.asarray(tag) == -1
+    Lx, Ly, Lz = (float(b) for b in box)
+    b = np.clip(np.floor(x[plasma, 1] * nbins / Ly).astype(np.int64), 0, nbins - 1)
+    n = np.bincount(b, minlength=nbins).astype(np.float64)
+    s = np.bincount(b, weights=v[plasma, 0], minlength=nbins)
+    mean = np.where(n > 0, s / np.maximum(n, 1.0), 0.0)
+    return mean, n / (Lx * Lz * Ly / nbins)

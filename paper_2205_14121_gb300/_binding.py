@@ -137,6 +137,7 @@ def lib():
     L.md_mts_step.argtypes = [vp, i64, C.POINTER(md_mts_schedule)]
     L.md_set_platelet_levels.argtypes = [vp, ip]
     L.md_observables.argtypes = [vp, C.POINTER(md_observables_t)]
+    L.md_flow_profile.argtypes = [vp, C.c_int32, dp]
     L.md_neighbor_pairs.argtypes = [vp, i32, ip, i64, C.POINTER(C.c_int64)]
     L.md_get_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
     L.md_set_state.argtypes = [vp, vp, C.c_size_t]
@@ -151,7 +152,7 @@ def lib():
         getattr(L, name).restype = C.c_int
     for name in ("md_config_defaults", "md_workspace_size", "md_init", "md_set_particles", "md_set_bonds",
                  "md_neighbor_build", "md_forces", "md_read_forces", "md_read_particles", "md_mts_step",
-                 "md_set_platelet_levels",
+                 "md_set_platelet_levels", "md_flow_profile",
                  "md_observables", "md_neighbor_pairs", "md_get_state", "md_set_state", "md_profile_enable",
                  "md_profile_read", "md_philox", "md_philox_static"):
         getattr(L, name).restype = C.c_int
@@ -306,6 +307,14 @@ class System:
                     "md_set_platelet_levels")
 
     md_set_platelet_levels = set_platelet_levels
+
+    def flow_profile(self, nbins=20):
+        """(mean plasma v_x, plasma number density) per slab of y (Sec. 4.2)."""
+        out = np.zeros(2 * nbins)
+        self._check(lib().md_flow_profile(self.h, int(nbins), _dp(out)), "md_flow_profile")
+        return out[:nbins], out[nbins:]
+
+    md_flow_profile = flow_profile
 
     def observables(self):
         o = md_observables_t()

@@ -69,17 +69,18 @@ def decide(pred, windows, trust):
 
 
 def run_ai_mts(system, controller, n_steps, k_m=1, trust=None, T=128, log=None):
-    """Advance n_steps outer steps under AI-MTS: the measurements of every step
-    go to the feature ring inside the step graph; once a full window exists
-    the controller sets each platelet's ratio, and is asked again after the
-    shortest predicted hold."""
+    """Advance n_steps outer steps under AI-MTS: the measurements of the T
+    steps before each decision go to the feature ring from inside the step
+    graph; with a full window the controller sets each platelet's ratio and
+    is asked again after the shortest predicted hold."""
     trust = trust or TrustBound()
     P = system.cfg.n_platelets
     system.set_platelet_levels(np.full(P, trust.fallback_k, np.int32))
     done = 0
+    fresh = 0          # consecutive records at the end of the ring
     while done < n_steps:
         windows, count = system.read_feature_ring()
-        if count >= T:
+        if fresh >= T:
             pred = controller.predict(windows)
             k, hold, unsure = decide(pred, windows, trust)
             system.set_platelet_levels(k)
@@ -87,9 +88,15 @@ def run_ai_mts(system, controller, n_steps, k_m=1, trust=None, T=128, log=None):
             if log is not None:
                 log.append(dict(step=done, k=k.tolist(), hold=hold.tolist(), unsure=unsure.tolist()))
         else:
-            run = T - count
+            run = T - fresh
         run = max(1, min(run, n_steps - done))
-        system.mts_step(run, mode=B.MD_MODE_AI, k_m=k_m, record=True)
+        # only the T steps before the next decision need recording
+        quiet = max(0, run - T)
+        if quiet:
+            system.mts_step(quiet, mode=B.MD_MODE_AI, k_m=k_m)
+            fresh = 0
+        system.mts_step(run - quiet, mode=B.MD_MODE_AI, k_m=k_m, record=True)
+        fresh += run - quiet
         done += run
     return log
 

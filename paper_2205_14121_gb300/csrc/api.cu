@@ -172,6 +172,7 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
     if (s.red_blocks > RED_BLOCKS_MAX) s.red_blocks = RED_BLOCKS_MAX;
     s.red_part = cv.take<double>((int64_t)s.red_blocks * RED_WORDS);
     s.red_out = cv.take<double>(RED_WORDS);
+    s.prof_part = cv.take<double>((int64_t)(PROF_BLOCKS + 1) * 2 * PROF_BINS_MAX);
     s.vir_acc = cv.take<double>(9);
     s.ctl = cv.take<int32_t>(CTL_WORDS);
     s.ds = cv.take<md_dstate>(1);
@@ -1052,6 +1053,24 @@ int md_mts_step(md_system *s, int64_t n_outer, const md_mts_schedule *sched)
     }
     s->host_step += n_outer;
     return check_flags(s);
+}
+
+int md_flow_profile(md_system *s, int32_t nbins, double *out)
+{
+    if (!s || !out || nbins < 1 || nbins > PROF_BINS_MAX)
+        return set_error(s, MD_EINVAL, "md_flow_profile: nbins must be in [1, 256]");
+    CK(launch_flow_profile(s, nbins), "flow profile");
+    std::vector<double> r((size_t)(2 * nbins));
+    CK(cudaMemcpyAsync(r.data(), s->prof_part + (int64_t)PROF_BLOCKS * 2 * PROF_BINS_MAX, sizeof(double) * 2 * nbins,
+                       cudaMemcpyDeviceToHost, s->stream), "download profile");
+    CK(cudaStreamSynchronize(s->stream), "sync");
+    const md_config &c = s->cfg;
+    const double slab = c.box[0] * c.box[2] * c.box[1] / nbins;
+    for (int b = 0; b < nbins; ++b) {
+        out[b] = r[(size_t)(nbins + b)] > 0.0 ? r[(size_t)b] / r[(size_t)(nbins + b)] : 0.0;
+        out[nbins + b] = r[(size_t)(nbins + b)] / slab;
+    }
+    return MD_OK;
 }
 
 int md_observables(md_system *s, md_observables_t *o)

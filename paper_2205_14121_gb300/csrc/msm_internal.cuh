@@ -125,6 +125,7 @@ struct md_system {
     // reductions
     double *red_part;            // partial sums [RED_BLOCKS][RED_WORDS]
     double *red_out;             // [RED_WORDS]
+    double *prof_part;           // flow-profile partials [PROF_BLOCKS][2 * PROF_BINS_MAX], then the result
     double *vir_acc;             // 9 doubles (conservative virial)
     int red_blocks;
 
@@ -177,7 +178,7 @@ void prof_end(md_system *s);
 #define MSM_COUNT(s, k) ((s)->nlaunch += (k))
 
 // reductions layout
-enum { RED_WORDS = 16, RED_BLOCKS_MAX = 1024 };
+enum { RED_WORDS = 16, RED_BLOCKS_MAX = 1024, PROF_BINS_MAX = 256, PROF_BLOCKS = 304 };
 
 // ---------------------------------------------------------------------------
 // device helpers
@@ -342,6 +343,8 @@ cudaError_t launch_set_loop(md_system *s, int64_t n);
 cudaError_t launch_zero_forces(md_system *s, unsigned levels);
 // reduce.cu
 cudaError_t launch_kinetics(md_system *s);
+// y-binned plasma v_x sums and counts into prof_part + PROF_BLOCKS * 2 * PROF_BINS_MAX
+cudaError_t launch_flow_profile(md_system *s, int nbins);
 // features.cu
 // f_plt: platelet-level forces to use (null: s->f[2]); hk: half kicks per
 // level still pending on the stored velocities (null: none)

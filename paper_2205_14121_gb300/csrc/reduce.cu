@@ -1,7 +1,8 @@
 // K8: FP64 reductions of the observables (Sec. 4.2): total momentum,
 // kinetic energy and the peculiar kinetic tensor (velocity relative to the
 // imposed Lees-Edwards profile), in two passes (per-block partials, then one
-// block over the partials) so the result does not depend on atomic order.
+// block over the partials) so the result does not depend on atomic order;
+// and the y-binned plasma flow profile (Fig. 4).
 #include "msm_internal.cuh"
 
 namespace {
@@ -59,7 +60,51 @@ __global__ void k_reduce_final(const double *part, int nblocks, double *out)
     out[w] = s;
 }
 
+// Flow profile: plasma v_x summed per slab of y in [0, Ly) (shared-memory
+// bins per block, then one pass over the block partials per bin).
+__global__ void __launch_bounds__(MSM_TPB) k_profile(int64_t n, const float4 *__restrict__ v,
+                                                    const double *__restrict__ ys, const int32_t *__restrict__ tag,
+                                                    double Ly, int nbins, double *part)
+{
+    __shared__ double sv[PROF_BINS_MAX], sn[PROF_BINS_MAX];
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) { sv[b] = 0.0; sn[b] = 0.0; }
+    __syncthreads();
+    const double scale = nbins / Ly;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        if (tag[k] != MD_TAG_FLUID) continue;
+        int b = (int)floor(ys[k] * scale);
+        b = b < 0 ? 0 : (b >= nbins ? nbins - 1 : b);
+        atomicAdd(&sv[b], (double)v[k].x);
+        atomicAdd(&sn[b], 1.0);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        part[(int64_t)blockIdx.x * 2 * PROF_BINS_MAX + b] = sv[b];
+        part[(int64_t)blockIdx.x * 2 * PROF_BINS_MAX + PROF_BINS_MAX + b] = sn[b];
+    }
+}
+
+__global__ void k_profile_final(const double *part, int nblocks, int nbins, double *out)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= 2 * nbins) return;
+    const int col = w < nbins ? w : PROF_BINS_MAX + (w - nbins);
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * 2 * PROF_BINS_MAX + col];
+    out[w] = s;
+}
+
 }  // namespace
+
+cudaError_t launch_flow_profile(md_system *s, int nbins)
+{
+    k_profile<<<PROF_BLOCKS, MSM_TPB, 0, s->stream>>>(s->n, s->v, s->ys, s->tag_s, s->cfg.box[1], nbins, s->prof_part);
+    k_profile_final<<<(2 * nbins + 127) / 128, 128, 0, s->stream>>>(s->prof_part, PROF_BLOCKS, nbins,
+                                                                    s->prof_part + (int64_t)PROF_BLOCKS * 2 * PROF_BINS_MAX);
+    MSM_COUNT(s, 2);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_kinetics(md_system *s)
 {

@@ -1,0 +1,79 @@
+"""AI-MTS against fine-step STS on the same synthetic channel (Sec. 4.2): the
+flow profile and the per-platelet stresses of AI-MTS (dt_f = 0.01, ratios
+from the trained controller) agree with fine-step STS (dt = 0.001 for every
+particle) within the spread between two fine-step runs that differ only in
+their noise realisation."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+DATA = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2205_14121_gb300", "data")
+
+
+def channel():
+    import synth
+    box = (36.0, 18.0, 16.0)
+    g = synth.poiseuille_g(0.05, synth.ETA_DPD, 3.0, box[1])
+    return synth.platelet_system(box, int(3 * 36 * 18 * 16), 2, 2000, synth.scaled_radii(2000), walls=True,
+                                 body_force=g, seed=31)
+
+
+def sample(g, acc):
+    mean, _ = g.flow_profile(18)
+    f = g.platelet_features()
+    acc["prof"].append(mean)
+    acc["stress"].append(f[:, 6:9])
+
+
+def test_ai_mts_matches_fine_step_sts():
+    import paper_2205_14121_gb300 as M
+    from paper_2205_14121_gb300 import ai_mts as A
+    s = channel()
+    kw = dict(walls=s.walls, wall=s.wall, body_force=s.body_force, X0=s.X0, bonds=s.bonds, r0=s.r0)
+    eq = M.System(s.box, s.x, s.v, s.tag, dt=0.01, **kw)
+    eq.mts_step(300, mode=M.MD_MODE_RESPA, k_m=1, k_p=10)            # out of the synthetic start
+    x0, v0, _ = eq.read_particles()
+    eq.close()
+
+    def fine(seed):
+        g = M.System(s.box, x0, v0, s.tag, dt=0.001, seed=seed, **kw)
+        g.mts_step(1280)                                   # the AI arm's first window
+        acc = {"prof": [], "stress": []}
+        for _ in range(60):
+            g.mts_step(50)
+            sample(g, acc)
+        g.close()
+        return acc
+
+    ctl, trust = A.load_controller(os.path.join(DATA, "controller.npz"))
+    g = M.System(s.box, x0, v0, s.tag, dt=0.01, seed=5, **kw)
+    g.set_platelet_levels([trust.fallback_k] * 2)
+    g.mts_step(128, mode=M.MD_MODE_AI, k_m=1, record=True)
+    windows, _ = g.read_feature_ring()
+    k, _, _ = A.decide(ctl.predict(windows), windows, trust)
+    g.set_platelet_levels(k)
+    ai = {"prof": [], "stress": []}
+    for _ in range(60):
+        g.mts_step(5, mode=M.MD_MODE_AI, k_m=1)
+        sample(g, ai)
+    g.close()
+    # the fine runs cover the same 3 tau after the same 1.28 tau lead-in
+    f1, f2 = fine(11), fine(12)
+
+    def stats(acc):
+        return np.mean(acc["prof"], 0), np.mean(acc["stress"], 0)
+
+    (p1, s1), (p2, s2), (pa, sa) = stats(f1), stats(f2), stats(ai)
+    vmax = np.abs(p1).max()
+    noise_p = np.linalg.norm(p2 - p1) / np.linalg.norm(p1)
+    err_p = np.linalg.norm(pa - p1) / np.linalg.norm(p1)
+    noise_s = np.abs(s2 - s1).max() / np.abs(s1).max()
+    err_s = np.abs(sa - s1).max() / np.abs(s1).max()
+    print(dict(k=k.tolist(), vmax=vmax, profile_err=err_p, profile_noise=noise_p, stress_err=err_s,
+               stress_noise=noise_s))
+    assert vmax > 0.05                                  # the channel flows
+    assert err_p <= 3.0 * noise_p + 0.005
+    assert err_s <= 3.0 * noise_s + 0.005

@@ -371,6 +371,22 @@ def test_step_graph_records_features_every_step(plt_wall_sys, mode):
         assert np.all(np.abs(ra - rc_) <= 2e-3 * scale + 1e-6)
 
 
+@pytest.mark.parametrize("which", ["walls", "le"])
+def test_flow_profile_matches_oracle(wall_sys, plt_sys, which):
+    """Sec. 4.2 flow profile (FP64 device sums) against the oracle on the GPU's
+    own state."""
+    from oracle import features as OF
+    s = wall_sys if which == "walls" else plt_sys
+    g = make_gpu(s)
+    g.mts_step(5)
+    mean, dens = g.flow_profile(20)
+    x, v, _ = g.read_particles()
+    ref_mean, ref_dens = OF.flow_profile(x, v, s.tag, s.box, 20)
+    assert np.allclose(mean, ref_mean, rtol=1e-12, atol=1e-13)
+    assert np.allclose(dens, ref_dens, rtol=1e-12)
+    assert abs(dens.mean() - 3.0) < 0.5
+
+
 def test_checkpoint_roundtrip(plt_sys):
     s = plt_sys
     g = make_gpu(s)

@@ -72,3 +72,28 @@ def test_minimum_image_across_the_box():
                             np.zeros(0), BOX)
     b = F.platelet_features(xw, v, np.zeros((4, 3)), np.zeros(4, np.int32), np.zeros((0, 2), int), np.zeros(0), BOX)
     assert np.allclose(a[:, :10], b[:, :10], atol=1e-12)
+
+
+def test_flow_profile_of_a_linear_shear_field():
+    """Sec. 4.2 flow profile: particles at the slab centres moving with
+    v_x = a + b y give back a + b y_c in every slab and the density count /
+    slab volume; wall and platelet particles do not count."""
+    box = (4.0, 10.0, 5.0)
+    nb = 5
+    yc = (np.arange(nb) + 0.5) * 2.0
+    rng = np.random.default_rng(3)
+    pts, vel, tags = [], [], []
+    for k, y in enumerate(yc):
+        m = k + 2                                   # slab k holds k + 2 plasma particles
+        p = np.column_stack([rng.uniform(0, 4, m), np.full(m, y), rng.uniform(0, 5, m)])
+        pts.append(p)
+        vel.append(np.column_stack([0.3 + 0.05 * p[:, 1], rng.normal(size=m), rng.normal(size=m)]))
+        tags.append(np.full(m, -1))
+    # walls and a platelet with velocities that would spoil the profile
+    pts.append(np.array([[1.0, -0.5, 1.0], [1.0, 5.0, 1.0]]))
+    vel.append(np.array([[9.0, 0, 0], [-9.0, 0, 0]]))
+    tags.append(np.array([-2, 0]))
+    x, v, tag = np.concatenate(pts), np.concatenate(vel), np.concatenate(tags)
+    mean, dens = F.flow_profile(x, v, tag, box, nb)
+    assert np.allclose(mean, 0.3 + 0.05 * yc, rtol=0, atol=1e-14)
+    assert np.allclose(dens, (np.arange(nb) + 2) / (4.0 * 5.0 * 2.0), rtol=1e-14)
