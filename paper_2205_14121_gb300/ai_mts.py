@@ -75,11 +75,18 @@ def run_ai_mts(system, controller, n_steps, k_m=1, trust=None, T=128, log=None):
     is asked again after the shortest predicted hold."""
     trust = trust or TrustBound()
     P = system.cfg.n_platelets
-    system.set_platelet_levels(np.full(P, trust.fallback_k, np.int32))
+    # the ratios and the count of consecutive records at the end of the ring
+    # carry over from one call to the next on the same system
+    state = getattr(system, "_ai_mts_state", None)
+    if state is None:
+        system.set_platelet_levels(np.full(P, trust.fallback_k, np.int32))
+        state = {"fresh": 0}
+        system._ai_mts_state = state
     done = 0
-    fresh = 0          # consecutive records at the end of the ring
+    fresh = state["fresh"]
     while done < n_steps:
         windows, count = system.read_feature_ring()
+        fresh = min(fresh, count)          # new particles restart the ring
         if fresh >= T:
             pred = controller.predict(windows)
             k, hold, unsure = decide(pred, windows, trust)
@@ -98,6 +105,7 @@ def run_ai_mts(system, controller, n_steps, k_m=1, trust=None, T=128, log=None):
         system.mts_step(run - quiet, mode=B.MD_MODE_AI, k_m=k_m, record=True)
         fresh += run - quiet
         done += run
+    state["fresh"] = fresh
     return log
 
 

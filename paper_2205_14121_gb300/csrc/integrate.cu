@@ -37,6 +37,7 @@ struct kd_args {
     md_geom geom;
     const md_dstate *ds;
     int32_t *ctl;
+    int sparse_level;      // >= 0: a pure kick with this level only (most forces zero)
 };
 
 __device__ __forceinline__ bool selected(int which, int32_t t)
@@ -52,6 +53,11 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= a.n) return;
     const int64_t k = a.idx ? a.idx[r] : r;
+    if (a.sparse_level >= 0) {
+        // interface half kicks: only particles near a platelet carry a force
+        const float4 fl = a.f[a.sparse_level][k];
+        if (fl.x == 0.0f && fl.y == 0.0f && fl.z == 0.0f) return;
+    }
     const int32_t t = a.tag[k];
     const bool kick = selected(a.kick_which, t);
     const bool drift = selected(a.drift_which, t);
@@ -235,6 +241,7 @@ kd_args base_args(md_system *s)
     a.kick_which = -1;
     a.drift_which = -1;
     a.zero_levels = 0;
+    a.sparse_level = -1;
     return a;
 }
 
@@ -252,6 +259,8 @@ cudaError_t launch_kick_drift(md_system *s, const float h[3], int kick_which, do
     a.drift_which = drift_which;
     a.dt = dt;
     a.zero_levels = zero_levels;
+    a.sparse_level = -1;
+    if (drift_which < 0 && zero_levels == 0u && h[0] == 0.0f && h[2] == 0.0f && h[1] != 0.0f) a.sparse_level = 1;
     if (plt_rows) {
         a.idx = s->plt_sorted;
         a.n = s->n_plt;

@@ -276,11 +276,14 @@ def plasma_box(n=None, box=None, rho=3.0, walls=False, wall=1.0, body_force=0.0,
 
 def platelet_system(box, n_plasma, n_plt, n_shell, radii, walls=False, wall=1.0,
                     shear_rate=0.0, body_force=0.0, receptor_frac=0.05,
-                    seed=DEFAULT_SEED, centers=None, clusters=None, kT=1.0, plasma_gap=0.8):
+                    seed=DEFAULT_SEED, centers=None, clusters=None, kT=1.0, plasma_gap=0.8, developed_flow=False):
     """Plasma + spheroid platelet shells (Fig. 1 shapes, synthetic sizes).
 
     n_plasma plasma positions are drawn uniformly; see _fill_platelets for
-    how the plasma meets the membranes."""
+    how the plasma meets the membranes.  developed_flow (walls and a body
+    force): mobile particles start on the steady Poiseuille profile
+    u_x(y) = rho g y (Ly - y) / (2 eta) with eta = ETA_DPD, which the flow would
+    otherwise take about rho Ly^2 / eta time units to develop."""
     rng = rng_for(seed)
     box = tuple(float(b) for b in box)
     lo = np.zeros(3)
@@ -307,6 +310,10 @@ def platelet_system(box, n_plasma, n_plt, n_shell, radii, walls=False, wall=1.0,
         fx = _fill_platelets(rng, fx, plts, radii, box, plasma_gap)
     wx = wall_layers(rng, box, wall) if walls else np.zeros((0, 3))
     x, v, tag, bonds, r0 = _assemble(box, fx, wx, plts, rng, n_shell, receptor_frac, kT)
+    if developed_flow and walls and body_force:
+        mob = tag != TAG_WALL
+        y = x[mob, 1]
+        v[mob, 0] += 3.0 * body_force * y * (box[1] - y) / (2.0 * ETA_DPD)
     return System(box=box, x=x, v=v, tag=tag, X0=x.copy(), bonds=bonds, r0=r0,
                   walls=walls, wall=wall, shear_rate=shear_rate, body_force=body_force,
                   n_platelets=n_plt, meta=dict(kind="platelets", seed=seed, n_shell=n_shell,

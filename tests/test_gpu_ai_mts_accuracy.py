@@ -18,7 +18,7 @@ def channel():
     box = (36.0, 18.0, 16.0)
     g = synth.poiseuille_g(0.05, synth.ETA_DPD, 3.0, box[1])
     return synth.platelet_system(box, int(3 * 36 * 18 * 16), 2, 2000, synth.scaled_radii(2000), walls=True,
-                                 body_force=g, seed=31)
+                                 body_force=g, seed=31, developed_flow=True)
 
 
 def sample(g, acc):
