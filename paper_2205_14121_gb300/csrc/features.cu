@@ -131,33 +131,41 @@ constexpr int FS_N = 25;
 // FP64 atomics, the largest bond strain by an integer max on float bits.
 __global__ void __launch_bounds__(FT_TPB) k_feat_sums(feat_args a, double *sums, unsigned *strain)
 {
-    __shared__ double sh[FT_TPB / 32][FS_N];
+    // FP64 is scarce on this part: a thread sums its few members' position
+    // and velocity terms in FP32 (each term rounded once, |r| < half the
+    // box), the force moments in FP64; the block and platelet sums are FP64
+    __shared__ double sh[5][FT_TPB];
     const int p = blockIdx.x;
     const int b = a.plt_off[p], e = a.plt_off[p + 1];
     const bool py = !a.geom.walls;
     const float4 ref = a.x32[a.pos_of_id[a.plt_ids[b]]];
-    double t[FS_N];
+    float ta[16];
 #pragma unroll
-    for (int q = 0; q < FS_N; ++q) t[q] = 0.0;
+    for (int q = 0; q < 16; ++q) ta[q] = 0.0f;
+    double tb[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) tb[q] = 0.0;
     const int stride = gridDim.y * FT_TPB;
     for (int m = b + blockIdx.y * FT_TPB + threadIdx.x; m < e; m += stride) {
         const int k = a.pos_of_id[a.plt_ids[m]];
         const float4 xk = a.x32[k];
         const float4 vk = vel_at(a, k);
-        const double rx = img64((double)xk.x - ref.x, a.L[0], true), ry = img64((double)xk.y - ref.y, a.L[1], py),
-                     rz = img64((double)xk.z - ref.z, a.L[2], true);
-        double fx = 0, fy = 0, fz = 0;
+        const float rx = (float)img64((double)xk.x - ref.x, a.L[0], true);
+        const float ry = (float)img64((double)xk.y - ref.y, a.L[1], py);
+        const float rz = (float)img64((double)xk.z - ref.z, a.L[2], true);
+        float fx = 0.f, fy = 0.f, fz = 0.f;
         if (a.f0) { const float4 q = a.f0[k]; fx += q.x; fy += q.y; fz += q.z; fx += a.g_body; }
         if (a.f1) { const float4 q = a.f1[k]; fx += q.x; fy += q.y; fz += q.z; }
         if (a.f2) { const float4 q = a.f2[k]; fx += q.x; fy += q.y; fz += q.z; }
-        t[0] += 1.0;
-        t[1] += rx; t[2] += ry; t[3] += rz;
-        t[4] += vk.x; t[5] += vk.y; t[6] += vk.z;
-        t[7] += ry * vk.z - rz * vk.y; t[8] += rz * vk.x - rx * vk.z; t[9] += rx * vk.y - ry * vk.x;
-        t[10] += rx * rx; t[11] += ry * ry; t[12] += rz * rz; t[13] += rx * ry; t[14] += rx * rz; t[15] += ry * rz;
-        t[16] += fx; t[17] += fy; t[18] += fz;
-        t[19] += rx * fx; t[20] += ry * fy; t[21] += rz * fz;
-        t[22] += 0.5 * (rx * fy + fx * ry); t[23] += 0.5 * (rx * fz + fx * rz); t[24] += 0.5 * (ry * fz + fy * rz);
+        ta[0] += 1.0f;
+        ta[1] += rx; ta[2] += ry; ta[3] += rz;
+        ta[4] += vk.x; ta[5] += vk.y; ta[6] += vk.z;
+        ta[7] += ry * vk.z - rz * vk.y; ta[8] += rz * vk.x - rx * vk.z; ta[9] += rx * vk.y - ry * vk.x;
+        ta[10] += rx * rx; ta[11] += ry * ry; ta[12] += rz * rz; ta[13] += rx * ry; ta[14] += rx * rz; ta[15] += ry * rz;
+        const double dx = rx, dy = ry, dz = rz, gx = fx, gy = fy, gz = fz;
+        tb[0] += gx; tb[1] += gy; tb[2] += gz;
+        tb[3] += dx * gx; tb[4] += dy * gy; tb[5] += dz * gz;
+        tb[6] += 0.5 * (dx * gy + gx * dy); tb[7] += 0.5 * (dx * gz + gx * dz); tb[8] += 0.5 * (dy * gz + gy * dz);
     }
     float smax = 0.f;
     for (int bb = a.bond_off[p] + blockIdx.y * FT_TPB + threadIdx.x; bb < a.bond_off[p + 1]; bb += stride) {
@@ -169,20 +177,25 @@ __global__ void __launch_bounds__(FT_TPB) k_feat_sums(feat_args a, double *sums,
         const float r0 = a.bond_r0[bb];
         smax = fmaxf(smax, fabsf(sqrtf(dx * dx + dy * dy + dz * dz) - r0) / r0);
     }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < FS_N; ++q) {
-        double v = t[q];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[w][q] = v;
-    }
     smax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(smax)));   // smax >= 0
-    if (lane == 0 && smax > 0.f) atomicMax(&strain[p], __float_as_uint(smax));
-    __syncthreads();
-    if (threadIdx.x < FS_N) {
-        double v = 0.0;
-        for (int q = 0; q < FT_TPB / 32; ++q) v += sh[q][threadIdx.x];
-        atomicAdd(&sums[(int64_t)p * FS_N + threadIdx.x], v);
+    if ((threadIdx.x & 31) == 0 && smax > 0.f) atomicMax(&strain[p], __float_as_uint(smax));
+    // block sums in FP64, five quantities at a time (a tree in shared memory)
+#pragma unroll
+    for (int g = 0; g < FS_N / 5; ++g) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const int w = 5 * g + q;
+            sh[q][threadIdx.x] = w < 16 ? (double)ta[w < 16 ? w : 0] : tb[w >= 16 ? w - 16 : 0];
+        }
+        __syncthreads();
+        for (int st = FT_TPB / 2; st > 0; st >>= 1) {
+            if (threadIdx.x < st)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + st];
+            __syncthreads();
+        }
+        if (threadIdx.x < 5) atomicAdd(&sums[(int64_t)p * FS_N + 5 * g + threadIdx.x], sh[threadIdx.x][0]);
+        __syncthreads();
     }
 }
 
@@ -344,7 +357,7 @@ cudaError_t launch_features(md_system *s, double *out_dev, const float4 *f_plt, 
     if (e != cudaSuccess) return e;
     unsigned *strain = (unsigned *)(s->feat_sums + (int64_t)FS_N * P);
     const int mean_members = (int)((s->n_plt + P - 1) / P);
-    const int chunks = min(256, mean_members / FT_TPB + 1);    // blocks per platelet: about a member per thread
+    const int chunks = min(256, mean_members / (2 * FT_TPB) + 1);    // blocks per platelet: two members per thread
     k_feat_sums<<<dim3(P, chunks), FT_TPB, 0, s->stream>>>(a, s->feat_sums, strain);
     k_feat_final<<<P, FT_TPB, 0, s->stream>>>(a, s->feat_sums, strain);
     MSM_COUNT(s, 2);
