@@ -209,6 +209,13 @@ __global__ void k_import_v(int64_t n, const double *__restrict__ aos, const int3
     pos_of_id[k] = (int32_t)k;
 }
 
+// Clear the rows idx[0..n) of a float4 buffer.
+__global__ void k_zero_rows(const int32_t *__restrict__ idx, int64_t n, float4 *buf)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) buf[idx[r]] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 __global__ void k_import_f4(int64_t n, const double *__restrict__ aos, float4 *out, float w)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -445,7 +452,9 @@ int enqueue_record(md_system *s, int mode)
     prof_begin(s, MD_PROF_OTHER);
     const float4 *fp = nullptr;
     if (mode == MD_MODE_AI) {
-        CK(cudaMemsetAsync(s->altf[2], 0, sizeof(float4) * s->n, s->stream), "zero scratch forces");
+        k_zero_rows<<<blocks_for(s->n_plt), MSM_TPB, 0, s->stream>>>(s->plt_sorted, s->n_plt, s->altf[2]);
+        CK(cudaGetLastError(), "zero scratch forces");
+        MSM_COUNT(s, 1);
         float4 *out[3] = {nullptr, nullptr, s->altf[2]};
         CK(launch_forces(s, MD_LEVEL_PLT, out, false), "record forces");
         fp = s->altf[2];

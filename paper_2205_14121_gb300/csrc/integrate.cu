@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
     const int32_t t = a.tag[k];
     const bool kick = selected(a.kick_which, t);
     const bool drift = selected(a.drift_which, t);
+    unsigned zero_seen = 0u;   // levels read as exactly zero: no need to clear them
     if (kick || drift) {
         float4 vv = a.v[k];
         if (kick) {
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
             for (int l = 0; l < a.nf; ++l) {
                 if (a.h[l] == 0.0f) continue;
                 const float4 fl = a.f[l][k];
+                if (fl.x == 0.0f && fl.y == 0.0f && fl.z == 0.0f) zero_seen |= 1u << l;
                 ax += a.h[l] * fl.x; ay += a.h[l] * fl.y; az += a.h[l] * fl.z;
             }
             ax += a.h[0] * a.g;
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
         a.v[k] = vv;
     }
     for (int l = 0; l < a.nf; ++l)
-        if (a.zero_levels & (1u << l)) a.f[l][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((a.zero_levels & ~zero_seen) & (1u << l)) a.f[l][k] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Set the device time index (n, c) and the time n dt + c dt_m + q dt_p;
