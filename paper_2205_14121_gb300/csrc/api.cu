@@ -770,9 +770,13 @@ int md_set_particles(md_system *s, const double *x, const double *v, const int32
 {
     if (!s || !x || !v || !tag) return set_error(s, MD_EINVAL, "md_set_particles: null argument");
     const int64_t n = s->n;
+    // the same particle set as before (a new state of it): the tags were
+    // validated and the platelet member lists built then
+    const bool same = s->have_particles && s->h_tag.size() == (size_t)n &&
+                      memcmp(s->h_tag.data(), tag, sizeof(int32_t) * (size_t)n) == 0;
     // host-side validation of the tag counts
     int64_t np = 0, nr = 0, npl = 0;
-    for (int64_t k = 0; k < n; ++k) {
+    for (int64_t k = 0; k < (same ? 0 : n); ++k) {
         const int32_t t = tag[k];
         if (t < MD_TAG_WALL) return set_error(s, MD_EINVAL, "md_set_particles: invalid tag");
         if (t >= 0) {
@@ -783,13 +787,13 @@ int md_set_particles(md_system *s, const double *x, const double *v, const int32
         }
         if (t == MD_TAG_WALL && !s->geom.walls) return set_error(s, MD_EINVAL, "wall particles without walls");
     }
-    if (np != s->n_plt || nr != s->n_rec)
+    if (!same && (np != s->n_plt || nr != s->n_rec))
         return set_error(s, MD_EINVAL, "md_set_particles: platelet/receptor counts differ from the configuration");
-    if (npl > (s->n_plt > 0 ? s->cfg.n_platelets : 0))
+    if (!same && npl > (s->n_plt > 0 ? s->cfg.n_platelets : 0))
         return set_error(s, MD_EINVAL, "md_set_particles: platelet id beyond cfg.n_platelets");
     cudaStream_t st = s->stream;
-    s->h_tag.assign(tag, tag + n);
-    if (s->n_plt > 0) {
+    if (!same) s->h_tag.assign(tag, tag + n);
+    if (s->n_plt > 0 && !same) {
         // member lists per platelet (ids ascending)
         const int P = s->cfg.n_platelets;
         std::vector<int32_t> off((size_t)P + 1, 0), ids((size_t)s->n_plt);
