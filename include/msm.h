@@ -241,7 +241,9 @@ typedef struct md_observables_t {
     double  time;            /* step * dt_f                                    */
     double  momentum[3];     /* total momentum of mobile particles             */
     double  kinetic;         /* 1/2 sum m v^2 (mobile)                         */
-    double  temperature;     /* sum m|v-u|^2 / N_dof (u: Lees-Edwards profile) */
+    double  temperature;     /* sum m|v-u|^2 / N_dof; u: the Lees-Edwards profile,
+                                or with walls the mean v_x of the mobile particles
+                                in each of 20 slabs of y (N_dof = 3N - 3, 3N with walls) */
     double  kin_tensor[9];   /* sum m (v-u)_a (v-u)_b                          */
     double  virial_c[9];     /* sum over pairs r_a F^C_b (conservative), last forces with MD_FORCE_VIRIAL */
     double  pressure;        /* (trace kin_tensor + trace virial_c) / (3V)     */

@@ -343,8 +343,12 @@ cudaError_t launch_set_loop(md_system *s, int64_t n);
 cudaError_t launch_zero_forces(md_system *s, unsigned levels);
 // reduce.cu
 cudaError_t launch_kinetics(md_system *s);
-// y-binned plasma v_x sums and counts into prof_part + PROF_BLOCKS * 2 * PROF_BINS_MAX
-cudaError_t launch_flow_profile(md_system *s, int nbins);
+// y-binned v_x sums and counts into prof_part + PROF_BLOCKS * 2 * PROF_BINS_MAX:
+// plasma, edge slabs clamped (mobile false); mobile particles inside [0, Ly)
+// (mobile true, the local flow of the wall temperature)
+cudaError_t launch_flow_profile(md_system *s, int nbins, bool mobile = false);
+// slabs of the local flow subtracted from the wall-bounded kinetic tensor
+constexpr int KIN_BINS = 20;
 // features.cu
 // f_plt: platelet-level forces to use (null: s->f[2]); hk: half kicks per
 // level still pending on the stored velocities (null: none)

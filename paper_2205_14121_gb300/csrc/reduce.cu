@@ -19,8 +19,17 @@ __device__ __forceinline__ double warp_sum(double v)
 
 __global__ void __launch_bounds__(MSM_TPB) k_kinetics(int64_t n, const float4 *__restrict__ v,
                                                      const double *__restrict__ ys, const int32_t *__restrict__ tag,
-                                                     int le, double rate, double half_Ly, double *part)
+                                                     int le, double rate, double half_Ly, const double *flow,
+                                                     int nbins, double *part)
 {
+    // walls: the local flow is the y-binned mean v_x of the mobile particles
+    // (flow = [sum v_x][count] per bin); Lees-Edwards: the imposed profile
+    __shared__ double ub[PROF_BINS_MAX];
+    if (flow)
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+            ub[b] = flow[nbins + b] > 0.0 ? flow[b] / flow[nbins + b] : 0.0;
+    __syncthreads();
+    const double scale = nbins / (2.0 * half_Ly);
     double acc[W_COUNT];
 #pragma unroll
     for (int w = 0; w < W_COUNT; ++w) acc[w] = 0.0;
@@ -29,7 +38,12 @@ __global__ void __launch_bounds__(MSM_TPB) k_kinetics(int64_t n, const float4 *_
         if (tag[k] == MD_TAG_WALL) continue;
         const float4 vv = v[k];
         const double vx = vv.x, vy = vv.y, vz = vv.z;
-        const double ux = le ? vx - rate * (ys[k] - half_Ly) : vx;
+        double ux = le ? vx - rate * (ys[k] - half_Ly) : vx;
+        if (flow) {
+            int b = (int)floor(ys[k] * scale);
+            b = b < 0 ? 0 : (b >= nbins ? nbins - 1 : b);
+            ux -= ub[b];
+        }
         acc[W_PX] += vx; acc[W_PY] += vy; acc[W_PZ] += vz;
         acc[W_KE] += 0.5 * (vx * vx + vy * vy + vz * vz);
         acc[W_KXX] += ux * ux; acc[W_KYY] += vy * vy; acc[W_KZZ] += vz * vz;
@@ -64,7 +78,7 @@ __global__ void k_reduce_final(const double *part, int nblocks, double *out)
 // bins per block, then one pass over the block partials per bin).
 __global__ void __launch_bounds__(MSM_TPB) k_profile(int64_t n, const float4 *__restrict__ v,
                                                     const double *__restrict__ ys, const int32_t *__restrict__ tag,
-                                                    double Ly, int nbins, double *part)
+                                                    double Ly, int nbins, int mobile, double *part)
 {
     __shared__ double sv[PROF_BINS_MAX], sn[PROF_BINS_MAX];
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) { sv[b] = 0.0; sn[b] = 0.0; }
@@ -72,7 +86,8 @@ __global__ void __launch_bounds__(MSM_TPB) k_profile(int64_t n, const float4 *__
     const double scale = nbins / Ly;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-        if (tag[k] != MD_TAG_FLUID) continue;
+        // plasma, clamped to the edge slabs; or every mobile particle inside [0, Ly)
+        if (mobile ? (tag[k] == MD_TAG_WALL || ys[k] < 0.0 || ys[k] >= Ly) : tag[k] != MD_TAG_FLUID) continue;
         int b = (int)floor(ys[k] * scale);
         b = b < 0 ? 0 : (b >= nbins ? nbins - 1 : b);
         atomicAdd(&sv[b], (double)v[k].x);
@@ -97,9 +112,10 @@ __global__ void k_profile_final(const double *part, int nblocks, int nbins, doub
 
 }  // namespace
 
-cudaError_t launch_flow_profile(md_system *s, int nbins)
+cudaError_t launch_flow_profile(md_system *s, int nbins, bool mobile)
 {
-    k_profile<<<PROF_BLOCKS, MSM_TPB, 0, s->stream>>>(s->n, s->v, s->ys, s->tag_s, s->cfg.box[1], nbins, s->prof_part);
+    k_profile<<<PROF_BLOCKS, MSM_TPB, 0, s->stream>>>(s->n, s->v, s->ys, s->tag_s, s->cfg.box[1], nbins, mobile ? 1 : 0,
+                                                    s->prof_part);
     k_profile_final<<<(2 * nbins + 127) / 128, 128, 0, s->stream>>>(s->prof_part, PROF_BLOCKS, nbins,
                                                                     s->prof_part + (int64_t)PROF_BLOCKS * 2 * PROF_BINS_MAX);
     MSM_COUNT(s, 2);
@@ -109,8 +125,14 @@ cudaError_t launch_flow_profile(md_system *s, int nbins)
 cudaError_t launch_kinetics(md_system *s)
 {
     const int nb = s->red_blocks;
+    const double *flow = nullptr;
+    if (s->geom.walls) {
+        cudaError_t e = launch_flow_profile(s, KIN_BINS, true);
+        if (e != cudaSuccess) return e;
+        flow = s->prof_part + (int64_t)PROF_BLOCKS * 2 * PROF_BINS_MAX;
+    }
     k_kinetics<<<nb, MSM_TPB, 0, s->stream>>>(s->n, s->v, s->ys, s->tag_s, s->geom.le, s->cfg.shear_rate,
-                                              0.5 * s->cfg.box[1], s->red_part);
+                                              0.5 * s->cfg.box[1], flow, KIN_BINS, s->red_part);
     k_reduce_final<<<1, 32, 0, s->stream>>>(s->red_part, nb, s->red_out);
     MSM_COUNT(s, 2);
     return cudaGetLastError();

@@ -163,6 +163,34 @@ def test_virial_and_kinetics_match_oracle(plt_sys):
     assert np.allclose(o["momentum"], kin["momentum"], rtol=0, atol=1e-9 * np.abs(v).sum())
     assert o["kinetic"] == pytest.approx(kin["ke"], rel=1e-10)
     assert np.allclose(o["virial_c"], acc["vir_c"], rtol=1e-4, atol=1e-4 * np.abs(acc["vir_c"]).max())
+    assert o["temperature"] == pytest.approx(kin["T"], rel=1e-10)
+    assert np.allclose(o["kin_tensor"], kin["K"], rtol=1e-10, atol=1e-10 * np.abs(kin["K"]).max())
+
+
+def test_wall_temperature_subtracts_local_flow(plt_wall_sys):
+    """With walls the peculiar velocity is relative to the 20-slab mean v_x of
+    the mobile particles (Sec. 4.2): a parabolic stream of amplitude 0.5 laid on
+    the thermal velocities leaves the temperature near its thermal value, and
+    the GPU's FP64 sums equal the oracle's on the GPU's own state."""
+    s = plt_wall_sys
+    Ly = s.box[1]
+    v0 = f32(s.v)
+    y = s.x[:, 1]
+    mob = s.tag != synth.TAG_WALL
+    v0[mob, 0] += (2.0 * y[mob] * (Ly - y[mob]) / Ly ** 2).astype(np.float32)
+    g = make_gpu(s, x=f32(s.x), v=v0)
+    g.mts_step(2)
+    o = g.observables()
+    x, v, _ = g.read_particles()
+    kin = O.kinetics(O.system_params(s), x, v, s.tag, nbins=20)
+    assert o["temperature"] == pytest.approx(kin["T"], rel=1e-10)
+    assert np.allclose(o["kin_tensor"], kin["K"], rtol=1e-10, atol=1e-10 * np.abs(kin["K"]).max())
+    assert o["kinetic"] == pytest.approx(kin["ke"], rel=1e-10)
+    assert abs(kin["T"] - 1.0) < 0.1
+    # the stream itself is not temperature: without the subtraction the sum
+    # would exceed 3 N_mobile T by the stream's kinetic energy
+    stream = 2.0 * kin["ke"] - np.trace(kin["K"])
+    assert stream > 0.01 * mob.sum()
 
 
 def test_sts_trajectory_tracks_oracle(plt_sys):

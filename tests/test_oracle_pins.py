@@ -508,6 +508,34 @@ def test_ideal_gas_pressure():
     assert np.mean(Ts) == pytest.approx(1.0, abs=0.03)
 
 
+def test_wall_temperature_hand_built_slabs():
+    """Walls: the peculiar velocity is taken against the mean v_x of the mobile
+    particles in each slab of y.  Each of 4 slabs holds two particles at
+    u_b +- a_b in x plus (0, c, 0): K_xx = sum 2 a_b^2 and K_yy = 8 c^2 whatever
+    the stream u_b; a wall particle (any velocity) and a particle above Ly (out
+    of every slab mean, but peculiar against the top slab) complete the set."""
+    p = O.make_params((4.0, 8.0, 4.0), walls=True)
+    u = [0.3, 1.1, -0.7, 2.0]
+    a = [0.1, 0.25, 0.4, 0.05]
+    c = 0.2
+    x, v, tag = [], [], []
+    for b in range(4):
+        for sgn in (1.0, -1.0):
+            x.append((1.0, 2.0 * b + 0.5 + 0.5 * (sgn > 0), 1.0))
+            v.append((u[b] + sgn * a[b], c, 0.0))
+            tag.append(synth.TAG_FLUID)
+    x.append((2.0, 4.0, 2.0)); v.append((50.0, -30.0, 9.0)); tag.append(synth.TAG_WALL)
+    x.append((2.0, 8.3, 2.0)); v.append((u[3] + 0.5, 0.0, 0.0)); tag.append(synth.TAG_FLUID)
+    x, v, tag = np.array(x), np.array(v), np.array(tag, np.int32)
+    kin = O.kinetics(p, x, v, tag, nbins=4)
+    Kxx = 2.0 * sum(ai * ai for ai in a) + 0.25
+    assert kin["K"][0, 0] == pytest.approx(Kxx, rel=1e-14)
+    assert kin["K"][1, 1] == pytest.approx(8 * c * c, rel=1e-14)
+    assert kin["K"][0, 1] == pytest.approx(0.0, abs=1e-15)
+    assert kin["T"] == pytest.approx((Kxx + 8 * c * c) / (3 * 9), rel=1e-14)
+    assert kin["ke"] == pytest.approx(0.5 * (v[tag != synth.TAG_WALL] ** 2).sum(), rel=1e-14)
+
+
 @pytest.mark.slow
 def test_couette_linear_profile_under_lees_edwards():
     """Lees-Edwards shear gives a linear v_x(y) with the imposed slope."""
