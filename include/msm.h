@@ -76,7 +76,7 @@ extern "C" {
  * 100; Eq. 2/4 Morse D = 2, alpha = 2, r0 = 1 with cut-off 5.
  */
 typedef struct md_config {
-    int64_t  n;               /* particles (plasma + wall + platelet)            */
+    int64_t  n;               /* particles (plasma + wall + platelet), 1 .. 2^27  */
     int64_t  n_bonds;         /* harmonic bonds                                   */
     int64_t  n_plt_particles; /* particles with tag >= 0                          */
     int64_t  n_receptors;     /* platelet particles with the receptor bit         */
@@ -140,6 +140,16 @@ const char *md_last_error(const md_system *sys);
  */
 int md_set_particles(md_system *sys, const double *x, const double *v, const int32_t *tag,
                      const double *X0, int64_t step0);
+
+/*
+ * Load a new state of the particle set last given to md_set_particles():
+ * x[n*3] positions and v[n*3] velocities as HOST arrays in id order; tags,
+ * rest positions and bonds are kept on the device (nothing but x and v
+ * crosses to the GPU).  Resets the step counter to step0 and marks lists and
+ * forces stale, as md_set_particles does.  Errors: MD_EINVAL (null argument,
+ * or no earlier md_set_particles), MD_ECUDA.
+ */
+int md_set_xv(md_system *sys, const double *x, const double *v, int64_t step0);
 
 /*
  * Harmonic bonds (Eq. 2) as HOST arrays: ij[nb*2] particle ids, r0[nb] rest

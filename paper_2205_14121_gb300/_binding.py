@@ -129,6 +129,7 @@ def lib():
     L.md_last_error.argtypes = [vp]
     L.md_last_error.restype = C.c_char_p
     L.md_set_particles.argtypes = [vp, dp, dp, ip, dp, i64]
+    L.md_set_xv.argtypes = [vp, dp, dp, i64]
     L.md_set_bonds.argtypes = [vp, ip, dp, i64]
     L.md_neighbor_build.argtypes = [vp, u32, C.c_int]
     L.md_forces.argtypes = [vp, u32, u32]
@@ -150,7 +151,7 @@ def lib():
     L.md_read_feature_ring.argtypes = [vp, fp, C.POINTER(C.c_int64)]
     for name in ("md_platelet_features", "md_record_features", "md_read_feature_ring"):
         getattr(L, name).restype = C.c_int
-    for name in ("md_config_defaults", "md_workspace_size", "md_init", "md_set_particles", "md_set_bonds",
+    for name in ("md_config_defaults", "md_workspace_size", "md_init", "md_set_particles", "md_set_xv", "md_set_bonds",
                  "md_neighbor_build", "md_forces", "md_read_forces", "md_read_particles", "md_mts_step",
                  "md_set_platelet_levels", "md_flow_profile",
                  "md_observables", "md_neighbor_pairs", "md_get_state", "md_set_state", "md_profile_enable",
@@ -259,6 +260,15 @@ class System:
         self._check(lib().md_set_particles(self.h, _dp(x), _dp(v), _ip(tag), X0p, int(step0)), "md_set_particles")
 
     md_set_particles = set_particles
+
+    def set_xv(self, x, v, step0=0):
+        """New positions and velocities of the same particle set (tags, rest
+        positions and bonds kept on the device)."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        self._check(lib().md_set_xv(self.h, _dp(x), _dp(v), int(step0)), "md_set_xv")
+
+    md_set_xv = set_xv
 
     def set_bonds(self, bonds, r0):
         bonds = np.ascontiguousarray(bonds, dtype=np.int32)

@@ -61,7 +61,8 @@ int default_cap(int v, int d) { return v > 0 ? v : d; }
 
 bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
 {
-    if (c.n <= 0 || c.n >= (int64_t)1 << 31) { err = "n out of range"; return false; }
+    // the plasma list packs a partner index into 27 bits
+    if (c.n <= 0 || c.n > MSM_STREAM_JMASK + 1) { err = "n out of range (1 .. 2^27)"; return false; }
     if (c.n_plt_particles < 0 || c.n_plt_particles > c.n || c.n_receptors < 0 ||
         c.n_receptors > c.n_plt_particles || c.n_bonds < 0) {
         err = "inconsistent particle counts"; return false;
@@ -114,6 +115,7 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
     s.altv = cv.take<float4>(n);
     s.altx = cv.take<float4>(n);
     s.alt_tag = cv.take<int32_t>(n);
+    s.tag_id = cv.take<int32_t>(n);
     s.X0 = plt ? cv.take<float4>(n) : nullptr;
     s.gmain.start = cv.take<int32_t>(s.gmain.ncell + 1);
     s.gmain.count = cv.take<int32_t>(s.gmain.ncell);
@@ -765,6 +767,8 @@ const char *md_last_error(const md_system *s)
     return s->err.empty() ? "no error" : s->err.c_str();
 }
 
+static int load_xv(md_system *s, const double *x, const double *v, int64_t step0);
+
 int md_set_particles(md_system *s, const double *x, const double *v, const int32_t *tag, const double *X0,
                      int64_t step0)
 {
@@ -815,19 +819,29 @@ int md_set_particles(md_system *s, const double *x, const double *v, const int32
             CK(cudaStreamSynchronize(st), "sync");
         }
     }
-    CK(cudaMemcpyAsync(s->alt64, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload x");
-    k_import_x<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->alt64, s->xs, s->ys, s->zs, s->x32, s->xb);
-    CK(cudaGetLastError(), "import x");
-    CK(cudaMemcpyAsync(s->alt_tag, tag, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st), "upload tag");
-    CK(cudaMemcpyAsync(s->alt64, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload v");
-    k_import_v<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->alt64, s->alt_tag, s->v, s->tag_s, s->pos_of_id, s->x32,
-                                                   s->xb);
-    CK(cudaGetLastError(), "import v");
+    if (!same) CK(cudaMemcpyAsync(s->tag_id, tag, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st), "upload tag");
     if (s->X0) {
         CK(cudaMemcpyAsync(s->alt64, X0 ? X0 : x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload X0");
         k_import_f4<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->alt64, s->X0, 0.0f);
         CK(cudaGetLastError(), "import X0");
     }
+    s->have_particles = true;
+    return load_xv(s, x, v, step0);
+}
+
+// Upload of positions and velocities (id order) with the tags kept on the
+// device; storage back in id order, time index step0, lists and forces stale.
+static int load_xv(md_system *s, const double *x, const double *v, int64_t step0)
+{
+    const int64_t n = s->n;
+    cudaStream_t st = s->stream;
+    CK(cudaMemcpyAsync(s->alt64, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload x");
+    k_import_x<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->alt64, s->xs, s->ys, s->zs, s->x32, s->xb);
+    CK(cudaGetLastError(), "import x");
+    CK(cudaMemcpyAsync(s->alt64, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload v");
+    k_import_v<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->alt64, s->tag_id, s->v, s->tag_s, s->pos_of_id, s->x32,
+                                                   s->xb);
+    CK(cudaGetLastError(), "import v");
     for (int l = 0; l < 3; ++l)
         if (s->f[l]) CK(cudaMemsetAsync(s->f[l], 0, sizeof(float4) * n, st), "zero f");
     md_dstate *h = s->h_ds;
@@ -851,8 +865,14 @@ int md_set_particles(md_system *s, const double *x, const double *v, const int32
     s->lists_stale = true;
     s->forces_stale = true;
     s->forces_levels = 0;
-    s->have_particles = true;
     return MD_OK;
+}
+
+int md_set_xv(md_system *s, const double *x, const double *v, int64_t step0)
+{
+    if (!s || !x || !v) return set_error(s, MD_EINVAL, "md_set_xv: null argument");
+    if (!s->have_particles) return set_error(s, MD_EINVAL, "md_set_xv: md_set_particles was never called");
+    return load_xv(s, x, v, step0);
 }
 
 int md_set_bonds(md_system *s, const int32_t *ij, const double *r0, int64_t nb)
@@ -1199,6 +1219,26 @@ int md_neighbor_pairs(md_system *s, int32_t kind, int32_t *pairs, int64_t cap, i
         return id;
     };
     int64_t total = 0;
+    if (kind == MD_LIST_FLUID) {
+        // warp-stream layout: rows 32w .. 32w + 31 store their entries back
+        // to back from row 32w's slot, each entry j | (row - 32w) << 27
+        for (int64_t r0 = 0; r0 < rows; r0 += 32) {
+            int64_t tot = 0;
+            for (int64_t r = r0; r < rows && r < r0 + 32; ++r) tot += nc[(size_t)r] < cp ? nc[(size_t)r] : cp;
+            for (int64_t f = 0; f < tot; ++f) {
+                const uint32_t e = (uint32_t)nl[(size_t)(r0 * cp + f)];
+                const int32_t idi = id_of_h(r0 + (e >> MSM_STREAM_SHIFT));
+                const int32_t idj = id_of_h((int64_t)(e & MSM_STREAM_JMASK));
+                if (pairs && total < cap) {
+                    pairs[2 * total] = idi < idj ? idi : idj;
+                    pairs[2 * total + 1] = idi < idj ? idj : idi;
+                }
+                ++total;
+            }
+        }
+        *count = total;
+        return MD_OK;
+    }
     for (int64_t r = 0; r < rows; ++r) {
         const int64_t i = ridx.empty() ? r : ridx[(size_t)r];
         const int32_t idi = id_of_h(i);

@@ -220,6 +220,21 @@ __global__ void __launch_bounds__(FT_TPB) k_feat_final(feat_args a, const double
                        (int)floor((cz - g.lo[2]) / g.h[2])};
     const int span[3] = {min(2 * reach[0] + 1, g.nc[0]), min(2 * reach[1] + 1, g.nc[1]), min(2 * reach[2] + 1, g.nc[2])};
     const int ncand = span[0] * span[1] * span[2];
+    // the sphere test runs in FP32 (FP64 instructions are scarce on this
+    // part); only candidates whose FP32 d^2 lies within `band` of the radius,
+    // far more than the FP32 rounding of the coordinates can move it, repeat
+    // it in FP64
+    const float cf[3] = {(float)cx, (float)cy, (float)cz};
+    const float Lf[3] = {(float)a.L[0], (float)a.L[1], (float)a.L[2]};
+    const float r2f = (float)a.flow_r2;
+    const float band = 1e-5f * (fmaxf(Lf[0], fmaxf(Lf[1], Lf[2])) + 1.0f) * (1.0f + r2f);
+    auto img32 = [](float d, float L, bool periodic) {
+        if (periodic) {
+            if (d > 0.5f * L) d -= L;
+            else if (d < -0.5f * L) d += L;
+        }
+        return d;
+    };
     double fs = 0.0, fn = 0.0;
     for (int q = threadIdx.x; q < ncand; q += FT_TPB) {
         const int ox = q % span[0], oy = (q / span[0]) % span[1], oz = q / (span[0] * span[1]);
@@ -232,10 +247,17 @@ __global__ void __launch_bounds__(FT_TPB) k_feat_final(feat_args a, const double
         for (int32_t k = g.start[c]; k < g.start[c + 1]; ++k) {
             const float4 xk = a.x32[k];
             if (class_of(xk) != CLS_FLUID) continue;
-            const double dx = img64((double)xk.x - cx, a.L[0], true);
-            const double dy = img64((double)xk.y - cy, a.L[1], py);
-            const double dz = img64((double)xk.z - cz, a.L[2], true);
-            if (dx * dx + dy * dy + dz * dz < a.flow_r2) {
+            const float ex = img32(xk.x - cf[0], Lf[0], true), ey = img32(xk.y - cf[1], Lf[1], py),
+                        ez = img32(xk.z - cf[2], Lf[2], true);
+            const float d2f = ex * ex + ey * ey + ez * ez;
+            bool inside = d2f < r2f;
+            if (fabsf(d2f - r2f) <= band) {
+                const double dx = img64((double)xk.x - cx, a.L[0], true);
+                const double dy = img64((double)xk.y - cy, a.L[1], py);
+                const double dz = img64((double)xk.z - cz, a.L[2], true);
+                inside = dx * dx + dy * dy + dz * dz < a.flow_r2;
+            }
+            if (inside) {
                 const float4 vk = vel_at(a, k);
                 fs += (double)sqrtf(vk.x * vk.x + vk.y * vk.y + vk.z * vk.z);
                 fn += 1.0;

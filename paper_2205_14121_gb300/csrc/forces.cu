@@ -80,7 +80,7 @@ __device__ __forceinline__ void scatter(float4 *f, int32_t j, float fx, float fy
 // lists 32 entries at a time, so every lane has work whatever the row
 // lengths (the row of flat entry f is found by a shuffle binary search over
 // the rows' prefix offsets).  Candidates inside rc are appended to a per-warp
-// queue in shared memory (ballot + popc give the slots); whenever 32 pairs
+// ring queue in shared memory (ballot + popc give the slots); whenever 32 pairs
 // are queued each lane evaluates one -- Philox, Box-Muller and Eq. 1 -- and
 // scatters -F_ij to j.  Queue entries keep their row order, so the row sums
 // are a segmented shuffle reduction over each batch.
@@ -92,21 +92,20 @@ struct dpd_smem {
     float4 xi[DPD_WARPS][32];          // row positions (w: id)
     float4 vi[DPD_WARPS][32];          // row velocities (w: tag)
     float4 fi[DPD_WARPS][32];          // row force sums
-    float4 qa[DPD_WARPS][DPD_QCAP];    // queued pairs: dx, dy, dz, image v-shift
-    int4 qb[DPD_WARPS][DPD_QCAP];      // j, source row (lane), id_j, -
+    float4 qa[DPD_WARPS][DPD_QCAP];    // queued pairs (a ring): dx, dy, dz, image v-shift
+    int4 qb[DPD_WARPS][DPD_QCAP];      // j, source row (lane), id_j, id_i
 };
 
 template <bool VIR>
 __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int warp, int lane, bool valid,
-                                          uint32_t nt, uint32_t cs, vir6 &w)
+                                          int slot, const philox_pre &pq, vir6 &w)
 {
     float px = 0.f, py = 0.f, pz = 0.f;
     int src = -1;
     if (valid) {
-        const float4 q = sm.qa[warp][lane];
-        const int4 b = sm.qb[warp][lane];
+        const float4 q = sm.qa[warp][slot];
+        const int4 b = sm.qb[warp][slot];
         src = b.y;
-        const float4 xi = sm.xi[warp][src];
         const float4 vi = sm.vi[warp][src];
         const float4 vj = a.v[b.x];
         const float r2 = q.x * q.x + q.y * q.y + q.z * q.z;
@@ -116,7 +115,7 @@ __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int 
         const float wr = 1.0f - r2 * inv_r * a.inv_rc;
         const float ex = q.x * inv_r, ey = q.y * inv_r, ez = q.z * inv_r;
         const float edv = ex * (vi.x - vj.x - q.w) + ey * (vi.y - vj.y) + ez * (vi.z - vj.z);
-        const float zeta = pair_zeta(id_of(xi), (uint32_t)b.z, nt, cs, a.key);
+        const float zeta = pair_zeta_pre((uint32_t)b.w, (uint32_t)b.z, pq);
         const float fc = aij * wr;
         const float fp = fc - a.gamma * wr * wr * edv + a.sig_isdt * wr * zeta;
         px = fp * ex; py = fp * ey; pz = fp * ez;
@@ -140,7 +139,11 @@ __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int 
     }
 }
 
-template <bool VIR>
+// STREAM: the list is in the warp-stream layout (the plasma list): entry f
+// of the warp's concatenated rows is word f of the first row's slot, with the
+// row's lane in its top bits; otherwise ELL rows (the interface list) and the
+// row of an entry comes from a binary search over the rows' prefix offsets.
+template <bool VIR, bool STREAM>
 __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
 {
     __shared__ dpd_smem sm;
@@ -154,22 +157,33 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
     sm.xi[warp][lane] = xi;
     sm.vi[warp][lane] = active ? a.v[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     sm.fi[warp][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const uint32_t nt = (uint32_t)a.ds->step, cs = (uint32_t)a.ds->sub;
+    const philox_pre pq = philox_prepare((uint32_t)a.ds->step, (uint32_t)a.ds->sub, a.key);
     const float delta = a.ds->le_offset_f;
     const unsigned lt = (1u << lane) - 1u;
     vir6 w = {0, 0, 0, 0, 0, 0};
     // exclusive prefix of the row lengths: row L owns flat entries [pre_L, pre_L + cnt_L)
-    int pre = cnt;
+    int pre = cnt, total;
+    if (STREAM) {
+        total = __reduce_add_sync(0xffffffffu, cnt);
+    } else {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, pre, o);
-        if (lane >= o) pre += t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += t;
+        }
+        total = __shfl_sync(0xffffffffu, pre, 31);
+        pre -= cnt;
     }
-    const int total = __shfl_sync(0xffffffffu, pre, 31);
-    pre -= cnt;
-    int qn = 0;
+    const int32_t *wst = a.nl + r0 * a.cap;
+    int qn = 0, qh = 0;     // queued pairs, ring slot of the oldest
     // row of flat entry f (the last lane whose prefix is <= f) and its list entry
     auto locate = [&](int f, int &row, int32_t &j) {
+        if (STREAM) {
+            const uint32_t e = f < total ? (uint32_t)wst[f] : 0u;
+            row = (int)(e >> MSM_STREAM_SHIFT);
+            j = (int32_t)(e & MSM_STREAM_JMASK);
+            return;
+        }
         row = 0;
 #pragma unroll
         for (int step = 16; step > 0; step >>= 1) {
@@ -194,33 +208,32 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
         locate(base + 64 + lane, row_nn, j_nn);
         bool hit = false;
         float dx = 0.f, dy = 0.f, dz = 0.f, vsh = 0.f;
+        uint32_t id_i = 0;
         if (valid) {
-            min_image_f32(a.geom, delta, sm.xi[warp][row_c], xj_c, dx, dy, dz, vsh);
+            const float4 xi = sm.xi[warp][row_c];
+            id_i = id_of(xi);
+            min_image_f32(a.geom, delta, xi, xj_c, dx, dy, dz, vsh);
             const float r2 = dx * dx + dy * dy + dz * dz;
             hit = r2 < a.rc2 && r2 > 0.0f;
         }
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) {
-            const int pos = qn + __popc(m & lt);
+            const int pos = (qh + qn + __popc(m & lt)) & (DPD_QCAP - 1);
             sm.qa[warp][pos] = make_float4(dx, dy, dz, vsh);
-            sm.qb[warp][pos] = make_int4(j_c, row_c, (int)id_of(xj_c), 0);
+            sm.qb[warp][pos] = make_int4(j_c, row_c, (int)id_of(xj_c), (int)id_i);
         }
         qn += __popc(m);
         __syncwarp();
         if (qn >= 32) {
-            dpd_batch<VIR>(a, sm, warp, lane, true, nt, cs, w);
-            __syncwarp();
-            if (lane < qn - 32) {
-                sm.qa[warp][lane] = sm.qa[warp][32 + lane];
-                sm.qb[warp][lane] = sm.qb[warp][32 + lane];
-            }
+            dpd_batch<VIR>(a, sm, warp, lane, true, (qh + lane) & (DPD_QCAP - 1), pq, w);
+            qh = (qh + 32) & (DPD_QCAP - 1);
             qn -= 32;
             __syncwarp();
         }
         row_c = row_n; j_c = j_n; xj_c = xj_n;
         row_n = row_nn; j_n = j_nn;
     }
-    if (qn > 0) dpd_batch<VIR>(a, sm, warp, lane, lane < qn, nt, cs, w);
+    if (qn > 0) dpd_batch<VIR>(a, sm, warp, lane, lane < qn, (qh + lane) & (DPD_QCAP - 1), pq, w);
     __syncwarp();
     if (active && cnt > 0) {
         const float4 t = sm.fi[warp][lane];
@@ -378,8 +391,8 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
         a.a_same = (float)c.a_ff;
         a.a_wall = (float)c.a_fw;
         a.sig_isdt = (float)(c.sigma / sqrt(c.dt));
-        if (virial) k_dpd<true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
-        else k_dpd<false><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        if (virial) k_dpd<true, true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        else k_dpd<false, true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
         MSM_COUNT(s, 1);
     }
     if ((level_mask & MD_LEVEL_IFACE) && s->n_plt > 0) {
@@ -392,8 +405,8 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
         a.a_same = (float)c.a_fp;
         a.a_wall = (float)c.a_fp;
         a.sig_isdt = (float)(c.sigma / sqrt(c.dt / km));
-        if (virial) k_dpd<true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
-        else k_dpd<false><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        if (virial) k_dpd<true, false><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        else k_dpd<false, false><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
         MSM_COUNT(s, 1);
     }
     if ((level_mask & MD_LEVEL_PLT) && s->n_plt > 0) {

@@ -78,6 +78,7 @@ struct md_system {
     double *alt64;               // 3n
     float4 *altv, *altx, *altf[3];
     int32_t *alt_tag;
+    int32_t *tag_id;             // tags in id order, as last given to md_set_particles
     float4 *X0;                  // rest positions, id order
 
     // grids
@@ -187,6 +188,10 @@ __device__ __forceinline__ int tag_of(float4 v) { return __float_as_int(v.w); }
 // x32.w holds the particle id in bits 0-29 and its class in bits 30-31
 // (0 plasma, 1 wall, 2 platelet), so list builds need no tag load.
 #define MSM_ID_MASK 0x3FFFFFFFu
+// Plasma-list entries in the warp-stream layout: partner index in the low 27
+// bits, the row's lane within its warp of 32 rows above
+#define MSM_STREAM_SHIFT 27
+#define MSM_STREAM_JMASK 0x07FFFFFF
 enum { CLS_FLUID = 0, CLS_WALL = 1, CLS_PLT = 2 };
 __device__ __host__ __forceinline__ uint32_t pack_w(uint32_t id, int32_t tag)
 {
@@ -233,6 +238,39 @@ __device__ __forceinline__ float gauss_from_bits(uint32_t r0, uint32_t r1)
     }
     const float u2 = (float)(r1 >> 8) * (1.0f / 16777216.0f) - 0.5f;
     return -(t * rsqrtf(fmaxf(t, 1e-30f))) * __cosf(6.28318531f * u2);
+}
+
+// The first Philox round applied to the counter words that do not depend on
+// the pair, (nt, cs) with the key: the round's multiply of the third word and
+// the key-mixed fourth word.  philox_pre + the pair words reproduce
+// philox4x32_10 bit for bit.
+struct philox_pre {
+    uint32_t hi1k, lo1, cwk;
+    uint2 k1;                      // key after the first round's bump
+};
+__device__ __forceinline__ philox_pre philox_prepare(uint32_t nt, uint32_t cs, uint2 key)
+{
+    philox_pre q;
+    q.hi1k = __umulhi(0xCD9E8D57u, nt) ^ key.x;
+    q.lo1 = 0xCD9E8D57u * nt;
+    q.cwk = cs ^ key.y;
+    q.k1 = make_uint2(key.x + 0x9E3779B9u, key.y + 0xBB67AE85u);
+    return q;
+}
+__device__ __forceinline__ float pair_zeta_pre(uint32_t a, uint32_t b, const philox_pre &q)
+{
+    const uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
+    uint4 c = make_uint4(q.hi1k ^ hi, q.lo1, __umulhi(0xD2511F53u, lo) ^ q.cwk, 0xD2511F53u * lo);
+    uint2 k = q.k1;
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return gauss_from_bits(c.x, c.y);
 }
 
 // Pair noise zeta_ij at time index (nt, cs).

@@ -10,13 +10,16 @@
 // comes first in the grid's cell-sorted order; a row therefore only scans
 // cells whose index is not below its own, half of the neighbourhood.
 //
-// Lists are row-major ELL (entry k of row r at r*cap + k): a row's entries
-// are contiguous, so a warp that streams the concatenated rows of 32
-// consecutive particles reads them nearly coalesced.  Row counts beyond the
-// capacity are recorded (overflow bit + longest row) and never written.
+// Lists are built row-major ELL (entry k of row r at r*cap + k): a row's
+// entries are contiguous, so a warp that streams the concatenated rows of 32
+// consecutive particles reads them nearly coalesced; the plasma list is then
+// repacked so that they are (below).  Row counts beyond the capacity are
+// recorded (overflow bit + longest row) and never written.
 //
 //   MD_LIST_FLUID  rows: every particle (cell-sorted); later plasma/wall
-//                  partners, plasma-plasma and plasma-wall pairs (Eq. 1)
+//                  partners, plasma-plasma and plasma-wall pairs (Eq. 1);
+//                  stored as warp streams (each warp's 32 rows back to back
+//                  from its first row's slot, entry = j | lane << 27)
 //   MD_LIST_IFACE  rows: platelet particles; partners: every plasma or wall
 //                  particle (Eq. 3)
 //   MD_LIST_LJ     rows: platelet particles in platelet sub-grid order; later
@@ -258,6 +261,40 @@ done:
     if ((threadIdx.x & 31) == 0 && m > 0) {
         atomicMax(&a.ctl[CTL_MAXROW + KIND], m);
         if (m > a.cap) atomicOr(&a.ctl[CTL_OVERFLOW], 1 << KIND);
+    }
+    if (KIND == MD_LIST_FLUID) {
+        // Warp-stream layout for the force pass: the warp's 32 rows, written
+        // one per slot of cap entries, are packed back to back from the first
+        // row's slot, each entry carrying its row's lane.  In place: flat entry
+        // f of row L (prefix P_L <= L cap) moves from L cap + f - P_L to f,
+        // never above its source, and each round of 32 reads before it writes.
+        const int lane = threadIdx.x & 31;
+        const int64_t r0 = r - lane;
+        const int c = active ? min(cnt, a.cap) : 0;
+        int pre = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, pre, 31);
+        pre -= c;
+        int32_t *slot = a.nl + r0 * a.cap;
+        __syncwarp();      // the rows' entries, written by each lane, visible to the warp
+        for (int base = 0; base < total; base += 32) {
+            const int f = base + lane;
+            int row = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int p = __shfl_sync(0xffffffffu, pre, row + step);
+                if (p <= f) row += step;
+            }
+            const int k = f - __shfl_sync(0xffffffffu, pre, row);
+            const int32_t e = f < total ? (slot[row * a.cap + k] | (row << MSM_STREAM_SHIFT)) : 0;
+            __syncwarp();
+            if (f < total) slot[f] = e;
+            __syncwarp();
+        }
     }
 }
 

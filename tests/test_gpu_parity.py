@@ -415,6 +415,28 @@ def test_flow_profile_matches_oracle(wall_sys, plt_sys, which):
     assert abs(dens.mean() - 3.0) < 0.5
 
 
+def test_set_xv_equals_full_upload(plt_wall_sys):
+    """md_set_xv (positions and velocities only, tags and rest positions kept
+    on the device) leaves the same state as md_set_particles with the same
+    tags: two RESPA steps from it agree to FP32 atomic-order noise (a wrong
+    tag, rest position or stale list would move particles by orders more)."""
+    import paper_2205_14121_gb300 as M
+    s = plt_wall_sys
+    rng = np.random.default_rng(5)
+    x1 = f32(s.x + 0.01 * rng.standard_normal(s.x.shape) * (s.tag != synth.TAG_WALL)[:, None])
+    v1 = f32(s.v * 0.9)
+    a = make_gpu(s, x=x1, v=v1, step0=7)
+    b = make_gpu(s, step0=0)
+    b.mts_step(1)
+    b.set_xv(x1, v1, step0=7)
+    for g in (a, b):
+        g.mts_step(2, mode=M.MD_MODE_RESPA, k_m=1, k_p=5)
+    xa, va, _ = a.read_particles()
+    xb, vb, _ = b.read_particles()
+    assert np.abs(xa - xb).max() < 1e-5
+    assert np.abs(va - vb).max() < 1e-3 * np.sqrt((va ** 2).mean())
+
+
 def test_checkpoint_roundtrip(plt_sys):
     s = plt_sys
     g = make_gpu(s)
