@@ -122,17 +122,20 @@ __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int 
         scatter(a.f, b.x, -px, -py, -pz);
         if (VIR) w.add(q.x, q.y, q.z, fc * inv_r);
     }
-    // segmented sum over runs of equal src (entries are in row order)
+    // segmented sum over runs of equal src (entries are in row order): lane
+    // l adds lane l + o's partial while no run starts in (l, l + o]
+    const int prev = __shfl_up_sync(0xffffffffu, src, 1);
+    const bool head = lane == 0 || prev != src;
+    const unsigned hm = __ballot_sync(0xffffffffu, head);
+    const unsigned above = lane == 31 ? 0xffffffffu : (hm >> (lane + 1));
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const float ox = __shfl_down_sync(0xffffffffu, px, o);
         const float oy = __shfl_down_sync(0xffffffffu, py, o);
         const float oz = __shfl_down_sync(0xffffffffu, pz, o);
-        const int os = __shfl_down_sync(0xffffffffu, src, o);
-        if (lane + o < 32 && os == src) { px += ox; py += oy; pz += oz; }
+        if (lane + o < 32 && (above & ((1u << o) - 1u)) == 0u) { px += ox; py += oy; pz += oz; }
     }
-    const int prev = __shfl_up_sync(0xffffffffu, src, 1);
-    if (valid && (lane == 0 || prev != src)) {     // head of a run holds its total
+    if (valid && head) {     // head of a run holds its total
         float4 t = sm.fi[warp][src];
         t.x += px; t.y += py; t.z += pz;
         sm.fi[warp][src] = t;

@@ -117,12 +117,10 @@ __device__ __forceinline__ void for_ranges(const md_grid &g, const md_geom &geom
             else if (xlo < 0) { a0 = xlo + nx; b0 = nx - 1; a1 = 0; b1 = xhi; }
             else if (xhi >= nx) { a0 = xlo; b0 = nx - 1; a1 = 0; b1 = xhi - nx; }
             const int rowc = row * nx;
-#pragma unroll 1
-            for (int seg = 0; seg < 2; ++seg) {
-                int a = seg ? a1 : a0;
-                const int b = seg ? b1 : b0;
+            // one run of cells [a, b] of this row
+            auto run = [&](int a, int b) {
                 if (HALF && row == own_row) a = max(a, ox);
-                if (a > b) continue;
+                if (a > b) return;
                 // cells that cannot hold a partner are cut out of the run
                 while (a <= b && skip_cell(rowc + a)) ++a;
                 int bb = b;
@@ -137,7 +135,9 @@ __device__ __forceinline__ void for_ranges(const md_grid &g, const md_geom &geom
                     c = d + 1;
                     while (c <= bb && skip_cell(rowc + c)) ++c;
                 }
-            }
+            };
+            run(a0, b0);
+            if (a1 <= b1) run(a1, b1);
         }
     }
 }
