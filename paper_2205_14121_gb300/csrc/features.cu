@@ -43,37 +43,40 @@ __device__ __forceinline__ double block_max(double v, double *sh)
     return s;
 }
 
-__device__ __forceinline__ double dimg(double d, double L, bool periodic)
-{
-    return periodic ? d - L * nearbyint(d / L) : d;
-}
-
-// Eigenvalues of a symmetric 3x3 matrix (trigonometric closed form, Smith 1961), ascending.
-__device__ void sym3_eigvals(const double a[6], double out[3])
+// Eigenvalues of a symmetric 3x3 matrix (trigonometric closed form, Smith
+// 1961), ascending.  In FP32 (FP64 transcendental functions are long
+// sequences on the scarce FP64 pipe): the matrix is shifted by its mean
+// eigenvalue and scaled by the spread p before the closed form, so the
+// result keeps FP32 relative accuracy in p.
+__device__ void sym3_eigvals(const double ad[6], double out[3])
 {
     // a: xx, yy, zz, xy, xz, yz
-    const double p1 = a[3] * a[3] + a[4] * a[4] + a[5] * a[5];
-    const double q = (a[0] + a[1] + a[2]) / 3.0;
-    if (p1 <= 1e-300 * (1.0 + q * q)) {
-        double e[3] = {a[0], a[1], a[2]};
-        for (int i = 0; i < 3; ++i)
-            for (int j = i + 1; j < 3; ++j)
-                if (e[j] < e[i]) { const double t = e[i]; e[i] = e[j]; e[j] = t; }
-        out[0] = e[0]; out[1] = e[1]; out[2] = e[2];
+    const double qd = (ad[0] + ad[1] + ad[2]) / 3.0;
+    const float a0 = (float)(ad[0] - qd), a1 = (float)(ad[1] - qd), a2 = (float)(ad[2] - qd);
+    const float a3 = (float)ad[3], a4 = (float)ad[4], a5 = (float)ad[5];
+    const float p1 = a3 * a3 + a4 * a4 + a5 * a5;
+    const float p2 = a0 * a0 + a1 * a1 + a2 * a2 + 2.0f * p1;
+    if (!(p2 > 0.0f)) {
+        out[0] = out[1] = out[2] = qd;
         return;
     }
-    const double p2 = (a[0] - q) * (a[0] - q) + (a[1] - q) * (a[1] - q) + (a[2] - q) * (a[2] - q) + 2.0 * p1;
-    const double p = sqrt(p2 / 6.0);
-    const double b0 = (a[0] - q) / p, b1 = (a[1] - q) / p, b2 = (a[2] - q) / p;
-    const double b3 = a[3] / p, b4 = a[4] / p, b5 = a[5] / p;
-    const double detb = b0 * (b1 * b2 - b5 * b5) - b3 * (b3 * b2 - b5 * b4) + b4 * (b3 * b5 - b1 * b4);
-    double rr = detb / 2.0;
-    rr = rr <= -1.0 ? -1.0 : (rr >= 1.0 ? 1.0 : rr);
-    const double phi = acos(rr) / 3.0;
-    const double e1 = q + 2.0 * p * cos(phi);
-    const double e3 = q + 2.0 * p * cos(phi + 2.0943951023931954923);
-    const double e2 = 3.0 * q - e1 - e3;
-    out[0] = e3; out[1] = e2; out[2] = e1;
+    if (p1 <= 1e-30f * p2) {
+        float e[3] = {a0, a1, a2};
+        for (int i = 0; i < 3; ++i)
+            for (int j = i + 1; j < 3; ++j)
+                if (e[j] < e[i]) { const float t = e[i]; e[i] = e[j]; e[j] = t; }
+        out[0] = qd + e[0]; out[1] = qd + e[1]; out[2] = qd + e[2];
+        return;
+    }
+    const float p = sqrtf(p2 / 6.0f), ip = 1.0f / p;
+    const float b0 = a0 * ip, b1 = a1 * ip, b2 = a2 * ip, b3 = a3 * ip, b4 = a4 * ip, b5 = a5 * ip;
+    const float detb = b0 * (b1 * b2 - b5 * b5) - b3 * (b3 * b2 - b5 * b4) + b4 * (b3 * b5 - b1 * b4);
+    const float rr = fminf(fmaxf(0.5f * detb, -1.0f), 1.0f);
+    const float phi = acosf(rr) / 3.0f;
+    const float e1 = 2.0f * p * cosf(phi);
+    const float e3 = 2.0f * p * cosf(phi + 2.09439510f);
+    const float e2 = -e1 - e3;
+    out[0] = qd + e3; out[1] = qd + e2; out[2] = qd + e1;
 }
 
 struct feat_args {
@@ -129,30 +132,62 @@ constexpr int FS_N = 25;
 // Blocks (p, chunk): members and bonds of platelet p strided over the chunks
 // of the y grid dimension; block sums go to the platelet's accumulators by
 // FP64 atomics, the largest bond strain by an integer max on float bits.
+// FP32 pair accumulator (hi, lo): Knuth's TwoSum keeps the rounding error
+// of every addition, the fma residual that of every product.
+struct ffacc {
+    float hi, lo;
+    __device__ void add(float x)
+    {
+        const float s = __fadd_rn(hi, x);
+        const float bb = __fsub_rn(s, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb)));
+        hi = s;
+    }
+    __device__ void add_prod(float p, float q)
+    {
+        const float m = __fmul_rn(p, q);
+        add(m);
+        lo = __fadd_rn(lo, fmaf(p, q, -m));
+    }
+};
+
+// Separation along one axis in FP32 (the correctly rounded difference of two
+// FP32 coordinates) with the periodic image.
+__device__ __forceinline__ float img32(float d, float L, bool periodic)
+{
+    if (periodic) {
+        if (d > 0.5f * L) d -= L;
+        else if (d < -0.5f * L) d += L;
+    }
+    return d;
+}
+
 __global__ void __launch_bounds__(FT_TPB) k_feat_sums(feat_args a, double *sums, unsigned *strain)
 {
     // FP64 is scarce on this part: a thread sums its few members' position
     // and velocity terms in FP32 (each term rounded once, |r| < half the
-    // box), the force moments in FP64; the block and platelet sums are FP64
-    __shared__ double sh[5][FT_TPB];
+    // box) and the force moments, whose terms cancel, in FP32 pairs with
+    // exact products; warps reduce in FP32 pairs, blocks in FP64
+    __shared__ double sh[FT_TPB / 32][FS_N];
     const int p = blockIdx.x;
     const int b = a.plt_off[p], e = a.plt_off[p + 1];
     const bool py = !a.geom.walls;
     const float4 ref = a.x32[a.pos_of_id[a.plt_ids[b]]];
+    const float Lf[3] = {(float)a.L[0], (float)a.L[1], (float)a.L[2]};
     float ta[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) ta[q] = 0.0f;
-    double tb[9];
+    ffacc tb[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) tb[q] = 0.0;
+    for (int q = 0; q < 9; ++q) tb[q] = ffacc{0.0f, 0.0f};
     const int stride = gridDim.y * FT_TPB;
     for (int m = b + blockIdx.y * FT_TPB + threadIdx.x; m < e; m += stride) {
         const int k = a.pos_of_id[a.plt_ids[m]];
         const float4 xk = a.x32[k];
         const float4 vk = vel_at(a, k);
-        const float rx = (float)img64((double)xk.x - ref.x, a.L[0], true);
-        const float ry = (float)img64((double)xk.y - ref.y, a.L[1], py);
-        const float rz = (float)img64((double)xk.z - ref.z, a.L[2], true);
+        const float rx = img32(xk.x - ref.x, Lf[0], true);
+        const float ry = img32(xk.y - ref.y, Lf[1], py);
+        const float rz = img32(xk.z - ref.z, Lf[2], true);
         float fx = 0.f, fy = 0.f, fz = 0.f;
         if (a.f0) { const float4 q = a.f0[k]; fx += q.x; fy += q.y; fz += q.z; fx += a.g_body; }
         if (a.f1) { const float4 q = a.f1[k]; fx += q.x; fy += q.y; fz += q.z; }
@@ -162,40 +197,46 @@ __global__ void __launch_bounds__(FT_TPB) k_feat_sums(feat_args a, double *sums,
         ta[4] += vk.x; ta[5] += vk.y; ta[6] += vk.z;
         ta[7] += ry * vk.z - rz * vk.y; ta[8] += rz * vk.x - rx * vk.z; ta[9] += rx * vk.y - ry * vk.x;
         ta[10] += rx * rx; ta[11] += ry * ry; ta[12] += rz * rz; ta[13] += rx * ry; ta[14] += rx * rz; ta[15] += ry * rz;
-        const double dx = rx, dy = ry, dz = rz, gx = fx, gy = fy, gz = fz;
-        tb[0] += gx; tb[1] += gy; tb[2] += gz;
-        tb[3] += dx * gx; tb[4] += dy * gy; tb[5] += dz * gz;
-        tb[6] += 0.5 * (dx * gy + gx * dy); tb[7] += 0.5 * (dx * gz + gx * dz); tb[8] += 0.5 * (dy * gz + gy * dz);
+        tb[0].add(fx); tb[1].add(fy); tb[2].add(fz);
+        tb[3].add_prod(rx, fx); tb[4].add_prod(ry, fy); tb[5].add_prod(rz, fz);
+        // (r_a F_b + F_a r_b) / 2, halved at the end
+        tb[6].add_prod(rx, fy); tb[6].add_prod(fx, ry);
+        tb[7].add_prod(rx, fz); tb[7].add_prod(fx, rz);
+        tb[8].add_prod(ry, fz); tb[8].add_prod(fy, rz);
     }
     float smax = 0.f;
     for (int bb = a.bond_off[p] + blockIdx.y * FT_TPB + threadIdx.x; bb < a.bond_off[p + 1]; bb += stride) {
         const float4 xi = a.x32[a.bond_ij[2 * bb]], xj = a.x32[a.bond_ij[2 * bb + 1]];
         // the largest strain needs no FP64 arithmetic: the exact separation rounded to FP32
-        const float dx = (float)img64((double)xi.x - xj.x, a.L[0], true);
-        const float dy = (float)img64((double)xi.y - xj.y, a.L[1], py);
-        const float dz = (float)img64((double)xi.z - xj.z, a.L[2], true);
+        const float dx = img32(xi.x - xj.x, Lf[0], true);
+        const float dy = img32(xi.y - xj.y, Lf[1], py);
+        const float dz = img32(xi.z - xj.z, Lf[2], true);
         const float r0 = a.bond_r0[bb];
         smax = fmaxf(smax, fabsf(sqrtf(dx * dx + dy * dy + dz * dz) - r0) / r0);
     }
     smax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(smax)));   // smax >= 0
     if ((threadIdx.x & 31) == 0 && smax > 0.f) atomicMax(&strain[p], __float_as_uint(smax));
-    // block sums in FP64, five quantities at a time (a tree in shared memory)
+    // warp sums in FP32 pairs (shuffles), one FP64 value per warp and word,
+    // the block's warps in FP64, one atomic per word
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int g = 0; g < FS_N / 5; ++g) {
+    for (int w = 0; w < FS_N; ++w) {
+        ffacc v = w < 16 ? ffacc{ta[w < 16 ? w : 0], 0.0f} : tb[w >= 16 ? w - 16 : 0];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            const int w = 5 * g + q;
-            sh[q][threadIdx.x] = w < 16 ? (double)ta[w < 16 ? w : 0] : tb[w >= 16 ? w - 16 : 0];
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, v.hi, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, v.lo, o);
+            v.add(oh);
+            v.lo = __fadd_rn(v.lo, ol);
         }
-        __syncthreads();
-        for (int st = FT_TPB / 2; st > 0; st >>= 1) {
-            if (threadIdx.x < st)
+        if (lane == 0) sh[wid][w] = ((double)v.hi + (double)v.lo) * (w >= 22 ? 0.5 : 1.0);
+    }
+    __syncthreads();
+    if (threadIdx.x < FS_N) {
+        double v = 0.0;
 #pragma unroll
-                for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + st];
-            __syncthreads();
-        }
-        if (threadIdx.x < 5) atomicAdd(&sums[(int64_t)p * FS_N + 5 * g + threadIdx.x], sh[threadIdx.x][0]);
-        __syncthreads();
+        for (int q = 0; q < FT_TPB / 32; ++q) v += sh[q][threadIdx.x];
+        atomicAdd(&sums[(int64_t)p * FS_N + threadIdx.x], v);
     }
 }
 
@@ -228,13 +269,6 @@ __global__ void __launch_bounds__(FT_TPB) k_feat_final(feat_args a, const double
     const float Lf[3] = {(float)a.L[0], (float)a.L[1], (float)a.L[2]};
     const float r2f = (float)a.flow_r2;
     const float band = 1e-5f * (fmaxf(Lf[0], fmaxf(Lf[1], Lf[2])) + 1.0f) * (1.0f + r2f);
-    auto img32 = [](float d, float L, bool periodic) {
-        if (periodic) {
-            if (d > 0.5f * L) d -= L;
-            else if (d < -0.5f * L) d += L;
-        }
-        return d;
-    };
     double fs = 0.0, fn = 0.0;
     for (int q = threadIdx.x; q < ncand; q += FT_TPB) {
         const int ox = q % span[0], oy = (q / span[0]) % span[1], oz = q / (span[0] * span[1]);

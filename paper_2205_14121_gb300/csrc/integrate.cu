@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
         if (kick) {
             float ax = 0.f, ay = 0.f, az = 0.f;
             for (int l = 0; l < a.nf; ++l) {
-                if (a.h[l] == 0.0f) continue;
+                if (a.h[l] == 0.0f || (l == 2 && t < 0)) continue;   // platelet-level forces act on platelets only
                 const float4 fl = a.f[l][k];
                 if (fl.x == 0.0f && fl.y == 0.0f && fl.z == 0.0f) zero_seen |= 1u << l;
                 ax += a.h[l] * fl.x; ay += a.h[l] * fl.y; az += a.h[l] * fl.z;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
         a.v[k] = vv;
     }
     for (int l = 0; l < a.nf; ++l)
-        if ((a.zero_levels & ~zero_seen) & (1u << l)) a.f[l][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (((a.zero_levels & ~zero_seen) & (1u << l)) && !(l == 2 && t < 0)) a.f[l][k] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Set the device time index (n, c) and the time n dt + c dt_m + q dt_p;
