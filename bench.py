@@ -209,14 +209,14 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload_name):
+def ncu_traffic(workload_name, skin):
     """DRAM bytes per launch of the fluid DPD kernel from a committed ncu
-    summary, if it was taken on the current kernel source."""
+    summary, if it was taken on the current kernel source and list skin."""
     path = os.path.join(ROOT, "profiles", "k_dpd_traffic.json")
     try:
         d = json.load(open(path))
         e = d.get(workload_name)
-        if e and e.get("source_hash") == kernel_source_hash():
+        if e and e.get("source_hash") == kernel_source_hash() and e.get("skin") == skin:
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -361,7 +361,7 @@ def main():
     bytes_per_particle = 16 + 16 + 4 * n_half + 16      # x32 + v + list + f
     achieved = n * bytes_per_particle / (fl_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
-    traffic = ncu_traffic(args.workload)
+    traffic = ncu_traffic(args.workload, wl["skin"])
 
     # ---- end to end through the C ABI with host buffers ------------------
     e2e = None
@@ -398,9 +398,10 @@ def main():
     # ---- comparison arms on the same system ------------------------------
     compare = {}
     if args.workload == "channel" and not args.no_compare:
-        # each arm at the Verlet skin that suits it best on this system (a sweep
-        # of 0.2-0.5: fine-step STS rebuilds rarely and prefers the shorter
-        # lists of skin 0.2; the dt = 0.01 arms are flat between 0.3 and 0.5)
+        # each arm at the Verlet skin that suits it (a sweep of 0.15-0.6:
+        # fine-step STS rebuilds rarely and prefers the shorter lists of skin
+        # 0.2; the dt = 0.01 arms run 2-3% faster at 0.5 than at 0.3, but the
+        # end-to-end step, which rebuilds every call, 9% slower: 0.3 is kept)
         arms = [("fine_sts", 0.001, 0.2, lambda h, k: h.mts_step(k, direct=args.direct)),
                 ("respa_k10", 0.01, wl["skin"], lambda h, k: h.mts_step(k, mode=M.MD_MODE_RESPA, k_m=1, k_p=10,
                                                                         direct=args.direct))]

@@ -94,7 +94,7 @@ typedef struct md_config {
     double   k_bond;                                       /* Eq. 2 bonds        */
     uint64_t seed;            /* key of the Philox4x32-10 pair noise              */
     int32_t  cap_fluid, cap_iface, cap_lj, cap_morse; /* list capacities per row;
-                                                   0: 64, 96, 1024, 256        */
+                                                   0: 96, 96, 1024, 256        */
 } md_config;
 
 /* Fill *cfg with the defaults above for n particles in box (no platelets). */

@@ -78,7 +78,10 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
     s.n_plt = c.n_plt_particles;
     s.n_rec = c.n_receptors;
     s.nb = c.n_bonds;
-    s.cap[MD_LIST_FLUID] = default_cap(c.cap_fluid, 64);
+    // a half row holds up to the full neighbour count (a particle early in the
+    // cell order): 27.6 on average at rho = 3 within 1.3, beyond 64 in the
+    // far tail of the density fluctuations of a few million particles
+    s.cap[MD_LIST_FLUID] = default_cap(c.cap_fluid, 96);
     s.cap[MD_LIST_IFACE] = default_cap(c.cap_iface, 96);
     s.cap[MD_LIST_LJ] = default_cap(c.cap_lj, 1024);   // shells in contact: hundreds of partners
     s.cap[MD_LIST_MORSE] = default_cap(c.cap_morse, 256);

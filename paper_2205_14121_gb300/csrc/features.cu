@@ -167,8 +167,8 @@ __global__ void __launch_bounds__(FT_TPB) k_feat_sums(feat_args a, double *sums,
     // FP64 is scarce on this part: a thread sums its few members' position
     // and velocity terms in FP32 (each term rounded once, |r| < half the
     // box) and the force moments, whose terms cancel, in FP32 pairs with
-    // exact products; warps reduce in FP32 pairs, blocks in FP64
-    __shared__ double sh[FT_TPB / 32][FS_N];
+    // exact products; warps and blocks reduce in FP32 pairs, platelets in FP64
+    __shared__ float2 sh[FT_TPB / 32][FS_N];
     const int p = blockIdx.x;
     const int b = a.plt_off[p], e = a.plt_off[p + 1];
     const bool py = !a.geom.walls;
@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(FT_TPB) k_feat_sums(feat_args a, double *sums,
     }
     smax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(smax)));   // smax >= 0
     if ((threadIdx.x & 31) == 0 && smax > 0.f) atomicMax(&strain[p], __float_as_uint(smax));
-    // warp sums in FP32 pairs (shuffles), one FP64 value per warp and word,
-    // the block's warps in FP64, one atomic per word
+    // warp sums and then the block's warps in FP32 pairs, one FP64 value
+    // and atomic per block and word
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int w = 0; w < FS_N; ++w) {
@@ -229,14 +229,19 @@ __global__ void __launch_bounds__(FT_TPB) k_feat_sums(feat_args a, double *sums,
             v.add(oh);
             v.lo = __fadd_rn(v.lo, ol);
         }
-        if (lane == 0) sh[wid][w] = ((double)v.hi + (double)v.lo) * (w >= 22 ? 0.5 : 1.0);
+        if (lane == 0) sh[wid][w] = make_float2(v.hi, v.lo);
     }
     __syncthreads();
     if (threadIdx.x < FS_N) {
-        double v = 0.0;
+        ffacc v = {0.0f, 0.0f};
 #pragma unroll
-        for (int q = 0; q < FT_TPB / 32; ++q) v += sh[q][threadIdx.x];
-        atomicAdd(&sums[(int64_t)p * FS_N + threadIdx.x], v);
+        for (int q = 0; q < FT_TPB / 32; ++q) {
+            const float2 t = sh[q][threadIdx.x];
+            v.add(t.x);
+            v.lo = __fadd_rn(v.lo, t.y);
+        }
+        const double d = ((double)v.hi + (double)v.lo) * (threadIdx.x >= 22 ? 0.5 : 1.0);
+        atomicAdd(&sums[(int64_t)p * FS_N + threadIdx.x], d);
     }
 }
 
