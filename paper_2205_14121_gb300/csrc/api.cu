@@ -109,6 +109,9 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
         s.altf[l] = l < nf ? cv.take<float4>(n) : nullptr;
     }
     s.xb = cv.take<float4>(n);
+    s.fast_max = n / 64 > 4096 ? n / 64 : 4096;
+    s.fast_idx = cv.take<int32_t>(s.fast_max);
+    s.fast_flag = cv.take<uint32_t>(n);
     s.tag_s = cv.take<int32_t>(n);
     s.cellid = cv.take<int32_t>(n);
     s.slot = cv.take<int32_t>(n);
@@ -412,8 +415,13 @@ int enqueue_forces(md_system *s, unsigned levels)
         const unsigned bit = 1u << l;
         if (!(levels & bit) || (l > 0 && s->n_plt == 0)) continue;
         prof_begin(s, cls[l]);
-        CK(launch_forces(s, bit, out, false), "forces");
+        CK(launch_forces(s, bit, out, false, false), "forces");
         prof_end(s);
+        if (l < 2) {   // the fast-particle pass of a DPD level, timed apart
+            prof_begin(s, MD_PROF_OTHER);
+            CK(launch_fast_pairs(s, bit, out, false), "fast pairs");
+            prof_end(s);
+        }
     }
     return MD_OK;
 }
@@ -847,6 +855,7 @@ static int load_xv(md_system *s, const double *x, const double *v, int64_t step0
     CK(cudaGetLastError(), "import v");
     for (int l = 0; l < 3; ++l)
         if (s->f[l]) CK(cudaMemsetAsync(s->f[l], 0, sizeof(float4) * n, st), "zero f");
+    CK(cudaMemsetAsync(s->fast_flag, 0, sizeof(uint32_t) * n, st), "zero fast flags");
     md_dstate *h = s->h_ds;
     memset(h, 0, sizeof *h);
     h->step = step0;
@@ -856,6 +865,7 @@ static int load_xv(md_system *s, const double *x, const double *v, int64_t step0
     h->le_offset = host_le_offset(s, h->time);
     h->le_offset_f = (float)h->le_offset;
     h->le_build_f = h->le_offset_f;
+    h->fast_stamp = 1;          // fast_flag starts at 0: no particle listed
     CK(cudaMemcpyAsync(s->ds, h, sizeof(md_dstate), cudaMemcpyHostToDevice, st), "upload dstate");
     CK(cudaMemsetAsync(s->ctl, 0, sizeof(int32_t) * CTL_WORDS, st), "reset ctl");
     // empty rows until the first build (the workspace holds stale contents)

@@ -245,6 +245,165 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
     if (VIR) flush_virial(a.vir, w);
 }
 
+// K3 for the fast plasma particles: those that moved beyond skin/2 (but
+// within the skin) since the list build, listed by the kick-drift instead of
+// triggering a rebuild.  A pair of two particles within skin/2 of their build
+// positions that came within rc was within rc + skin at the build, so it is
+// in the list; a pair with a fast particle may not be.  For every fast
+// particle i this pass scans the cells within rc + skin (its partners, at most
+// a skin from their build cells), keeps the partners now within rc, and
+// evaluates those that the list lacks -- decided by the builder's predicate
+// on the build positions, row particle first (plasma list: the lower storage
+// index; interface list: the platelet particle), so no pair is counted twice.
+// Two fast particles meet once, from the lower index.  Eq. 1 as in k_dpd.
+struct fast_args {
+    const int32_t *fast_idx;
+    const uint32_t *fast_flag;
+    const int32_t *ctl;
+    int64_t fast_max;
+    md_grid g;                 // cells of the candidates: main grid, or the platelet sub-grid
+    const int32_t *members;    // null: main grid (storage order); else platelet rows
+    const float4 *xb;          // positions at the build
+    float R;                   // scan reach
+    float cut2;                // the list's cut-off squared (the builder's predicate)
+};
+
+// One warp per fast particle: lane t takes (y, z) stencil row t of the cells
+// within reach (at most 25 rows for cells at least half the reach wide) and
+// its one or two runs of members, then the warp tests the concatenated
+// candidates 32 at a time; a few dependent loads per particle instead of one
+// per candidate.
+template <bool VIR, bool IFACE>
+__global__ void __launch_bounds__(128) k_dpd_fast(pair_args a, fast_args fa)
+{
+    const int64_t nf = min((int64_t)fa.ctl[CTL_NFAST], fa.fast_max);
+    const float delta = a.ds->le_offset_f, dbuild = a.ds->le_build_f;
+    const uint32_t stamp = a.ds->fast_stamp;
+    const philox_pre pq = philox_prepare((uint32_t)a.ds->step, (uint32_t)a.ds->sub, a.key);
+    const int lane = threadIdx.x & 31;
+    const md_grid &g = fa.g;
+    vir6 w = {0, 0, 0, 0, 0, 0};
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = warp0; q < nf; q += nwarps) {
+        const int32_t i = fa.fast_idx[q];
+        const float4 xi = a.x32[i], vi = a.v[i], xbi = fa.xb[i];
+        const uint32_t idi = id_of(xi);
+        int zlo, zhi, ylo, yhi;
+        cell_span(xi.z, g.lo[2], fa.R, g.inv_h[2], g.nc[2], zlo, zhi);
+        cell_span(xi.y, g.lo[1], fa.R, g.inv_h[1], g.nc[1], ylo, yhi);
+        if (a.geom.walls) {
+            ylo = max(ylo, 0);
+            yhi = min(yhi, g.nc[1] - 1);
+        }
+        const int ny = max(yhi - ylo + 1, 0), nrows = ny * max(zhi - zlo + 1, 0);
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        for (int r0 = 0; r0 < nrows; r0 += 32) {
+            // this lane's stencil row: up to two runs [sb0, se0), [sb1, se1)
+            int32_t sb0 = 0, se0 = 0, sb1 = 0, se1 = 0;
+            const int t = r0 + lane;
+            if (t < nrows) {
+                const int cz = zlo + t / ny, cy = ylo + t % ny;
+                const int wz = wrapc(cz, g.nc[2]);
+                int wy = cy;
+                float sx = 0.0f;
+                if (!a.geom.walls) {
+                    if (cy < 0) {
+                        wy = wrapc(cy, g.nc[1]);
+                        if (a.geom.le) sx = delta;
+                    } else if (cy >= g.nc[1]) {
+                        wy = wrapc(cy, g.nc[1]);
+                        if (a.geom.le) sx = -delta;
+                    }
+                }
+                const float gz = slab_gap(xi.z, g.lo[2] + cz * g.h[2], g.h[2]);
+                const float gy = slab_gap(xi.y, g.lo[1] + cy * g.h[1], g.h[1]);
+                const float rem = fa.R * fa.R - (gy * gy + gz * gz);
+                if (rem >= 0.0f) {
+                    const int nx = g.nc[0];
+                    int xlo, xhi;
+                    cell_span(xi.x + sx, g.lo[0], sqrtf(rem) + 1e-4f, g.inv_h[0], nx, xlo, xhi);
+                    int a0 = xlo, b0 = xhi, a1 = 0, b1 = -1;
+                    if (xhi < 0) { a0 += nx; b0 += nx; }
+                    else if (xlo >= nx) { a0 -= nx; b0 -= nx; }
+                    else if (xlo < 0) { a0 = xlo + nx; b0 = nx - 1; b1 = xhi; }
+                    else if (xhi >= nx) { b0 = nx - 1; b1 = xhi - nx; }
+                    const int rowc = (wz * g.nc[1] + wy) * nx;
+                    sb0 = g.start[rowc + a0];
+                    se0 = g.start[rowc + b0 + 1];
+                    if (a1 <= b1) {
+                        sb1 = g.start[rowc + a1];
+                        se1 = g.start[rowc + b1 + 1];
+                    }
+                }
+            }
+            const int len0 = se0 - sb0, len = len0 + (se1 - sb1);
+            int pre = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, pre, o);
+                if (lane >= o) pre += u;
+            }
+            const int total = __shfl_sync(0xffffffffu, pre, 31);
+            pre -= len;
+            for (int base = 0; base < total; base += 32) {
+                const int f = base + lane;
+                int owner = 0;     // the last lane whose prefix is <= f
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1) {
+                    const int pv = __shfl_sync(0xffffffffu, pre, owner + st);
+                    if (pv <= f) owner += st;
+                }
+                const int k = f - __shfl_sync(0xffffffffu, pre, owner);
+                const int l0 = __shfl_sync(0xffffffffu, len0, owner);
+                const int32_t b_0 = __shfl_sync(0xffffffffu, sb0, owner), b_1 = __shfl_sync(0xffffffffu, sb1, owner);
+                if (f >= total) continue;
+                const int32_t sm = k < l0 ? b_0 + k : b_1 + (k - l0);
+                const int32_t j = fa.members ? fa.members[sm] : sm;
+                if (j == i) continue;
+                const float4 xj = a.x32[j];
+                if (IFACE) {
+                    if (class_of(xj) != CLS_PLT) continue;
+                } else {
+                    if (class_of(xj) == CLS_PLT) continue;
+                    if (fa.fast_flag[j] == stamp && j < i) continue;
+                }
+                float dx, dy, dz, vsh;
+                min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < a.rc2) || r2 == 0.0f) continue;
+                float ex, ey, ez, es;
+                const float4 xbj = fa.xb[j];
+                if (IFACE || j < i) min_image_f32(a.geom, dbuild, xbj, xbi, ex, ey, ez, es);
+                else min_image_f32(a.geom, dbuild, xbi, xbj, ex, ey, ez, es);
+                if (r2_f32(ex, ey, ez) < fa.cut2) continue;       // in the list
+                const float4 vj = a.v[j];
+                const bool wall = tag_of(vj) == MD_TAG_WALL;
+                const float aij = wall ? a.a_wall : a.a_same;
+                const float inv_r = rsqrtf(r2);
+                const float wr = 1.0f - r2 * inv_r * a.inv_rc;
+                const float nx = dx * inv_r, ny_ = dy * inv_r, nz = dz * inv_r;
+                const float edv = nx * (vi.x - vj.x - vsh) + ny_ * (vi.y - vj.y) + nz * (vi.z - vj.z);
+                const float zeta = pair_zeta_pre(idi, id_of(xj), pq);
+                const float fc = aij * wr;
+                const float fp = fc - a.gamma * wr * wr * edv + a.sig_isdt * wr * zeta;
+                const float px = fp * nx, py = fp * ny_, pz = fp * nz;
+                fx += px; fy += py; fz += pz;
+                scatter(a.f, j, -px, -py, -pz);
+                if (VIR) w.add(dx, dy, dz, fc * inv_r);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if (lane == 0 && (fx != 0.f || fy != 0.f || fz != 0.f)) scatter(a.f, i, fx, fy, fz);
+    }
+    if (VIR) flush_virial(a.vir, w);
+}
+
 // K5a: LJ 12-6 (Eq. 2), shifted potential: the force is unshifted.
 template <bool VIR>
 __global__ void __launch_bounds__(MSM_TPB) k_lj(pair_args a)
@@ -356,7 +515,70 @@ inline unsigned blocks_for(int64_t n) { return (unsigned)(n > 0 ? (n + MSM_TPB -
 
 // Forces of the levels in level_mask, accumulated into out[level] (the
 // buffers must be zero or hold partial sums of the same evaluation).
-cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3], bool virial)
+constexpr int FAST_BLOCKS = 608;   // warps grid-striding over the fast list (four blocks of 4 warps per SM)
+
+static fast_args fast_for(md_system *s, const md_grid &g, const int32_t *members, float cut2)
+{
+    fast_args fa;
+    fa.fast_idx = s->fast_idx;
+    fa.fast_flag = s->fast_flag;
+    fa.ctl = s->ctl;
+    fa.fast_max = s->fast_max;
+    fa.g = g;
+    fa.members = members;
+    fa.xb = s->xb;
+    fa.R = (float)(s->cfg.rc + s->cfg.skin) * (1.0f + 1e-5f);
+    fa.cut2 = cut2;
+    return fa;
+}
+
+// pair_args of the DPD levels (the fields the pair kernels read)
+static pair_args dpd_args(md_system *s)
+{
+    const md_config &c = s->cfg;
+    pair_args a;
+    a.x32 = s->x32;
+    a.v = s->v;
+    a.geom = s->geom;
+    a.ds = s->ds;
+    a.key = make_uint2((uint32_t)(c.seed & 0xffffffffu), (uint32_t)(c.seed >> 32));
+    a.gamma = (float)c.gamma;
+    a.rc2 = (float)(c.rc * c.rc);
+    a.inv_rc = (float)(1.0 / c.rc);
+    a.vir = s->vir_acc;
+    a.tag = s->tag_s;
+    return a;
+}
+
+cudaError_t launch_fast_pairs(md_system *s, unsigned level_mask, float4 *const out[3], bool virial)
+{
+    const md_config &c = s->cfg;
+    pair_args a = dpd_args(s);
+    if (level_mask & MD_LEVEL_FLUID) {
+        a.f = out[0];
+        a.a_same = (float)c.a_ff;
+        a.a_wall = (float)c.a_fw;
+        a.sig_isdt = (float)(c.sigma / sqrt(c.dt));
+        const fast_args fa = fast_for(s, s->gmain, nullptr, s->cut2[MD_LIST_FLUID]);
+        if (virial) k_dpd_fast<true, false><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
+        else k_dpd_fast<false, false><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
+        MSM_COUNT(s, 1);
+    }
+    if ((level_mask & MD_LEVEL_IFACE) && s->n_plt > 0) {
+        const int km = s->cfg_k_m > 0 ? s->cfg_k_m : 1;
+        a.f = out[1];
+        a.a_same = (float)c.a_fp;
+        a.a_wall = (float)c.a_fp;
+        a.sig_isdt = (float)(c.sigma / sqrt(c.dt / km));
+        const fast_args fa = fast_for(s, s->gplt, s->plt_sorted, s->cut2[MD_LIST_IFACE]);
+        if (virial) k_dpd_fast<true, true><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
+        else k_dpd_fast<false, true><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
+        MSM_COUNT(s, 1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3], bool virial, bool with_fast)
 {
     const md_config &c = s->cfg;
     pair_args a;
@@ -442,5 +664,8 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
             else k_morse<false><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
         }
     }
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && with_fast && (level_mask & (MD_LEVEL_FLUID | MD_LEVEL_IFACE)))
+        e = launch_fast_pairs(s, level_mask, out, virial);
+    return e;
 }

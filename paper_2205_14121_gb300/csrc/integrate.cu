@@ -38,6 +38,9 @@ struct kd_args {
     const md_dstate *ds;
     int32_t *ctl;
     int sparse_level;      // >= 0: a pure kick with this level only (most forces zero)
+    int32_t *fast_idx;     // plasma beyond skin/2 and within the skin: listed here
+    uint32_t *fast_flag;
+    int64_t fast_max;
 };
 
 __device__ __forceinline__ bool selected(int which, int32_t t)
@@ -139,7 +142,20 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
                 dd = fminf(dd, a.geom.L[0] - dd);
                 thr = 0.5f * (a.skin - dd) - mg;
             }
-            if (!(d2 <= thr * thr) || thr <= 0.0f) a.ctl[CTL_REBUILD] = 1;
+            if (!(d2 <= thr * thr) || thr <= 0.0f) {
+                // plasma up to twice the threshold keeps the lists: its pairs
+                // that they lack are evaluated by the fast-particle pass (every
+                // partner within rc is then in a list or found there)
+                int q = -1;
+                if (t == MD_TAG_FLUID && thr > 0.0f && d2 <= 4.0f * thr * thr) {
+                    q = atomicAdd(&a.ctl[CTL_NFAST], 1);
+                    if (q < a.fast_max) {
+                        a.fast_idx[q] = (int32_t)k;
+                        a.fast_flag[k] = a.ds->fast_stamp;
+                    }
+                }
+                if (q < 0 || q >= a.fast_max) a.ctl[CTL_REBUILD] = 1;
+            }
             const bool bad = !(fabsf(xf) + fabsf(yf) + fabsf(zf) < 1e30f) ||
                              !(fabsf(vv.x) + fabsf(vv.y) + fabsf(vv.z) < 1e30f) ||
                              (a.geom.walls && (yf < -(float)a.wall || yf > a.geom.L[1] + (float)a.wall));
@@ -210,6 +226,13 @@ __global__ void k_cond_rebuild(const int32_t *ctl, cudaGraphConditionalHandle h)
 
 __global__ void k_set_loop(md_dstate *ds, int64_t n) { ds->steps_left = n; }
 
+// Before a drift of the plasma: an empty fast list under a new stamp.
+__global__ void k_fast_reset(md_dstate *ds, int32_t *ctl)
+{
+    ds->fast_stamp += 1;
+    ctl[CTL_NFAST] = 0;
+}
+
 __global__ void k_zero_f4(float4 *p, int64_t n)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -244,6 +267,9 @@ kd_args base_args(md_system *s)
     a.drift_which = -1;
     a.zero_levels = 0;
     a.sparse_level = -1;
+    a.fast_idx = s->fast_idx;
+    a.fast_flag = s->fast_flag;
+    a.fast_max = s->fast_max;
     return a;
 }
 
@@ -268,6 +294,10 @@ cudaError_t launch_kick_drift(md_system *s, const float h[3], int kick_which, do
         a.n = s->n_plt;
     }
     if (a.n <= 0) return cudaSuccess;
+    if (!plt_rows && (drift_which == DRIFT_ALL || drift_which == DRIFT_FLUID)) {
+        k_fast_reset<<<1, 1, 0, s->stream>>>(s->ds, s->ctl);
+        MSM_COUNT(s, 1);
+    }
     k_kick_drift<<<blocks_for(a.n), MSM_TPB, 0, s->stream>>>(a);
     MSM_COUNT(s, 1);
     return cudaGetLastError();

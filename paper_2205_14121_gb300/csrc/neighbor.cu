@@ -31,127 +31,6 @@
 
 namespace {
 
-// Periodic cell wrap; the integer division only runs for the few cells
-// outside the grid.
-__device__ __forceinline__ int wrapc(int c, int n)
-{
-    if (c >= 0 && c < n) return c;
-    c %= n;
-    return c < 0 ? c + n : c;
-}
-
-__device__ __forceinline__ int cell_index32(const md_grid &g, int cx, int cy, int cz)
-{
-    return (cz * g.nc[1] + cy) * g.nc[0] + cx;
-}
-
-// Cells [lo, hi] within reach R of coordinate x along one axis, clamped to
-// [-2, n+1] and to at most n cells, so that a non-finite or escaped position
-// (reported by the integrator's unstable flag) still gives a bounded scan.
-__device__ __forceinline__ void cell_span(float x, float lo0, float R, float inv_h, int n, int &lo, int &hi)
-{
-    lo = __float2int_rd((x - lo0 - R) * inv_h);
-    hi = __float2int_rd((x - lo0 + R) * inv_h);
-    lo = min(max(lo, -2), n + 1);
-    hi = min(max(hi, -2), n + 1);
-    if (hi - lo + 1 > n) hi = lo + n - 1;
-}
-
-// Distance from x to the slab [c0, c0 + h] along one axis, less a slack that
-// covers the rounding of the cell assignment (positions sit within a few ulp
-// of their cell's nominal bounds).
-__device__ __forceinline__ float slab_gap(float x, float c0, float h)
-{
-    const float gap = fmaxf(fmaxf(c0 - x, x - (c0 + h)), 0.0f);
-    return fmaxf(gap - 1e-4f, 0.0f);
-}
-
-// Emit (sb, se) for every non-empty run of member positions in the cells
-// within reach R of xi.  Cells are at least R/2 wide; each (y, z) row of
-// cells is one or two contiguous member runs, rows out of reach are skipped
-// and the x extent of a row is trimmed to the sphere of radius R.
-// Lees-Edwards rows that cross the y boundary are shifted by the image
-// offset.  half: skip cells with a lower index than xi's own cell, and in
-// that cell the members up to r.
-template <bool HALF, class E, class K>
-__device__ __forceinline__ void for_ranges(const md_grid &g, const md_geom &geom, float delta, float4 xi, float R,
-                                           int32_t r, E emit, K skip_cell)
-{
-    const int ox = cell_coord(g, 0, xi.x);
-    const int own_row = cell_coord(g, 2, xi.z) * g.nc[1] + cell_coord(g, 1, xi.y);
-    const float R2 = R * R;
-    const int nx = g.nc[0];
-    int zlo, zhi, ylo, yhi;
-    cell_span(xi.z, g.lo[2], R, g.inv_h[2], g.nc[2], zlo, zhi);
-    cell_span(xi.y, g.lo[1], R, g.inv_h[1], g.nc[1], ylo, yhi);
-    if (geom.walls) {
-        ylo = max(ylo, 0);
-        yhi = min(yhi, g.nc[1] - 1);
-    }
-    for (int cz = zlo; cz <= zhi; ++cz) {
-        const int wz = wrapc(cz, g.nc[2]);
-        const float gz = slab_gap(xi.z, g.lo[2] + cz * g.h[2], g.h[2]);
-        for (int cy = ylo; cy <= yhi; ++cy) {
-            int wy = cy;
-            float sx = 0.0f;
-            if (!geom.walls) {
-                if (cy < 0) {
-                    wy = wrapc(cy, g.nc[1]);
-                    if (geom.le) sx = delta;
-                } else if (cy >= g.nc[1]) {
-                    wy = wrapc(cy, g.nc[1]);
-                    if (geom.le) sx = -delta;
-                }
-            }
-            const int row = wz * g.nc[1] + wy;
-            if (HALF && row < own_row) continue;
-            const float gy = slab_gap(xi.y, g.lo[1] + cy * g.h[1], g.h[1]);
-            const float rem = R2 - (gy * gy + gz * gz);
-            if (rem < 0.0f) continue;
-            int xlo, xhi;
-            cell_span(xi.x + sx, g.lo[0], sqrtf(rem) + 1e-4f, g.inv_h[0], nx, xlo, xhi);
-            // the span as at most two runs of wrapped cell indices
-            int a0 = xlo, b0 = xhi, a1 = 0, b1 = -1;
-            if (xhi < 0) { a0 += nx; b0 += nx; }
-            else if (xlo >= nx) { a0 -= nx; b0 -= nx; }
-            else if (xlo < 0) { a0 = xlo + nx; b0 = nx - 1; a1 = 0; b1 = xhi; }
-            else if (xhi >= nx) { a0 = xlo; b0 = nx - 1; a1 = 0; b1 = xhi - nx; }
-            const int rowc = row * nx;
-            // one run of cells [a, b] of this row
-            auto run = [&](int a, int b) {
-                if (HALF && row == own_row) a = max(a, ox);
-                if (a > b) return;
-                // cells that cannot hold a partner are cut out of the run
-                while (a <= b && skip_cell(rowc + a)) ++a;
-                int bb = b;
-                while (bb >= a && skip_cell(rowc + bb)) --bb;
-                for (int c = a; c <= bb;) {
-                    int d = c;
-                    while (d < bb && !skip_cell(rowc + d + 1)) ++d;
-                    int32_t sb = g.start[rowc + c];
-                    const int32_t se = g.start[rowc + d + 1];
-                    if (HALF && row == own_row && sb <= r) sb = r + 1;
-                    if (sb < se) emit(sb, se);
-                    c = d + 1;
-                    while (c <= bb && skip_cell(rowc + c)) ++c;
-                }
-            };
-            run(a0, b0);
-            if (a1 <= b1) run(a1, b1);
-        }
-    }
-}
-
-// Visit (member position s, particle index) of every candidate of xi.
-template <bool HALF, class F, class K>
-__device__ __forceinline__ void for_candidates(const md_grid &g, const md_geom &geom, float delta, float4 xi,
-                                               float R, const int32_t *__restrict__ members, int32_t r, F fn, K skip)
-{
-    for_ranges<HALF>(g, geom, delta, xi, R, r, [&](int32_t sb, int32_t se) {
-        for (int32_t s = sb; s < se; ++s) fn(s, members ? members[s] : s);
-    }, skip);
-}
-
 struct build_args {
     int64_t n;
     int64_t rows;

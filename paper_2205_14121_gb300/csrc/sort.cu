@@ -245,6 +245,7 @@ __global__ void k_finish_build(int32_t *ctl, md_dstate *ds, const int32_t *gate)
     ds->n_builds += 1;
     ds->le_build_f = ds->le_offset_f;
     ctl[CTL_REBUILD] = 0;
+    ctl[CTL_NFAST] = 0;      // every particle at its build position
 }
 
 inline unsigned blocks_for(int64_t n, int tpb = MSM_TPB)

@@ -193,6 +193,46 @@ def test_wall_temperature_subtracts_local_flow(plt_wall_sys):
     assert stream > 0.01 * mob.sum()
 
 
+def test_fast_particles_keep_the_lists_and_every_pair(plt_wall_sys):
+    """Plasma that moved beyond skin/2 but within the skin keeps the lists:
+    40 plasma particles next to the shells are launched at speed 7 toward
+    their platelet's centre; after three STS steps they are 0.15-0.3 from their
+    build positions, no rebuild has run, and the forces of every level equal
+    the oracle's brute-force forces on the GPU's state -- the pairs the lists
+    lack (plasma and interface) come from the fast-particle pass."""
+    import paper_2205_14121_gb300 as M
+    s = plt_wall_sys
+    x0, v0 = f32(s.x), f32(s.v)
+    plt = np.flatnonzero(s.tag >= 0)
+    plasma = np.flatnonzero(s.tag == synth.TAG_FLUID)
+    rng = np.random.default_rng(31)
+    d = np.sqrt(((x0[plasma, None, :] - x0[None, plt[::7], :]) ** 2).sum(-1)).min(1)
+    near = plasma[(d > 1.2) & (d < 2.0)]
+    pick = rng.choice(near, 40, replace=False)
+    for k in pick:
+        p = s.tag[plt[np.argmin(((x0[plt] - x0[k]) ** 2).sum(1))]] & ~(1 << 30)
+        c = x0[s.tag == p].mean(0) if (s.tag == p).any() else x0[plt].mean(0)
+        u = c - x0[k]
+        v0[k] = 7.0 * u / np.linalg.norm(u)
+    g = make_gpu(s, x=x0, v=v0, step0=3)
+    g.mts_step(3)
+    o = g.observables()
+    x, v, x32 = g.read_particles()
+    dx = x - x0
+    L = np.array(s.box)
+    for ax in (0, 2):
+        dx[:, ax] -= L[ax] * np.round(dx[:, ax] / L[ax])
+    moved = np.sqrt((dx ** 2).sum(1))
+    assert o["n_builds"] == 1, "a rebuild ran: the fast particles did not stay within the skin"
+    assert 10 <= (moved[pick] > 0.15).sum() and moved.max() < 0.3, np.sort(moved)[-5:]
+    g.forces()
+    fg = g.read_forces()
+    fo, _ = oracle_forces(s, x32, v, 6)
+    assert_force_parity(fg, fo)
+    for lvl in (M.MD_LEVEL_FLUID, M.MD_LEVEL_IFACE):
+        assert_force_parity(g.read_forces(lvl), oracle_forces(s, x32, v, 6, level_mask=lvl)[0])
+
+
 def test_sts_trajectory_tracks_oracle(plt_sys):
     """Five velocity-Verlet steps from identical FP32-exact states: positions
     agree to 1e-4 (FP32 force rounding ~1e-5 F times dt^2 growth) and
