@@ -63,10 +63,10 @@ def workload(name, seed):
                  "STS velocity-Verlet dt=0.01, skin 0.3")
     if name == "channel":
         return synth.config_channel_platelets(seed=seed), dict(
-            dt=0.01, skin=0.3,
+            dt=0.01, skin=0.3, skin_plt=0.5,
             desc="platelet channel: 8,040,000 plasma at rho=3 in 400x100x67, y walls, Poiseuille g for wall "
                  "shear rate 0.05, 16 platelets x 10,000 CG particles (5% receptors); AI-MTS dt_f=0.01, k_m=1, "
-                 "per-platelet k from the controller vs fine-step STS dt=0.001; skin 0.3")
+                 "per-platelet k from the controller vs fine-step STS dt=0.001; skin 0.3, platelet skin 0.5")
     raise ValueError(name)
 
 
@@ -253,9 +253,13 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def make_system(M, s, dt, skin, seed):
+FINE_SKIN_PLT = 0.0      # fine-step STS: the plasma skin for the platelets too
+
+
+def make_system(M, s, dt, skin, seed, skin_plt=0.0):
     return M.System(s.box, s.x, s.v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, walls=s.walls, wall=s.wall,
-                    shear_rate=s.shear_rate, body_force=s.body_force, dt=dt, skin=skin, seed=seed)
+                    shear_rate=s.shear_rate, body_force=s.body_force, dt=dt, skin=skin, seed=seed,
+                    skin_plt=skin_plt)
 
 
 def timed(g, step, n, barrier):
@@ -300,7 +304,7 @@ def main():
     seed = 20220528 + rank
     s, wl = workload(args.workload, seed=seed)
     n = s.n
-    g = make_system(M, s, wl["dt"], wl["skin"], seed)
+    g = make_system(M, s, wl["dt"], wl["skin"], seed, wl.get("skin_plt", 0.0))
 
     mode_info = {}
     decisions = []
@@ -398,20 +402,23 @@ def main():
     # ---- comparison arms on the same system ------------------------------
     compare = {}
     if args.workload == "channel" and not args.no_compare:
-        # each arm at the Verlet skin that suits it (a sweep of 0.15-0.6:
-        # fine-step STS rebuilds rarely and prefers the shorter lists of skin
-        # 0.2; the dt = 0.01 arms run 2-3% faster at 0.5 than at 0.3, but the
-        # end-to-end step, which rebuilds every call, 9% slower: 0.3 is kept)
-        arms = [("fine_sts", 0.001, 0.2, lambda h, k: h.mts_step(k, direct=args.direct)),
-                ("respa_k10", 0.01, wl["skin"], lambda h, k: h.mts_step(k, mode=M.MD_MODE_RESPA, k_m=1, k_p=10,
-                                                                        direct=args.direct))]
-        for name, dt, skin, fn in arms:
-            h = make_system(M, s, dt, skin, seed)
+        # each arm at the Verlet skins that suit it (sweeps of the plasma skin
+        # over 0.15-0.6 and of the platelet skin over 0.2-0.9: fine-step STS
+        # rebuilds rarely and prefers the shorter lists of skin 0.2; the
+        # dt = 0.01 arms run 2-3% faster at a plasma skin of 0.5 than at 0.3,
+        # but the end-to-end step, which rebuilds every call, 9% slower, so
+        # 0.3 is kept; their platelet particles, which tripped most rebuilds,
+        # get a skin of 0.5: a rebuild every 5 instead of 3 outer steps)
+        arms = [("fine_sts", 0.001, 0.2, FINE_SKIN_PLT, lambda h, k: h.mts_step(k, direct=args.direct)),
+                ("respa_k10", 0.01, wl["skin"], wl["skin_plt"],
+                 lambda h, k: h.mts_step(k, mode=M.MD_MODE_RESPA, k_m=1, k_p=10, direct=args.direct))]
+        for name, dt, skin, skin_plt, fn in arms:
+            h = make_system(M, s, dt, skin, seed, skin_plt)
             fn(h, args.warmup)
             t_ms = timed(h, lambda k: fn(h, k), args.steps, barrier)
             u2, s2 = whole_job_rate(n * args.steps, t_ms / 1e3, world, device="cuda")
             compare[name] = {"ns_per_day": ns_per_day(args.steps, s2, dt) * (u2 / (n * args.steps)),
-                             "ms_per_step": s2 * 1e3 / args.steps, "dt": dt, "skin": skin,
+                             "ms_per_step": s2 * 1e3 / args.steps, "dt": dt, "skin": skin, "skin_plt": skin_plt,
                              "particle_steps_per_s": u2 / s2}
             h.close()
             del h

@@ -95,6 +95,10 @@ typedef struct md_config {
     uint64_t seed;            /* key of the Philox4x32-10 pair noise              */
     int32_t  cap_fluid, cap_iface, cap_lj, cap_morse; /* list capacities per row;
                                                    0: 96, 96, 1024, 256        */
+    double   skin_plt;        /* skin of the platelet particles (0: skin): the
+                                 LJ and Morse lists reach cut-off + skin_plt, the
+                                 interface list rc + (skin + skin_plt) / 2, and a
+                                 platelet particle trips a rebuild at skin_plt/2 */
 } md_config;
 
 /* Fill *cfg with the defaults above for n particles in box (no platelets). */

@@ -45,6 +45,7 @@ class md_config(C.Structure):
         ("f_A", C.c_double), ("k_bond", C.c_double),
         ("seed", C.c_uint64),
         ("cap_fluid", C.c_int32), ("cap_iface", C.c_int32), ("cap_lj", C.c_int32), ("cap_morse", C.c_int32),
+        ("skin_plt", C.c_double),
     ]
 
 

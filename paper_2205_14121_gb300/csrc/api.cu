@@ -93,9 +93,11 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
         return false;
     }
     const bool plt = s.n_plt > 0;
+    if (!(c.skin_plt >= 0)) { err = "skin_plt must not be negative"; return false; }
+    s.skin_p = c.skin_plt > 0 ? c.skin_plt : c.skin;
     if (plt) {
-        if (!setup_grid(c, 0.5 * (c.lj_rc + c.skin), s.gplt, err)) return false;
-        if (s.n_rec > 0 && !setup_grid(c, 0.5 * (c.morse_rc + c.skin), s.grec, err)) return false;
+        if (!setup_grid(c, 0.5 * (c.lj_rc + s.skin_p), s.gplt, err)) return false;
+        if (s.n_rec > 0 && !setup_grid(c, 0.5 * (c.morse_rc + s.skin_p), s.grec, err)) return false;
     }
     const int64_t n = s.n;
     s.xs = cv.take<double>(n);
@@ -683,6 +685,7 @@ int md_config_defaults(md_config *c)
     c->wall = 1.0;
     c->dt = 0.01;
     c->skin = 0.3;
+    c->skin_plt = 0.0;   // the plasma skin
     c->rc = 1.0; c->a_ff = 25.0; c->a_fw = 25.0; c->a_fp = 50.0; c->gamma = 4.5; c->sigma = 3.0;
     c->lj_eps = 1.0; c->lj_sigma = 0.8; c->lj_rc = 2.0; c->lj_excl = 1e30;   // no LJ within one platelet
     c->morse_D = 2.0; c->morse_alpha = 2.0; c->morse_r0 = 1.0; c->morse_rc = 5.0; c->f_A = 0.0;
@@ -733,7 +736,10 @@ int md_init(const md_config *cfg, const md_buffers *bufs, void *cuda_stream, md_
         s->geom.hL[d] = 0.5f * s->geom.L[d];
     }
     s->geom.shear_v = (float)(c.shear_rate * c.box[1]);
-    const double cuts[4] = {c.rc + c.skin, c.rc + c.skin, c.lj_rc + c.skin, c.morse_rc + c.skin};
+    // a plasma-platelet pair: plasma within skin/2, the platelet particle
+    // within skin_plt/2 of their build positions
+    const double cuts[4] = {c.rc + c.skin, c.rc + 0.5 * (c.skin + s->skin_p), c.lj_rc + s->skin_p,
+                            c.morse_rc + s->skin_p};
     for (int k = 0; k < 4; ++k) s->cut2[k] = (float)(cuts[k] * cuts[k]);
     s->excl2 = (float)(c.lj_excl * c.lj_excl);
     cudaError_t e = cudaHostAlloc((void **)&s->h_ctl, sizeof(int32_t) * CTL_WORDS, cudaHostAllocDefault);

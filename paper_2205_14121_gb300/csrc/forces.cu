@@ -527,7 +527,8 @@ static fast_args fast_for(md_system *s, const md_grid &g, const int32_t *members
     fa.g = g;
     fa.members = members;
     fa.xb = s->xb;
-    fa.R = (float)(s->cfg.rc + s->cfg.skin) * (1.0f + 1e-5f);
+    // partners at most a skin (plasma) or skin_plt / 2 (platelets) from their build cells
+    fa.R = (float)(s->cfg.rc + (s->cfg.skin > s->skin_p ? s->cfg.skin : s->skin_p)) * (1.0f + 1e-5f);
     fa.cut2 = cut2;
     return fa;
 }

@@ -34,6 +34,7 @@ struct kd_args {
     double wall;
     double shear_v;
     float skin_half, margin, skin;
+    float skin_p;          // skin of the platelet particles
     md_geom geom;
     const md_dstate *ds;
     int32_t *ctl;
@@ -136,11 +137,12 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
             // inner substeps after this check and before the rebuild point at
             // the end of the interface substep; plasma does not move in between
             const float mg = t >= 0 ? a.margin : 0.0f;
-            float thr = a.skin_half - mg;
+            const float sk = t >= 0 ? a.skin_p : a.skin;
+            float thr = 0.5f * sk - mg;
             if (a.geom.le) {
                 float dd = fabsf(a.ds->le_offset_f - a.ds->le_build_f);
                 dd = fminf(dd, a.geom.L[0] - dd);
-                thr = 0.5f * (a.skin - dd) - mg;
+                thr = 0.5f * (sk - dd) - mg;
             }
             if (!(d2 <= thr * thr) || thr <= 0.0f) {
                 // plasma up to twice the threshold keeps the lists: its pairs
@@ -259,6 +261,7 @@ kd_args base_args(md_system *s)
     a.shear_v = s->cfg.shear_rate * s->cfg.box[1];
     a.skin = (float)s->cfg.skin;
     a.skin_half = 0.5f * (float)s->cfg.skin;
+    a.skin_p = (float)s->skin_p;
     a.margin = s->margin;
     a.geom = s->geom;
     a.ds = s->ds;
@@ -307,7 +310,7 @@ cudaError_t launch_set_time(md_system *s, int64_t n, int32_t c, double t)
 {
     const md_config &cf = s->cfg;
     k_set_time<<<1, 1, 0, s->stream>>>(s->ds, n, c, t, cf.shear_rate * cf.box[1], cf.box[0], s->geom.le,
-                                       (float)cf.skin, s->margin, s->ctl);
+                                       (float)(cf.skin < s->skin_p ? cf.skin : s->skin_p), s->margin, s->ctl);
     MSM_COUNT(s, 1);
     return cudaGetLastError();
 }
@@ -323,7 +326,7 @@ cudaError_t launch_time_rel(md_system *s, int dn, int c, double t_off)
 {
     const md_config &cf = s->cfg;
     k_time_rel<<<1, 1, 0, s->stream>>>(s->ds, dn, c, t_off, cf.dt, cf.shear_rate * cf.box[1], cf.box[0], s->geom.le,
-                                       (float)cf.skin, s->margin, s->ctl);
+                                       (float)(cf.skin < s->skin_p ? cf.skin : s->skin_p), s->margin, s->ctl);
     MSM_COUNT(s, 1);
     return cudaGetLastError();
 }

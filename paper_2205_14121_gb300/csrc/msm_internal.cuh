@@ -147,6 +147,7 @@ struct md_system {
 
     md_geom geom;
     float cut2[4];               // list cut-offs squared (FP32)
+    double skin_p;               // skin of the platelet particles (cfg.skin_plt, else cfg.skin)
     float excl2;
     float disp2;                 // rebuild threshold on displacement^2
 
@@ -365,14 +366,15 @@ __device__ __forceinline__ int cell_index32(const md_grid &g, int cx, int cy, in
 }
 
 // Cells [lo, hi] within reach R of coordinate x along one axis, clamped to
-// [-2, n+1] and to at most n cells, so that a non-finite or escaped position
-// (reported by the integrator's unstable flag) still gives a bounded scan.
+// [-n, 2n - 1] (one period either side: a reach may span several cells) and
+// to at most n cells, so that a non-finite or escaped position (reported by
+// the integrator's unstable flag) still gives a bounded scan.
 __device__ __forceinline__ void cell_span(float x, float lo0, float R, float inv_h, int n, int &lo, int &hi)
 {
     lo = __float2int_rd((x - lo0 - R) * inv_h);
     hi = __float2int_rd((x - lo0 + R) * inv_h);
-    lo = min(max(lo, -2), n + 1);
-    hi = min(max(hi, -2), n + 1);
+    lo = min(max(lo, -n), 2 * n - 1);
+    hi = min(max(hi, -n), 2 * n - 1);
     if (hi - lo + 1 > n) hi = lo + n - 1;
 }
 

@@ -325,6 +325,7 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
         // interface: platelet rows (platelet sub-grid order) against the main grid
         a.rows = s->n_plt;
         a.row_idx = s->plt_sorted;
+        a.R = (float)(s->cfg.rc + 0.5 * (s->cfg.skin + s->skin_p)) * margin;
         a.cut2 = s->cut2[MD_LIST_IFACE];
         a.nl = s->nl[MD_LIST_IFACE];
         a.nc = s->nc[MD_LIST_IFACE];
@@ -345,8 +346,8 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
             k_plt_radius<<<dim3(P, chunks), 256, 0, s->stream>>>(s->plt_off, s->plt_ids, s->pos_of_id, s->x32,
                                                                   s->geom, s->ds, s->plt_bound, gate);
             k_plt_near<<<1, 256, 0, s->stream>>>(s->plt_off, s->plt_ids, s->pos_of_id, s->x32, s->plt_bound, P,
-                                                 s->geom, (float)(s->cfg.lj_rc + s->cfg.skin),
-                                                 (float)(s->cfg.morse_rc + s->cfg.skin), s->plt_near, gate);
+                                                 s->geom, (float)(s->cfg.lj_rc + s->skin_p),
+                                                 (float)(s->cfg.morse_rc + s->skin_p), s->plt_near, gate);
         }
         a.near = prefilter ? s->plt_near : nullptr;
         a.near_bit = 1;
@@ -358,7 +359,7 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
         a.cell_pid = s->cell_pid;
         a.g = s->gplt;
         a.members = s->plt_sorted;
-        a.R = (float)(s->cfg.lj_rc + s->cfg.skin) * margin;
+        a.R = (float)(s->cfg.lj_rc + s->skin_p) * margin;
         a.cut2 = s->cut2[MD_LIST_LJ];
         a.nl = s->nl[MD_LIST_LJ];
         a.nc = s->nc[MD_LIST_LJ];
@@ -370,7 +371,7 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
             a.row_idx = s->rec_sorted;
             a.g = s->grec;
             a.members = s->rec_sorted;
-            a.R = (float)(s->cfg.morse_rc + s->cfg.skin) * margin;
+            a.R = (float)(s->cfg.morse_rc + s->skin_p) * margin;
             a.near_bit = 2;
             if (prefilter)
                 k_cell_pid<<<blocks_for(s->grec.ncell), MSM_TPB, 0, s->stream>>>(s->grec.ncell, s->grec.start,

@@ -84,18 +84,24 @@ def wall_sys():
     return synth.plasma_box(box=(9.0, 8.0, 7.0), walls=True, body_force=0.02, seed=12)
 
 
-@pytest.mark.parametrize("excl", [2.5, None])
+@pytest.mark.parametrize("excl,skin_plt", [(2.5, None), (None, None), (None, 0.7)])
 @pytest.mark.parametrize("kind", [0, 1, 2, 3])
-def test_neighbor_sets_bit_exact(plt_sys, kind, excl):
+def test_neighbor_sets_bit_exact(plt_sys, kind, excl, skin_plt):
     """Every list kind equals the oracle's brute-force FP32 pair set: with an LJ
-    exclusion radius of 2.5 (far-at-rest pairs of one platelet kept) and with
-    the default (no same-platelet LJ; the bounding-sphere prefilter active)."""
+    exclusion radius of 2.5 (far-at-rest pairs of one platelet kept), with the
+    default (no same-platelet LJ; the bounding-sphere prefilter active), and
+    with a platelet skin of 0.7 (interface reach rc + (0.3 + 0.7) / 2, LJ and
+    Morse reaches cut-off + 0.7)."""
     s = plt_sys
-    g = make_gpu(s, step0=17, **({} if excl is None else {"lj_excl": excl}))
+    kw = {} if excl is None else {"lj_excl": excl}
+    if skin_plt is not None:
+        kw["skin_plt"] = skin_plt
+    g = make_gpu(s, step0=17, **kw)
     g.neighbor_build(force=True)
     got = g.neighbor_pairs(kind)
     _, _, x32 = g.read_particles()
-    cut = [1.3, 1.3, 2.3, 5.3][kind]
+    sp = 0.3 if skin_plt is None else skin_plt
+    cut = [1.3, 1.0 + 0.5 * (0.3 + sp), 2.0 + sp, 5.0 + sp][kind]
     excl2 = np.float32(np.inf) if excl is None else np.float32(excl * excl)
     ref = O.pairs_f32(x32, s.tag, np.array(s.box, np.float32), kind, np.float32(cut * cut),
                       X0f=s.X0.astype(np.float32), excl2=excl2, le=True,
