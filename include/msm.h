@@ -149,9 +149,13 @@ int md_set_particles(md_system *sys, const double *x, const double *v, const int
  * Load a new state of the particle set last given to md_set_particles():
  * x[n*3] positions and v[n*3] velocities as HOST arrays in id order; tags,
  * rest positions and bonds are kept on the device (nothing but x and v
- * crosses to the GPU).  Resets the step counter to step0 and marks lists and
- * forces stale, as md_set_particles does.  Errors: MD_EINVAL (null argument,
- * or no earlier md_set_particles), MD_ECUDA.
+ * crosses to the GPU).  Resets the step counter to step0 and marks forces
+ * stale.  When neighbour lists are built, the state goes into their particle
+ * order and they are kept if it passes the rebuild check of a step (every
+ * particle within its skin threshold of the last build, plasma beyond skin/2
+ * listed for the fast-particle pass); otherwise the next call rebuilds them.
+ * Synchronises the stream.  Errors: MD_EINVAL (null argument, or no earlier
+ * md_set_particles), MD_EUNSTABLE (non-finite or escaped position), MD_ECUDA.
  */
 int md_set_xv(md_system *sys, const double *x, const double *v, int64_t step0);
 

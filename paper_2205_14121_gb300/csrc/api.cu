@@ -891,7 +891,29 @@ int md_set_xv(md_system *s, const double *x, const double *v, int64_t step0)
 {
     if (!s || !x || !v) return set_error(s, MD_EINVAL, "md_set_xv: null argument");
     if (!s->have_particles) return set_error(s, MD_EINVAL, "md_set_xv: md_set_particles was never called");
-    return load_xv(s, x, v, step0);
+    if (s->lists_stale) return load_xv(s, x, v, step0);
+    // lists built: the new state goes into the current storage order and
+    // keeps them if the kick-drift's rebuild check passes on it
+    const int64_t n = s->n;
+    cudaStream_t st = s->stream;
+    CK(cudaMemcpyAsync(s->alt64, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload x");
+    CK(launch_place_state(s, s->alt64, false), "place x");
+    CK(cudaMemcpyAsync(s->alt64, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload v");
+    CK(launch_place_state(s, s->alt64, true), "place v");
+    CK(cudaMemsetAsync(s->ctl + CTL_UNSTABLE, 0, sizeof(int32_t), st), "reset unstable");
+    CK(launch_set_time(s, step0, 0, (double)step0 * s->cfg.dt), "time");
+    CK(launch_check_placed(s, step0), "check");
+    for (int l = 0; l < 3; ++l)
+        if (s->f[l]) CK(cudaMemsetAsync(s->f[l], 0, sizeof(float4) * n, st), "zero f");
+    CK(cudaMemcpyAsync(s->h_ctl, s->ctl, sizeof(int32_t) * CTL_WORDS, cudaMemcpyDeviceToHost, st), "read ctl");
+    CK(cudaStreamSynchronize(st), "set_xv sync");
+    s->host_step = step0;
+    s->host_sub = 0;
+    s->lists_stale = s->h_ctl[CTL_REBUILD] != 0;
+    s->forces_stale = true;
+    s->forces_levels = 0;
+    if (s->h_ctl[CTL_UNSTABLE]) return set_error(s, MD_EUNSTABLE, "md_set_xv: non-finite or escaped position");
+    return MD_OK;
 }
 
 int md_set_bonds(md_system *s, const int32_t *ij, const double *r0, int64_t nb)

@@ -52,6 +52,39 @@ __device__ __forceinline__ bool selected(int which, int32_t t)
     return t >= 0;
 }
 
+// Rebuild check of particle k (storage slot, tag t) at position xn against
+// its position at the last build.  The margin covers platelet particles,
+// which keep drifting in the inner substeps after this check and before the
+// rebuild point at the end of the interface substep; plasma does not move in
+// between.  Plasma up to twice the threshold keeps the lists: its pairs that
+// they lack are evaluated by the fast-particle pass (every partner within rc
+// is then in a list or found there).
+__device__ __forceinline__ void check_moved(const kd_args &a, int64_t k, int32_t t, float4 xn)
+{
+    float dx, dy, dz, vs;
+    min_image_f32(a.geom, a.ds->le_offset_f, xn, a.xb[k], dx, dy, dz, vs);
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    const float mg = t >= 0 ? a.margin : 0.0f;
+    const float sk = t >= 0 ? a.skin_p : a.skin;
+    float thr = 0.5f * sk - mg;
+    if (a.geom.le) {
+        float dd = fabsf(a.ds->le_offset_f - a.ds->le_build_f);
+        dd = fminf(dd, a.geom.L[0] - dd);
+        thr = 0.5f * (sk - dd) - mg;
+    }
+    if (!(d2 <= thr * thr) || thr <= 0.0f) {
+        int q = -1;
+        if (t == MD_TAG_FLUID && thr > 0.0f && d2 <= 4.0f * thr * thr) {
+            q = atomicAdd(&a.ctl[CTL_NFAST], 1);
+            if (q < a.fast_max) {
+                a.fast_idx[q] = (int32_t)k;
+                a.fast_flag[k] = a.ds->fast_stamp;
+            }
+        }
+        if (q < 0 || q >= a.fast_max) a.ctl[CTL_REBUILD] = 1;
+    }
+}
+
 __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -129,35 +162,7 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
             float4 xn = a.x32[k];
             xn.x = xf; xn.y = yf; xn.z = zf;
             a.x32[k] = xn;
-            // rebuild check against the positions of the last build
-            float dx, dy, dz, vs;
-            min_image_f32(a.geom, a.ds->le_offset_f, xn, a.xb[k], dx, dy, dz, vs);
-            const float d2 = dx * dx + dy * dy + dz * dz;
-            // the margin covers platelet particles, which keep drifting in the
-            // inner substeps after this check and before the rebuild point at
-            // the end of the interface substep; plasma does not move in between
-            const float mg = t >= 0 ? a.margin : 0.0f;
-            const float sk = t >= 0 ? a.skin_p : a.skin;
-            float thr = 0.5f * sk - mg;
-            if (a.geom.le) {
-                float dd = fabsf(a.ds->le_offset_f - a.ds->le_build_f);
-                dd = fminf(dd, a.geom.L[0] - dd);
-                thr = 0.5f * (sk - dd) - mg;
-            }
-            if (!(d2 <= thr * thr) || thr <= 0.0f) {
-                // plasma up to twice the threshold keeps the lists: its pairs
-                // that they lack are evaluated by the fast-particle pass (every
-                // partner within rc is then in a list or found there)
-                int q = -1;
-                if (t == MD_TAG_FLUID && thr > 0.0f && d2 <= 4.0f * thr * thr) {
-                    q = atomicAdd(&a.ctl[CTL_NFAST], 1);
-                    if (q < a.fast_max) {
-                        a.fast_idx[q] = (int32_t)k;
-                        a.fast_flag[k] = a.ds->fast_stamp;
-                    }
-                }
-                if (q < 0 || q >= a.fast_max) a.ctl[CTL_REBUILD] = 1;
-            }
+            check_moved(a, k, t, xn);
             const bool bad = !(fabsf(xf) + fabsf(yf) + fabsf(zf) < 1e30f) ||
                              !(fabsf(vv.x) + fabsf(vv.y) + fabsf(vv.z) < 1e30f) ||
                              (a.geom.walls && (yf < -(float)a.wall || yf > a.geom.L[1] + (float)a.wall));
@@ -228,6 +233,13 @@ __global__ void k_cond_rebuild(const int32_t *ctl, cudaGraphConditionalHandle h)
 
 __global__ void k_set_loop(md_dstate *ds, int64_t n) { ds->steps_left = n; }
 
+// Outer-step counters at step n (a new state set at time index n).
+__global__ void k_set_counters(md_dstate *ds, int64_t n)
+{
+    ds->base = n;
+    ds->done = n;
+}
+
 // Before a drift of the plasma: an empty fast list under a new stamp.
 __global__ void k_fast_reset(md_dstate *ds, int32_t *ctl)
 {
@@ -239,6 +251,46 @@ __global__ void k_zero_f4(float4 *p, int64_t n)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) p[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// A new state in the current storage order (md_set_xv keeping the lists):
+// particle id k goes to its slot pos_of_id[k]; the id / tag bits stay.
+__global__ void k_place_x(int64_t n, const double *__restrict__ aos, const int32_t *__restrict__ pos_of_id,
+                          double *xs, double *ys, double *zs, float4 *x32)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int32_t q = pos_of_id[k];
+    const double x = aos[3 * k], y = aos[3 * k + 1], z = aos[3 * k + 2];
+    xs[q] = x; ys[q] = y; zs[q] = z;
+    float4 p = x32[q];
+    p.x = (float)x; p.y = (float)y; p.z = (float)z;
+    x32[q] = p;
+}
+
+__global__ void k_place_v(int64_t n, const double *__restrict__ aos, const int32_t *__restrict__ pos_of_id, float4 *v)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int32_t q = pos_of_id[k];
+    float4 u = v[q];
+    u.x = (float)aos[3 * k]; u.y = (float)aos[3 * k + 1]; u.z = (float)aos[3 * k + 2];
+    v[q] = u;
+}
+
+// The rebuild check of the kick-drift on every particle of a placed state
+// (walls included, held to the plasma threshold); NaN / escape -> unstable.
+__global__ void __launch_bounds__(MSM_TPB) k_check_placed(kd_args a)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.n) return;
+    const float4 xn = a.x32[k];
+    check_moved(a, k, a.tag[k], xn);
+    const float4 vv = a.v[k];
+    const bool bad = !(fabsf(xn.x) + fabsf(xn.y) + fabsf(xn.z) < 1e30f) ||
+                     !(fabsf(vv.x) + fabsf(vv.y) + fabsf(vv.z) < 1e30f) ||
+                     (a.geom.walls && (xn.y < -(float)a.wall || xn.y > a.geom.L[1] + (float)a.wall));
+    if (bad) a.ctl[CTL_UNSTABLE] = 1;
 }
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)(n > 0 ? (n + MSM_TPB - 1) / MSM_TPB : 1); }
@@ -303,6 +355,27 @@ cudaError_t launch_kick_drift(md_system *s, const float h[3], int kick_which, do
     }
     k_kick_drift<<<blocks_for(a.n), MSM_TPB, 0, s->stream>>>(a);
     MSM_COUNT(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_place_state(md_system *s, const double *x_dev, bool velocities)
+{
+    if (velocities) k_place_v<<<blocks_for(s->n), MSM_TPB, 0, s->stream>>>(s->n, x_dev, s->pos_of_id, s->v);
+    else k_place_x<<<blocks_for(s->n), MSM_TPB, 0, s->stream>>>(s->n, x_dev, s->pos_of_id, s->xs, s->ys, s->zs,
+                                                                  s->x32);
+    MSM_COUNT(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_placed(md_system *s, int64_t step0)
+{
+    k_set_counters<<<1, 1, 0, s->stream>>>(s->ds, step0);
+    MSM_COUNT(s, 1);
+    kd_args a = base_args(s);
+    a.margin = 0.05f;        // the larger of the two schedules' margins
+    k_fast_reset<<<1, 1, 0, s->stream>>>(s->ds, s->ctl);
+    k_check_placed<<<blocks_for(s->n), MSM_TPB, 0, s->stream>>>(a);
+    MSM_COUNT(s, 2);
     return cudaGetLastError();
 }
 

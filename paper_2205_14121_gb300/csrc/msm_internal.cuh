@@ -519,6 +519,10 @@ cudaError_t launch_time_rel(md_system *s, int dn, int c, double t_off);
 cudaError_t launch_cond_rebuild(md_system *s, cudaGraphConditionalHandle h);
 cudaError_t launch_set_loop(md_system *s, int64_t n);
 cudaError_t launch_zero_forces(md_system *s, unsigned levels);
+// md_set_xv keeping the lists: scatter an id-order state (device AoS, 3n
+// doubles) into the storage slots, then the rebuild check of every particle
+cudaError_t launch_place_state(md_system *s, const double *aos_dev, bool velocities);
+cudaError_t launch_check_placed(md_system *s, int64_t step0);
 // reduce.cu
 cudaError_t launch_kinetics(md_system *s);
 // y-binned v_x sums and counts into prof_part + PROF_BLOCKS * 2 * PROF_BINS_MAX:

@@ -461,19 +461,26 @@ def test_flow_profile_matches_oracle(wall_sys, plt_sys, which):
     assert abs(dens.mean() - 3.0) < 0.5
 
 
-def test_set_xv_equals_full_upload(plt_wall_sys):
+@pytest.mark.parametrize("shift", [0.0, 1.7])
+def test_set_xv_equals_full_upload(plt_wall_sys, shift):
     """md_set_xv (positions and velocities only, tags and rest positions kept
     on the device) leaves the same state as md_set_particles with the same
     tags: two RESPA steps from it agree to FP32 atomic-order noise (a wrong
-    tag, rest position or stale list would move particles by orders more)."""
+    tag, rest position or stale list would move particles by orders more).
+    Near the state of the last build (shift 0) it keeps the lists and the
+    cell order; the whole system moved by 1.7 along x trips the rebuild check."""
     import paper_2205_14121_gb300 as M
     s = plt_wall_sys
     rng = np.random.default_rng(5)
-    x1 = f32(s.x + 0.01 * rng.standard_normal(s.x.shape) * (s.tag != synth.TAG_WALL)[:, None])
+    mob = (s.tag != synth.TAG_WALL)[:, None]
+    x1 = s.x + 0.01 * rng.standard_normal(s.x.shape) * mob
+    x1[:, 0] = (x1[:, 0] + shift) % s.box[0]
+    x1 = f32(x1)
     v1 = f32(s.v * 0.9)
     a = make_gpu(s, x=x1, v=v1, step0=7)
     b = make_gpu(s, step0=0)
     b.mts_step(1)
+    builds = b.observables()["n_builds"]
     b.set_xv(x1, v1, step0=7)
     for g in (a, b):
         g.mts_step(2, mode=M.MD_MODE_RESPA, k_m=1, k_p=5)
@@ -481,6 +488,9 @@ def test_set_xv_equals_full_upload(plt_wall_sys):
     xb, vb, _ = b.read_particles()
     assert np.abs(xa - xb).max() < 1e-5
     assert np.abs(va - vb).max() < 1e-3 * np.sqrt((va ** 2).mean())
+    assert a.observables()["step"] == b.observables()["step"] == 9
+    if shift == 0.0:
+        assert b.observables()["n_builds"] == builds, "a rebuild ran on a state within the skin"
 
 
 def test_checkpoint_roundtrip(plt_sys):
