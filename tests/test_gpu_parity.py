@@ -199,15 +199,18 @@ def test_wall_temperature_subtracts_local_flow(plt_wall_sys):
     assert stream > 0.01 * mob.sum()
 
 
-def test_fast_particles_keep_the_lists_and_every_pair(plt_wall_sys):
+@pytest.mark.parametrize("which", ["walls", "le"])
+def test_fast_particles_keep_the_lists_and_every_pair(plt_wall_sys, plt_sys, which):
     """Plasma that moved beyond skin/2 but within the skin keeps the lists:
     40 plasma particles next to the shells are launched at speed 7 toward
     their platelet's centre; after three STS steps they are 0.15-0.3 from their
     build positions, no rebuild has run, and the forces of every level equal
     the oracle's brute-force forces on the GPU's state -- the pairs the lists
-    lack (plasma and interface) come from the fast-particle pass."""
+    lack (plasma and interface) come from the fast-particle pass.  With walls
+    and with Lees-Edwards images (whose offset moves between the build and
+    the check)."""
     import paper_2205_14121_gb300 as M
-    s = plt_wall_sys
+    s = plt_wall_sys if which == "walls" else plt_sys
     x0, v0 = f32(s.x), f32(s.v)
     plt = np.flatnonzero(s.tag >= 0)
     plasma = np.flatnonzero(s.tag == synth.TAG_FLUID)
@@ -226,6 +229,10 @@ def test_fast_particles_keep_the_lists_and_every_pair(plt_wall_sys):
     x, v, x32 = g.read_particles()
     dx = x - x0
     L = np.array(s.box)
+    if which == "le":       # an image across y carries the offset in x
+        cross = np.round(dx[:, 1] / L[1])
+        dx[:, 1] -= L[1] * cross
+        dx[:, 0] -= cross * (s.shear_rate * L[1] * 0.01 * 6)   # the offset at the end, within 0.02 of the crossing's
     for ax in (0, 2):
         dx[:, ax] -= L[ax] * np.round(dx[:, ax] / L[ax])
     moved = np.sqrt((dx ** 2).sum(1))
@@ -235,6 +242,8 @@ def test_fast_particles_keep_the_lists_and_every_pair(plt_wall_sys):
     fg = g.read_forces()
     fo, _ = oracle_forces(s, x32, v, 6)
     assert_force_parity(fg, fo)
+    if which == "le":
+        assert le_offset_f32(s, 6) != le_offset_f32(s, 3)
     for lvl in (M.MD_LEVEL_FLUID, M.MD_LEVEL_IFACE):
         assert_force_parity(g.read_forces(lvl), oracle_forces(s, x32, v, 6, level_mask=lvl)[0])
 
