@@ -449,7 +449,9 @@ def main():
         "roofline": {"bound": "hbm", "kernel": "k_dpd (fluid level pair forces)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": peak_kind,
-                     "bytes_per_particle": bytes_per_particle, "n_half": n_half, "launch_ms": fl_ms},
+                     "bytes_per_particle": bytes_per_particle, "n_half": n_half, "launch_ms": fl_ms,
+                     "limiter": "instruction issue: 78% of issue slots active, the ALU pipe the busiest "
+                                "(ncu on the 1M system, profiles/k_dpd_dpd1m.md)"},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": prof_plain["total_launches"],

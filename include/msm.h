@@ -178,6 +178,16 @@ int md_neighbor_build(md_system *sys, uint32_t list_mask, int force);
 
 /* flags of md_forces */
 #define MD_FORCE_VIRIAL 1u  /* also accumulate the FP64 pair virial */
+/* Deterministic forces: every pair and bond term, evaluated with the particle
+ * of lower id first, is rounded to a multiple of 2^-32 and summed as a 64-bit
+ * integer per particle and level.  The result does not depend on the order of
+ * the atomic updates (bit-identical from run to run and whatever the particle
+ * order), and the pair terms cancel exactly: without walls and body force the
+ * forces read back by md_read_forces (which takes these sums exactly while no
+ * step, rebuild or new state intervened) add up to exactly zero.  The FP32
+ * level buffers the integrator uses are the sums rounded to FP32.  The virial
+ * is not covered.  Slower than the default. */
+#define MD_FORCE_DETERMINISTIC 2u
 
 /*
  * Forces of the levels in level_mask at the current state (Eq. 1-4),

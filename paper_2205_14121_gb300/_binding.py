@@ -18,6 +18,7 @@ MD_LEVEL_FLUID, MD_LEVEL_IFACE, MD_LEVEL_PLT, MD_LEVEL_ALL = 1, 2, 4, 7
 MD_CFG_WALLS, MD_CFG_LEES_EDWARDS = 1, 2
 MD_LIST_FLUID, MD_LIST_IFACE, MD_LIST_LJ, MD_LIST_MORSE = 0, 1, 2, 3
 MD_FORCE_VIRIAL = 1
+MD_FORCE_DETERMINISTIC = 2
 MD_MODE_STS, MD_MODE_RESPA, MD_MODE_AI = 0, 1, 2
 RECEPTOR_BIT = 1 << 30
 
@@ -283,8 +284,9 @@ class System:
 
     md_neighbor_build = neighbor_build
 
-    def forces(self, level_mask=MD_LEVEL_ALL, virial=False):
-        self._check(lib().md_forces(self.h, level_mask, MD_FORCE_VIRIAL if virial else 0), "md_forces")
+    def forces(self, level_mask=MD_LEVEL_ALL, virial=False, deterministic=False):
+        flags = (MD_FORCE_VIRIAL if virial else 0) | (MD_FORCE_DETERMINISTIC if deterministic else 0)
+        self._check(lib().md_forces(self.h, level_mask, flags), "md_forces")
 
     md_forces = forces
 

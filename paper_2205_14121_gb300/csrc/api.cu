@@ -114,6 +114,8 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
     s.fast_max = n / 64 > 4096 ? n / 64 : 4096;
     s.fast_idx = cv.take<int32_t>(s.fast_max);
     s.fast_flag = cv.take<uint32_t>(n);
+    for (int l = 0; l < 3; ++l)
+        s.fdet[l] = (l == 0 || c.n_plt_particles > 0) ? cv.take<unsigned long long>(3 * n) : nullptr;
     s.tag_s = cv.take<int32_t>(n);
     s.cellid = cv.take<int32_t>(n);
     s.slot = cv.take<int32_t>(n);
@@ -280,6 +282,27 @@ __global__ void k_export_forces(int64_t n, const float4 *f0, const float4 *f1, c
     aos[3 * id] = fx; aos[3 * id + 1] = fy; aos[3 * id + 2] = fz;
 }
 
+// Forces of a deterministic md_forces, exactly: the levels' fixed-point sums
+// added as integers, then scaled by 2^-32 (exact in FP64 below 2^21).
+__global__ void k_export_fixed(int64_t n, const unsigned long long *q0, const unsigned long long *q1,
+                               const unsigned long long *q2, const float4 *x32, const int32_t *tag, float g,
+                               double *aos)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t id = id_of(x32[k]);
+    const double u = 1.0 / 4294967296.0;
+    for (int d = 0; d < 3; ++d) {
+        unsigned long long t = 0;
+        if (q0) t += q0[3 * k + d];
+        if (q1) t += q1[3 * k + d];
+        if (q2) t += q2[3 * k + d];
+        double v = (double)(long long)t * u;
+        if (d == 0 && q0 && tag[k] != MD_TAG_WALL) v += g;
+        aos[3 * id + d] = v;
+    }
+}
+
 __global__ void k_set_word(int32_t *p, int32_t v) { *p = v; }
 
 // ---------------------------------------------------------------------------
@@ -331,6 +354,7 @@ double host_le_offset(const md_system *s, double t)
 
 int request_rebuild(md_system *s)
 {
+    s->det_levels = 0;   // the re-sort moves the particles: no exact forces to export
     k_set_word<<<1, 1, 0, s->stream>>>(s->ctl + CTL_REBUILD, 1);
     CK(cudaGetLastError(), "rebuild request");
     CK(launch_rebuild(s, s->ctl + CTL_REBUILD), "rebuild");
@@ -344,12 +368,25 @@ int ensure_lists(md_system *s)
     return request_rebuild(s);
 }
 
-int eval_forces(md_system *s, unsigned levels, bool virial)
+int eval_forces(md_system *s, unsigned levels, bool virial, bool det = false)
 {
     CK(launch_zero_forces(s, levels), "zero forces");
     if (virial) CK(cudaMemsetAsync(s->vir_acc, 0, 9 * sizeof(double), s->stream), "virial reset");
     float4 *out[3] = {s->f[0], s->f[1], s->f[2]};
-    CK(launch_forces(s, levels, out, virial), "forces");
+    s->det_levels = 0;
+    if (!det) {
+        CK(launch_forces(s, levels, out, virial), "forces");
+        return MD_OK;
+    }
+    // one level at a time into its fixed-point sums, then its FP32 buffer
+    for (int l = 0; l < 3; ++l) {
+        const unsigned bit = 1u << l;
+        if (!(levels & bit) || !s->fdet[l]) continue;
+        CK(cudaMemsetAsync(s->fdet[l], 0, sizeof(unsigned long long) * 3 * s->n, s->stream), "zero fixed sums");
+        CK(launch_forces(s, bit, out, virial, true, s->fdet[l]), "forces (deterministic)");
+        CK(launch_fixed_to_f4(s, s->fdet[l], s->f[l]), "fixed to float");
+    }
+    s->det_levels = levels;
     return MD_OK;
 }
 
@@ -851,6 +888,7 @@ int md_set_particles(md_system *s, const double *x, const double *v, const int32
 static int load_xv(md_system *s, const double *x, const double *v, int64_t step0)
 {
     const int64_t n = s->n;
+    s->det_levels = 0;
     cudaStream_t st = s->stream;
     CK(cudaMemcpyAsync(s->alt64, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload x");
     k_import_x<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->alt64, s->xs, s->ys, s->zs, s->x32, s->xb);
@@ -895,6 +933,7 @@ int md_set_xv(md_system *s, const double *x, const double *v, int64_t step0)
     // lists built: the new state goes into the current storage order and
     // keeps them if the kick-drift's rebuild check passes on it
     const int64_t n = s->n;
+    s->det_levels = 0;
     cudaStream_t st = s->stream;
     CK(cudaMemcpyAsync(s->alt64, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload x");
     CK(launch_place_state(s, s->alt64, false), "place x");
@@ -984,6 +1023,7 @@ int md_neighbor_build(md_system *s, uint32_t list_mask, int force)
 {
     if (!s || !s->have_particles) return set_error(s, MD_EINVAL, "md_neighbor_build: no particles");
     if (list_mask & ~0xFu) return set_error(s, MD_EINVAL, "md_neighbor_build: bad list mask");
+    s->det_levels = 0;
     if (force || s->lists_stale) {
         int rc = request_rebuild(s);
         if (rc) return rc;
@@ -1001,7 +1041,8 @@ int md_forces(md_system *s, uint32_t level_mask, uint32_t flags)
     int rc = ensure_lists(s);
     if (rc) return rc;
     if (s->n_plt == 0) level_mask &= MD_LEVEL_FLUID;
-    rc = eval_forces(s, level_mask, (flags & MD_FORCE_VIRIAL) != 0);
+    if (flags & ~(MD_FORCE_VIRIAL | MD_FORCE_DETERMINISTIC)) return set_error(s, MD_EINVAL, "md_forces: bad flags");
+    rc = eval_forces(s, level_mask, (flags & MD_FORCE_VIRIAL) != 0, (flags & MD_FORCE_DETERMINISTIC) != 0);
     if (rc) return rc;
     s->forces_levels = level_mask;
     s->forces_stale = level_mask != (s->n_plt > 0 ? MD_LEVEL_ALL : MD_LEVEL_FLUID);
@@ -1014,11 +1055,18 @@ int md_read_forces(md_system *s, uint32_t level_mask, double *f)
     const int rc = ensure_forces(s);
     if (rc) return rc;
     const int64_t n = s->n;
-    const float4 *f0 = (level_mask & MD_LEVEL_FLUID) ? s->f[0] : nullptr;
-    const float4 *f1 = (level_mask & MD_LEVEL_IFACE) ? s->f[1] : nullptr;
-    const float4 *f2 = (level_mask & MD_LEVEL_PLT) ? s->f[2] : nullptr;
-    k_export_forces<<<blocks_for(n), MSM_TPB, 0, s->stream>>>(n, f0, f1, f2, s->x32, s->tag_s,
-                                                               (float)s->cfg.body_force, s->alt64);
+    if (s->det_levels && !(level_mask & ~s->det_levels)) {
+        // the last md_forces was deterministic and covers the levels: exact sums
+        k_export_fixed<<<blocks_for(n), MSM_TPB, 0, s->stream>>>(
+            n, (level_mask & MD_LEVEL_FLUID) ? s->fdet[0] : nullptr, (level_mask & MD_LEVEL_IFACE) ? s->fdet[1] : nullptr,
+            (level_mask & MD_LEVEL_PLT) ? s->fdet[2] : nullptr, s->x32, s->tag_s, (float)s->cfg.body_force, s->alt64);
+    } else {
+        const float4 *f0 = (level_mask & MD_LEVEL_FLUID) ? s->f[0] : nullptr;
+        const float4 *f1 = (level_mask & MD_LEVEL_IFACE) ? s->f[1] : nullptr;
+        const float4 *f2 = (level_mask & MD_LEVEL_PLT) ? s->f[2] : nullptr;
+        k_export_forces<<<blocks_for(n), MSM_TPB, 0, s->stream>>>(n, f0, f1, f2, s->x32, s->tag_s,
+                                                                   (float)s->cfg.body_force, s->alt64);
+    }
     CK(cudaGetLastError(), "export forces");
     CK(cudaMemcpyAsync(f, s->alt64, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream), "download forces");
     CK(cudaStreamSynchronize(s->stream), "read_forces sync");
@@ -1057,6 +1105,7 @@ int md_mts_step(md_system *s, int64_t n_outer, const md_mts_schedule *sched)
     if (!s->have_particles) return set_error(s, MD_EINVAL, "md_mts_step: no particles");
     if (s->nb > 0 && !s->have_bonds) return set_error(s, MD_EINVAL, "md_mts_step: bonds not set");
     if (n_outer == 0) return MD_OK;
+    s->det_levels = 0;
     const int mode = sched->mode;
     const bool record = (sched->flags & MD_SCHED_RECORD) != 0;
     if (record && s->n_plt == 0) return set_error(s, MD_EINVAL, "md_mts_step: recording needs platelets");
@@ -1345,6 +1394,7 @@ int md_get_state(md_system *s, void *blob, size_t *nbytes)
 int md_set_state(md_system *s, const void *blob, size_t nbytes)
 {
     if (!s || !blob || nbytes < sizeof(blob_header)) return MD_EINVAL;
+    s->det_levels = 0;
     blob_header h;
     memcpy(&h, blob, sizeof h);
     const int64_t n = s->n;

@@ -36,6 +36,8 @@ struct pair_args {
     // AI-MTS: platelet-level pairs scaled to impulses, or skipped, per term_scale
     md_due due;
     const int32_t *tag;
+    // deterministic mode: every pair term added in 64-bit fixed point here
+    unsigned long long *fdet;
 };
 
 struct vir6 {
@@ -73,6 +75,27 @@ __device__ __forceinline__ void scatter(float4 *f, int32_t j, float fx, float fy
     atomicAdd(&f[j], make_float4(fx, fy, fz, 0.0f));
 }
 
+// Deterministic mode: a pair term in units of 2^-32 (exact scaling, rounding
+// to the nearest integer, symmetric under negation), added as a 64-bit
+// integer: the sums are independent of the order of the atomic updates, and
+// +q and -q of a pair cancel exactly.
+__device__ __forceinline__ void put_fixed(unsigned long long *f, int32_t j, float fx, float fy, float fz)
+{
+    const float s = 4294967296.0f;
+    atomicAdd(&f[3 * (int64_t)j], (unsigned long long)__float2ll_rn(fx * s));
+    atomicAdd(&f[3 * (int64_t)j + 1], (unsigned long long)__float2ll_rn(fy * s));
+    atomicAdd(&f[3 * (int64_t)j + 2], (unsigned long long)__float2ll_rn(fz * s));
+}
+
+// A pair term on i (+) and j (-), evaluated with the particle of lower id
+// first so that its FP32 value does not depend on which of the two owns the
+// list row (the minimum image rounds differently in the two orientations).
+__device__ __forceinline__ void put_pair(const pair_args &a, int32_t i, int32_t j, float px, float py, float pz)
+{
+    put_fixed(a.fdet, i, px, py, pz);
+    put_fixed(a.fdet, j, -px, -py, -pz);
+}
+
 // ---------------------------------------------------------------------------
 // K3: DPD pair forces over one list (fluid level or interface level).
 //
@@ -96,10 +119,47 @@ struct dpd_smem {
     int4 qb[DPD_WARPS][DPD_QCAP];      // j, source row (lane), id_j, id_i
 };
 
+// Eq. 1 for one pair, the particle with the lower id first (deterministic
+// mode): the pair's FP32 terms then do not depend on which particle owns the
+// list row; the cut-off is decided here too.
 template <bool VIR>
-__device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int warp, int lane, bool valid,
-                                          int slot, const philox_pre &pq, vir6 &w)
+__device__ __forceinline__ void dpd_pair_fixed(const pair_args &a, int32_t i, int32_t j, const philox_pre &pq,
+                                               vir6 &w)
 {
+    const float4 xi = a.x32[i], xj = a.x32[j];
+    const bool sw = id_of(xi) > id_of(xj);
+    const int32_t p = sw ? j : i, q = sw ? i : j;
+    const float4 xp = sw ? xj : xi, xq = sw ? xi : xj;
+    const float4 vp = a.v[p], vq = a.v[q];
+    float dx, dy, dz, vsh;
+    min_image_f32(a.geom, a.ds->le_offset_f, xp, xq, dx, dy, dz, vsh);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (!(r2 < a.rc2) || r2 == 0.0f) return;
+    const bool wall = tag_of(vp) == MD_TAG_WALL || tag_of(vq) == MD_TAG_WALL;
+    const float aij = wall ? a.a_wall : a.a_same;
+    const float inv_r = rsqrtf(r2);
+    const float wr = 1.0f - r2 * inv_r * a.inv_rc;
+    const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
+    const float edv = ex * (vp.x - vq.x - vsh) + ey * (vp.y - vq.y) + ez * (vp.z - vq.z);
+    const float zeta = pair_zeta_pre(id_of(xp), id_of(xq), pq);
+    const float fc = aij * wr;
+    const float fp = fc - a.gamma * wr * wr * edv + a.sig_isdt * wr * zeta;
+    put_pair(a, p, q, fp * ex, fp * ey, fp * ez);
+    if (VIR) w.add(dx, dy, dz, fc * inv_r);
+}
+
+template <bool VIR, bool DET>
+__device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int warp, int lane, bool valid,
+                                          int slot, const philox_pre &pq, vir6 &w, int64_t r0)
+{
+    if (DET) {
+        if (valid) {
+            const int4 b = sm.qb[warp][slot];
+            const int32_t i = a.row_idx ? a.row_idx[r0 + b.y] : (int32_t)(r0 + b.y);
+            dpd_pair_fixed<VIR>(a, i, b.x, pq, w);
+        }
+        return;
+    }
     float px = 0.f, py = 0.f, pz = 0.f;
     int src = -1;
     if (valid) {
@@ -146,7 +206,7 @@ __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int 
 // of the warp's concatenated rows is word f of the first row's slot, with the
 // row's lane in its top bits; otherwise ELL rows (the interface list) and the
 // row of an entry comes from a binary search over the rows' prefix offsets.
-template <bool VIR, bool STREAM>
+template <bool VIR, bool STREAM, bool DET = false>
 __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
 {
     __shared__ dpd_smem sm;
@@ -217,7 +277,9 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
             id_i = id_of(xi);
             min_image_f32(a.geom, delta, xi, xj_c, dx, dy, dz, vsh);
             const float r2 = dx * dx + dy * dy + dz * dz;
-            hit = r2 < a.rc2 && r2 > 0.0f;
+            // deterministic mode: a slightly wider net, the cut-off decided
+            // again in the pair's canonical orientation
+            hit = r2 < (DET ? a.rc2 * 1.000002f : a.rc2) && r2 > 0.0f;
         }
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) {
@@ -228,7 +290,7 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
         qn += __popc(m);
         __syncwarp();
         if (qn >= 32) {
-            dpd_batch<VIR>(a, sm, warp, lane, true, (qh + lane) & (DPD_QCAP - 1), pq, w);
+            dpd_batch<VIR, DET>(a, sm, warp, lane, true, (qh + lane) & (DPD_QCAP - 1), pq, w, r0);
             qh = (qh + 32) & (DPD_QCAP - 1);
             qn -= 32;
             __syncwarp();
@@ -236,9 +298,9 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
         row_c = row_n; j_c = j_n; xj_c = xj_n;
         row_n = row_nn; j_n = j_nn;
     }
-    if (qn > 0) dpd_batch<VIR>(a, sm, warp, lane, lane < qn, (qh + lane) & (DPD_QCAP - 1), pq, w);
+    if (qn > 0) dpd_batch<VIR, DET>(a, sm, warp, lane, lane < qn, (qh + lane) & (DPD_QCAP - 1), pq, w, r0);
     __syncwarp();
-    if (active && cnt > 0) {
+    if (!DET && active && cnt > 0) {
         const float4 t = sm.fi[warp][lane];
         scatter(a.f, i, t.x, t.y, t.z);
     }
@@ -273,7 +335,7 @@ struct fast_args {
 // its one or two runs of members, then the warp tests the concatenated
 // candidates 32 at a time; a few dependent loads per particle instead of one
 // per candidate.
-template <bool VIR, bool IFACE>
+template <bool VIR, bool IFACE, bool DET = false>
 __global__ void __launch_bounds__(128) k_dpd_fast(pair_args a, fast_args fa)
 {
     const int64_t nf = min((int64_t)fa.ctl[CTL_NFAST], fa.fast_max);
@@ -371,12 +433,16 @@ __global__ void __launch_bounds__(128) k_dpd_fast(pair_args a, fast_args fa)
                 float dx, dy, dz, vsh;
                 min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
                 const float r2 = dx * dx + dy * dy + dz * dz;
-                if (!(r2 < a.rc2) || r2 == 0.0f) continue;
+                if (!(r2 < (DET ? a.rc2 * 1.000002f : a.rc2)) || r2 == 0.0f) continue;
                 float ex, ey, ez, es;
                 const float4 xbj = fa.xb[j];
                 if (IFACE || j < i) min_image_f32(a.geom, dbuild, xbj, xbi, ex, ey, ez, es);
                 else min_image_f32(a.geom, dbuild, xbi, xbj, ex, ey, ez, es);
                 if (r2_f32(ex, ey, ez) < fa.cut2) continue;       // in the list
+                if (DET) {
+                    dpd_pair_fixed<VIR>(a, i, j, pq, w);
+                    continue;
+                }
                 const float4 vj = a.v[j];
                 const bool wall = tag_of(vj) == MD_TAG_WALL;
                 const float aij = wall ? a.a_wall : a.a_same;
@@ -423,8 +489,10 @@ __global__ void __launch_bounds__(MSM_TPB) k_lj(pair_args a)
                 const float sc = a.due.plt_k ? term_scale(a.due, ti, a.tag[j]) : 1.0f;
                 if (sc == 0.0f) continue;
                 const float4 xj = a.x32[j];
+                // deterministic mode: the particle of lower id first
+                const bool sw = a.fdet && id_of(xi) > id_of(xj);
                 float dx, dy, dz, vsh;
-                min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
+                min_image_f32(a.geom, delta, sw ? xj : xi, sw ? xi : xj, dx, dy, dz, vsh);
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 >= a.lj_rc2 || r2 == 0.0f) continue;
                 const float inv_r2 = 1.0f / r2;
@@ -432,11 +500,15 @@ __global__ void __launch_bounds__(MSM_TPB) k_lj(pair_args a)
                 const float s6 = s2 * s2 * s2;
                 const float fr = a.lj_eps24 * (2.0f * s6 * s6 - s6) * inv_r2 * sc;
                 const float px = fr * dx, py = fr * dy, pz = fr * dz;
-                fx += px; fy += py; fz += pz;
-                scatter(a.f, j, -px, -py, -pz);
+                if (a.fdet) {
+                    put_pair(a, sw ? j : i, sw ? i : j, px, py, pz);
+                } else {
+                    fx += px; fy += py; fz += pz;
+                    scatter(a.f, j, -px, -py, -pz);
+                }
                 if (VIR) w.add(dx, dy, dz, fr);
             }
-            scatter(a.f, i, fx, fy, fz);
+            if (!a.fdet) scatter(a.f, i, fx, fy, fz);
         }
     }
     if (VIR) flush_virial(a.vir, w);
@@ -461,8 +533,9 @@ __global__ void __launch_bounds__(MSM_TPB) k_morse(pair_args a)
                 const float sc = a.due.plt_k ? term_scale(a.due, ti, a.tag[j]) : 1.0f;
                 if (sc == 0.0f) continue;
                 const float4 xj = a.x32[j];
+                const bool sw = a.fdet && id_of(xi) > id_of(xj);
                 float dx, dy, dz, vsh;
-                min_image_f32(a.geom, delta, xi, xj, dx, dy, dz, vsh);
+                min_image_f32(a.geom, delta, sw ? xj : xi, sw ? xi : xj, dx, dy, dz, vsh);
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 >= a.m_rc2 || r2 == 0.0f) continue;
                 const float inv_r = rsqrtf(r2);
@@ -471,11 +544,15 @@ __global__ void __launch_bounds__(MSM_TPB) k_morse(pair_args a)
                 const float fm = a.m_Da_r0 * (expf(t) - expf(0.5f * t)) + a.f_A * (1.0f - rr * a.m_inv_r0);
                 const float s = fm * inv_r * sc;
                 const float px = s * dx, py = s * dy, pz = s * dz;
-                fx += px; fy += py; fz += pz;
-                scatter(a.f, j, -px, -py, -pz);
+                if (a.fdet) {
+                    put_pair(a, sw ? j : i, sw ? i : j, px, py, pz);
+                } else {
+                    fx += px; fy += py; fz += pz;
+                    scatter(a.f, j, -px, -py, -pz);
+                }
                 if (VIR) w.add(dx, dy, dz, s);
             }
-            scatter(a.f, i, fx, fy, fz);
+            if (!a.fdet) scatter(a.f, i, fx, fy, fz);
         }
     }
     if (VIR) flush_virial(a.vir, w);
@@ -486,7 +563,7 @@ template <bool VIR>
 __global__ void __launch_bounds__(MSM_TPB) k_bonds(int64_t nb, const int32_t *__restrict__ ij,
                                                   const float *__restrict__ r0, float kb2, const float4 *__restrict__ x32,
                                                   float4 *f, md_geom geom, const md_dstate *ds, double *vir, md_due due,
-                                                  const int32_t *tag)
+                                                  const int32_t *tag, unsigned long long *fdet)
 {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     vir6 w = {0, 0, 0, 0, 0, 0};
@@ -501,8 +578,13 @@ __global__ void __launch_bounds__(MSM_TPB) k_bonds(int64_t nb, const int32_t *__
             const float inv_r = rsqrtf(r2);
             const float rr = r2 * inv_r;
             const float s = -kb2 * (rr - r0[b]) * inv_r * sc;
-            scatter(f, i, s * dx, s * dy, s * dz);
-            scatter(f, j, -s * dx, -s * dy, -s * dz);
+            if (fdet) {     // a bond's orientation is fixed by its definition
+                put_fixed(fdet, i, s * dx, s * dy, s * dz);
+                put_fixed(fdet, j, -s * dx, -s * dy, -s * dz);
+            } else {
+                scatter(f, i, s * dx, s * dy, s * dz);
+                scatter(f, j, -s * dx, -s * dy, -s * dz);
+            }
             if (VIR) w.add(dx, dy, dz, s);
         }
     }
@@ -534,6 +616,23 @@ static fast_args fast_for(md_system *s, const md_grid &g, const int32_t *members
 }
 
 // pair_args of the DPD levels (the fields the pair kernels read)
+// Deterministic mode: a level's fixed-point sums to its FP32 buffer.
+__global__ void k_fixed_to_f4(int64_t n, const unsigned long long *__restrict__ q, float4 *f)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double u = 1.0 / 4294967296.0;
+    f[k] = make_float4((float)((double)(long long)q[3 * k] * u), (float)((double)(long long)q[3 * k + 1] * u),
+                       (float)((double)(long long)q[3 * k + 2] * u), 0.0f);
+}
+
+cudaError_t launch_fixed_to_f4(md_system *s, const unsigned long long *q, float4 *f)
+{
+    k_fixed_to_f4<<<blocks_for(s->n), MSM_TPB, 0, s->stream>>>(s->n, q, f);
+    MSM_COUNT(s, 1);
+    return cudaGetLastError();
+}
+
 static pair_args dpd_args(md_system *s)
 {
     const md_config &c = s->cfg;
@@ -548,20 +647,25 @@ static pair_args dpd_args(md_system *s)
     a.inv_rc = (float)(1.0 / c.rc);
     a.vir = s->vir_acc;
     a.tag = s->tag_s;
+    a.fdet = nullptr;
     return a;
 }
 
-cudaError_t launch_fast_pairs(md_system *s, unsigned level_mask, float4 *const out[3], bool virial)
+cudaError_t launch_fast_pairs(md_system *s, unsigned level_mask, float4 *const out[3], bool virial,
+                              unsigned long long *fdet)
 {
     const md_config &c = s->cfg;
     pair_args a = dpd_args(s);
+    a.fdet = fdet;
     if (level_mask & MD_LEVEL_FLUID) {
         a.f = out[0];
         a.a_same = (float)c.a_ff;
         a.a_wall = (float)c.a_fw;
         a.sig_isdt = (float)(c.sigma / sqrt(c.dt));
         const fast_args fa = fast_for(s, s->gmain, nullptr, s->cut2[MD_LIST_FLUID]);
-        if (virial) k_dpd_fast<true, false><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
+        if (fdet && virial) k_dpd_fast<true, false, true><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
+        else if (fdet) k_dpd_fast<false, false, true><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
+        else if (virial) k_dpd_fast<true, false><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
         else k_dpd_fast<false, false><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
         MSM_COUNT(s, 1);
     }
@@ -572,17 +676,21 @@ cudaError_t launch_fast_pairs(md_system *s, unsigned level_mask, float4 *const o
         a.a_wall = (float)c.a_fp;
         a.sig_isdt = (float)(c.sigma / sqrt(c.dt / km));
         const fast_args fa = fast_for(s, s->gplt, s->plt_sorted, s->cut2[MD_LIST_IFACE]);
-        if (virial) k_dpd_fast<true, true><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
+        if (fdet && virial) k_dpd_fast<true, true, true><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
+        else if (fdet) k_dpd_fast<false, true, true><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
+        else if (virial) k_dpd_fast<true, true><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
         else k_dpd_fast<false, true><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
         MSM_COUNT(s, 1);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3], bool virial, bool with_fast)
+cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3], bool virial, bool with_fast,
+                          unsigned long long *fdet)
 {
     const md_config &c = s->cfg;
     pair_args a;
+    a.fdet = fdet;
     a.x32 = s->x32;
     a.v = s->v;
     a.geom = s->geom;
@@ -617,7 +725,9 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
         a.a_same = (float)c.a_ff;
         a.a_wall = (float)c.a_fw;
         a.sig_isdt = (float)(c.sigma / sqrt(c.dt));
-        if (virial) k_dpd<true, true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        if (fdet && virial) k_dpd<true, true, true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        else if (fdet) k_dpd<false, true, true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        else if (virial) k_dpd<true, true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
         else k_dpd<false, true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
         MSM_COUNT(s, 1);
     }
@@ -631,7 +741,9 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
         a.a_same = (float)c.a_fp;
         a.a_wall = (float)c.a_fp;
         a.sig_isdt = (float)(c.sigma / sqrt(c.dt / km));
-        if (virial) k_dpd<true, false><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        if (fdet && virial) k_dpd<true, false, true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        else if (fdet) k_dpd<false, false, true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
+        else if (virial) k_dpd<true, false><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
         else k_dpd<false, false><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
         MSM_COUNT(s, 1);
     }
@@ -640,11 +752,13 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
             if (virial)
                 k_bonds<true><<<blocks_for(s->nb), MSM_TPB, 0, s->stream>>>(s->nb, s->bond_ij, s->bond_r0,
                                                                            (float)(2.0 * c.k_bond), s->x32, out[2],
-                                                                           s->geom, s->ds, s->vir_acc, a.due, s->tag_s);
+                                                                           s->geom, s->ds, s->vir_acc, a.due, s->tag_s,
+                                                                           a.fdet);
             else
                 k_bonds<false><<<blocks_for(s->nb), MSM_TPB, 0, s->stream>>>(s->nb, s->bond_ij, s->bond_r0,
                                                                             (float)(2.0 * c.k_bond), s->x32, out[2],
-                                                                            s->geom, s->ds, s->vir_acc, a.due, s->tag_s);
+                                                                            s->geom, s->ds, s->vir_acc, a.due, s->tag_s,
+                                                                           a.fdet);
         }
         a.rows = s->n_plt;
         a.row_idx = s->plt_sorted;
@@ -667,6 +781,6 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && with_fast && (level_mask & (MD_LEVEL_FLUID | MD_LEVEL_IFACE)))
-        e = launch_fast_pairs(s, level_mask, out, virial);
+        e = launch_fast_pairs(s, level_mask, out, virial, fdet);
     return e;
 }

@@ -82,6 +82,9 @@ struct md_system {
     int32_t *fast_idx;           // [fast_max] slots
     uint32_t *fast_flag;         // [n] == ds->fast_stamp: listed now
     int64_t fast_max;
+    // deterministic mode (MD_FORCE_DETERMINISTIC): fixed-point sums per level
+    unsigned long long *fdet[3];  // [3 n] each
+    unsigned det_levels = 0;      // levels of the last deterministic md_forces (0: none current)
     int32_t *tag_s;              // tags in sorted order
     int32_t *cellid, *slot, *perm, *pos_of_id;
     double *alt64;               // 3n
@@ -505,11 +508,16 @@ cudaError_t launch_scan(md_system *s, const int32_t *in, int32_t *out, int64_t c
 // neighbor.cu
 cudaError_t launch_build_lists(md_system *s, const int32_t *gate);
 // forces.cu
-// with_fast: also the fast-particle pass of the DPD levels (launch_fast_pairs)
+// with_fast: also the fast-particle pass of the DPD levels (launch_fast_pairs);
+// fdet: deterministic mode, every pair term added to these 64-bit fixed-point
+// sums (3 per particle, units of 2^-32) instead of out
 cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3], bool virial,
-                          bool with_fast = true);
+                          bool with_fast = true, unsigned long long *fdet = nullptr);
 // pairs of the listed fast plasma particles that the plasma / interface lists lack
-cudaError_t launch_fast_pairs(md_system *s, unsigned level_mask, float4 *const out[3], bool virial);
+cudaError_t launch_fast_pairs(md_system *s, unsigned level_mask, float4 *const out[3], bool virial,
+                              unsigned long long *fdet = nullptr);
+// a level's fixed-point sums to its FP32 buffer
+cudaError_t launch_fixed_to_f4(md_system *s, const unsigned long long *q, float4 *f);
 // integrate.cu
 cudaError_t launch_kick_drift(md_system *s, const float h[3], int kick_which, double dt, int drift_which,
                               unsigned zero_levels, bool plt_rows);

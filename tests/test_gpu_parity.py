@@ -157,6 +157,30 @@ def test_net_force_vanishes(plt_sys):
     assert np.abs(f.sum(0)).max() < 1e-5 * np.abs(f).sum()
 
 
+@pytest.mark.parametrize("which", ["le", "walls"])
+def test_deterministic_forces(plt_sys, plt_wall_sys, which):
+    """MD_FORCE_DETERMINISTIC: the forces of every level equal the oracle's,
+    are bit-identical between two systems built from the same state (their
+    particle orders differ: the cell sort places particles by atomics), and,
+    without walls or body force, add up to exactly zero (every pair term
+    cancels in 64-bit fixed point)."""
+    s = plt_sys if which == "le" else plt_wall_sys
+    g1 = make_gpu(s, step0=5)
+    g2 = make_gpu(s, step0=5)
+    _, _, x32 = g1.read_particles()
+    g1.forces(deterministic=True)
+    g2.forces(deterministic=True)
+    f1, f2 = g1.read_forces(), g2.read_forces()
+    assert np.array_equal(f1, f2)
+    fo, _ = oracle_forces(s, x32, s.v, 5)
+    assert_force_parity(f1, fo)
+    if which == "le":
+        assert np.all(f1.sum(0) == 0.0), f1.sum(0)
+    # the default mode agrees to FP32 summation order
+    g1.forces()
+    assert_force_parity(g1.read_forces(), fo)
+
+
 def test_virial_and_kinetics_match_oracle(plt_sys):
     s = plt_sys
     g = make_gpu(s, step0=4)
