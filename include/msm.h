@@ -49,6 +49,15 @@ extern "C" {
 /* ---- configuration flags ----------------------------------------------- */
 #define MD_CFG_WALLS        1  /* frozen wall layers outside y in [0,Ly], bounce-back */
 #define MD_CFG_LEES_EDWARDS 2  /* sliding periodic images in y at shear_rate       */
+#define MD_CFG_MORSE_STANDARD 4 /* morse_alpha is the standard form's range a, U =
+                                   D [e^(-2a(r-r0)) - 2 e^(-a(r-r0))]: the printed
+                                   form of Eq. 2 with alpha = 2 a r0 (default: the
+                                   printed form's alpha)                             */
+#define MD_CFG_IFACE_LJ     8  /* Eq. 3 with an LJ conservative term: the plasma-
+                                   platelet conservative force is the LJ (lj_eps,
+                                   lj_sigma) cut at its minimum 2^(1/6) lj_sigma
+                                   instead of a_fp (1 - r/rc); dissipative and random
+                                   parts as Eq. 1                                     */
 
 /* ---- neighbour-list kinds ---------------------------------------------- */
 #define MD_LIST_FLUID 0  /* plasma-plasma, plasma-wall (half list)             */

@@ -55,6 +55,11 @@ typedef struct {
      * ratios, max(k_i, k_j), equals lvl_k */
     const int32_t *plt_k;
     int32_t lvl_k;
+    /* Eq. 3 read with an LJ conservative term (the selectable variant): the
+     * plasma-platelet conservative force is LJ(lj_eps, lj_sigma) cut at its
+     * minimum 2^(1/6) lj_sigma (purely repulsive, shifted to zero there)
+     * instead of a_fp (1 - r/rc); dissipative and random parts as Eq. 1 */
+    int32_t iface_lj;
 } orc_params;
 
 static int term_selected(const orc_params *p, int32_t ti, int32_t tj)
@@ -262,11 +267,16 @@ static int pair_force(const pair_ctx *c, int32_t i, int32_t j, double *F, double
         double fc, fd, fr;
         dpd_parts(a, p->gamma, p->sigma, p->rc, r, edotv, zeta, iface ? c->isdt_m : c->isdt_f,
                   &fc, &fd, &fr);
+        double w = 1.0 - r / p->rc;
+        *u = 0.5 * a * p->rc * w * w;
+        if (iface && p->iface_lj) {
+            const double rmin = pow(2.0, 1.0 / 6.0) * p->lj_sigma;
+            fc = r < rmin ? lj_force(p->lj_eps, p->lj_sigma, r) : 0.0;
+            *u = r < rmin ? lj_energy(p->lj_eps, p->lj_sigma, r) + p->lj_eps : 0.0;
+        }
         double f = fc + fd + fr;
         F[0] = f * ex; F[1] = f * ey; F[2] = f * ez;
         Fc[0] = fc * ex; Fc[1] = fc * ey; Fc[2] = fc * ez;
-        double w = 1.0 - r / p->rc;
-        *u = 0.5 * a * p->rc * w * w;
         return 1;
     }
     /* platelet-platelet: LJ (Eq. 2) with the rest-distance exclusion, Morse +

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 MD_OK = 0
 MD_LEVEL_FLUID, MD_LEVEL_IFACE, MD_LEVEL_PLT, MD_LEVEL_ALL = 1, 2, 4, 7
-MD_CFG_WALLS, MD_CFG_LEES_EDWARDS = 1, 2
+MD_CFG_WALLS, MD_CFG_LEES_EDWARDS, MD_CFG_MORSE_STANDARD, MD_CFG_IFACE_LJ = 1, 2, 4, 8
 MD_LIST_FLUID, MD_LIST_IFACE, MD_LIST_LJ, MD_LIST_MORSE = 0, 1, 2, 3
 MD_FORCE_VIRIAL = 1
 MD_FORCE_DETERMINISTIC = 2
@@ -172,8 +172,9 @@ def _ip(a):
 
 
 def config_for(n, box, tag=None, n_bonds=0, walls=False, wall=1.0, shear_rate=0.0, body_force=0.0, dt=0.01,
-               skin=0.3, seed=20220528, caps=None, **params):
-    """md_config for n particles (counts of platelet / receptor particles from tag)."""
+               skin=0.3, seed=20220528, caps=None, flags=0, **params):
+    """md_config for n particles (counts of platelet / receptor particles from tag);
+    flags: extra MD_CFG_* bits (MD_CFG_MORSE_STANDARD, MD_CFG_IFACE_LJ)."""
     cfg = md_config()
     cfg.n = int(n)
     for k in range(3):
@@ -188,7 +189,8 @@ def config_for(n, box, tag=None, n_bonds=0, walls=False, wall=1.0, shear_rate=0.
         cfg.n_plt_particles = int(plt.sum())
         cfg.n_receptors = int((plt & ((t & RECEPTOR_BIT) != 0)).sum())
         cfg.n_platelets = int(((t[plt] & ~RECEPTOR_BIT).max() + 1) if plt.any() else 0)
-    cfg.flags = (MD_CFG_WALLS if walls else 0) | (MD_CFG_LEES_EDWARDS if (shear_rate and not walls) else 0)
+    cfg.flags = ((MD_CFG_WALLS if walls else 0) | (MD_CFG_LEES_EDWARDS if (shear_rate and not walls) else 0) |
+                 int(flags))
     cfg.wall = float(wall)
     cfg.shear_rate = float(shear_rate)
     cfg.body_force = float(body_force)

@@ -38,7 +38,24 @@ struct pair_args {
     const int32_t *tag;
     // deterministic mode: every pair term added in 64-bit fixed point here
     unsigned long long *fdet;
+    // interface level, Eq. 3 with an LJ conservative term (MD_CFG_IFACE_LJ):
+    // 24 eps / s^2 and s^2 of the LJ, cut at its minimum (wca_rc2 0: off)
+    float wca_eps24, wca_sig2, wca_rc2;
 };
+
+// Conservative part of a DPD-level pair: a (1 - r/rc), or on the interface
+// level the repulsive LJ when selected (force magnitude along e_ij)
+template <bool IF>
+__device__ __forceinline__ float dpd_conservative(const pair_args &a, float aij, float wr, float r2, float inv_r)
+{
+    if (IF && a.wca_rc2 > 0.0f) {
+        if (!(r2 < a.wca_rc2)) return 0.0f;
+        const float s2 = a.wca_sig2 / r2;
+        const float s6 = s2 * s2 * s2;
+        return a.wca_eps24 * (2.0f * s6 * s6 - s6) * inv_r;
+    }
+    return aij * wr;
+}
 
 struct vir6 {
     float xx, yy, zz, xy, xz, yz;
@@ -122,7 +139,7 @@ struct dpd_smem {
 // Eq. 1 for one pair, the particle with the lower id first (deterministic
 // mode): the pair's FP32 terms then do not depend on which particle owns the
 // list row; the cut-off is decided here too.
-template <bool VIR>
+template <bool VIR, bool IF>
 __device__ __forceinline__ void dpd_pair_fixed(const pair_args &a, int32_t i, int32_t j, const philox_pre &pq,
                                                vir6 &w)
 {
@@ -142,13 +159,13 @@ __device__ __forceinline__ void dpd_pair_fixed(const pair_args &a, int32_t i, in
     const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
     const float edv = ex * (vp.x - vq.x - vsh) + ey * (vp.y - vq.y) + ez * (vp.z - vq.z);
     const float zeta = pair_zeta_pre(id_of(xp), id_of(xq), pq);
-    const float fc = aij * wr;
+    const float fc = dpd_conservative<IF>(a, aij, wr, r2, inv_r);
     const float fp = fc - a.gamma * wr * wr * edv + a.sig_isdt * wr * zeta;
     put_pair(a, p, q, fp * ex, fp * ey, fp * ez);
     if (VIR) w.add(dx, dy, dz, fc * inv_r);
 }
 
-template <bool VIR, bool DET>
+template <bool VIR, bool DET, bool IF>
 __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int warp, int lane, bool valid,
                                           int slot, const philox_pre &pq, vir6 &w, int64_t r0)
 {
@@ -156,7 +173,7 @@ __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int 
         if (valid) {
             const int4 b = sm.qb[warp][slot];
             const int32_t i = a.row_idx ? a.row_idx[r0 + b.y] : (int32_t)(r0 + b.y);
-            dpd_pair_fixed<VIR>(a, i, b.x, pq, w);
+            dpd_pair_fixed<VIR, IF>(a, i, b.x, pq, w);
         }
         return;
     }
@@ -176,7 +193,7 @@ __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int 
         const float ex = q.x * inv_r, ey = q.y * inv_r, ez = q.z * inv_r;
         const float edv = ex * (vi.x - vj.x - q.w) + ey * (vi.y - vj.y) + ez * (vi.z - vj.z);
         const float zeta = pair_zeta_pre((uint32_t)b.w, (uint32_t)b.z, pq);
-        const float fc = aij * wr;
+        const float fc = dpd_conservative<IF>(a, aij, wr, r2, inv_r);
         const float fp = fc - a.gamma * wr * wr * edv + a.sig_isdt * wr * zeta;
         px = fp * ex; py = fp * ey; pz = fp * ez;
         scatter(a.f, b.x, -px, -py, -pz);
@@ -290,7 +307,7 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
         qn += __popc(m);
         __syncwarp();
         if (qn >= 32) {
-            dpd_batch<VIR, DET>(a, sm, warp, lane, true, (qh + lane) & (DPD_QCAP - 1), pq, w, r0);
+            dpd_batch<VIR, DET, !STREAM>(a, sm, warp, lane, true, (qh + lane) & (DPD_QCAP - 1), pq, w, r0);
             qh = (qh + 32) & (DPD_QCAP - 1);
             qn -= 32;
             __syncwarp();
@@ -298,7 +315,7 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
         row_c = row_n; j_c = j_n; xj_c = xj_n;
         row_n = row_nn; j_n = j_nn;
     }
-    if (qn > 0) dpd_batch<VIR, DET>(a, sm, warp, lane, lane < qn, (qh + lane) & (DPD_QCAP - 1), pq, w, r0);
+    if (qn > 0) dpd_batch<VIR, DET, !STREAM>(a, sm, warp, lane, lane < qn, (qh + lane) & (DPD_QCAP - 1), pq, w, r0);
     __syncwarp();
     if (!DET && active && cnt > 0) {
         const float4 t = sm.fi[warp][lane];
@@ -440,7 +457,7 @@ __global__ void __launch_bounds__(128) k_dpd_fast(pair_args a, fast_args fa)
                 else min_image_f32(a.geom, dbuild, xbi, xbj, ex, ey, ez, es);
                 if (r2_f32(ex, ey, ez) < fa.cut2) continue;       // in the list
                 if (DET) {
-                    dpd_pair_fixed<VIR>(a, i, j, pq, w);
+                    dpd_pair_fixed<VIR, IFACE>(a, i, j, pq, w);
                     continue;
                 }
                 const float4 vj = a.v[j];
@@ -451,7 +468,7 @@ __global__ void __launch_bounds__(128) k_dpd_fast(pair_args a, fast_args fa)
                 const float nx = dx * inv_r, ny_ = dy * inv_r, nz = dz * inv_r;
                 const float edv = nx * (vi.x - vj.x - vsh) + ny_ * (vi.y - vj.y) + nz * (vi.z - vj.z);
                 const float zeta = pair_zeta_pre(idi, id_of(xj), pq);
-                const float fc = aij * wr;
+                const float fc = dpd_conservative<IFACE>(a, aij, wr, r2, inv_r);
                 const float fp = fc - a.gamma * wr * wr * edv + a.sig_isdt * wr * zeta;
                 const float px = fp * nx, py = fp * ny_, pz = fp * nz;
                 fx += px; fy += py; fz += pz;
@@ -616,6 +633,17 @@ static fast_args fast_for(md_system *s, const md_grid &g, const int32_t *members
 }
 
 // pair_args of the DPD levels (the fields the pair kernels read)
+// The interface level's LJ conservative term when MD_CFG_IFACE_LJ selects it.
+static void set_wca(md_system *s, pair_args &a, bool iface)
+{
+    const md_config &c = s->cfg;
+    const bool on = iface && (c.flags & MD_CFG_IFACE_LJ);
+    const double rmin = pow(2.0, 1.0 / 6.0) * c.lj_sigma;
+    a.wca_eps24 = (float)(24.0 * c.lj_eps);
+    a.wca_sig2 = (float)(c.lj_sigma * c.lj_sigma);
+    a.wca_rc2 = on ? (float)(rmin * rmin) : 0.0f;
+}
+
 // Deterministic mode: a level's fixed-point sums to its FP32 buffer.
 __global__ void k_fixed_to_f4(int64_t n, const unsigned long long *__restrict__ q, float4 *f)
 {
@@ -648,6 +676,7 @@ static pair_args dpd_args(md_system *s)
     a.vir = s->vir_acc;
     a.tag = s->tag_s;
     a.fdet = nullptr;
+    set_wca(s, a, false);
     return a;
 }
 
@@ -675,6 +704,7 @@ cudaError_t launch_fast_pairs(md_system *s, unsigned level_mask, float4 *const o
         a.a_same = (float)c.a_fp;
         a.a_wall = (float)c.a_fp;
         a.sig_isdt = (float)(c.sigma / sqrt(c.dt / km));
+        set_wca(s, a, true);
         const fast_args fa = fast_for(s, s->gplt, s->plt_sorted, s->cut2[MD_LIST_IFACE]);
         if (fdet && virial) k_dpd_fast<true, true, true><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
         else if (fdet) k_dpd_fast<false, true, true><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
@@ -702,8 +732,11 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
     a.lj_eps24 = (float)(24.0 * c.lj_eps);
     a.lj_sig2 = (float)(c.lj_sigma * c.lj_sigma);
     a.lj_rc2 = (float)(c.lj_rc * c.lj_rc);
-    a.m_Da_r0 = (float)(c.morse_D * c.morse_alpha / c.morse_r0);
-    a.m_alpha = (float)c.morse_alpha;
+    // the printed form's alpha; MD_CFG_MORSE_STANDARD gives the standard
+    // form's range a, and the printed form with alpha = 2 a r0 is the same curve
+    const double m_alpha = (c.flags & MD_CFG_MORSE_STANDARD) ? 2.0 * c.morse_alpha * c.morse_r0 : c.morse_alpha;
+    a.m_Da_r0 = (float)(c.morse_D * m_alpha / c.morse_r0);
+    a.m_alpha = (float)m_alpha;
     a.m_inv_r0 = (float)(1.0 / c.morse_r0);
     a.m_rc2 = (float)(c.morse_rc * c.morse_rc);
     a.f_A = (float)c.f_A;
@@ -714,6 +747,7 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
     a.due.K = s->plt_K;
     a.due.dtm = (float)s->due_dtm;
     const int km = s->cfg_k_m > 0 ? s->cfg_k_m : 1;
+    set_wca(s, a, false);
 
     if (level_mask & MD_LEVEL_FLUID) {
         a.rows = s->n;
@@ -741,6 +775,7 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
         a.a_same = (float)c.a_fp;
         a.a_wall = (float)c.a_fp;
         a.sig_isdt = (float)(c.sigma / sqrt(c.dt / km));
+        set_wca(s, a, true);
         if (fdet && virial) k_dpd<true, false, true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
         else if (fdet) k_dpd<false, false, true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
         else if (virial) k_dpd<true, false><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);

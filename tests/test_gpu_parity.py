@@ -35,8 +35,8 @@ def le_offset_f32(s, step, dt=0.01):
     return float(np.float32((s.shear_rate * s.box[1] * step * dt) % s.box[0]))
 
 
-def oracle_forces(s, x32, v, step, level_mask=O.LVL_ALL, dt=0.01, dt_m=None):
-    p = O.system_params(s, le_offset=le_offset_f32(s, step, dt))
+def oracle_forces(s, x32, v, step, level_mask=O.LVL_ALL, dt=0.01, dt_m=None, **kw):
+    p = O.system_params(s, le_offset=le_offset_f32(s, step, dt), **kw)
     f, acc = O.forces_brute(p, f32(x32), f32(v), s.tag, X0=f32(s.X0), bonds=s.bonds, r0=f32(s.r0),
                             level_mask=level_mask, n_time=step, dt=dt, dt_m=dt_m)
     return f, acc
@@ -136,6 +136,26 @@ def test_forces_match_oracle_all_levels(plt_sys):
         fg = g.read_forces(mask)
         fo, _ = oracle_forces(s, x32, s.v, 5, level_mask=mask)
         assert_force_parity(fg, fo)
+
+
+def test_force_variants_match_oracle(plt_sys):
+    """The readings' selectable variants: Eq. 3 with the repulsive LJ as the
+    interface's conservative term (MD_CFG_IFACE_LJ), and the Morse term of
+    Eq. 2 given by the standard form's range a = 1.5 (MD_CFG_MORSE_STANDARD:
+    the printed form with alpha = 2 a r0 = 3)."""
+    import paper_2205_14121_gb300 as M
+    from paper_2205_14121_gb300._binding import MD_CFG_IFACE_LJ, MD_CFG_MORSE_STANDARD
+    s = plt_sys
+    g = make_gpu(s, step0=5, flags=MD_CFG_IFACE_LJ | MD_CFG_MORSE_STANDARD, morse_alpha=1.5)
+    _, _, x32 = g.read_particles()
+    g.forces()
+    fo_i, _ = oracle_forces(s, x32, s.v, 5, level_mask=O.LVL_IFACE, iface_lj=True)
+    assert_force_parity(g.read_forces(M.MD_LEVEL_IFACE), fo_i)
+    fo_p, _ = oracle_forces(s, x32, s.v, 5, level_mask=O.LVL_PLT, m_alpha=3.0)
+    assert_force_parity(g.read_forces(M.MD_LEVEL_PLT), fo_p)
+    # the variants change the forces: not the default's
+    fd_i, _ = oracle_forces(s, x32, s.v, 5, level_mask=O.LVL_IFACE)
+    assert np.abs(fd_i - fo_i).max() > 1.0
 
 
 def test_forces_walls_body_force(wall_sys):

@@ -36,6 +36,26 @@ def test_dpd_conservative_matches_eq1_at_points(r):
     assert np.all(f == 0.0)
 
 
+@pytest.mark.parametrize("r", [0.7, 0.85, 0.95])
+def test_interface_lj_variant_is_repulsive_lj(r):
+    """Eq. 3 read with an LJ conservative term (the selectable variant): the
+    plasma-platelet conservative force is 24 eps [2 (s/r)^12 - (s/r)^6] / r
+    (eps 1, s 0.8) below the LJ minimum 2^(1/6) s and zero beyond it, and its
+    energy the LJ potential shifted up by eps; the default reading gives
+    a_fp (1 - r/rc) with a_fp = 50."""
+    x, v, tag = two_body(r, tags=(-1, 0))
+    p = O.make_params((10, 10, 10), gamma=0.0, sigma=0.0, iface_lj=True)
+    f, acc = O.forces_brute(p, x, v, tag, X0=x)
+    s6 = (0.8 / r) ** 6
+    inside = r < 2.0 ** (1.0 / 6.0) * 0.8
+    assert f[0, 0] == pytest.approx(24.0 * (2.0 * s6 * s6 - s6) / r if inside else 0.0, rel=1e-12, abs=1e-14)
+    assert f[1, 0] == -f[0, 0]
+    assert acc["epot"] == pytest.approx(4.0 * (s6 * s6 - s6) + 1.0 if inside else 0.0, rel=1e-12, abs=1e-14)
+    p0 = O.make_params((10, 10, 10), gamma=0.0, sigma=0.0)
+    f0, _ = O.forces_brute(p0, x, v, tag, X0=x)
+    assert f0[0, 0] == pytest.approx(50.0 * (1.0 - r), rel=1e-13)
+
+
 def test_dpd_conservative_is_minus_gradient_of_energy():
     """F^C = -dU/dr with U = (a rc / 2)(1 - r/rc)^2 -- central difference of the
     oracle's potential energy, a separate code path from its force."""
