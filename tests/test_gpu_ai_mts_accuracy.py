@@ -2,7 +2,8 @@
 flow profile and the per-platelet stresses of AI-MTS (dt_f = 0.01, ratios
 from the trained controller) agree with fine-step STS (dt = 0.001 for every
 particle) within the spread between two fine-step runs that differ only in
-their noise realisation."""
+their noise realisation; temperature and pressure within the paper's 0.7% and
+1.2% of the fine-step mean."""
 import os
 
 import numpy as np
@@ -26,6 +27,10 @@ def sample(g, acc):
     f = g.platelet_features()
     acc["prof"].append(mean)
     acc["stress"].append(f[:, 6:9])
+    g.forces(virial=True)
+    o = g.observables()
+    acc["T"].append(o["temperature"])
+    acc["P"].append(o["pressure"])
 
 
 def test_ai_mts_matches_fine_step_sts():
@@ -41,7 +46,7 @@ def test_ai_mts_matches_fine_step_sts():
     def fine(seed):
         g = M.System(s.box, x0, v0, s.tag, dt=0.001, seed=seed, **kw)
         g.mts_step(1280)                                   # the AI arm's first window
-        acc = {"prof": [], "stress": []}
+        acc = {"prof": [], "stress": [], "T": [], "P": []}
         for _ in range(60):
             g.mts_step(50)
             sample(g, acc)
@@ -55,7 +60,7 @@ def test_ai_mts_matches_fine_step_sts():
     windows, _ = g.read_feature_ring()
     k, _, _ = A.decide(ctl.predict(windows), windows, trust)
     g.set_platelet_levels(k)
-    ai = {"prof": [], "stress": []}
+    ai = {"prof": [], "stress": [], "T": [], "P": []}
     for _ in range(60):
         g.mts_step(5, mode=M.MD_MODE_AI, k_m=1)
         sample(g, ai)
@@ -72,8 +77,16 @@ def test_ai_mts_matches_fine_step_sts():
     err_p = np.linalg.norm(pa - p1) / np.linalg.norm(p1)
     noise_s = np.abs(s2 - s1).max() / np.abs(s1).max()
     err_s = np.abs(sa - s1).max() / np.abs(s1).max()
+    T = [np.mean(a["T"]) for a in (f1, f2, ai)]
+    P = [np.mean(a["P"]) for a in (f1, f2, ai)]
     print(dict(k=k.tolist(), vmax=vmax, profile_err=err_p, profile_noise=noise_p, stress_err=err_s,
-               stress_noise=noise_s))
+               stress_noise=noise_s, T=T, P=P))
     assert vmax > 0.05                                  # the channel flows
     assert err_p <= 3.0 * noise_p + 0.005
     assert err_s <= 3.0 * noise_s + 0.005
+    # temperature and pressure against the fine-step mean: within the paper's
+    # 0.7% and 1.2% (Sec. 4.2), or twice the spread of the two fine runs
+    # where the noise of this short average is larger
+    tf, pf = 0.5 * (T[0] + T[1]), 0.5 * (P[0] + P[1])
+    assert abs(T[2] - tf) <= max(0.007 * tf, 2.0 * abs(T[0] - T[1]))
+    assert abs(P[2] - pf) <= max(0.012 * abs(pf), 2.0 * abs(P[0] - P[1]))
