@@ -58,6 +58,13 @@ extern "C" {
                                    lj_sigma) cut at its minimum 2^(1/6) lj_sigma
                                    instead of a_fp (1 - r/rc); dissipative and random
                                    parts as Eq. 1                                     */
+#define MD_CFG_UNIFORM_NOISE 16 /* zeta_ij of Eq. 1 / Eq. 3 as a uniform variate of
+                                   zero mean and unit variance, sqrt(3) (2u - 1) with
+                                   u = (b + 1/2) 2^-24 from the top 24 bits b of the
+                                   pair's first Philox word, instead of the normal
+                                   variate the paper names (a speed option: the
+                                   fluctuation-dissipation balance needs only the
+                                   first two moments)                                 */
 
 /* ---- neighbour-list kinds ---------------------------------------------- */
 #define MD_LIST_FLUID 0  /* plasma-plasma, plasma-wall (half list)             */

@@ -44,6 +44,7 @@ class Params(C.Structure):
         ("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32),
         ("plt_k", C.POINTER(C.c_int32)), ("lvl_k", C.c_int32),
         ("iface_lj", C.c_int32),
+        ("uniform_noise", C.c_int32),
     ]
 
 
@@ -64,6 +65,7 @@ def make_params(box, walls=False, le_rate=0.0, le_offset=0.0, g=0.0, seed=202205
     d = dict(DEFAULTS)
     d.update(kw)
     p.iface_lj = int(bool(d.pop("iface_lj", False)))
+    p.uniform_noise = int(bool(d.pop("uniform_noise", False)))
     for k, v in d.items():
         setattr(p, k, float(v))
     p.seed_lo = seed & 0xFFFFFFFF

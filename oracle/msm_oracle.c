@@ -60,6 +60,11 @@ typedef struct {
      * minimum 2^(1/6) lj_sigma (purely repulsive, shifted to zero there)
      * instead of a_fp (1 - r/rc); dissipative and random parts as Eq. 1 */
     int32_t iface_lj;
+    /* zeta read as any variate of zero mean and unit variance (the
+     * fluctuation-dissipation balance of Eq. 1 fixes only these two moments),
+     * the selectable speed option: the uniform variate sqrt(3) (2u - 1), u the
+     * midpoint of the 2^-24 bin given by the top 24 bits of the first word */
+    int32_t uniform_noise;
 } orc_params;
 
 static int term_selected(const orc_params *p, int32_t ti, int32_t tj)
@@ -102,6 +107,13 @@ double orc_gauss_from_bits(uint32_t r0, uint32_t r1)
     return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
 }
 
+/* Uniform variate of zero mean and unit variance on the top 24 bits of one word. */
+double orc_uniform_from_bits(uint32_t r0)
+{
+    double u = ((double)(r0 >> 8) + 0.5) / 16777216.0;
+    return sqrt(3.0) * (2.0 * u - 1.0);
+}
+
 double orc_zeta(const orc_params *p, int32_t id_i, int32_t id_j, uint32_t n_time, uint32_t c_sub)
 {
     uint32_t a = (uint32_t)(id_i < id_j ? id_i : id_j);
@@ -110,6 +122,7 @@ double orc_zeta(const orc_params *p, int32_t id_i, int32_t id_j, uint32_t n_time
     uint32_t key[2] = {p->seed_lo, p->seed_hi};
     uint32_t r[4];
     orc_philox4x32_10(ctr, key, r);
+    if (p->uniform_noise) return orc_uniform_from_bits(r[0]);
     return orc_gauss_from_bits(r[0], r[1]);
 }
 

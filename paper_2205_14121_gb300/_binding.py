@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 MD_OK = 0
 MD_LEVEL_FLUID, MD_LEVEL_IFACE, MD_LEVEL_PLT, MD_LEVEL_ALL = 1, 2, 4, 7
 MD_CFG_WALLS, MD_CFG_LEES_EDWARDS, MD_CFG_MORSE_STANDARD, MD_CFG_IFACE_LJ = 1, 2, 4, 8
+MD_CFG_UNIFORM_NOISE = 16
 MD_LIST_FLUID, MD_LIST_IFACE, MD_LIST_LJ, MD_LIST_MORSE = 0, 1, 2, 3
 MD_FORCE_VIRIAL = 1
 MD_FORCE_DETERMINISTIC = 2
@@ -174,7 +175,8 @@ def _ip(a):
 def config_for(n, box, tag=None, n_bonds=0, walls=False, wall=1.0, shear_rate=0.0, body_force=0.0, dt=0.01,
                skin=0.3, seed=20220528, caps=None, flags=0, **params):
     """md_config for n particles (counts of platelet / receptor particles from tag);
-    flags: extra MD_CFG_* bits (MD_CFG_MORSE_STANDARD, MD_CFG_IFACE_LJ)."""
+    flags: extra MD_CFG_* bits (MD_CFG_MORSE_STANDARD, MD_CFG_IFACE_LJ,
+    MD_CFG_UNIFORM_NOISE)."""
     cfg = md_config()
     cfg.n = int(n)
     for k in range(3):

@@ -41,6 +41,8 @@ struct pair_args {
     // interface level, Eq. 3 with an LJ conservative term (MD_CFG_IFACE_LJ):
     // 24 eps / s^2 and s^2 of the LJ, cut at its minimum (wca_rc2 0: off)
     float wca_eps24, wca_sig2, wca_rc2;
+    // MD_CFG_UNIFORM_NOISE: zeta_ij a unit-variance uniform variate
+    int uniform_noise;
 };
 
 // Conservative part of a DPD-level pair: a (1 - r/rc), or on the interface
@@ -237,7 +239,8 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
     sm.xi[warp][lane] = xi;
     sm.vi[warp][lane] = active ? a.v[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     sm.fi[warp][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const philox_pre pq = philox_prepare((uint32_t)a.ds->step, (uint32_t)a.ds->sub, a.key);
+    philox_pre pq = philox_prepare((uint32_t)a.ds->step, (uint32_t)a.ds->sub, a.key);
+    pq.uniform = a.uniform_noise;
     const float delta = a.ds->le_offset_f;
     const unsigned lt = (1u << lane) - 1u;
     vir6 w = {0, 0, 0, 0, 0, 0};
@@ -358,7 +361,8 @@ __global__ void __launch_bounds__(128) k_dpd_fast(pair_args a, fast_args fa)
     const int64_t nf = min((int64_t)fa.ctl[CTL_NFAST], fa.fast_max);
     const float delta = a.ds->le_offset_f, dbuild = a.ds->le_build_f;
     const uint32_t stamp = a.ds->fast_stamp;
-    const philox_pre pq = philox_prepare((uint32_t)a.ds->step, (uint32_t)a.ds->sub, a.key);
+    philox_pre pq = philox_prepare((uint32_t)a.ds->step, (uint32_t)a.ds->sub, a.key);
+    pq.uniform = a.uniform_noise;
     const int lane = threadIdx.x & 31;
     const md_grid &g = fa.g;
     vir6 w = {0, 0, 0, 0, 0, 0};
@@ -633,10 +637,13 @@ static fast_args fast_for(md_system *s, const md_grid &g, const int32_t *members
 }
 
 // pair_args of the DPD levels (the fields the pair kernels read)
-// The interface level's LJ conservative term when MD_CFG_IFACE_LJ selects it.
-static void set_wca(md_system *s, pair_args &a, bool iface)
+// The selectable variants of the DPD levels: the interface level's LJ
+// conservative term (MD_CFG_IFACE_LJ) and the uniform noise variate
+// (MD_CFG_UNIFORM_NOISE).
+static void set_variants(md_system *s, pair_args &a, bool iface)
 {
     const md_config &c = s->cfg;
+    a.uniform_noise = (c.flags & MD_CFG_UNIFORM_NOISE) ? 1 : 0;
     const bool on = iface && (c.flags & MD_CFG_IFACE_LJ);
     const double rmin = pow(2.0, 1.0 / 6.0) * c.lj_sigma;
     a.wca_eps24 = (float)(24.0 * c.lj_eps);
@@ -676,7 +683,7 @@ static pair_args dpd_args(md_system *s)
     a.vir = s->vir_acc;
     a.tag = s->tag_s;
     a.fdet = nullptr;
-    set_wca(s, a, false);
+    set_variants(s, a, false);
     return a;
 }
 
@@ -704,7 +711,7 @@ cudaError_t launch_fast_pairs(md_system *s, unsigned level_mask, float4 *const o
         a.a_same = (float)c.a_fp;
         a.a_wall = (float)c.a_fp;
         a.sig_isdt = (float)(c.sigma / sqrt(c.dt / km));
-        set_wca(s, a, true);
+        set_variants(s, a, true);
         const fast_args fa = fast_for(s, s->gplt, s->plt_sorted, s->cut2[MD_LIST_IFACE]);
         if (fdet && virial) k_dpd_fast<true, true, true><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
         else if (fdet) k_dpd_fast<false, true, true><<<FAST_BLOCKS, 128, 0, s->stream>>>(a, fa);
@@ -747,7 +754,7 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
     a.due.K = s->plt_K;
     a.due.dtm = (float)s->due_dtm;
     const int km = s->cfg_k_m > 0 ? s->cfg_k_m : 1;
-    set_wca(s, a, false);
+    set_variants(s, a, false);
 
     if (level_mask & MD_LEVEL_FLUID) {
         a.rows = s->n;
@@ -775,7 +782,7 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
         a.a_same = (float)c.a_fp;
         a.a_wall = (float)c.a_fp;
         a.sig_isdt = (float)(c.sigma / sqrt(c.dt / km));
-        set_wca(s, a, true);
+        set_variants(s, a, true);
         if (fdet && virial) k_dpd<true, false, true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
         else if (fdet) k_dpd<false, false, true><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);
         else if (virial) k_dpd<true, false><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a);

@@ -236,6 +236,17 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 // the Taylor series of -ln(1 - v), v = 1 - u1 (exact), is summed to v^8.
 // cos(2 pi u2) = -cos(2 pi (u2 - 1/2)) keeps the hardware cosine's argument
 // in [-pi, pi).
+__device__ __forceinline__ float gauss_from_bits(uint32_t r0, uint32_t r1);
+
+// Uniform variate of zero mean and unit variance from the top 24 bits b of
+// one word: sqrt(3) (2 (b + 1/2) 2^-24 - 1), as one FMA on the exact float b.
+// The 2^24 values are symmetric about zero, so the mean is exactly zero.
+__device__ __forceinline__ float uniform_from_bits(uint32_t r0)
+{
+    return fmaf((float)(r0 >> 8), 1.7320508075688772f / 8388608.0f,
+                1.7320508075688772f * (1.0f / 16777216.0f - 1.0f));
+}
+
 __device__ __forceinline__ float gauss_from_bits(uint32_t r0, uint32_t r1)
 {
     const uint32_t k = r0 >> 8;
@@ -260,6 +271,7 @@ __device__ __forceinline__ float gauss_from_bits(uint32_t r0, uint32_t r1)
 struct philox_pre {
     uint32_t hi1k, lo1, cwk;
     uint2 k1;                      // key after the first round's bump
+    int uniform;                   // MD_CFG_UNIFORM_NOISE: zeta from uniform_from_bits
 };
 __device__ __forceinline__ philox_pre philox_prepare(uint32_t nt, uint32_t cs, uint2 key)
 {
@@ -268,6 +280,7 @@ __device__ __forceinline__ philox_pre philox_prepare(uint32_t nt, uint32_t cs, u
     q.lo1 = 0xCD9E8D57u * nt;
     q.cwk = cs ^ key.y;
     q.k1 = make_uint2(key.x + 0x9E3779B9u, key.y + 0xBB67AE85u);
+    q.uniform = 0;
     return q;
 }
 __device__ __forceinline__ float pair_zeta_pre(uint32_t a, uint32_t b, const philox_pre &q)
@@ -283,7 +296,7 @@ __device__ __forceinline__ float pair_zeta_pre(uint32_t a, uint32_t b, const phi
         k.x += 0x9E3779B9u;
         k.y += 0xBB67AE85u;
     }
-    return gauss_from_bits(c.x, c.y);
+    return q.uniform ? uniform_from_bits(c.x) : gauss_from_bits(c.x, c.y);
 }
 
 // Pair noise zeta_ij at time index (nt, cs).

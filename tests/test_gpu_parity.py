@@ -158,6 +158,26 @@ def test_force_variants_match_oracle(plt_sys):
     assert np.abs(fd_i - fo_i).max() > 1.0
 
 
+@pytest.mark.parametrize("det", [False, True])
+def test_uniform_noise_variant_matches_oracle(plt_sys, det):
+    """MD_CFG_UNIFORM_NOISE: zeta_ij of Eq. 1 and Eq. 3 as the unit-variance
+    uniform variate; plasma and interface levels against the oracle's
+    uniform_noise reading, in the ordinary and the deterministic modes."""
+    import paper_2205_14121_gb300 as M
+    from paper_2205_14121_gb300._binding import MD_CFG_UNIFORM_NOISE
+    s = plt_sys
+    g = make_gpu(s, step0=7, flags=MD_CFG_UNIFORM_NOISE)
+    _, _, x32 = g.read_particles()
+    g.forces(deterministic=det)
+    for lvl, mask in ((O.LVL_FLUID, M.MD_LEVEL_FLUID), (O.LVL_IFACE, M.MD_LEVEL_IFACE)):
+        fo, _ = oracle_forces(s, x32, s.v, 7, level_mask=lvl, uniform_noise=True)
+        fg = g.read_forces(mask)
+        assert_force_parity(fg, fo)
+        # not the Gaussian draw
+        fd, _ = oracle_forces(s, x32, s.v, 7, level_mask=lvl)
+        assert np.abs(fd - fo).max() > 1.0
+
+
 def test_forces_walls_body_force(wall_sys):
     s = wall_sys
     g = make_gpu(s, step0=2)

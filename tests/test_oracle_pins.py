@@ -112,6 +112,43 @@ def test_zeta_moments_are_standard_normal():
     assert O.zeta(p, 0, 1, 7, 1) != O.zeta(p, 0, 1, 7, 0)
 
 
+def test_uniform_noise_variant_moments():
+    """The speed option's zeta: a uniform variate on [-sqrt(3), sqrt(3)] has mean
+    0, variance 1 and fourth moment 9/5; within 4 standard errors over 40,000
+    pair/time counters, bounded by sqrt(3), and flat over 12 equal bins."""
+    p = O.make_params((10, 10, 10), uniform_noise=True)
+    z = np.array([O.zeta(p, i, i + 1 + (i % 7), t, 0) for i in range(4000) for t in range(10)])
+    n = z.size
+    assert abs(z.mean()) < 4.0 / math.sqrt(n)
+    assert abs((z ** 2).mean() - 1.0) < 4.0 * math.sqrt(0.8 / n)
+    assert abs((z ** 4).mean() - 1.8) < 4.0 * math.sqrt((9.0 - 1.8 ** 2) / n)
+    assert np.abs(z).max() < math.sqrt(3.0)
+    counts, _ = np.histogram(z, bins=12, range=(-math.sqrt(3.0), math.sqrt(3.0)))
+    e = n / 12.0
+    assert ((counts - e) ** 2 / e).sum() < 40.0          # chi-square, 11 dof: p ~ 4e-5
+    # the same counters as the Gaussian draw, only the transform differs
+    g = O.make_params((10, 10, 10))
+    assert O.zeta(p, 3, 9, 4, 0) != O.zeta(g, 3, 9, 4, 0)
+    assert O.zeta(p, 9, 3, 4, 0) == O.zeta(p, 3, 9, 4, 0)
+
+
+def test_uniform_noise_variant_thermalises_to_kT():
+    """Fluctuation-dissipation (Eq. 1 with sigma^2 = 2 gamma kT) needs only the
+    noise's first two moments: the DPD fluid driven by the uniform variate
+    settles at kT = 1 as well."""
+    s = synth.plasma_box(n=3 * 8 ** 3, seed=11)
+    p = O.system_params(s, uniform_noise=True)
+    x, v, f = s.x, s.v, None
+    n0 = 0
+    Ts = []
+    for block in range(24):
+        x, v, f = O.run_respa(p, x, v, s.tag, dt_f=0.01, n_outer=25, n0=n0, t0=n0 * 0.01, forces=f)
+        n0 += 25
+        if block >= 14:
+            Ts.append(O.kinetics(p, x, v, s.tag)["T"])
+    assert np.mean(Ts) == pytest.approx(1.0, abs=0.03)
+
+
 def test_philox_words_are_uniform_and_avalanche():
     """Philox4x32-10 (SC'11) output words: uniform top bytes (chi-square) and a
     single flipped counter bit changes about half of the 128 output bits."""
