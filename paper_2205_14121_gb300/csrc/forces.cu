@@ -167,7 +167,7 @@ __device__ __forceinline__ void dpd_pair_fixed(const pair_args &a, int32_t i, in
     if (VIR) w.add(dx, dy, dz, fc * inv_r);
 }
 
-template <bool VIR, bool DET, bool IF>
+template <bool VIR, bool DET, bool IF, bool UNI>
 __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int warp, int lane, bool valid,
                                           int slot, const philox_pre &pq, vir6 &w, int64_t r0)
 {
@@ -194,7 +194,7 @@ __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int 
         const float wr = 1.0f - r2 * inv_r * a.inv_rc;
         const float ex = q.x * inv_r, ey = q.y * inv_r, ez = q.z * inv_r;
         const float edv = ex * (vi.x - vj.x - q.w) + ey * (vi.y - vj.y) + ez * (vi.z - vj.z);
-        const float zeta = pair_zeta_pre((uint32_t)b.w, (uint32_t)b.z, pq);
+        const float zeta = pair_zeta_pre<UNI ? 1 : 0>((uint32_t)b.w, (uint32_t)b.z, pq);
         const float fc = dpd_conservative<IF>(a, aij, wr, r2, inv_r);
         const float fp = fc - a.gamma * wr * wr * edv + a.sig_isdt * wr * zeta;
         px = fp * ex; py = fp * ey; pz = fp * ez;
@@ -225,10 +225,11 @@ __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int 
 // of the warp's concatenated rows is word f of the first row's slot, with the
 // row's lane in its top bits; otherwise ELL rows (the interface list) and the
 // row of an entry comes from a binary search over the rows' prefix offsets.
-template <bool VIR, bool STREAM, bool DET = false>
-__global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
+// UNI: the noise variate (MD_CFG_UNIFORM_NOISE) fixed at compile time; the
+// kernel picks the instance once.
+template <bool VIR, bool STREAM, bool DET, bool UNI>
+__device__ __forceinline__ void dpd_rows(const pair_args &a, dpd_smem &sm)
 {
-    __shared__ dpd_smem sm;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t r0 = r - lane;
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
         qn += __popc(m);
         __syncwarp();
         if (qn >= 32) {
-            dpd_batch<VIR, DET, !STREAM>(a, sm, warp, lane, true, (qh + lane) & (DPD_QCAP - 1), pq, w, r0);
+            dpd_batch<VIR, DET, !STREAM, UNI>(a, sm, warp, lane, true, (qh + lane) & (DPD_QCAP - 1), pq, w, r0);
             qh = (qh + 32) & (DPD_QCAP - 1);
             qn -= 32;
             __syncwarp();
@@ -318,13 +319,21 @@ __global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
         row_c = row_n; j_c = j_n; xj_c = xj_n;
         row_n = row_nn; j_n = j_nn;
     }
-    if (qn > 0) dpd_batch<VIR, DET, !STREAM>(a, sm, warp, lane, lane < qn, (qh + lane) & (DPD_QCAP - 1), pq, w, r0);
+    if (qn > 0) dpd_batch<VIR, DET, !STREAM, UNI>(a, sm, warp, lane, lane < qn, (qh + lane) & (DPD_QCAP - 1), pq, w, r0);
     __syncwarp();
     if (!DET && active && cnt > 0) {
         const float4 t = sm.fi[warp][lane];
         scatter(a.f, i, t.x, t.y, t.z);
     }
     if (VIR) flush_virial(a.vir, w);
+}
+
+template <bool VIR, bool STREAM, bool DET = false>
+__global__ void __launch_bounds__(MSM_TPB, 5) k_dpd(pair_args a)
+{
+    __shared__ dpd_smem sm;
+    if (a.uniform_noise) dpd_rows<VIR, STREAM, DET, true>(a, sm);
+    else dpd_rows<VIR, STREAM, DET, false>(a, sm);
 }
 
 // K3 for the fast plasma particles: those that moved beyond skin/2 (but

@@ -283,6 +283,8 @@ __device__ __forceinline__ philox_pre philox_prepare(uint32_t nt, uint32_t cs, u
     q.uniform = 0;
     return q;
 }
+// NOISE: 1 the uniform variate, 0 the Gaussian, -1 as q.uniform says
+template <int NOISE = -1>
 __device__ __forceinline__ float pair_zeta_pre(uint32_t a, uint32_t b, const philox_pre &q)
 {
     const uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
@@ -296,7 +298,8 @@ __device__ __forceinline__ float pair_zeta_pre(uint32_t a, uint32_t b, const phi
         k.x += 0x9E3779B9u;
         k.y += 0xBB67AE85u;
     }
-    return q.uniform ? uniform_from_bits(c.x) : gauss_from_bits(c.x, c.y);
+    const bool uni = NOISE < 0 ? q.uniform != 0 : NOISE == 1;
+    return uni ? uniform_from_bits(c.x) : gauss_from_bits(c.x, c.y);
 }
 
 // Pair noise zeta_ij at time index (nt, cs).
