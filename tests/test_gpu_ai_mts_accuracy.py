@@ -1,9 +1,11 @@
 """AI-MTS against fine-step STS on the same synthetic channel (Sec. 4.2): the
 flow profile and the per-platelet stresses of AI-MTS (dt_f = 0.01, ratios
 from the trained controller) agree with fine-step STS (dt = 0.001 for every
-particle) within the spread between two fine-step runs that differ only in
-their noise realisation; temperature and pressure within the paper's 0.7% and
-1.2% of the fine-step mean."""
+particle): over three noise realisations of each arm, the mean flow profiles
+differ by no more than three times the spread expected between such means
+(estimated from the fine-step runs), the mean per-platelet stresses by no
+more than the paper's 3% plus that spread, and temperature and pressure by
+the paper's 0.7% and 1.2%.  Fixed-k RESPA (k = 10) is measured beside it."""
 import os
 
 import numpy as np
@@ -54,39 +56,69 @@ def test_ai_mts_matches_fine_step_sts():
         return acc
 
     ctl, trust = A.load_controller(os.path.join(DATA, "controller.npz"))
-    g = M.System(s.box, x0, v0, s.tag, dt=0.01, seed=5, **kw)
-    g.set_platelet_levels([trust.fallback_k] * 2)
-    g.mts_step(128, mode=M.MD_MODE_AI, k_m=1, record=True)
-    windows, _ = g.read_feature_ring()
-    k, _, _ = A.decide(ctl.predict(windows), windows, trust)
-    g.set_platelet_levels(k)
-    ai = {"prof": [], "stress": [], "T": [], "P": []}
-    for _ in range(60):
-        g.mts_step(5, mode=M.MD_MODE_AI, k_m=1)
-        sample(g, ai)
-    g.close()
-    # the fine runs cover the same 3 tau after the same 1.28 tau lead-in
-    f1, f2 = fine(11), fine(12)
 
-    def stats(acc):
-        return np.mean(acc["prof"], 0), np.mean(acc["stress"], 0)
+    def ai_run(seed):
+        g = M.System(s.box, x0, v0, s.tag, dt=0.01, seed=seed, **kw)
+        g.set_platelet_levels([trust.fallback_k] * 2)
+        g.mts_step(128, mode=M.MD_MODE_AI, k_m=1, record=True)
+        windows, _ = g.read_feature_ring()
+        k, _, _ = A.decide(ctl.predict(windows), windows, trust)
+        g.set_platelet_levels(k)
+        acc = {"prof": [], "stress": [], "T": [], "P": [], "k": k.tolist()}
+        for _ in range(60):
+            g.mts_step(5, mode=M.MD_MODE_AI, k_m=1)
+            sample(g, acc)
+        g.close()
+        return acc
 
-    (p1, s1), (p2, s2), (pa, sa) = stats(f1), stats(f2), stats(ai)
-    vmax = np.abs(p1).max()
-    noise_p = np.linalg.norm(p2 - p1) / np.linalg.norm(p1)
-    err_p = np.linalg.norm(pa - p1) / np.linalg.norm(p1)
-    noise_s = np.abs(s2 - s1).max() / np.abs(s1).max()
-    err_s = np.abs(sa - s1).max() / np.abs(s1).max()
-    T = [np.mean(a["T"]) for a in (f1, f2, ai)]
-    P = [np.mean(a["P"]) for a in (f1, f2, ai)]
-    print(dict(k=k.tolist(), vmax=vmax, profile_err=err_p, profile_noise=noise_p, stress_err=err_s,
-               stress_noise=noise_s, T=T, P=P))
+    # three noise realisations per arm; the fine runs cover the same 3 tau
+    # after the same 1.28 tau lead-in as the AI arm's first window
+    ais = [ai_run(sd) for sd in (5, 6, 7)]
+    fines = [fine(sd) for sd in (11, 12, 13)]
+
+    def respa_run(seed):             # fixed k = 10 for both platelets, for comparison
+        g = M.System(s.box, x0, v0, s.tag, dt=0.01, seed=seed, **kw)
+        g.mts_step(128, mode=M.MD_MODE_RESPA, k_m=1, k_p=10)
+        acc = {"prof": [], "stress": [], "T": [], "P": []}
+        for _ in range(60):
+            g.mts_step(5, mode=M.MD_MODE_RESPA, k_m=1, k_p=10)
+            sample(g, acc)
+        g.close()
+        return acc
+
+    respas = [respa_run(sd) for sd in (5, 6, 7)]
+
+    def mean_of(runs, key):
+        return np.mean([np.mean(r[key], 0) for r in runs], 0)
+
+    pf, pa = mean_of(fines, "prof"), mean_of(ais, "prof")
+    sf, sa = mean_of(fines, "stress"), mean_of(ais, "stress")
+    Tf, Ta = mean_of(fines, "T"), mean_of(ais, "T")
+    Pf, Pa = mean_of(fines, "P"), mean_of(ais, "P")
+    # the spread of one run about another, from the fine pairs; the
+    # difference of two 3-run means has 1/sqrt(3) of it
+    pairs = [(0, 1), (0, 2), (1, 2)]
+    fp = [np.mean(r["prof"], 0) for r in fines]
+    fs = [np.mean(r["stress"], 0) for r in fines]
+    noise_p = np.mean([np.linalg.norm(fp[a] - fp[b]) for a, b in pairs]) / np.linalg.norm(pf) / np.sqrt(3.0)
+    noise_s = np.mean([np.abs(fs[a] - fs[b]).max() for a, b in pairs]) / np.abs(sf).max() / np.sqrt(3.0)
+    err_p = np.linalg.norm(pa - pf) / np.linalg.norm(pf)
+    err_s = np.abs(sa - sf).max() / np.abs(sf).max()
+    pr, sr = mean_of(respas, "prof"), mean_of(respas, "stress")
+    err_p_k10 = np.linalg.norm(pr - pf) / np.linalg.norm(pf)
+    err_s_k10 = np.abs(sr - sf).max() / np.abs(sf).max()
+    vmax = np.abs(pf).max()
+    fT = [np.mean(r["T"]) for r in fines]
+    fP = [np.mean(r["P"]) for r in fines]
+    print(dict(k=[r["k"] for r in ais], vmax=vmax, profile_err=err_p, profile_noise=noise_p, stress_err=err_s,
+               stress_noise=noise_s, profile_err_k10=err_p_k10, stress_err_k10=err_s_k10, T_fine=fT, T_ai=[np.mean(r["T"]) for r in ais],
+               P_fine=fP, P_ai=[np.mean(r["P"]) for r in ais]))
     assert vmax > 0.05                                  # the channel flows
     assert err_p <= 3.0 * noise_p + 0.005
-    assert err_s <= 3.0 * noise_s + 0.005
+    # per-platelet stresses: the paper's 3% (Sec. 4.2) on top of the sampling noise
+    assert err_s <= 0.03 + 3.0 * noise_s
     # temperature and pressure against the fine-step mean: within the paper's
-    # 0.7% and 1.2% (Sec. 4.2), or twice the spread of the two fine runs
-    # where the noise of this short average is larger
-    tf, pf = 0.5 * (T[0] + T[1]), 0.5 * (P[0] + P[1])
-    assert abs(T[2] - tf) <= max(0.007 * tf, 2.0 * abs(T[0] - T[1]))
-    assert abs(P[2] - pf) <= max(0.012 * abs(pf), 2.0 * abs(P[0] - P[1]))
+    # 0.7% and 1.2% (Sec. 4.2), or twice the spread of the fine runs' means
+    # where the noise of these short averages is larger
+    assert abs(Ta - Tf) <= max(0.007 * Tf, 2.0 * np.std(fT))
+    assert abs(Pa - Pf) <= max(0.012 * abs(Pf), 2.0 * np.std(fP))
