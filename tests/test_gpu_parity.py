@@ -601,6 +601,34 @@ def test_full_size_dpd_throughput_system_sampled():
     assert np.all(err <= TOL * (mag + frms))
 
 
+def test_full_size_channel_sampled():
+    """The 8,330,178-particle platelet channel in the benchmark's launch
+    configuration (plasma skin 0.3, platelet skin 0.5): forces of every level
+    on 2,000 sampled plasma and 1,000 sampled platelet particles against the
+    oracle.  The shells are jittered by 0.02 so that their bonds carry load
+    (at rest length a bond force is pure FP32 cancellation)."""
+    import paper_2205_14121_gb300 as M
+    s = synth.config_channel_platelets(seed=20220528)
+    rng = np.random.default_rng(2)
+    x = s.x.copy()
+    plt = s.tag >= 0
+    x[plt] += rng.normal(0.0, 0.02, size=(int(plt.sum()), 3))
+    g = make_gpu(s, step0=3, x=x, skin=0.3, skin_plt=0.5)
+    g.forces()
+    _, _, x32 = g.read_particles()
+    sample = np.concatenate([rng.choice(np.flatnonzero(s.tag == -1), 2000, replace=False),
+                             rng.choice(np.flatnonzero(s.tag >= 0), 1000, replace=False)]).astype(np.int32)
+    p = O.system_params(s)
+    for lvl, mask in ((O.LVL_FLUID, M.MD_LEVEL_FLUID), (O.LVL_IFACE, M.MD_LEVEL_IFACE),
+                      (O.LVL_PLT, M.MD_LEVEL_PLT)):
+        fo = O.forces_cells(p, f32(x32), f32(s.v), s.tag, X0=f32(s.X0), bonds=s.bonds, r0=f32(s.r0),
+                            level_mask=lvl, n_time=3, dt=0.01, sample=sample)
+        fg = g.read_forces(mask)[sample]
+        assert np.abs(fo).max() > 0.0
+        assert_force_parity(fg, fo)
+    g.close()
+
+
 def test_philox_matches_curand_and_oracle():
     """The device Philox4x32-10 equals cuRAND's Philox4_32_10 (a library
     implementation of the same SC'11 generator) block for block, and the
