@@ -254,25 +254,26 @@ __global__ void k_zero_f4(float4 *p, int64_t n)
 }
 
 // A new state in the current storage order (md_set_xv keeping the lists):
-// particle id k goes to its slot pos_of_id[k]; the id / tag bits stay.
-__global__ void k_place_x(int64_t n, const double *__restrict__ aos, const int32_t *__restrict__ pos_of_id,
-                          double *xs, double *ys, double *zs, float4 *x32)
+// slot q takes the values of the particle it holds (id from the position
+// word), read from the id-ordered upload; the id / tag bits stay.  Gathered
+// by slot, so the random accesses are reads and every write is coalesced.
+__global__ void k_place_x(int64_t n, const double *__restrict__ aos, double *xs, double *ys, double *zs, float4 *x32)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int32_t q = pos_of_id[k];
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    float4 p = x32[q];
+    const int64_t k = id_of(p);
     const double x = aos[3 * k], y = aos[3 * k + 1], z = aos[3 * k + 2];
     xs[q] = x; ys[q] = y; zs[q] = z;
-    float4 p = x32[q];
     p.x = (float)x; p.y = (float)y; p.z = (float)z;
     x32[q] = p;
 }
 
-__global__ void k_place_v(int64_t n, const double *__restrict__ aos, const int32_t *__restrict__ pos_of_id, float4 *v)
+__global__ void k_place_v(int64_t n, const double *__restrict__ aos, const float4 *__restrict__ x32, float4 *v)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int32_t q = pos_of_id[k];
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int64_t k = id_of(x32[q]);
     float4 u = v[q];
     u.x = (float)aos[3 * k]; u.y = (float)aos[3 * k + 1]; u.z = (float)aos[3 * k + 2];
     v[q] = u;
@@ -360,9 +361,8 @@ cudaError_t launch_kick_drift(md_system *s, const float h[3], int kick_which, do
 
 cudaError_t launch_place_state(md_system *s, const double *x_dev, bool velocities)
 {
-    if (velocities) k_place_v<<<blocks_for(s->n), MSM_TPB, 0, s->stream>>>(s->n, x_dev, s->pos_of_id, s->v);
-    else k_place_x<<<blocks_for(s->n), MSM_TPB, 0, s->stream>>>(s->n, x_dev, s->pos_of_id, s->xs, s->ys, s->zs,
-                                                                  s->x32);
+    if (velocities) k_place_v<<<blocks_for(s->n), MSM_TPB, 0, s->stream>>>(s->n, x_dev, s->x32, s->v);
+    else k_place_x<<<blocks_for(s->n), MSM_TPB, 0, s->stream>>>(s->n, x_dev, s->xs, s->ys, s->zs, s->x32);
     MSM_COUNT(s, 1);
     return cudaGetLastError();
 }
