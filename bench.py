@@ -48,6 +48,8 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the fine-STS and fixed-k arms")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--clock-log", default=None,
+                    help="directory for the nvidia-smi clock samples of the timed region (default: a temp dir)")
     ap.add_argument("--direct", action="store_true",
                     help="launch every kernel from the host instead of replaying the captured graph "
                          "(profilers cannot see kernels inside conditional graphs)")
@@ -336,7 +338,8 @@ def main():
 
     # ---- timed region --------------------------------------------------
     g.profile_read(reset=True)
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+    import tempfile
+    clk_path = os.path.join(args.clock_log or tempfile.gettempdir(), f"clocks_rank{rank}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
     with ClockSampler(clk_path) as clk:
         ms = timed(g, step, args.steps, barrier)
