@@ -925,20 +925,12 @@ static int load_xv(md_system *s, const double *x, const double *v, int64_t step0
     return MD_OK;
 }
 
-int md_set_xv(md_system *s, const double *x, const double *v, int64_t step0)
+// md_set_xv after the placement: counters, rebuild check, forces cleared,
+// the check's verdict read back.
+static int finish_set_xv(md_system *s, int64_t step0)
 {
-    if (!s || !x || !v) return set_error(s, MD_EINVAL, "md_set_xv: null argument");
-    if (!s->have_particles) return set_error(s, MD_EINVAL, "md_set_xv: md_set_particles was never called");
-    if (s->lists_stale) return load_xv(s, x, v, step0);
-    // lists built: the new state goes into the current storage order and
-    // keeps them if the kick-drift's rebuild check passes on it
     const int64_t n = s->n;
-    s->det_levels = 0;
     cudaStream_t st = s->stream;
-    CK(cudaMemcpyAsync(s->alt64, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload x");
-    CK(launch_place_state(s, s->alt64, false), "place x");
-    CK(cudaMemcpyAsync(s->alt64, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload v");
-    CK(launch_place_state(s, s->alt64, true), "place v");
     CK(cudaMemsetAsync(s->ctl + CTL_UNSTABLE, 0, sizeof(int32_t), st), "reset unstable");
     CK(launch_set_time(s, step0, 0, (double)step0 * s->cfg.dt), "time");
     CK(launch_check_placed(s, step0), "check");
@@ -953,6 +945,61 @@ int md_set_xv(md_system *s, const double *x, const double *v, int64_t step0)
     s->forces_levels = 0;
     if (s->h_ctl[CTL_UNSTABLE]) return set_error(s, MD_EUNSTABLE, "md_set_xv: non-finite or escaped position");
     return MD_OK;
+}
+
+int md_set_xv(md_system *s, const double *x, const double *v, int64_t step0)
+{
+    if (!s || !x || !v) return set_error(s, MD_EINVAL, "md_set_xv: null argument");
+    if (!s->have_particles) return set_error(s, MD_EINVAL, "md_set_xv: md_set_particles was never called");
+    if (s->lists_stale) return load_xv(s, x, v, step0);
+    // lists built: the new state goes into the current storage order and
+    // keeps them if the kick-drift's rebuild check passes on it
+    const int64_t n = s->n;
+    s->det_levels = 0;
+    cudaStream_t st = s->stream;
+    // page-locked host arrays: both uploads back to back on a side stream
+    // (after the work already on st), the positions placed while the
+    // velocities are still arriving, staged in the deterministic-mode buffer
+    // of the fluid level (3n words, free here: this call voids the
+    // deterministic results anyway).  Pageable arrays: one stream (their
+    // copies go through the driver's staging and gain nothing from it).
+    cudaPointerAttributes ax, av;
+    const bool pinned = cudaPointerGetAttributes(&ax, x) == cudaSuccess &&
+                        cudaPointerGetAttributes(&av, v) == cudaSuccess && ax.type == cudaMemoryTypeHost &&
+                        av.type == cudaMemoryTypeHost;
+    cudaGetLastError();   // an unregistered pointer may leave an error behind on older runtimes
+    if (!pinned) {
+        CK(cudaMemcpyAsync(s->alt64, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload x");
+        CK(launch_place_state(s, s->alt64, false), "place x");
+        CK(cudaMemcpyAsync(s->alt64, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st), "upload v");
+        CK(launch_place_state(s, s->alt64, true), "place v");
+        return finish_set_xv(s, step0);
+    }
+    struct side_t {
+        cudaStream_t cs = nullptr;
+        cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+        ~side_t()
+        {
+            if (cs) cudaStreamSynchronize(cs);   // no copy outlives the call, on any path
+            for (auto e : ev)
+                if (e) cudaEventDestroy(e);
+            if (cs) cudaStreamDestroy(cs);
+        }
+    } side;
+    CK(cudaStreamCreateWithFlags(&side.cs, cudaStreamNonBlocking), "upload stream");
+    for (auto &e : side.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "upload events");
+    double *vstage = reinterpret_cast<double *>(s->fdet[0]);
+    CK(cudaEventRecord(side.ev[0], st), "fork");
+    CK(cudaStreamWaitEvent(side.cs, side.ev[0], 0), "fork wait");
+    CK(cudaMemcpyAsync(s->alt64, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, side.cs), "upload x");
+    CK(cudaEventRecord(side.ev[1], side.cs), "x uploaded");
+    CK(cudaMemcpyAsync(vstage, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, side.cs), "upload v");
+    CK(cudaEventRecord(side.ev[2], side.cs), "v uploaded");
+    CK(cudaStreamWaitEvent(st, side.ev[1], 0), "x wait");
+    CK(launch_place_state(s, s->alt64, false), "place x");
+    CK(cudaStreamWaitEvent(st, side.ev[2], 0), "v wait");
+    CK(launch_place_state(s, vstage, true), "place v");
+    return finish_set_xv(s, step0);
 }
 
 int md_set_bonds(md_system *s, const int32_t *ij, const double *r0, int64_t nb)

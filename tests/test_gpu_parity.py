@@ -534,14 +534,15 @@ def test_flow_profile_matches_oracle(wall_sys, plt_sys, which):
     assert abs(dens.mean() - 3.0) < 0.5
 
 
-@pytest.mark.parametrize("shift", [0.0, 1.7])
-def test_set_xv_equals_full_upload(plt_wall_sys, shift):
+@pytest.mark.parametrize("shift,pinned", [(0.0, False), (1.7, False), (0.0, True)])
+def test_set_xv_equals_full_upload(plt_wall_sys, shift, pinned):
     """md_set_xv (positions and velocities only, tags and rest positions kept
     on the device) leaves the same state as md_set_particles with the same
     tags: two RESPA steps from it agree to FP32 atomic-order noise (a wrong
     tag, rest position or stale list would move particles by orders more).
     Near the state of the last build (shift 0) it keeps the lists and the
-    cell order; the whole system moved by 1.7 along x trips the rebuild check."""
+    cell order; the whole system moved by 1.7 along x trips the rebuild check.
+    From page-locked host arrays the two uploads take a side stream."""
     import paper_2205_14121_gb300 as M
     s = plt_wall_sys
     rng = np.random.default_rng(5)
@@ -554,7 +555,12 @@ def test_set_xv_equals_full_upload(plt_wall_sys, shift):
     b = make_gpu(s, step0=0)
     b.mts_step(1)
     builds = b.observables()["n_builds"]
-    b.set_xv(x1, v1, step0=7)
+    if pinned:
+        import torch
+        b.set_xv(torch.from_numpy(np.ascontiguousarray(x1, np.float64)).pin_memory().numpy(),
+                 torch.from_numpy(np.ascontiguousarray(v1, np.float64)).pin_memory().numpy(), step0=7)
+    else:
+        b.set_xv(x1, v1, step0=7)
     for g in (a, b):
         g.mts_step(2, mode=M.MD_MODE_RESPA, k_m=1, k_p=5)
     xa, va, _ = a.read_particles()
