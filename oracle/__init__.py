@@ -94,7 +94,7 @@ def lib():
         L.orc_forces_cells.argtypes = [P, C.c_int32, dp, dp, ip, ip, dp, ip, ip, dp,
                                        C.c_uint32, C.c_uint32, C.c_uint32, C.c_double,
                                        C.c_uint32, C.c_uint32, C.c_double,
-                                       C.c_int32, ip, dp]
+                                       C.c_int32, ip, dp, dp]
         L.orc_r2_f32.argtypes = [fp, fp, fp, C.c_int32, C.c_int32, C.c_float]
         L.orc_r2_f32.restype = C.c_float
         L.orc_pairs_f32.argtypes = [C.c_int32, fp, ip, fp, fp, C.c_int32, C.c_int32, C.c_float,
@@ -187,9 +187,11 @@ def bond_csr(n, bonds, r0):
 
 def forces_cells(p, x, v, tag, X0=None, bonds=None, r0=None, ids=None, level_mask=LVL_ALL,
                  n_time=0, c_sub=0, dt=0.01, n_time_m=None, c_sub_m=None, dt_m=None,
-                 sample=None):
+                 sample=None, with_acc=False):
     """Forces on ``sample`` (default: all) particles via a cell list; same
-    definition and summation order as :func:`forces_brute`."""
+    definition and summation order as :func:`forces_brute`.  with_acc: also
+    return dict(epot, vir, vir_c) of the pair terms (bonds excluded), which
+    are the system's totals when every particle is in the sample."""
     n = x.shape[0]
     x, xp = _d(x)
     v, vp = _d(v)
@@ -213,12 +215,16 @@ def forces_cells(p, x, v, tag, X0=None, bonds=None, r0=None, ids=None, level_mas
         sample, sp = _i(sample)
         ns = sample.shape[0]
     f = np.zeros((ns, 3))
+    acc = np.zeros(19)
     lib().orc_forces_cells(C.byref(p), n, xp, vp, idp, tp, X0p, offp, nbrp, rrp, level_mask,
                            n_time, c_sub, dt,
                            n_time if n_time_m is None else n_time_m,
                            c_sub if c_sub_m is None else c_sub_m,
                            dt if dt_m is None else dt_m,
-                           ns, sp, f.ctypes.data_as(C.POINTER(C.c_double)))
+                           ns, sp, f.ctypes.data_as(C.POINTER(C.c_double)),
+                           acc.ctypes.data_as(C.POINTER(C.c_double)))
+    if with_acc:
+        return f, dict(epot=acc[0], vir=acc[1:10].reshape(3, 3), vir_c=acc[10:19].reshape(3, 3))
     return f
 
 

@@ -520,7 +520,7 @@ void orc_forces_cells(const orc_params *p, int32_t n, const double *x, const dou
                       const int32_t *bond_off, const int32_t *bond_nbr, const double *bond_r0,
                       uint32_t level_mask, uint32_t n_time_f, uint32_t c_sub_f, double dt_f,
                       uint32_t n_time_m, uint32_t c_sub_m, double dt_m,
-                      int32_t ns, const int32_t *sample, double *f_out)
+                      int32_t ns, const int32_t *sample, double *f_out, double *acc_out)
 {
     pair_ctx c = {p, n, x, v, X0, id, tag, level_mask, n_time_f, c_sub_f, n_time_m, c_sub_m,
                   1.0 / sqrt(dt_f), 1.0 / sqrt(dt_m)};
@@ -528,8 +528,12 @@ void orc_forces_cells(const orc_params *p, int32_t n, const double *x, const dou
     cells_t cl;
     cells_build(p, n, x, cell, &cl);
     double Rmax_plt = p->lj_rc > p->m_rc ? p->lj_rc : p->m_rc;
+    orc_acc acc;
+    memset(&acc, 0, sizeof acc);
 #pragma omp parallel
     {
+        orc_acc la;
+        memset(&la, 0, sizeof la);
         char *seen = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
         int32_t *seen_list = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
         int32_t *cands = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
@@ -547,6 +551,9 @@ void orc_forces_cells(const orc_params *p, int32_t n, const double *x, const dou
                 double F[3], Fc[3], u, rij[3];
                 if (!pair_force(&c, i, cands[k], F, Fc, &u, rij)) continue;
                 fi[0] += F[0]; fi[1] += F[1]; fi[2] += F[2];
+                /* each pair is visited from both ends: half of its energy and virial per visit */
+                la.epot += 0.5 * u;
+                acc_pair(&la, rij[0], rij[1], rij[2], F[0], F[1], F[2], Fc[0], Fc[1], Fc[2], 0.5);
             }
             if ((level_mask & LVL_FLUID) && tag[i] != TAG_WALL) fi[0] += p->g;
             if ((level_mask & LVL_PLT) && bond_off) {
@@ -560,8 +567,20 @@ void orc_forces_cells(const orc_params *p, int32_t n, const double *x, const dou
             f_out[3 * s] = fi[0]; f_out[3 * s + 1] = fi[1]; f_out[3 * s + 2] = fi[2];
         }
         free(seen); free(seen_list); free(cands);
+#pragma omp critical
+        {
+            acc.epot += la.epot;
+            for (int k = 0; k < 9; ++k) { acc.vir[k] += la.vir[k]; acc.vir_c[k] += la.vir_c[k]; }
+        }
     }
     cells_free(&cl);
+    /* pair sums of every particle (sample == NULL) give the system's pair
+     * energy and virial; bond terms are not included */
+    if (acc_out) {
+        acc_out[0] = acc.epot;
+        memcpy(acc_out + 1, acc.vir, 9 * sizeof(double));
+        memcpy(acc_out + 10, acc.vir_c, 9 * sizeof(double));
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -741,7 +760,7 @@ static void eval_level(orc_params *p, const orc_state *s, const bond_csr_t *csr,
                        uint32_t nt, uint32_t cs, double dt_f, double dt_m, double *f)
 {
     orc_forces_cells(p, s->n, s->x, s->v, s->id, s->tag, s->X0, csr->off, csr->nbr, csr->r0,
-                     mask, nt, cs, dt_f, nt, cs, dt_m, s->n, NULL, f);
+                     mask, nt, cs, dt_f, nt, cs, dt_m, s->n, NULL, f, NULL);
 }
 
 static void kick(const orc_state *s, const double *f, double h)

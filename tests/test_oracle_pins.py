@@ -149,6 +149,27 @@ def test_uniform_noise_variant_thermalises_to_kT():
     assert np.mean(Ts) == pytest.approx(1.0, abs=0.03)
 
 
+# Known-answer vectors of Philox4x32-10 published with the SC'11 generator
+# (Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy as 1, 2,
+# 3"; the Random123 distribution's known-answer file): counter, key, output.
+PHILOX4X32_10_KAT = [
+    ((0x00000000, 0x00000000, 0x00000000, 0x00000000), (0x00000000, 0x00000000),
+     (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+    ((0xffffffff, 0xffffffff, 0xffffffff, 0xffffffff), (0xffffffff, 0xffffffff),
+     (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+    ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+     (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1)),
+]
+
+
+@pytest.mark.parametrize("ctr,key,out", PHILOX4X32_10_KAT)
+def test_philox4x32_10_known_answers(ctr, key, out):
+    """Philox4x32-10 (the generator of Eq. 1's zeta_ij) reproduces the published
+    known-answer vectors bit for bit: a wrong multiplier, Weyl constant, round
+    count or word order fails here."""
+    assert O.philox4x32_10(ctr, key) == list(out)
+
+
 def test_philox_words_are_uniform_and_avalanche():
     """Philox4x32-10 (SC'11) output words: uniform top bytes (chi-square) and a
     single flipped counter bit changes about half of the 128 output bits."""
@@ -514,8 +535,8 @@ def test_bounce_back_independent_of_substeps():
 
 @pytest.mark.slow
 def test_dpd_temperature_and_equation_of_state():
-    """sigma^2 = 2 gamma kT fixes kT = 1 (within the known dt = 0.01 artefact).
-    Pressure: the C virial sum equals an independent numpy sum over pair
+    """sigma^2 = 2 gamma kT fixes kT = 1: within 1.5% at dt = 0.01 (the
+    discretisation leaves the measured kT about 1% high).  Pressure: the C virial sum equals an independent numpy sum over pair
     distances, and the excess-pressure coefficient alpha = (p - rho kT)/(a rho^2)
     lies between 0.088 and Groot & Warren's high-density fit 0.101 (their fit
     overshoots at rho = 3, where alpha is ~0.092)."""
@@ -525,15 +546,17 @@ def test_dpd_temperature_and_equation_of_state():
     x, v, f = s.x, s.v, None
     n0 = 0
     Ts, Ps, Pex_c, Pex_np = [], [], [], []
-    for block in range(30):   # 4.5 tau of relaxation from random positions, then 3 tau
+    for block in range(138):   # 4.5 tau of relaxation from random positions, then 30 tau
         x, v, f = O.run_respa(p, x, v, s.tag, dt_f=0.01, n_outer=25, n0=n0, t0=n0 * 0.01,
                               forces=f)
         n0 += 25
         if block < 18:
             continue
-        _, acc = O.forces_brute(p, x, v, s.tag, n_time=n0)
         kin = O.kinetics(p, x, v, s.tag)
         Ts.append(kin["T"])
+        if block % 10:
+            continue
+        _, acc = O.forces_cells(p, x, v, s.tag, n_time=n0, with_acc=True)
         Ps.append(O.pressure(p, kin, acc))
         Pex_c.append(np.trace(acc["vir_c"]) / (3 * L ** 3))
         d = x[:, None, :] - x[None, :, :]
@@ -541,7 +564,8 @@ def test_dpd_temperature_and_equation_of_state():
         r = np.sqrt((d * d).sum(-1))[np.triu_indices(len(x), 1)]
         r = r[r < 1.0]
         Pex_np.append((25.0 * (1.0 - r) * r).sum() / (3 * L ** 3))
-    assert np.mean(Ts) == pytest.approx(1.0, abs=0.03)
+    # 120 samples 0.25 tau apart: the standard error of the mean is about 0.2%
+    assert np.mean(Ts) == pytest.approx(1.0, rel=0.015)
     assert np.mean(Pex_c) == pytest.approx(np.mean(Pex_np), rel=1e-10)
     alpha = (np.mean(Ps) - 3.0 * np.mean(Ts)) / (25.0 * 9.0)
     assert 0.088 < alpha < 0.101
@@ -593,28 +617,124 @@ def test_wall_temperature_hand_built_slabs():
     assert kin["ke"] == pytest.approx(0.5 * (v[tag != synth.TAG_WALL] ** 2).sum(), rel=1e-14)
 
 
-@pytest.mark.slow
-def test_couette_linear_profile_under_lees_edwards():
-    """Lees-Edwards shear gives a linear v_x(y) with the imposed slope."""
-    s = synth.plasma_box(n=3 * 8 ** 3, seed=9, shear_rate=0.5)
+COUETTE_RATE = 0.5
+
+
+def couette_run(n_blocks=55, rate=COUETTE_RATE, seed=9):
+    """An 8^3 Lees-Edwards box sheared at `rate` from the linear profile:
+    the y-binned v_x and the xy shear stress (kinetic + every pair force)
+    sampled every 0.3 tau after 3 tau."""
+    s = synth.plasma_box(n=3 * 8 ** 3, seed=seed, shear_rate=rate)
     p = O.system_params(s)
-    rate = 0.5
     v = s.v.copy()
     v[:, 0] += rate * (s.x[:, 1] - s.box[1] / 2)
     x, f, n0 = s.x, None, 0
-    profs = []
-    for block in range(20):
+    V = s.box[0] * s.box[1] * s.box[2]
+    profs, sxy = [], []
+    for block in range(n_blocks):
         x, v, f = O.run_respa(p, x, v, s.tag, dt_f=0.01, n_outer=30, n0=n0, t0=n0 * 0.01, forces=f)
         n0 += 30
-        if block >= 10:
-            profs.append(O.kinetics(p, x, v, s.tag, nbins=8)["prof_vx"])
-    prof = np.mean(profs, axis=0)
+        if block < 10:
+            continue
+        kin = O.kinetics(p, x, v, s.tag, nbins=8)
+        profs.append(kin["prof_vx"])
+        p.le_offset = (rate * s.box[1] * n0 * 0.01) % s.box[0]
+        _, acc = O.forces_cells(p, x, v, s.tag, n_time=n0, with_acc=True)
+        sxy.append((kin["K"][0, 1] + acc["vir"][0, 1]) / V)
+    return s, np.array(profs), np.array(sxy)
+
+
+@pytest.fixture(scope="module")
+def couette():
+    return couette_run()
+
+
+@pytest.mark.slow
+def test_couette_linear_profile_under_lees_edwards(couette):
+    """Lees-Edwards shear gives a linear v_x(y) with the imposed slope: within 5%
+    and R^2 > 0.99, at a shear rate of 0.5 over 13.5 tau.  (At the survey's
+    0.05 the thermal noise of the slope in this box is about 15% after 30 tau;
+    the tenfold rate keeps the pin within seconds.)"""
+    s, profs, _ = couette
+    prof = profs.mean(0)
     yc = (np.arange(8) + 0.5) * s.box[1] / 8
     slope, icpt = np.polyfit(yc, prof, 1)
-    assert slope == pytest.approx(rate, rel=0.1)
+    assert slope == pytest.approx(COUETTE_RATE, rel=0.05)
     pred = slope * yc + icpt
     r2 = 1 - ((prof - pred) ** 2).sum() / ((prof - prof.mean()) ** 2).sum()
-    assert r2 > 0.98
+    assert r2 > 0.99
+
+
+def block_mean(a, nb=9):
+    a = np.asarray(a)
+    b = a[:len(a) // nb * nb].reshape(nb, -1).mean(1)
+    return b.mean(), b.std(ddof=1) / np.sqrt(nb)
+
+
+@pytest.mark.slow
+def test_poiseuille_viscosity_consistent_with_couette_stress(couette):
+    """Two independent measurements of the plasma viscosity agree within their
+    error bars: eta = -<sigma_xy> / shear rate from the Lees-Edwards stress,
+    and eta from the curvature of the Poiseuille profile of a walled channel
+    under a body force g, u(y) = rho g y (Ly - y) / (2 eta) (no-slip walls of
+    Sec. 3.1, started on the profile of a guess and averaged for 20 tau)."""
+    _, _, sxy = couette
+    eta_c, se_c = block_mean(-sxy / COUETTE_RATE)
+    box, g = (6.0, 12.0, 6.0), 0.05
+    s = synth.plasma_box(box=box, walls=True, body_force=g, seed=31)
+    p = O.system_params(s)
+    mob = s.tag == synth.TAG_FLUID
+    v = s.v.copy()
+    y = s.x[mob, 1]
+    v[mob, 0] += 3.0 * g * y * (box[1] - y) / (2.0 * 0.85)
+    x, f, n0 = s.x, None, 0
+    nb = 12
+    yc = (np.arange(nb) + 0.5) * box[1] / nb
+    etas = []
+    for block in range(75):
+        x, v, f = O.run_respa(p, x, v, s.tag, dt_f=0.01, n_outer=40, n0=n0, t0=n0 * 0.01, forces=f)
+        n0 += 40
+        if block < 25:
+            continue
+        u = O.kinetics(p, x, v, s.tag, nbins=nb)["prof_vx"]
+        c = np.polyfit(yc, u, 2)
+        etas.append(-3.0 * g / (2.0 * c[0]))
+    eta_p, se_p = block_mean(etas, nb=10)
+    assert 0.6 < eta_c < 1.1
+    assert abs(eta_p - eta_c) < 3.0 * np.hypot(se_c, se_p) + 0.02 * eta_c
+
+
+@pytest.mark.slow
+def test_nve_energy_drift_of_bonded_shells_with_lj():
+    """CGMD in NVE (no fluid, no thermostat): two bonded 200-particle shells
+    that start within the LJ range of each other (Eq. 2 bonds and LJ; the
+    receptor Morse switched off), velocity-Verlet at dt = 0.001 for 10^4 steps.
+    The total energy stays within 1e-4 of its start, and its linear drift
+    over the run (the fitted slope times the duration) is below 1e-4 of it."""
+    n_shell, gap = 200, 1.2
+    r = synth.scaled_radii(n_shell)
+    s = synth.platelet_system((30.0, 30.0, 30.0), 0, 2, n_shell, r, seed=23,
+                              centers=[(15.0 - r[0] - gap / 2, 15.0, 15.0), (15.0 + r[0] + gap / 2, 15.0, 15.0)])
+    p = O.system_params(s, m_D=0.0, m_rc=2.0)
+    v = 0.5 * s.v
+
+    def energy(x, v):
+        _, acc = O.forces_brute(p, x, v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, level_mask=O.LVL_PLT)
+        return 0.5 * (v * v).sum() + acc["epot"]
+
+    d = np.linalg.norm(s.x[:n_shell, None] - s.x[None, n_shell:], axis=-1)
+    assert (d < 2.0).sum() > 10          # the LJ acts between the shells at the start
+    x, f, n0 = s.x, None, 0
+    es = [energy(x, v)]
+    for block in range(10):
+        x, v, f = O.run_respa(p, x, v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, dt_f=0.001, n_outer=1000,
+                              forces=f, n0=n0)
+        n0 += 1000
+        es.append(energy(x, v))
+    es = np.array(es)
+    e = abs(es.mean())
+    assert np.abs(es - es[0]).max() < 1e-4 * e
+    assert abs(np.polyfit(np.arange(11), es, 1)[0] * 10) < 1e-4 * e
 
 
 # --------------------------------------------------------------------------
