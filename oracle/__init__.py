@@ -45,15 +45,22 @@ class Params(C.Structure):
         ("plt_k", C.POINTER(C.c_int32)), ("lvl_k", C.c_int32),
         ("iface_lj", C.c_int32),
         ("uniform_noise", C.c_int32),
+        ("n_angles", C.c_int32),
+        ("angles", C.POINTER(C.c_int32)),
+        ("theta0", C.POINTER(C.c_double)),
+        ("k_a", C.c_double),
     ]
 
 
 DEFAULTS = dict(rc=1.0, a_ff=25.0, a_fw=25.0, a_fp=50.0, gamma=4.5, sigma=3.0,
                 lj_eps=1.0, lj_sigma=0.8, lj_rc=2.0, lj_excl=1e30,
-                m_D=2.0, m_alpha=2.0, m_r0=1.0, m_rc=5.0, f_A=0.0, k_b=100.0)
+                m_D=2.0, m_alpha=2.0, m_r0=1.0, m_rc=5.0, f_A=0.0, k_b=100.0, k_a=20.0)
 
 
-def make_params(box, walls=False, le_rate=0.0, le_offset=0.0, g=0.0, seed=20220528, **kw):
+def make_params(box, walls=False, le_rate=0.0, le_offset=0.0, g=0.0, seed=20220528, angles=None, theta0=None,
+                **kw):
+    """Oracle parameters; angles [na, 3] particle rows (i, vertex j, k) with
+    rest angles theta0 [na] for the Eq. 2 angle term (kept alive on p)."""
     p = Params()
     for k in range(3):
         p.L[k] = float(box[k])
@@ -70,6 +77,25 @@ def make_params(box, walls=False, le_rate=0.0, le_offset=0.0, g=0.0, seed=202205
         setattr(p, k, float(v))
     p.seed_lo = seed & 0xFFFFFFFF
     p.seed_hi = (seed >> 32) & 0xFFFFFFFF
+    set_angles(p, angles, theta0)
+    return p
+
+
+def set_angles(p, angles, theta0):
+    """Attach (or with None, detach) the angle triplets of the Eq. 2 angle term."""
+    if angles is None or len(angles) == 0:
+        p.n_angles = 0
+        p._angles = p._theta0 = None
+        p.angles = C.cast(None, C.POINTER(C.c_int32))
+        p.theta0 = C.cast(None, C.POINTER(C.c_double))
+        return p
+    a = np.ascontiguousarray(angles, dtype=np.int32).reshape(-1, 3)
+    t = np.ascontiguousarray(theta0, dtype=np.float64).reshape(-1)
+    assert a.shape[0] == t.shape[0]
+    p._angles, p._theta0 = a, t
+    p.n_angles = a.shape[0]
+    p.angles = a.ctypes.data_as(C.POINTER(C.c_int32))
+    p.theta0 = t.ctypes.data_as(C.POINTER(C.c_double))
     return p
 
 
@@ -363,6 +389,8 @@ def pressure(p, kin, acc, volume=None):
 
 
 def system_params(sysm, seed=20220528, le_offset=0.0, **kw):
-    """Oracle parameters for a :class:`synth.System`."""
+    """Oracle parameters for a :class:`synth.System` (its angle triplets included)."""
+    kw.setdefault("angles", getattr(sysm, "angles", None))
+    kw.setdefault("theta0", getattr(sysm, "theta0", None))
     return make_params(sysm.box, walls=sysm.walls, le_rate=sysm.shear_rate, le_offset=le_offset,
                        g=sysm.body_force, seed=seed, **kw)

@@ -292,8 +292,33 @@ def heads_loss_and_grads(p, zl, k_class, log_hold, w_hold=1.0):
 # inference (Table 2 steps 1-6) and the trust bound
 # ---------------------------------------------------------------------------
 
-def predict(p, raw, mean, std, rec_threshold=np.inf, p_min=0.6, hold_range=(100, 2000), w=5):
-    """raw [B, T, F] -> dict(k, hold, prob, rec_err, trusted)."""
+UNSURE_PROB, UNSURE_REC, UNSURE_STRAIN = 1, 2, 4
+
+
+def trust_decision(prob, rec, log_hold, raw, p_min=0.6, rec_threshold=np.inf, strain_max=np.inf, strain_col=None,
+                   fallback_k=10, hold_range=(100, 2000), k_set=K_SET):
+    """Table 2 steps 5-6: the most probable class's ratio, or fallback_k when
+    the window is unsure -- top probability below p_min, reconstruction error
+    above rec_threshold, or the raw window's strain column above strain_max at
+    any step (NaN fails each test) -- and the hold exp(log_hold) clipped to
+    hold_range, truncated to whole steps.  Returns (k, hold, why bits)."""
+    prob = np.asarray(prob, np.float64)
+    why = np.zeros(prob.shape[0], np.int32)
+    why |= np.where(~(prob.max(1) >= p_min), UNSURE_PROB, 0).astype(np.int32)
+    why |= np.where(~(np.asarray(rec) <= rec_threshold), UNSURE_REC, 0).astype(np.int32)
+    if strain_col is not None:
+        smax = np.asarray(raw)[:, :, strain_col].max(1)
+        why |= np.where(~(smax <= strain_max), UNSURE_STRAIN, 0).astype(np.int32)
+    k = np.where(why != 0, fallback_k, np.asarray(k_set)[prob.argmax(1)]).astype(np.int32)
+    h = np.exp(np.asarray(log_hold, np.float64))
+    hold = np.floor(np.where(np.isnan(h), hold_range[0], np.clip(h, hold_range[0], hold_range[1])))
+    return k, hold.astype(np.int32), why
+
+
+def predict(p, raw, mean, std, rec_threshold=np.inf, p_min=0.6, hold_range=(100, 2000), w=5, strain_max=np.inf,
+            strain_col=None, fallback_k=10):
+    """raw [B, T, F] -> dict(k, hold, prob, rec_err, trusted, k_final, why):
+    Table 2 steps 1-4, then the trust bound and ratio map of steps 5-6."""
     x = (denoise(raw, w) - mean) / std
     zl, _ = encode(p, x)
     y, _ = decode(p, zl, x.shape[1])
@@ -303,8 +328,10 @@ def predict(p, raw, mean, std, rec_threshold=np.inf, p_min=0.6, hold_range=(100,
     cls = pr.argmax(1)
     lh, _ = mlp_forward(p["lhead"], zl)
     hold = np.clip(np.exp(lh[:, 0]), hold_range[0], hold_range[1])
-    trusted = (pr.max(1) >= p_min) & (rec <= rec_threshold)
-    return dict(k=np.array(K_SET)[cls], cls=cls, hold=hold, prob=pr, rec_err=rec, trusted=trusted)
+    k_final, _, why = trust_decision(pr, rec, lh[:, 0], raw, p_min, rec_threshold, strain_max, strain_col, fallback_k,
+                                     hold_range)
+    return dict(k=np.array(K_SET)[cls], cls=cls, hold=hold, prob=pr, rec_err=rec, trusted=why == 0,
+                k_final=k_final, why=why, log_hold=lh[:, 0])
 
 
 # ---------------------------------------------------------------------------

@@ -9,7 +9,8 @@
  *          w = 1 - r/rc  (Groot-Warren discretisation of the sqrt(dt) noise term,
  *          fluctuation-dissipation w_D = w_R^2, sigma^2 = 2 gamma kT)
  *   Eq. 2  intra-platelet potential: LJ 12-6, Morse (the printed form), harmonic
- *          bonds U = k_b (r - r0)^2 (no 1/2, as printed)
+ *          bonds U = k_b (r - r0)^2 and angles U = k_a (theta - theta0)^2 (no 1/2,
+ *          as printed)
  *   Eq. 3  fluid-platelet interface: DPD with its own conservative amplitude
  *   Eq. 4  inter-platelet: Morse + f_A (1 - r/r0) receptor term
  *   Table 1  velocity-Verlet and the multi-level RESPA loop
@@ -65,6 +66,12 @@ typedef struct {
      * the selectable speed option: the uniform variate sqrt(3) (2u - 1), u the
      * midpoint of the 2^-24 bin given by the top 24 bits of the first word */
     int32_t uniform_noise;
+    /* Eq. 2 angle term k_a (theta - theta0)^2 over triplets (i, j, k) of
+     * particle rows, j the vertex (NULL / 0: none) */
+    int32_t n_angles;
+    const int32_t *angles;     /* [3 n_angles] */
+    const double *theta0;      /* [n_angles] */
+    double k_a;
 } orc_params;
 
 static int term_selected(const orc_params *p, int32_t ti, int32_t tj)
@@ -338,6 +345,62 @@ static void bond_force(const orc_params *p, const double *x, int32_t i, int32_t 
     rij[0] = dx; rij[1] = dy; rij[2] = dz;
 }
 
+/* Angle (Eq. 2): U = k_a (theta - theta0)^2, theta the angle at vertex j
+ * between r_ij = x_i - x_j and r_kj = x_k - x_j (minimum images).  With
+ * c = cos theta, dc/dx_i = (e_kj - c e_ij) / |r_ij|, and theta = arccos c,
+ * F_i = -dU/dx_i = 2 k_a (theta - theta0) / sin(theta) (e_kj - c e_ij) / |r_ij|,
+ * F_k likewise with i and k exchanged, F_j = -F_i - F_k.  sin(theta) is held
+ * at 1e-3 at least (the potential has a cone point at theta = pi, where the
+ * direction of the force is undefined).  Returns the energy; rij, rkj get the
+ * two arms (for the virial). */
+static double angle_force(const orc_params *p, const double *x, int32_t i, int32_t j, int32_t k, double th0,
+                          double *Fi, double *Fk, double *rij, double *rkj)
+{
+    double a[3], b[3], dv = 0.0;
+    for (int d = 0; d < 3; ++d) { a[d] = x[3 * i + d] - x[3 * j + d]; b[d] = x[3 * k + d] - x[3 * j + d]; }
+    min_image(p, &a[0], &a[1], &a[2], &dv);
+    dv = 0.0;
+    min_image(p, &b[0], &b[1], &b[2], &dv);
+    double ra = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    double rb = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    double c = (a[0] * b[0] + a[1] * b[1] + a[2] * b[2]) / (ra * rb);
+    if (c > 1.0) c = 1.0;
+    if (c < -1.0) c = -1.0;
+    double th = acos(c);
+    double sn = sqrt(1.0 - c * c);
+    if (sn < 1e-3) sn = 1e-3;
+    double g = 2.0 * p->k_a * (th - th0) / sn;
+    for (int d = 0; d < 3; ++d) {
+        Fi[d] = g * (b[d] / rb - c * a[d] / ra) / ra;
+        Fk[d] = g * (a[d] / ra - c * b[d] / rb) / rb;
+        rij[d] = a[d];
+        rkj[d] = b[d];
+    }
+    return p->k_a * (th - th0) * (th - th0);
+}
+
+/* Angle forces of every triplet selected for the platelet level, added to f
+ * (3n); energy and virial into acc when given. */
+static void add_angle_forces(const orc_params *p, const double *x, const int32_t *tag, double *f, orc_acc *acc)
+{
+    for (int32_t q = 0; q < p->n_angles; ++q) {
+        int32_t i = p->angles[3 * q], j = p->angles[3 * q + 1], k = p->angles[3 * q + 2];
+        if (!term_selected(p, tag[j], tag[j])) continue;
+        double Fi[3], Fk[3], rij[3], rkj[3];
+        double u = angle_force(p, x, i, j, k, p->theta0[q], Fi, Fk, rij, rkj);
+        for (int d = 0; d < 3; ++d) {
+            f[3 * i + d] += Fi[d];
+            f[3 * k + d] += Fk[d];
+            f[3 * j + d] -= Fi[d] + Fk[d];
+        }
+        if (acc) {
+            acc->epot += u;
+            acc_pair(acc, rij[0], rij[1], rij[2], Fi[0], Fi[1], Fi[2], Fi[0], Fi[1], Fi[2], 1.0);
+            acc_pair(acc, rkj[0], rkj[1], rkj[2], Fk[0], Fk[1], Fk[2], Fk[0], Fk[1], Fk[2], 1.0);
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* brute-force forces: every particle against every other                    */
 /* ------------------------------------------------------------------------ */
@@ -393,6 +456,7 @@ void orc_forces_brute(const orc_params *p, int32_t n, const double *x, const dou
             acc.epot += u;
             acc_pair(&acc, rij[0], rij[1], rij[2], F[0], F[1], F[2], F[0], F[1], F[2], 1.0);
         }
+        add_angle_forces(p, x, tag, f, &acc);
     }
     if (acc_out) {
         acc_out[0] = acc.epot;
@@ -530,6 +594,12 @@ void orc_forces_cells(const orc_params *p, int32_t n, const double *x, const dou
     double Rmax_plt = p->lj_rc > p->m_rc ? p->lj_rc : p->m_rc;
     orc_acc acc;
     memset(&acc, 0, sizeof acc);
+    /* angle terms: every triplet once into a full array, read per sample */
+    double *fang = NULL;
+    if ((level_mask & LVL_PLT) && p->n_angles > 0) {
+        fang = (double *)calloc((size_t)3 * (n > 0 ? n : 1), sizeof(double));
+        add_angle_forces(p, x, tag, fang, NULL);
+    }
 #pragma omp parallel
     {
         orc_acc la;
@@ -564,6 +634,7 @@ void orc_forces_cells(const orc_params *p, int32_t n, const double *x, const dou
                     fi[0] += F[0]; fi[1] += F[1]; fi[2] += F[2];
                 }
             }
+            if (fang) { fi[0] += fang[3 * i]; fi[1] += fang[3 * i + 1]; fi[2] += fang[3 * i + 2]; }
             f_out[3 * s] = fi[0]; f_out[3 * s + 1] = fi[1]; f_out[3 * s + 2] = fi[2];
         }
         free(seen); free(seen_list); free(cands);
@@ -574,6 +645,7 @@ void orc_forces_cells(const orc_params *p, int32_t n, const double *x, const dou
         }
     }
     cells_free(&cl);
+    free(fang);
     /* pair sums of every particle (sample == NULL) give the system's pair
      * energy and virial; bond terms are not included */
     if (acc_out) {

@@ -7,7 +7,9 @@ of the method's arithmetic (no forces, no integrator, no observables).
 
 Recipe (all draws from ``numpy.random.Generator(Philox(seed))``):
 
-* plasma: uniform positions in the fluid region, number density rho = 3;
+* plasma: uniform positions in the fluid region, number density rho = 3
+  (with platelets: drawn voxel by voxel, a multinomial count per voxel and
+  uniform positions inside it, which is the same distribution);
 * velocities: Maxwell-Boltzmann at kT = 1 (m = 1), net momentum removed;
 * walls (when present): frozen layers of thickness ``wall`` at rho = 3 just
   outside y in [0, Ly], velocity 0 (the no-slip vessel walls of Sec. 3.1);
@@ -49,6 +51,8 @@ class System:
     X0: np.ndarray                  # (N, 3) float64 rest positions (platelets; copy of x elsewhere)
     bonds: np.ndarray               # (nb, 2) int32 particle ids
     r0: np.ndarray                  # (nb,) float64 rest lengths
+    angles: np.ndarray = None       # (na, 3) int32 particle ids (i, vertex j, k) of the Eq. 2 angle term
+    theta0: np.ndarray = None       # (na,) float64 rest angles
     walls: bool = False
     wall: float = 1.0               # wall layer thickness
     shear_rate: float = 0.0         # Lees-Edwards rate (periodic y only)
@@ -117,6 +121,51 @@ def knn_bonds(points, k=6):
     return pairs.astype(np.int32), r0
 
 
+# Bending triplets: at each vertex j, every bonded neighbour i paired with
+# the bonded neighbour k across from it (the largest angle i-j-k, if above
+# 150 degrees) -- three nearly straight lines through each vertex of the
+# membrane, as in a triangulated sheet.  Their reference angle is pi (a flat
+# membrane, no spontaneous curvature): the (theta - theta0)^2 form of Eq. 2
+# has a cone point at theta = pi, where the force turns over unless theta0 is
+# pi itself, and thermal bending of the shells crosses it.
+ANGLE_MIN = 5.0 * math.pi / 6.0
+
+
+def angle_triplets(points, pairs, min_angle=ANGLE_MIN):
+    """Bending triplets (i, j, k) of a bonded shell, j the vertex and i < k,
+    and their reference angles (pi)."""
+    n = points.shape[0]
+    nb = [[] for _ in range(n)]
+    for a, b in pairs:
+        nb[a].append(b)
+        nb[b].append(a)
+    tri = set()
+    for j in range(n):
+        ns = nb[j]
+        if len(ns) < 2:
+            continue
+        u = points[ns] - points[j]
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        c = u @ u.T
+        np.fill_diagonal(c, 2.0)
+        for a in range(len(ns)):
+            b = int(np.argmin(c[a]))
+            if np.arccos(np.clip(c[a, b], -1.0, 1.0)) > min_angle:
+                i, k = sorted((ns[a], ns[b]))
+                tri.add((i, j, k))
+    if not tri:
+        return np.zeros((0, 3), np.int32), np.zeros(0)
+    t = np.asarray(sorted(tri), np.int32)
+    return t, np.full(len(t), math.pi)
+
+
+def triplet_angles(points, t):
+    a = points[t[:, 0]] - points[t[:, 1]]
+    b = points[t[:, 2]] - points[t[:, 1]]
+    c = (a * b).sum(1) / (np.linalg.norm(a, axis=1) * np.linalg.norm(b, axis=1))
+    return np.arccos(np.clip(c, -1.0, 1.0))
+
+
 def scaled_radii(n_shell, base_n=2000, base=(4.0, 2.0, 2.0)):
     """Radii keeping the 2,000-particle (4,2,2) shell's areal density."""
     s = math.sqrt(n_shell / base_n)
@@ -177,7 +226,49 @@ def _place_platelets(rng, n_plt, n_shell, radii, lo, hi, centers_fn=None,
     return out
 
 
-def _assemble(box, fluid_x, wall_x, plts, rng, n_shell, receptor_frac, kT=1.0):
+def small_rotation(rng, angle):
+    """Rotation by a uniform random angle in [0, angle] about a random axis."""
+    u = rng.standard_normal(3)
+    u /= np.linalg.norm(u)
+    t = angle * rng.random()
+    K = np.array([[0.0, -u[2], u[1]], [u[2], 0.0, -u[0]], [-u[1], u[0], 0.0]])
+    return np.eye(3) + math.sin(t) * K + (1.0 - math.cos(t)) * (K @ K)
+
+
+def _lattice_platelets(rng, count, n_shell, radii, x0, y_wall, up, Lz, lo, hi, occ, gap=2.5, jitter=0.03):
+    """A wall-attached aggregate: `count` shells lying with their long axis
+    along the flow (x), packed on a lattice that fills layer by layer away
+    from the wall at y = y_wall (`up` = +1 for the lower wall, -1 for the
+    upper), neighbours `gap` apart at their closest points (within the
+    receptor Morse range, so that the aggregate starts bound), each turned by
+    a small random rotation."""
+    a, b, _ = radii
+    sx, sy, sz = 2 * a + gap, 2 * b + gap, 2 * b + gap
+    nz = max(1, int((Lz - 2 * b - 1.0) // sz) + 1)
+    per_layer_x = max(1, int(math.ceil(count / (nz * max(1, int(math.ceil(count / (nz * 5))))))))
+    body = spheroid_shell(n_shell, radii)
+    out = []
+    k = 0
+    layer = 0
+    while len(out) < count:
+        yc = y_wall + up * (b + 1.5 + layer * sy)
+        for ix in range(per_layer_x):
+            for iz in range(nz):
+                if len(out) >= count:
+                    break
+                c = np.array([x0 + (ix - (per_layer_x - 1) / 2) * sx, yc, Lz / 2 + (iz - (nz - 1) / 2) * sz])
+                rot = small_rotation(rng, jitter)
+                pts = body @ rot.T + c
+                k += 1
+                if (pts < np.asarray(lo) + 0.5).any() or (pts > np.asarray(hi) - 0.5).any() or not occ.free(pts):
+                    raise RuntimeError("aggregate lattice does not fit the channel")
+                occ.mark(pts)
+                out.append((pts, c, rot))
+        layer += 1
+    return out
+
+
+def _assemble(box, fluid_x, wall_x, plts, rng, n_shell, receptor_frac, kT=1.0, body=None):
     nf = fluid_x.shape[0]
     nw = wall_x.shape[0]
     npl = len(plts)
@@ -189,7 +280,13 @@ def _assemble(box, fluid_x, wall_x, plts, rng, n_shell, receptor_frac, kT=1.0):
     tag[nf:nf + nw] = TAG_WALL
     bonds = []
     r0s = []
+    angs = []
+    th0s = []
     base = nf + nw
+    # every shell is a rigid motion of the same body-frame points: one
+    # neighbour search gives every shell's bond and angle topology
+    topo = knn_bonds(body)[0] if (npl and body is not None) else None
+    atopo = angle_triplets(body, topo)[0] if topo is not None else None
     for p in range(npl):
         off = base + p * n_shell
         t = np.full(n_shell, p, dtype=np.int32)
@@ -197,43 +294,106 @@ def _assemble(box, fluid_x, wall_x, plts, rng, n_shell, receptor_frac, kT=1.0):
         rec = rng.permutation(n_shell)[:nrec]
         t[rec] |= RECEPTOR_BIT
         tag[off:off + n_shell] = t
-        b, r0 = knn_bonds(plts[p][0])
+        pts = plts[p][0]
+        if topo is None:
+            b, r0 = knn_bonds(pts)
+            at, th0 = angle_triplets(pts, b)
+        else:
+            b = topo
+            r0 = np.linalg.norm(pts[b[:, 0]] - pts[b[:, 1]], axis=1)
+            at = atopo
+            th0 = np.full(len(at), math.pi)
         bonds.append(b + off)
         r0s.append(r0)
+        angs.append(at + off)
+        th0s.append(th0)
     v = maxwell(rng, n, kT)
     v[nf:nf + nw] = 0.0
-    mob = tag != TAG_WALL
-    if mob.any():
-        v[mob] -= v[mob].mean(axis=0, keepdims=True)
+    n_mob = n - nw
+    if n_mob > 0:               # net momentum of the mobile particles removed
+        v -= v.sum(axis=0, keepdims=True) / n_mob
+        v[nf:nf + nw] = 0.0
     bonds = np.concatenate(bonds, axis=0).astype(np.int32) if bonds else np.zeros((0, 2), np.int32)
     r0 = np.concatenate(r0s) if r0s else np.zeros((0,), np.float64)
-    return x, v, tag, bonds, r0
+    angles = np.concatenate(angs, axis=0).astype(np.int32) if angs else np.zeros((0, 3), np.int32)
+    theta0 = np.concatenate(th0s) if th0s else np.zeros((0,), np.float64)
+    return x, v, tag, bonds, r0, angles, theta0
 
 
-def _fill_platelets(rng, fx, plts, radii, box, gap, rho=3.0):
+class VoxelPlasma:
+    """Uniform plasma positions drawn voxel by voxel: the box is cut into
+    nv[0] x nv[1] x nv[2] equal voxels, the counts per voxel are one
+    multinomial draw with equal probabilities and each voxel's positions are
+    uniform inside it -- together exactly n independent uniform positions in
+    the box, stored grouped by voxel (start[v] .. start[v + 1]) so that the
+    plasma near a point is a few contiguous slices."""
+
+    def __init__(self, rng, n, box, cell):
+        self.L = np.asarray(box, dtype=np.float64)
+        self.nv = np.maximum(np.floor(self.L / cell).astype(np.int64), 1)
+        self.h = self.L / self.nv
+        nvox = int(self.nv.prod())
+        counts = rng.multinomial(n, np.full(nvox, 1.0 / nvox))
+        self.start = np.concatenate([[0], np.cumsum(counts)])
+        x = rng.random((n, 3))
+        vid = np.repeat(np.arange(nvox, dtype=np.int64), counts)
+        ny_nz = self.nv[1] * self.nv[2]
+        x[:, 0] += vid // ny_nz
+        x[:, 1] += (vid // self.nv[2]) % self.nv[1]
+        x[:, 2] += vid % self.nv[2]
+        del vid
+        x *= self.h
+        self.x = x
+
+    def near(self, c):
+        """Plasma rows in the 27 voxels around point c (periodic wrap): a
+        superset of those within one voxel edge of c."""
+        cv = np.minimum(np.floor((np.asarray(c) % self.L) / self.h).astype(np.int64), self.nv - 1)
+        offs = np.array([(i, j, k) for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)])
+        w = (cv[None, :] + offs) % self.nv
+        vs = np.unique((w[:, 0] * self.nv[1] + w[:, 1]) * self.nv[2] + w[:, 2])
+        return np.concatenate([np.arange(self.start[v], self.start[v + 1]) for v in vs])
+
+
+def _fill_platelets(rng, plasma, plts, radii, box, gap, rho=3.0, body=None):
     """Plasma around and inside the shells: positions inside a spheroid or
     closer than `gap` to its membrane are dropped, and each interior gets
     1.1 rho x (the volume of the spheroid shrunk by `gap`) positions drawn
     uniformly in that shrunken spheroid.  A plasma particle on top of the
     dense membrane would start under the summed repulsion of dozens of
     membrane particles, and a shell without its interior fluid collapses
-    under the outer pressure (it has no bending stiffness); a slightly denser
-    interior keeps it inflated."""
+    under the outer pressure; a slightly denser interior keeps it inflated.
+    `plasma` is a VoxelPlasma with voxels at least a.max() + gap wide."""
     from scipy.spatial import cKDTree
     L = np.asarray(box, dtype=np.float64)
     a = np.asarray(radii, dtype=np.float64)
+    fx = plasma.x
     keep = np.ones(len(fx), dtype=bool)
-    tree = cKDTree(fx % L, boxsize=L)
+    reach = a.max() + gap
+    # every shell is a rigid motion of the same body-frame points, so the
+    # distance to a membrane is measured in the body frame against one tree
+    tree = cKDTree(body)
     interiors = []
     for pts, c, rot in plts:
-        near = np.asarray(tree.query_ball_point(np.asarray(c) % L, a.max() + gap), dtype=np.int64)
+        cand = plasma.near(c)
+        d = fx[cand] - c
+        for k in range(3):                                # minimum image
+            dk = d[:, k]
+            dk[dk > 0.5 * L[k]] -= L[k]
+            dk[dk < -0.5 * L[k]] += L[k]
+        close = (d * d).sum(1) <= reach * reach
+        near, d = cand[close], d[close]
         if len(near):
-            d = fx[near] - c
-            d -= L * np.round(d / L)
             y = d @ rot                                   # body frame
-            inside = ((y / a) ** 2).sum(1) < 1.0
-            dm, _ = cKDTree(pts).query(c + d, distance_upper_bound=gap)
-            keep[near[inside | np.isfinite(dm)]] = False
+            er = np.sqrt(((y / a) ** 2).sum(1))           # ellipsoidal radius: the membrane is er = 1
+            inside = er < 1.0
+            # a point at er >= 1 lies on the shell scaled by er, at least
+            # (er - 1) times the smallest semi-axis from the membrane
+            band = ~inside & ((er - 1.0) * a.min() <= gap)
+            dm, _ = tree.query(y[band], distance_upper_bound=gap)
+            drop = inside.copy()
+            drop[np.nonzero(band)[0][np.isfinite(dm)]] = True
+            keep[near[drop]] = False
         b = np.maximum(a - gap, 0.05)
         n_in = int(round(1.1 * rho * 4.0 / 3.0 * np.pi * b.prod()))
         u = rng.standard_normal((n_in, 3))
@@ -268,15 +428,16 @@ def plasma_box(n=None, box=None, rho=3.0, walls=False, wall=1.0, body_force=0.0,
         n = int(round(rho * box[0] * box[1] * box[2]))
     fx = uniform_box(rng, n, (0, 0, 0), box)
     wx = wall_layers(rng, box, wall, rho) if walls else np.zeros((0, 3))
-    x, v, tag, bonds, r0 = _assemble(box, fx, wx, [], rng, 0, 0.0, kT)
-    return System(box=tuple(box), x=x, v=v, tag=tag, X0=x.copy(), bonds=bonds, r0=r0,
+    x, v, tag, bonds, r0, angles, theta0 = _assemble(box, fx, wx, [], rng, 0, 0.0, kT)
+    return System(box=tuple(box), x=x, v=v, tag=tag, X0=x.copy(), bonds=bonds, r0=r0, angles=angles, theta0=theta0,
                   walls=walls, wall=wall, shear_rate=shear_rate, body_force=body_force,
                   meta=dict(kind="plasma", seed=seed))
 
 
 def platelet_system(box, n_plasma, n_plt, n_shell, radii, walls=False, wall=1.0,
                     shear_rate=0.0, body_force=0.0, receptor_frac=0.05,
-                    seed=DEFAULT_SEED, centers=None, clusters=None, kT=1.0, plasma_gap=0.8, developed_flow=False):
+                    seed=DEFAULT_SEED, centers=None, clusters=None, kT=1.0, plasma_gap=0.8, developed_flow=False,
+                    aggregates=None):
     """Plasma + spheroid platelet shells (Fig. 1 shapes, synthetic sizes).
 
     n_plasma plasma positions are drawn uniformly; see _fill_platelets for
@@ -297,6 +458,8 @@ def platelet_system(box, n_plasma, n_plt, n_shell, radii, walls=False, wall=1.0,
             pts = body @ rot.T + np.asarray(c, dtype=np.float64)
             occ.mark(pts)
             plts.append((pts, np.asarray(c, dtype=np.float64), rot))
+    for (x0, y_wall, up, count) in (aggregates or ()):
+        plts += _lattice_platelets(rng, count, n_shell, radii, x0, y_wall, up, box[2], lo, hi, occ)
     if clusters:
         for (cx, cy, cz, spread, count) in clusters:
             def cfn(r, cx=cx, cy=cy, cz=cz, spread=spread):
@@ -305,16 +468,21 @@ def platelet_system(box, n_plasma, n_plt, n_shell, radii, walls=False, wall=1.0,
     rest = n_plt - len(plts)
     if rest > 0:
         plts += _place_platelets(rng, rest, n_shell, radii, lo, hi, occ=occ)
-    fx = uniform_box(rng, n_plasma, (0, 0, 0), box)
-    if plts and len(fx):
-        fx = _fill_platelets(rng, fx, plts, radii, box, plasma_gap)
+    body = spheroid_shell(n_shell, radii) if plts else None
+    if plts and n_plasma:
+        plasma = VoxelPlasma(rng, n_plasma, box, max(radii) + plasma_gap)
+        fx = _fill_platelets(rng, plasma, plts, radii, box, plasma_gap, body=body)
+        del plasma
+    else:
+        fx = uniform_box(rng, n_plasma, (0, 0, 0), box)
     wx = wall_layers(rng, box, wall) if walls else np.zeros((0, 3))
-    x, v, tag, bonds, r0 = _assemble(box, fx, wx, plts, rng, n_shell, receptor_frac, kT)
+    x, v, tag, bonds, r0, angles, theta0 = _assemble(box, fx, wx, plts, rng, n_shell, receptor_frac, kT, body=body)
+    del fx
     if developed_flow and walls and body_force:
         mob = tag != TAG_WALL
         y = x[mob, 1]
         v[mob, 0] += 3.0 * body_force * y * (box[1] - y) / (2.0 * ETA_DPD)
-    return System(box=box, x=x, v=v, tag=tag, X0=x.copy(), bonds=bonds, r0=r0,
+    return System(box=box, x=x, v=v, tag=tag, X0=x.copy(), bonds=bonds, r0=r0, angles=angles, theta0=theta0,
                   walls=walls, wall=wall, shear_rate=shear_rate, body_force=body_force,
                   n_platelets=n_plt, meta=dict(kind="platelets", seed=seed, n_shell=n_shell,
                                                radii=tuple(radii)))
@@ -359,14 +527,15 @@ def config_channel_platelets(box=(400.0, 100.0, 67.0), n_plt=16, n_shell=10_000,
 
 def config_paper_scale(box=(1100.0, 300.0, 93.0), n_flow=70, n_clot=90, n_shell=40_000,
                        seed=DEFAULT_SEED, shear_rate=0.05, eta=ETA_DPD):
-    """Paper-sized single-GPU system: two wall-attached clusters of n_clot shells at
-    the same x on opposite walls plus n_flow flowing shells in a walled channel."""
+    """Paper-sized single-GPU system (Sec. 3.1: a clot of about 102 M
+    particles): two wall-attached aggregates of n_clot shells at the same x on
+    opposite walls (packed from the wall outwards, neighbours within the
+    receptor Morse range) plus n_flow shells placed at random in the walled
+    channel; plasma at rho = 3 around and inside them."""
     Lx, Ly, Lz = box
     radii = scaled_radii(n_shell)
     n_pl = int(round(3.0 * Lx * Ly * Lz))
     g = poiseuille_g(shear_rate, eta, 3.0, Ly)
-    b = radii[1]
-    clusters = [(Lx / 2, b + 1.5, Lz / 2, 3.0 * radii[0], n_clot),
-                (Lx / 2, Ly - b - 1.5, Lz / 2, 3.0 * radii[0], n_clot)]
+    aggregates = [(Lx / 2, 0.0, 1, n_clot), (Lx / 2, Ly, -1, n_clot)]
     return platelet_system(box, n_pl, n_flow + 2 * n_clot, n_shell, radii, walls=True,
-                           body_force=g, seed=seed, clusters=clusters)
+                           body_force=g, seed=seed, aggregates=aggregates)

@@ -121,3 +121,27 @@ def test_predict_trust_bound():
     out = A.predict(p, raw, 0.0, 1.0, rec_threshold=-1.0, p_min=0.0)
     assert not out["trusted"].any()
     assert np.all((out["hold"] >= 100) & (out["hold"] <= 2000))
+
+
+def test_trust_decision_reasons_and_fallback():
+    """Table 2 steps 5-6 on hand-made outputs: a confident window keeps its
+    class's ratio; low top probability, a reconstruction error above the
+    bound and a bond strain above the bound (at a single step of the raw
+    window) each give the fallback ratio with their own reason bit; the hold
+    is exp(log hold) clipped to [100, 2000] and truncated, a NaN gives the
+    lower end."""
+    prob = np.array([[0.05, 0.05, 0.8, 0.05, 0.05],    # class 2 -> k = 5
+                     [0.3, 0.3, 0.2, 0.1, 0.1],         # top 0.3 < 0.6
+                     [0.0, 0.0, 0.0, 0.9, 0.1],         # rec too large
+                     [0.0, 0.0, 0.0, 0.0, 1.0],         # strain too large
+                     [np.nan, 0.0, 0.0, 0.0, 0.0]])
+    rec = np.array([0.1, 0.1, 5.0, 0.1, 0.1])
+    raw = np.zeros((5, 4, 12))
+    raw[3, 2, 9] = 0.9
+    log_hold = np.log([50.0, 150.7, 1e4, 999.9, 1.0])
+    log_hold[4] = np.nan
+    k, hold, why = A.trust_decision(prob, rec, log_hold, raw, p_min=0.6, rec_threshold=1.0, strain_max=0.5,
+                                    strain_col=9, fallback_k=10)
+    assert k.tolist() == [5, 10, 10, 10, 10]
+    assert why.tolist() == [0, A.UNSURE_PROB, A.UNSURE_REC, A.UNSURE_STRAIN, A.UNSURE_PROB]
+    assert hold.tolist() == [100, 150, 2000, 999, 100]

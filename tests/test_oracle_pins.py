@@ -457,12 +457,12 @@ def test_velocity_verlet_time_reversible():
 
 def test_nve_energy_error_scales_as_dt_squared():
     """Velocity-Verlet is second order: the energy fluctuation of a bonded shell
-    shrinks ~4x when dt is halved, and stays small."""
+    (bonds and angles) shrinks ~4x when dt is halved, and stays small."""
     s = shell_only()
     p = O.system_params(s)
     e0 = total_energy(p, s.x, s.v, s)
     errs = []
-    for dt, n in ((0.004, 50), (0.002, 100)):
+    for dt, n in ((0.002, 100), (0.001, 200)):
         x, v, _ = O.run_respa(p, s.x, s.v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, dt_f=dt,
                               n_outer=n)
         errs.append(abs(total_energy(p, x, v, s) - e0))
@@ -708,14 +708,15 @@ def test_poiseuille_viscosity_consistent_with_couette_stress(couette):
 def test_nve_energy_drift_of_bonded_shells_with_lj():
     """CGMD in NVE (no fluid, no thermostat): two bonded 200-particle shells
     that start within the LJ range of each other (Eq. 2 bonds and LJ; the
-    receptor Morse switched off), velocity-Verlet at dt = 0.001 for 10^4 steps.
+    receptor Morse and the angle term switched off), velocity-Verlet at
+    dt = 0.001 for 10^4 steps.
     The total energy stays within 1e-4 of its start, and its linear drift
     over the run (the fitted slope times the duration) is below 1e-4 of it."""
     n_shell, gap = 200, 1.2
     r = synth.scaled_radii(n_shell)
     s = synth.platelet_system((30.0, 30.0, 30.0), 0, 2, n_shell, r, seed=23,
                               centers=[(15.0 - r[0] - gap / 2, 15.0, 15.0), (15.0 + r[0] + gap / 2, 15.0, 15.0)])
-    p = O.system_params(s, m_D=0.0, m_rc=2.0)
+    p = O.system_params(s, m_D=0.0, m_rc=2.0, k_a=0.0)
     v = 0.5 * s.v
 
     def energy(x, v):
@@ -821,3 +822,120 @@ def test_ai_mts_time_reversible_with_mixed_ratios():
     x2, v2, _ = O.run_ai_respa(p, x1, -v1, s.tag, [1, 2], **kw)
     assert np.abs(x2 - s.x).max() < 1e-9
     assert np.abs(v2 + v0).max() < 1e-8
+
+
+# --------------------------------------------------------------------------
+# Eq. 2 -- angle term k_a (theta - theta0)^2
+# --------------------------------------------------------------------------
+
+def three_body(theta, r1=0.3, r2=0.25, box=(10.0, 10.0, 10.0), shift=(5.0, 5.0, 5.0)):
+    """i at r1 along x from the vertex j, k at r2 in the xy plane at angle theta."""
+    j = np.array(shift)
+    x = np.array([j + [r1, 0.0, 0.0], j, j + [r2 * math.cos(theta), r2 * math.sin(theta), 0.0]])
+    return x, np.zeros((3, 3)), np.zeros(3, np.int32)
+
+
+@pytest.mark.parametrize("theta,theta0", [(2.6, 2.8), (2.9, 2.7), (1.4, 1.0)])
+def test_angle_force_closed_form(theta, theta0):
+    """Eq. 2 angle term as printed, U = k_a (theta - theta0)^2: the energy, and
+    the force on each arm's end, 2 k_a |theta - theta0| / r perpendicular to
+    its arm in the plane, turning the angle back toward theta0; the vertex
+    takes the opposite of their sum."""
+    k_a = 20.0
+    x, v, tag = three_body(theta)
+    p = O.make_params((10, 10, 10), k_a=k_a, angles=[[0, 1, 2]], theta0=[theta0])
+    f, acc = O.forces_brute(p, x, v, tag, level_mask=O.LVL_PLT)
+    assert acc["epot"] == pytest.approx(k_a * (theta - theta0) ** 2, rel=1e-12)
+    mag = 2.0 * k_a * (theta - theta0)
+    # on i (arm along +x): along +y when the angle must shrink (theta > theta0)
+    assert f[0] == pytest.approx([0.0, mag / 0.3, 0.0], abs=1e-12)
+    # on k (arm at angle theta): along the inward normal (sin t, -cos t) times the same sign
+    assert f[2] == pytest.approx([mag / 0.25 * math.sin(theta), -mag / 0.25 * math.cos(theta), 0.0], abs=1e-12)
+    assert f[1] == pytest.approx(-(f[0] + f[2]), abs=1e-12)
+
+
+def test_angle_force_is_minus_gradient():
+    """F = -grad U for triplets in general position, one of them across the
+    periodic x face, by central differences of the oracle's energy."""
+    rng = np.random.default_rng(12)
+    x = rng.uniform(4.0, 6.0, (6, 3))
+    x[3:] = x[:3] * 0.2 + np.array([9.85, 3.0, 3.0])       # a triplet straddling x = 10
+    x[3, 0] = 0.1
+    x %= 10.0
+    tag = np.zeros(6, np.int32)
+    p = O.make_params((10, 10, 10), k_a=20.0, angles=[[0, 1, 2], [3, 4, 5]], theta0=[2.5, 2.0])
+    f, _ = O.forces_brute(p, x, np.zeros_like(x), tag, level_mask=O.LVL_PLT)
+    h = 1e-6
+    for a in range(6):
+        for d in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[a, d] += h
+            xm[a, d] -= h
+            up = O.forces_brute(p, xp, np.zeros_like(x), tag, level_mask=O.LVL_PLT)[1]["epot"]
+            um = O.forces_brute(p, xm, np.zeros_like(x), tag, level_mask=O.LVL_PLT)[1]["epot"]
+            assert f[a, d] == pytest.approx(-(up - um) / (2 * h), rel=1e-6, abs=1e-6)
+
+
+def test_angle_forces_conserve_momentum_and_angular_momentum():
+    """The angle term depends on relative positions and on nothing that turns
+    with the body: its forces sum to zero and exert no net torque."""
+    rng = np.random.default_rng(13)
+    x = 5.0 + rng.standard_normal((3, 3)) * 0.3
+    p = O.make_params((10, 10, 10), k_a=20.0, angles=[[0, 1, 2]], theta0=[2.0])
+    f, _ = O.forces_brute(p, x, np.zeros_like(x), np.zeros(3, np.int32), level_mask=O.LVL_PLT)
+    assert np.abs(f.sum(0)).max() < 1e-12
+    assert np.abs(np.cross(x - x.mean(0), f).sum(0)).max() < 1e-11
+
+
+def test_shell_angles_bend_straight_through_vertices_and_rest_at_theta0():
+    """The synthetic shells' angle triplets: both arms bonded to the vertex,
+    each the straight continuation across it (rest angle above 150 degrees),
+    every vertex in at least one triplet, reference angle pi; and a flat
+    triangular sheet, where those triplets are straight, feels no angle
+    force."""
+    s = synth.platelet_system((20.0, 20.0, 20.0), 0, 1, 400, synth.scaled_radii(400), seed=3,
+                              centers=[(10.0, 10.0, 10.0)])
+    bonded = set(map(tuple, np.sort(s.bonds, 1).tolist()))
+    for i, j, k in s.angles.tolist():
+        assert tuple(sorted((i, j))) in bonded and tuple(sorted((j, k))) in bonded
+    assert synth.triplet_angles(s.x, s.angles.astype(np.int64)).min() > np.radians(150.0)
+    assert np.all(s.theta0 == math.pi)
+    assert set(s.angles[:, 1].tolist()) == set(range(s.n))
+    # a flat triangular patch (spacing 0.22) and its own bending triplets
+    pts = np.array([[0.22 * (i + 0.5 * (j % 2)), 0.22 * math.sqrt(3) / 2 * j, 0.0]
+                    for j in range(6) for i in range(6)]) + 5.0
+    d = np.linalg.norm(pts[:, None] - pts[None], axis=-1)
+    pairs = np.argwhere(np.triu(np.abs(d - 0.22) < 1e-9, 1))      # the lattice's nearest neighbours
+    tri, th0 = synth.angle_triplets(pts, pairs)
+    assert len(tri) > 20
+    p = O.make_params((20, 20, 20), k_a=20.0, k_b=0.0, angles=tri, theta0=th0)
+    f, acc = O.forces_brute(p, pts, np.zeros_like(pts), np.zeros(len(pts), np.int32), level_mask=O.LVL_PLT)
+    assert np.abs(f).max() < 1e-9 and abs(acc["epot"]) < 1e-12
+
+
+@pytest.mark.slow
+def test_nve_energy_drift_of_a_shell_with_bonds_and_angles():
+    """CGMD in NVE: one bonded 200-particle shell with the Eq. 2 angle term on
+    its bending triplets (k = 20, flat reference), velocity-Verlet at
+    dt = 0.001 for 10^4 steps from Maxwell velocities at kT = 1: total energy
+    within 1e-4 of its start and fitted drift below 1e-4."""
+    s = synth.platelet_system((30.0, 30.0, 30.0), 0, 1, 200, synth.scaled_radii(200), seed=11,
+                              centers=[(15.0, 15.0, 15.0)])
+    p = O.system_params(s, m_rc=2.0)
+    assert p.n_angles == len(s.angles) > 400 and p.k_a == 20.0
+
+    def energy(x, v):
+        _, acc = O.forces_brute(p, x, v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, level_mask=O.LVL_PLT)
+        return 0.5 * (v * v).sum() + acc["epot"]
+
+    x, v, f, n0 = s.x, s.v, None, 0
+    es = [energy(x, v)]
+    for block in range(10):
+        x, v, f = O.run_respa(p, x, v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, dt_f=0.001, n_outer=1000,
+                              forces=f, n0=n0)
+        n0 += 1000
+        es.append(energy(x, v))
+    es = np.array(es)
+    e = abs(es.mean())
+    assert np.abs(es - es[0]).max() < 1e-4 * e
+    assert abs(np.polyfit(np.arange(11), es, 1)[0] * 10) < 1e-4 * e
