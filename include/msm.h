@@ -87,9 +87,9 @@ extern "C" {
  * sigma = 3, rc = 1; Eq. 3 interface DPD a_fp = 50; Eq. 2 LJ eps = 1,
  * sigma = 0.8, cut-off 2.5 sigma, between particles of different platelets
  * (lj_excl = 1e30: a same-platelet pair feels LJ only when its rest distance
- * is at least lj_excl -- the shells have no bending stiffness, so a fold of
- * the 0.22-spaced membrane would overlap dozens of LJ cores at once), k_b =
- * 100; Eq. 2/4 Morse D = 2, alpha = 2, r0 = 1 with cut-off 5.
+ * is at least lj_excl), k_b = 100, angle constant k_theta = 20 on the bending
+ * triplets given to md_set_angles; Eq. 2/4 Morse D = 2, alpha = 2, r0 = 1 with
+ * cut-off 5.
  */
 typedef struct md_config {
     int64_t  n;               /* particles (plasma + wall + platelet), 1 .. 2^27  */
@@ -115,6 +115,9 @@ typedef struct md_config {
                                  LJ and Morse lists reach cut-off + skin_plt, the
                                  interface list rc + (skin + skin_plt) / 2, and a
                                  platelet particle trips a rebuild at skin_plt/2 */
+    int64_t  n_angles;        /* angle triplets of the Eq. 2 angle term          */
+    double   k_angle;         /* its constant k_theta in U = k_theta (theta -
+                                 theta0)^2 (as printed, no 1/2); default 20      */
 } md_config;
 
 /* Fill *cfg with the defaults above for n particles in box (no platelets). */
@@ -182,6 +185,20 @@ int md_set_xv(md_system *sys, const double *x, const double *v, int64_t step0);
 int md_set_bonds(md_system *sys, const int32_t *ij, const double *r0, int64_t nb);
 
 /*
+ * Angle term of Eq. 2, U = k_angle (theta - theta0)^2 summed over triplets,
+ * as HOST arrays: ijk[na*3] particle ids (i, vertex j, k) of one platelet,
+ * theta0[na] rest angles in radians.  theta is the angle at j between the
+ * minimum images of x_i - x_j and x_k - x_j; the force on i is
+ * 2 k (theta - theta0) / sin(theta) (e_kj - cos(theta) e_ij) / |x_i - x_j|
+ * (sin theta held at 1e-3 at least), on k likewise, on j minus their sum.
+ * The term belongs to the platelet level (MD_LEVEL_PLT) and, under AI-MTS,
+ * to its platelet's step ratio.  na must equal cfg.n_angles.
+ * Errors: MD_EINVAL (count, an id out of range, a triplet spanning
+ * platelets), MD_ECUDA.
+ */
+int md_set_angles(md_system *sys, const int32_t *ijk, const double *theta0, int64_t na);
+
+/*
  * Verlet-skin neighbour lists (Table 1, "neighbor lists construction"):
  * cell binning and counting sort of every particle array (K1), then every
  * list (K2).  force = 0 rebuilds only when some particle moved more than
@@ -237,6 +254,13 @@ int md_read_particles(md_system *sys, double *x, double *v, float *x32);
 #define MD_SCHED_DIRECT 1  /* launch every kernel from the host (no CUDA graph) */
 #define MD_SCHED_RECORD 2  /* append the per-platelet measurements after every
                               outer step to the feature ring (md_record_features) */
+#define MD_SCHED_DETERMINISTIC 4  /* every force of the call summed as with
+                              MD_FORCE_DETERMINISTIC (64-bit fixed point, lower
+                              id first), so that a trajectory does not depend
+                              on the order of the atomic updates: two runs from
+                              the same state, or a run resumed from md_get_state,
+                              agree bit for bit.  STS and RESPA only (MD_EINVAL
+                              with MD_MODE_AI); slower than the default */
 
 typedef struct md_mts_schedule {
     int32_t mode;        /* MD_MODE_*                                            */
@@ -330,8 +354,9 @@ int md_platelet_features(md_system *sys, double *out);
 /*
  * Append the current measurements to the device ring of the last 128
  * records per platelet (no host copy), and read that ring back: HOST
- * out[n_platelets][128][12], oldest retained record first; *count gets the
- * number of records appended so far (records beyond 128 overwrite the oldest).
+ * out[n_platelets][128][12], oldest retained record first (out = NULL: only
+ * the count); *count gets the number of records appended so far (records
+ * beyond 128 overwrite the oldest).
  */
 int md_record_features(md_system *sys);
 int md_read_feature_ring(md_system *sys, float *out, int64_t *count);
@@ -426,6 +451,52 @@ int md_ai_grads(md_ai *ai, const float *x, const int32_t *k_class, const float *
                 float *grads, float *loss);
 int md_ai_train_step(md_ai *ai, const float *x, const int32_t *k_class, const float *log_hold, int32_t B,
                      int32_t what, float lr, float *loss);
+
+/*
+ * Table 2 steps 5-6 on the device: the trust bound and the step-ratio map.
+ * A window whose top class probability is below p_min, whose reconstruction
+ * error (mean square over the denoised, normalised window) is above rec_max,
+ * or whose raw measurement column strain_col (the largest bond strain; -1:
+ * no strain test) exceeds strain_max at any step is "unsure" and gets
+ * fallback_k (fixed-k RESPA); every other window gets the ratio of its most
+ * probable class.  The hold length is exp(predicted log hold) clipped to
+ * [hold_min, hold_max] steps, truncated to an integer.  NaN fails every test.
+ */
+typedef struct md_ai_trust {
+    float   p_min;        /* smallest accepted top class probability         */
+    float   rec_max;      /* largest accepted reconstruction error           */
+    float   strain_max;   /* largest accepted value of column strain_col     */
+    int32_t strain_col;   /* raw-window column of the bond strain, -1: none  */
+    int32_t fallback_k;   /* ratio of an unsure window                       */
+    float   hold_min, hold_max;
+} md_ai_trust;
+
+#define MD_AI_UNSURE_PROB   1   /* reason bits of an unsure window */
+#define MD_AI_UNSURE_REC    2
+#define MD_AI_UNSURE_STRAIN 4
+
+/*
+ * Table 2 steps 1-6 for B raw windows [B][T][F] (host or device memory per
+ * `where`): the md_ai_predict pipeline, then the trust bound and ratio map
+ * above on the device.  k_values[n_classes] (HOST): the step ratio of each
+ * class ({1, 2, 5, 10, 20}).  HOST outputs: k_out[B] ratio, hold_out[B] hold
+ * length in steps (may be NULL), why_out[B] MD_AI_UNSURE_* bits, 0 for a
+ * trusted window (may be NULL).  Errors: MD_EINVAL, MD_ENOTRAINED, MD_ECUDA.
+ */
+int md_ai_decide(md_ai *ai, const float *raw, int32_t B, int32_t where, const md_ai_trust *trust,
+                 const int32_t *k_values, int32_t *k_out, int32_t *hold_out, int32_t *why_out);
+
+/*
+ * md_ai_decide on the system's own feature ring (md_record_features; Table 1
+ * "compute and dump platelet physical properties"): the last T records of
+ * every platelet are gathered in time order on the device and decided there,
+ * one window per platelet (B = n_platelets), so that only the P decisions
+ * cross to the host.  Drains the system's stream first.  Errors: MD_EINVAL
+ * (no platelets, fewer than T records, or a controller whose batch, window
+ * or measurement count does not fit the system), MD_ENOTRAINED, MD_ECUDA.
+ */
+int md_ai_decide_system(md_ai *ai, md_system *sys, const md_ai_trust *trust, const int32_t *k_values,
+                        int32_t *k_out, int32_t *hold_out, int32_t *why_out);
 
 /* ---- diagnostics ---------------------------------------------------------- */
 #define MD_PROF_FLUID   0  /* K3 plasma-plasma / plasma-wall DPD pass          */

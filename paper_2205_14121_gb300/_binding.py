@@ -21,6 +21,7 @@ MD_LIST_FLUID, MD_LIST_IFACE, MD_LIST_LJ, MD_LIST_MORSE = 0, 1, 2, 3
 MD_FORCE_VIRIAL = 1
 MD_FORCE_DETERMINISTIC = 2
 MD_MODE_STS, MD_MODE_RESPA, MD_MODE_AI = 0, 1, 2
+MD_SCHED_DIRECT, MD_SCHED_RECORD, MD_SCHED_DETERMINISTIC = 1, 2, 4
 RECEPTOR_BIT = 1 << 30
 
 ERRORS = {-1: "MD_EINVAL", -2: "MD_ENOMEM", -3: "MD_ECUDA", -4: "MD_ENBR_OVERFLOW", -5: "MD_EUNSTABLE",
@@ -48,6 +49,7 @@ class md_config(C.Structure):
         ("seed", C.c_uint64),
         ("cap_fluid", C.c_int32), ("cap_iface", C.c_int32), ("cap_lj", C.c_int32), ("cap_morse", C.c_int32),
         ("skin_plt", C.c_double),
+        ("n_angles", C.c_int64), ("k_angle", C.c_double),
     ]
 
 
@@ -134,6 +136,7 @@ def lib():
     L.md_set_particles.argtypes = [vp, dp, dp, ip, dp, i64]
     L.md_set_xv.argtypes = [vp, dp, dp, i64]
     L.md_set_bonds.argtypes = [vp, ip, dp, i64]
+    L.md_set_angles.argtypes = [vp, ip, dp, i64]
     L.md_neighbor_build.argtypes = [vp, u32, C.c_int]
     L.md_forces.argtypes = [vp, u32, u32]
     L.md_read_forces.argtypes = [vp, u32, dp]
@@ -155,6 +158,7 @@ def lib():
     for name in ("md_platelet_features", "md_record_features", "md_read_feature_ring"):
         getattr(L, name).restype = C.c_int
     for name in ("md_config_defaults", "md_workspace_size", "md_init", "md_set_particles", "md_set_xv", "md_set_bonds",
+                 "md_set_angles",
                  "md_neighbor_build", "md_forces", "md_read_forces", "md_read_particles", "md_mts_step",
                  "md_set_platelet_levels", "md_flow_profile",
                  "md_observables", "md_neighbor_pairs", "md_get_state", "md_set_state", "md_profile_enable",
@@ -173,7 +177,7 @@ def _ip(a):
 
 
 def config_for(n, box, tag=None, n_bonds=0, walls=False, wall=1.0, shear_rate=0.0, body_force=0.0, dt=0.01,
-               skin=0.3, seed=20220528, caps=None, flags=0, **params):
+               skin=0.3, seed=20220528, caps=None, flags=0, n_angles=0, **params):
     """md_config for n particles (counts of platelet / receptor particles from tag);
     flags: extra MD_CFG_* bits (MD_CFG_MORSE_STANDARD, MD_CFG_IFACE_LJ,
     MD_CFG_UNIFORM_NOISE)."""
@@ -185,6 +189,7 @@ def config_for(n, box, tag=None, n_bonds=0, walls=False, wall=1.0, shear_rate=0.
     if rc:
         raise MdError(rc, "md_config_defaults")
     cfg.n_bonds = int(n_bonds)
+    cfg.n_angles = int(n_angles)
     if tag is not None:
         t = np.asarray(tag)
         plt = t >= 0
@@ -211,7 +216,8 @@ class System:
     """One md_system over a torch-allocated device workspace."""
 
     def __init__(self, box, x, v, tag, X0=None, bonds=None, r0=None, walls=False, wall=1.0, shear_rate=0.0,
-                 body_force=0.0, dt=0.01, skin=0.3, seed=20220528, step0=0, caps=None, stream=None, **params):
+                 body_force=0.0, dt=0.01, skin=0.3, seed=20220528, step0=0, caps=None, stream=None, angles=None,
+                 theta0=None, **params):
         import torch
 
         if not torch.cuda.is_available():
@@ -220,8 +226,10 @@ class System:
         x = np.ascontiguousarray(x, dtype=np.float64)
         n = x.shape[0]
         bonds = np.zeros((0, 2), np.int32) if bonds is None else np.ascontiguousarray(bonds, dtype=np.int32)
+        angles = np.zeros((0, 3), np.int32) if angles is None else np.ascontiguousarray(angles, dtype=np.int32)
         self.cfg = config_for(n, box, tag=tag, n_bonds=len(bonds), walls=walls, wall=wall, shear_rate=shear_rate,
-                              body_force=body_force, dt=dt, skin=skin, seed=seed, caps=caps, **params)
+                              body_force=body_force, dt=dt, skin=skin, seed=seed, caps=caps, n_angles=len(angles),
+                              **params)
         nbytes = C.c_size_t()
         self._check(L.md_workspace_size(C.byref(self.cfg), C.byref(nbytes)), "md_workspace_size", None)
         self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")
@@ -236,6 +244,8 @@ class System:
         self.set_particles(x, v, tag, X0, step0)
         if len(bonds):
             self.set_bonds(bonds, r0)
+        if len(angles):
+            self.set_angles(angles, theta0)
 
     # -- plumbing ---------------------------------------------------------
     def _check(self, rc, what, h="self"):
@@ -283,6 +293,14 @@ class System:
 
     md_set_bonds = set_bonds
 
+    def set_angles(self, angles, theta0):
+        """Angle triplets (i, vertex j, k) and rest angles of the Eq. 2 angle term."""
+        a = np.ascontiguousarray(angles, dtype=np.int32).reshape(-1, 3)
+        t = np.ascontiguousarray(theta0, dtype=np.float64).reshape(-1)
+        self._check(lib().md_set_angles(self.h, _ip(a), _dp(t), a.shape[0]), "md_set_angles")
+
+    md_set_angles = set_angles
+
     def neighbor_build(self, list_mask=0xF, force=True):
         self._check(lib().md_neighbor_build(self.h, list_mask, int(force)), "md_neighbor_build")
 
@@ -311,8 +329,9 @@ class System:
 
     md_read_particles = read_particles
 
-    def mts_step(self, n_outer, mode=MD_MODE_STS, k_m=1, k_p=1, direct=False, record=False):
-        sched = md_mts_schedule(mode, k_m, k_p, (1 if direct else 0) | (2 if record else 0))
+    def mts_step(self, n_outer, mode=MD_MODE_STS, k_m=1, k_p=1, direct=False, record=False, deterministic=False):
+        sched = md_mts_schedule(mode, k_m, k_p,
+                                (1 if direct else 0) | (2 if record else 0) | (4 if deterministic else 0))
         self._check(lib().md_mts_step(self.h, int(n_outer), C.byref(sched)), "md_mts_step")
 
     md_mts_step = mts_step
@@ -395,6 +414,12 @@ class System:
         return out[:, :min(cnt.value, 128)], cnt.value
 
     md_read_feature_ring = read_feature_ring
+
+    def feature_count(self):
+        """Records appended to the feature ring so far (no ring copy)."""
+        cnt = C.c_int64()
+        self._check(lib().md_read_feature_ring(self.h, None, C.byref(cnt)), "md_read_feature_ring")
+        return cnt.value
 
     def profile_enable(self, on=True):
         self._check(lib().md_profile_enable(self.h, int(on)), "md_profile_enable")

@@ -38,11 +38,13 @@ class TrustBound:
     """Fallback to a fixed ratio when the controller is unsure (Table 2): the
     top class probability is low, or the window lies outside the training
     data (reconstruction error or bond strain beyond their 99th percentiles
-    over the training windows)."""
+    over the training windows).  Applied on the device by md_ai_decide."""
     p_min: float = 0.6           # smallest accepted top class probability
     rec_max: float = math.inf    # largest accepted reconstruction error
     strain_max: float = 0.2      # largest accepted bond strain in the window
     fallback_k: int = 10
+    strain_col: int = F_STRAIN
+    hold_range: tuple = HOLD_RANGE
 
 
 def init_params(cfg, seed=0):
@@ -58,14 +60,11 @@ def init_params(cfg, seed=0):
     return np.concatenate(parts)
 
 
-def decide(pred, windows, trust):
-    """Per-platelet ratio and hold from one prediction, with the trust bound."""
-    k = np.asarray(pred["k"], np.int32).copy()
-    unsure = ((pred["prob"].max(1) < trust.p_min) | (pred["rec_err"] > trust.rec_max)
-              | (windows[:, :, F_STRAIN].max(1) > trust.strain_max))
-    k[unsure] = trust.fallback_k
-    hold = np.clip(np.exp(pred["log_hold"]), *HOLD_RANGE)
-    return k, hold, unsure
+def decide(controller, windows, trust):
+    """Per-platelet ratio, hold and unsure flags for raw windows (Table 2
+    steps 1-6, all on the device)."""
+    d = controller.decide(windows, trust)
+    return d["k"], d["hold"], d["unsure"]
 
 
 def run_ai_mts(system, controller, n_steps, k_m=1, trust=None, T=128, log=None):
@@ -85,15 +84,16 @@ def run_ai_mts(system, controller, n_steps, k_m=1, trust=None, T=128, log=None):
     done = 0
     fresh = state["fresh"]
     while done < n_steps:
-        windows, count = system.read_feature_ring()
+        count = system.feature_count()
         fresh = min(fresh, count)          # new particles restart the ring
         if fresh >= T:
-            pred = controller.predict(windows)
-            k, hold, unsure = decide(pred, windows, trust)
+            d = controller.decide_system(system, trust)
+            k, hold, unsure = d["k"], d["hold"], d["unsure"]
             system.set_platelet_levels(k)
             run = int(hold.min())
             if log is not None:
-                log.append(dict(step=done, k=k.tolist(), hold=hold.tolist(), unsure=unsure.tolist()))
+                log.append(dict(step=done, k=k.tolist(), hold=hold.tolist(), unsure=unsure.tolist(),
+                                why=d["why"].tolist()))
         else:
             run = T - fresh
         run = max(1, min(run, n_steps - done))
@@ -132,7 +132,8 @@ def training_system(seed, box=(36.0, 18.0, 16.0), n_shell=2000, shear_rate=0.05)
 
 
 def make_system(s, **kw):
-    return B.System(s.box, s.x, s.v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, walls=s.walls, wall=s.wall,
+    return B.System(s.box, s.x, s.v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, angles=s.angles,
+                    theta0=s.theta0, walls=s.walls, wall=s.wall,
                     shear_rate=s.shear_rate, body_force=s.body_force, **kw)
 
 
@@ -320,8 +321,7 @@ def evaluate(ctl, windows, err_s, err_v, trust, batch=128):
     n = windows.shape[0]
     ks = []
     for b in range(0, n, batch):
-        pred = ctl.predict(windows[b:b + batch])
-        k, _, _ = decide(pred, windows[b:b + batch], trust)
+        k, _, _ = decide(ctl, windows[b:b + batch], trust)
         ks.append(k)
     k = np.concatenate(ks)
     col = np.searchsorted(np.array(K_SET), k)

@@ -16,6 +16,14 @@ AI_HOST, AI_DEVICE = 0, 1
 TRAIN_AE, TRAIN_HEADS = 1, 2
 
 
+class md_ai_trust(C.Structure):
+    _fields_ = [("p_min", C.c_float), ("rec_max", C.c_float), ("strain_max", C.c_float), ("strain_col", C.c_int32),
+                ("fallback_k", C.c_int32), ("hold_min", C.c_float), ("hold_max", C.c_float)]
+
+
+UNSURE_PROB, UNSURE_REC, UNSURE_STRAIN = 1, 2, 4
+
+
 class md_ai_config(C.Structure):
     _fields_ = [("T", C.c_int32), ("F", C.c_int32), ("hidden", C.c_int32), ("latent", C.c_int32),
                 ("n_classes", C.c_int32), ("head_hidden", C.c_int32 * 3), ("batch_max", C.c_int32)]
@@ -47,6 +55,11 @@ def _bind():
     L.md_ai_prepare.argtypes = [vp, vp, C.c_int32, C.c_int32, fp]
     L.md_ai_grads.argtypes = [vp, fp, ip, fp, C.c_int32, C.c_int32, fp, fp]
     L.md_ai_train_step.argtypes = [vp, fp, ip, fp, C.c_int32, C.c_int32, C.c_float, fp]
+    tp = C.POINTER(md_ai_trust)
+    L.md_ai_decide.argtypes = [vp, vp, C.c_int32, C.c_int32, tp, ip, ip, ip, ip]
+    L.md_ai_decide_system.argtypes = [vp, vp, tp, ip, ip, ip, ip]
+    for n in ("md_ai_decide", "md_ai_decide_system"):
+        getattr(L, n).restype = C.c_int
     for n in ("md_ai_config_defaults", "md_ai_param_count", "md_ai_workspace_size", "md_ai_init", "md_ai_set_params",
               "md_ai_get_params", "md_ai_set_norm", "md_ai_predict", "md_ai_encode", "md_ai_grads", "md_ai_prepare",
               "md_ai_train_step"):
@@ -172,6 +185,42 @@ class Controller:
         probs = out[:, :self.cfg.n_classes]
         return dict(prob=probs, cls=probs.argmax(1), k=np.array(K_SET)[probs.argmax(1)],
                     log_hold=out[:, self.cfg.n_classes], rec_err=out[:, self.cfg.n_classes + 1])
+
+    @staticmethod
+    def _trust(trust):
+        t = md_ai_trust(float(trust.p_min), float(min(trust.rec_max, 3.0e38)), float(min(trust.strain_max, 3.0e38)),
+                        int(trust.strain_col), int(trust.fallback_k), float(trust.hold_range[0]),
+                        float(trust.hold_range[1]))
+        kv = np.ascontiguousarray(K_SET, np.int32)
+        return t, kv
+
+    def _decisions(self, B):
+        k = np.zeros(B, np.int32)
+        hold = np.zeros(B, np.int32)
+        why = np.zeros(B, np.int32)
+        ptr = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+        return k, hold, why, ptr
+
+    def decide(self, raw, trust):
+        """Table 2 steps 1-6 on the device: per-window ratio, hold length and
+        unsure-reason bits (0: the controller's own class was kept)."""
+        raw, rp = self._f(raw)
+        B = raw.shape[0]
+        t, kv = self._trust(trust)
+        k, hold, why, ptr = self._decisions(B)
+        self._check(_bind().md_ai_decide(self.h, C.cast(rp, C.c_void_p), B, AI_HOST, C.byref(t), ptr(kv), ptr(k),
+                                         ptr(hold), ptr(why)), "md_ai_decide")
+        return dict(k=k, hold=hold, why=why, unsure=why != 0)
+
+    def decide_system(self, system, trust):
+        """md_ai_decide on the system's own feature ring (one window per
+        platelet, gathered on the device)."""
+        B = system.cfg.n_platelets
+        t, kv = self._trust(trust)
+        k, hold, why, ptr = self._decisions(B)
+        self._check(_bind().md_ai_decide_system(self.h, system.h, C.byref(t), ptr(kv), ptr(k), ptr(hold), ptr(why)),
+                    "md_ai_decide_system")
+        return dict(k=k, hold=hold, why=why, unsure=why != 0)
 
     def prepare(self, raw):
         """Denoised, normalised windows [B][T][F] (Table 2 steps 1-2, on the device)."""

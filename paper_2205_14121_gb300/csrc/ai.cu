@@ -442,6 +442,70 @@ __global__ void k_adam(float *p, const float *g, float *m, float *v, int64_t n, 
     p[q] -= lr * (mq / c1) / (sqrtf(vq / c2) + eps);
 }
 
+// Table 2 steps 5-6 for window b: the most probable class and its ratio,
+// the trust bound (top probability, reconstruction error, largest bond strain
+// of the raw window), the fallback ratio for a window that fails it, and the
+// hold length exp(log hold) clipped to its range.  A NaN fails every test.
+// Largest value of column col of each raw window [B][T][F] (NaN if any is NaN).
+__global__ void k_window_max(const float *raw, int B, int T, int F, int col, float *out)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const float *w = raw + (int64_t)b * T * F + col;
+    float m = -INFINITY;
+    bool nan = false;
+    for (int t = 0; t < T; ++t) {
+        const float v = w[(int64_t)t * F];
+        nan |= v != v;
+        m = fmaxf(m, v);
+    }
+    out[b] = nan ? NAN : m;
+}
+
+struct decide_args {
+    const float *probs, *lh, *rec, *smax;   // smax: per-window strain maximum (k_window_max)
+    int B, C, T, F;
+    float p_min, rec_max, strain_max, hold_min, hold_max;
+    int strain_col, fallback_k;
+    int kv[8];                             // step ratio of each class
+    int32_t *out;                          // [3][B]: k, hold, reason bits
+};
+
+__global__ void k_decide(decide_args a)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= a.B) return;
+    const float *pr = a.probs + (int64_t)b * a.C;
+    int best = 0;
+    float pmax = pr[0];
+    for (int c = 1; c < a.C; ++c)
+        if (pr[c] > pmax) { pmax = pr[c]; best = c; }
+    int why = 0;
+    if (!(pmax >= a.p_min)) why |= MD_AI_UNSURE_PROB;
+    if (!(a.rec[b] <= a.rec_max)) why |= MD_AI_UNSURE_REC;
+    if (a.strain_col >= 0 && !(a.smax[b] <= a.strain_max)) why |= MD_AI_UNSURE_STRAIN;
+    float h = expf(a.lh[b]);
+    h = h != h ? a.hold_min : fminf(fmaxf(h, a.hold_min), a.hold_max);
+    a.out[b] = why ? a.fallback_k : a.kv[best];
+    a.out[a.B + b] = (int32_t)h;
+    a.out[2 * a.B + b] = why;
+}
+
+// The last T records of every platelet from the system's feature ring, in
+// time order, as raw windows [P][T][F] (the ring holds [P][T][F] with record
+// r at slot r mod T).
+__global__ void k_gather_ring(const float *ring, const md_dstate *ds, int P, int T, int F, float *out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)P * T * F) return;
+    const int f = (int)(q % F);
+    const int t = (int)((q / F) % T);
+    const int64_t p = q / ((int64_t)F * T);
+    const int64_t count = ds->ring_count;
+    const int64_t slot = ((count - T + t) % T + T) % T;
+    out[q] = ring[(p * T + slot) * F + f];
+}
+
 unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
 
 }  // namespace
@@ -474,6 +538,9 @@ struct md_ai {
     float *logits, *lh, *probs, *dlog, *dlh, *rec, *loss, *tmp;
     int32_t *cls;
     float *lht;
+    int32_t *dec;                  // [3][B] decisions: k, hold, reason bits
+    float *smax;                   // [B] per-window maximum of the strain column
+    cudaEvent_t ring_ready = nullptr;
     int64_t adam_t = 0, adam_t_heads = 0;
     bool has_params = false, has_norm = false;
 };
@@ -536,6 +603,8 @@ void plan_ai(md_ai &m, char *base, size_t &off)
     m.dlog = take(B * c.n_classes); m.dlh = take(B); m.rec = take(B); m.loss = take(4); m.tmp = take(B * H3);
     m.cls = reinterpret_cast<int32_t *>(take(B));
     m.lht = take(B);
+    m.dec = reinterpret_cast<int32_t *>(take(3 * B));
+    m.smax = take(B);
 }
 
 int ai_fail(md_ai *m, cudaError_t e, const char *where)
@@ -839,12 +908,24 @@ int md_ai_set_norm(md_ai *m, const float *mean, const float *stdv)
     return MD_OK;
 }
 
-int md_ai_predict(md_ai *m, const float *raw, int32_t B, int32_t where, float *out)
+}  // extern "C"
+
+namespace {
+
+// Table 2 steps 1-4 on the device: denoised, normalised windows through the
+// autoencoder and the heads, then the class probabilities (m->probs), the log
+// hold (m->lh) and the reconstruction error (m->rec).
+int predict_device(md_ai *m, const float *raw, int32_t B, int32_t where, int strain_col = -1)
 {
-    if (!m || !raw || !out || B < 1 || B > m->c.batch_max) return MD_EINVAL;
-    if (!m->has_params) return MD_ENOTRAINED;
     int rc = stage_windows(m, raw, B, where, true);
     if (rc) return rc;
+    if (strain_col >= 0) {
+        // the raw windows (staged in m->Y, or the caller's device array) before
+        // the autoencoder reuses m->Y for its reconstruction
+        const float *src = where == MD_AI_HOST ? m->Y : raw;
+        k_window_max<<<nblk(B, 128), 128, 0, m->st>>>(src, B, m->c.T, m->c.F, strain_col, m->smax);
+        AK(cudaGetLastError(), "window max");
+    }
     rc = ae_forward(m, B, false);
     if (rc) return rc;
     rc = heads_forward(m, B);
@@ -852,6 +933,98 @@ int md_ai_predict(md_ai *m, const float *raw, int32_t B, int32_t where, float *o
     k_heads_loss<<<nblk(B, 128), 128, 0, m->st>>>(m->logits, m->c.n_classes, m->lh, nullptr, nullptr, B, 0.f, nullptr,
                                              nullptr, nullptr, m->probs);
     AK(cudaGetLastError(), "softmax");
+    return MD_OK;
+}
+
+int check_trust(md_ai *m, const md_ai_trust *tr, const int32_t *k_values)
+{
+    if (!tr || !k_values || m->c.n_classes > 8) { m->err = "md_ai_decide: bad trust bound or class ratios"; return MD_EINVAL; }
+    if (!(tr->hold_min <= tr->hold_max) || tr->fallback_k < 1 || tr->strain_col >= m->c.F) {
+        m->err = "md_ai_decide: bad trust bound";
+        return MD_EINVAL;
+    }
+    for (int c = 0; c < m->c.n_classes; ++c)
+        if (k_values[c] < 1) { m->err = "md_ai_decide: class ratios must be >= 1"; return MD_EINVAL; }
+    return MD_OK;
+}
+
+// Steps 5-6 on windows already through predict_device (with the strain
+// column's maxima in m->smax); decisions copied to the host arrays.
+int decide_device(md_ai *m, int32_t B, const md_ai_trust *tr, const int32_t *k_values, int32_t *k_out,
+                  int32_t *hold_out, int32_t *why_out)
+{
+    decide_args a;
+    a.probs = m->probs; a.lh = m->lh; a.rec = m->rec; a.smax = m->smax;
+    a.B = B; a.C = m->c.n_classes; a.T = m->c.T; a.F = m->c.F;
+    a.p_min = tr->p_min; a.rec_max = tr->rec_max; a.strain_max = tr->strain_max;
+    a.hold_min = tr->hold_min; a.hold_max = tr->hold_max;
+    a.strain_col = tr->strain_col; a.fallback_k = tr->fallback_k;
+    for (int c = 0; c < 8; ++c) a.kv[c] = c < a.C ? k_values[c] : 1;
+    a.out = m->dec;
+    k_decide<<<nblk(B, 128), 128, 0, m->st>>>(a);
+    AK(cudaGetLastError(), "decide");
+    std::vector<int32_t> h((size_t)3 * B);
+    AK(cudaMemcpyAsync(h.data(), m->dec, sizeof(int32_t) * 3 * B, cudaMemcpyDeviceToHost, m->st), "decisions");
+    AK(cudaStreamSynchronize(m->st), "sync");
+    for (int b = 0; b < B; ++b) {
+        k_out[b] = h[(size_t)b];
+        if (hold_out) hold_out[b] = h[(size_t)B + b];
+        if (why_out) why_out[b] = h[(size_t)2 * B + b];
+    }
+    return MD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int md_ai_decide(md_ai *m, const float *raw, int32_t B, int32_t where, const md_ai_trust *trust,
+                 const int32_t *k_values, int32_t *k_out, int32_t *hold_out, int32_t *why_out)
+{
+    if (!m || !raw || !k_out || B < 1 || B > m->c.batch_max) return MD_EINVAL;
+    if (!m->has_params) return MD_ENOTRAINED;
+    int rc = check_trust(m, trust, k_values);
+    if (rc) return rc;
+    rc = predict_device(m, raw, B, where, trust->strain_col);
+    if (rc) return rc;
+    return decide_device(m, B, trust, k_values, k_out, hold_out, why_out);
+}
+
+int md_ai_decide_system(md_ai *m, md_system *s, const md_ai_trust *trust, const int32_t *k_values, int32_t *k_out,
+                        int32_t *hold_out, int32_t *why_out)
+{
+    if (!m || !s || !k_out) return MD_EINVAL;
+    if (!m->has_params) return MD_ENOTRAINED;
+    if (s->n_plt == 0 || !s->ring) { m->err = "md_ai_decide_system: the system has no platelets"; return MD_EINVAL; }
+    const int P = s->cfg.n_platelets;
+    if (P > m->c.batch_max || s->ring_T != m->c.T || m->c.F != 12) {
+        m->err = "md_ai_decide_system: controller batch, window length or measurement count does not match the system";
+        return MD_EINVAL;
+    }
+    int rc = check_trust(m, trust, k_values);
+    if (rc) return rc;
+    // the ring count decides whether a full window exists (one word from the
+    // system's pinned mirror after its stream drains)
+    AK(cudaMemcpyAsync(s->h_ds, s->ds, sizeof(md_dstate), cudaMemcpyDeviceToHost, s->stream), "ring count");
+    AK(cudaStreamSynchronize(s->stream), "sync system");
+    if (s->h_ds->ring_count < s->ring_T) {
+        m->err = "md_ai_decide_system: fewer recorded steps than one window";
+        return MD_EINVAL;
+    }
+    const int T = m->c.T, F = m->c.F;
+    k_gather_ring<<<nblk((int64_t)P * T * F), 256, 0, m->st>>>(s->ring, s->ds, P, T, F, m->Y);
+    AK(cudaGetLastError(), "gather ring");
+    rc = predict_device(m, m->Y, P, MD_AI_DEVICE, trust->strain_col);
+    if (rc) return rc;
+    return decide_device(m, P, trust, k_values, k_out, hold_out, why_out);
+}
+
+int md_ai_predict(md_ai *m, const float *raw, int32_t B, int32_t where, float *out)
+{
+    if (!m || !raw || !out || B < 1 || B > m->c.batch_max) return MD_EINVAL;
+    if (!m->has_params) return MD_ENOTRAINED;
+    int rc = predict_device(m, raw, B, where);
+    if (rc) return rc;
     const int C = m->c.n_classes;
     std::vector<float> probs((size_t)B * C), lh((size_t)B), rec((size_t)B);
     AK(cudaMemcpyAsync(probs.data(), m->probs, sizeof(float) * B * C, cudaMemcpyDeviceToHost, m->st), "probs");

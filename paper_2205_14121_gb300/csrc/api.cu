@@ -166,6 +166,13 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
         s.bond_ij = cv.take<int32_t>(2 * s.nb);
         s.bond_r0 = cv.take<float>(s.nb);
     }
+    if (c.n_angles < 0 || (c.n_angles > 0 && !plt)) { err = "angle triplets need platelet particles"; return false; }
+    s.na = c.n_angles;
+    if (s.na > 0) {
+        s.angle_id = cv.take<int32_t>(3 * s.na);
+        s.angle_ijk = cv.take<int32_t>(3 * s.na);
+        s.angle_t0 = cv.take<float>(s.na);
+    }
     if (plt) {
         const int64_t P = c.n_platelets > 0 ? c.n_platelets : 1;
         s.plt_off = cv.take<int32_t>(P + 1);
@@ -398,7 +405,7 @@ int ensure_forces(md_system *s)
     int rc = ensure_lists(s);
     if (rc) return rc;
     if (!s->forces_stale && (s->forces_levels & all) == all) return MD_OK;
-    rc = eval_forces(s, all, false);
+    rc = eval_forces(s, all, false, s->det_step);
     if (rc) return rc;
     s->forces_stale = false;
     s->forces_levels = all;
@@ -453,6 +460,21 @@ int enqueue_forces(md_system *s, unsigned levels)
     for (int l = 0; l < 3; ++l) {
         const unsigned bit = 1u << l;
         if (!(levels & bit) || (l > 0 && s->n_plt == 0)) continue;
+        if (s->det_step) {
+            // MD_SCHED_DETERMINISTIC: the level's fixed-point sums (pair and
+            // bond terms with the lower id first), then its FP32 buffer
+            CK(cudaMemsetAsync(s->fdet[l], 0, sizeof(unsigned long long) * 3 * s->n, s->stream), "zero fixed sums");
+            prof_begin(s, cls[l]);
+            CK(launch_forces(s, bit, out, false, false, s->fdet[l]), "forces (deterministic)");
+            prof_end(s);
+            if (l < 2) {
+                prof_begin(s, MD_PROF_OTHER);
+                CK(launch_fast_pairs(s, bit, out, false, s->fdet[l]), "fast pairs (deterministic)");
+                prof_end(s);
+            }
+            CK(launch_fixed_to_f4(s, s->fdet[l], s->f[l]), "fixed to float");
+            continue;
+        }
         prof_begin(s, cls[l]);
         CK(launch_forces(s, bit, out, false, false), "forces");
         prof_end(s);
@@ -618,7 +640,7 @@ void drop_graph(md_system *s)
 // Capture WHILE(steps_left) { outer step } once per schedule shape.
 int build_step_graph(md_system *s, int mode, int k_m, int k_p, bool record)
 {
-    const int key[4] = {mode | (record ? 256 : 0), k_m, k_p, (int)s->cfg_k_m};
+    const int key[4] = {mode | (record ? 256 : 0) | (s->det_step ? 512 : 0), k_m, k_p, (int)s->cfg_k_m};
     bool same = s->step_exec != nullptr;
     for (int k = 0; k < 4; ++k) same = same && s->graph_key[k] == key[k];
     if (same) return MD_OK;
@@ -727,6 +749,7 @@ int md_config_defaults(md_config *c)
     c->lj_eps = 1.0; c->lj_sigma = 0.8; c->lj_rc = 2.0; c->lj_excl = 1e30;   // no LJ within one platelet
     c->morse_D = 2.0; c->morse_alpha = 2.0; c->morse_r0 = 1.0; c->morse_rc = 5.0; c->f_A = 0.0;
     c->k_bond = 100.0;
+    c->k_angle = 20.0;
     c->seed = 20220528ull;
     return MD_OK;
 }
@@ -1044,6 +1067,38 @@ int md_set_bonds(md_system *s, const int32_t *ij, const double *r0, int64_t nb)
     return MD_OK;
 }
 
+int md_set_angles(md_system *s, const int32_t *ijk, const double *theta0, int64_t na)
+{
+    if (!s) return MD_EINVAL;
+    if (na != s->na) return set_error(s, MD_EINVAL, "md_set_angles: count differs from the configuration");
+    if (na == 0) return MD_OK;
+    if (!ijk || !theta0) return set_error(s, MD_EINVAL, "md_set_angles: null argument");
+    if ((int64_t)s->h_tag.size() != s->n) return set_error(s, MD_EINVAL, "md_set_angles: set particles first");
+    std::vector<float> t0((size_t)na);
+    for (int64_t q = 0; q < na; ++q) {
+        int32_t pl = -1;
+        for (int e = 0; e < 3; ++e) {
+            const int32_t i = ijk[3 * q + e];
+            if (i < 0 || i >= s->n) return set_error(s, MD_EINVAL, "md_set_angles: particle id out of range");
+            const int32_t t = s->h_tag[(size_t)i];
+            if (t < 0) return set_error(s, MD_EINVAL, "md_set_angles: a triplet must lie on one platelet");
+            if (pl >= 0 && (t & ~MD_RECEPTOR_BIT) != pl)
+                return set_error(s, MD_EINVAL, "md_set_angles: a triplet must lie on one platelet");
+            pl = t & ~MD_RECEPTOR_BIT;
+        }
+        if (!(theta0[q] >= 0.0 && theta0[q] <= 3.14159265358979323846))
+            return set_error(s, MD_EINVAL, "md_set_angles: rest angle outside [0, pi]");
+        t0[(size_t)q] = (float)theta0[q];
+    }
+    CK(cudaMemcpyAsync(s->angle_id, ijk, sizeof(int32_t) * 3 * na, cudaMemcpyHostToDevice, s->stream), "angles");
+    CK(cudaMemcpyAsync(s->angle_t0, t0.data(), sizeof(float) * na, cudaMemcpyHostToDevice, s->stream), "theta0");
+    CK(cudaStreamSynchronize(s->stream), "set_angles sync");
+    s->have_angles = true;
+    s->lists_stale = true;   // the remap of the triplets happens in the rebuild
+    s->forces_stale = true;
+    return MD_OK;
+}
+
 int md_set_platelet_levels(md_system *s, const int32_t *k)
 {
     if (!s || !k) return set_error(s, MD_EINVAL, "md_set_platelet_levels: null argument");
@@ -1085,6 +1140,7 @@ int md_forces(md_system *s, uint32_t level_mask, uint32_t flags)
     if (!s || !s->have_particles) return set_error(s, MD_EINVAL, "md_forces: no particles");
     if ((level_mask & ~MD_LEVEL_ALL) || !level_mask) return set_error(s, MD_EINVAL, "md_forces: bad level mask");
     if (s->nb > 0 && !s->have_bonds) return set_error(s, MD_EINVAL, "md_forces: bonds not set");
+    if (s->na > 0 && !s->have_angles) return set_error(s, MD_EINVAL, "md_forces: angles not set");
     int rc = ensure_lists(s);
     if (rc) return rc;
     if (s->n_plt == 0) level_mask &= MD_LEVEL_FLUID;
@@ -1151,11 +1207,20 @@ int md_mts_step(md_system *s, int64_t n_outer, const md_mts_schedule *sched)
     if (!s || !sched || n_outer < 0) return set_error(s, MD_EINVAL, "md_mts_step: bad argument");
     if (!s->have_particles) return set_error(s, MD_EINVAL, "md_mts_step: no particles");
     if (s->nb > 0 && !s->have_bonds) return set_error(s, MD_EINVAL, "md_mts_step: bonds not set");
+    if (s->na > 0 && !s->have_angles) return set_error(s, MD_EINVAL, "md_mts_step: angles not set");
     if (n_outer == 0) return MD_OK;
     s->det_levels = 0;
     const int mode = sched->mode;
     const bool record = (sched->flags & MD_SCHED_RECORD) != 0;
     if (record && s->n_plt == 0) return set_error(s, MD_EINVAL, "md_mts_step: recording needs platelets");
+    const bool det = (sched->flags & MD_SCHED_DETERMINISTIC) != 0;
+    if (det && mode == MD_MODE_AI)
+        return set_error(s, MD_EINVAL, "md_mts_step: deterministic steps cover STS and RESPA, not AI-MTS");
+    if (det != s->det_step) {
+        // the forces at hand were summed the other way: evaluate them again
+        s->det_step = det;
+        s->forces_stale = true;
+    }
     int k_m = sched->k_m > 0 ? sched->k_m : 1;
     int k_p = sched->k_p > 0 ? sched->k_p : 1;
     if (mode == MD_MODE_STS) { k_m = 1; k_p = 1; }
@@ -1296,8 +1361,14 @@ int md_record_features(md_system *s)
 
 int md_read_feature_ring(md_system *s, float *out, int64_t *count)
 {
-    if (!s || !out || !count) return MD_EINVAL;
+    if (!s || !count) return MD_EINVAL;
     if (s->n_plt == 0) return set_error(s, MD_EINVAL, "md_read_feature_ring: no platelets");
+    if (!out) {         // the record count alone
+        int rc = sync_ctl(s);
+        if (rc) return rc;
+        *count = s->h_ds->ring_count;
+        return MD_OK;
+    }
     const int P = s->cfg.n_platelets, T = s->ring_T;
     std::vector<float> raw((size_t)P * T * 12);
     CK(cudaMemcpyAsync(raw.data(), s->ring, sizeof(float) * raw.size(), cudaMemcpyDeviceToHost, s->stream), "ring");

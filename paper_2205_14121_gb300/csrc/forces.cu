@@ -66,6 +66,11 @@ struct vir6 {
         xx += dx * dx * s; yy += dy * dy * s; zz += dz * dz * s;
         xy += dx * dy * s; xz += dx * dz * s; yz += dy * dz * s;
     }
+    __device__ void add_rf(float rx, float ry, float rz, float fx, float fy, float fz)  // sym(r (x) F)
+    {
+        xx += rx * fx; yy += ry * fy; zz += rz * fz;
+        xy += 0.5f * (rx * fy + ry * fx); xz += 0.5f * (rx * fz + rz * fx); yz += 0.5f * (ry * fz + rz * fy);
+    }
 };
 
 __device__ __forceinline__ double warp_sum_d(double v)
@@ -621,6 +626,65 @@ __global__ void __launch_bounds__(MSM_TPB) k_bonds(int64_t nb, const int32_t *__
     if (VIR) flush_virial(vir, w);
 }
 
+// K4b: angle term of Eq. 2, U = k (theta - theta0)^2, one thread per
+// triplet (i, vertex j, k).  theta = atan2(|a x b|, a.b) for the arms
+// a = x_i - x_j, b = x_k - x_j (accurate near 0 and pi, where arccos of the
+// cosine loses digits); F_i = 2 k (theta - theta0) / sin(theta)
+// (e_b - cos(theta) e_a) / |a|, F_k likewise, F_j = -F_i - F_k, with
+// sin(theta) held at 1e-3 at least.
+template <bool VIR>
+__global__ void __launch_bounds__(MSM_TPB) k_angles(int64_t na, const int32_t *__restrict__ ijk,
+                                                   const float *__restrict__ t0, float k2,
+                                                   const float4 *__restrict__ x32, float4 *f, md_geom geom,
+                                                   const md_dstate *ds, double *vir, md_due due, const int32_t *tag,
+                                                   unsigned long long *fdet)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    vir6 w = {0, 0, 0, 0, 0, 0};
+    // the triplet lies on one platelet: it lives on that platelet's grid
+    const float sc = (q < na && due.plt_k) ? term_scale(due, tag[ijk[3 * q + 1]], tag[ijk[3 * q + 1]]) : 1.0f;
+    if (q < na && sc != 0.0f) {
+        const int32_t i = ijk[3 * q], j = ijk[3 * q + 1], k = ijk[3 * q + 2];
+        const float4 xj = x32[j];
+        float ax, ay, az, bx, by, bz, vs;
+        min_image_f32(geom, ds->le_offset_f, x32[i], xj, ax, ay, az, vs);
+        min_image_f32(geom, ds->le_offset_f, x32[k], xj, bx, by, bz, vs);
+        const float ia = rsqrtf(ax * ax + ay * ay + az * az), ib = rsqrtf(bx * bx + by * by + bz * bz);
+        const float dot = ax * bx + ay * by + az * bz;
+        const float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
+        const float crs = sqrtf(cx * cx + cy * cy + cz * cz);
+        const float th = atan2f(crs, dot);
+        const float c = dot * ia * ib;
+        const float sn = fmaxf(crs * ia * ib, 1e-3f);
+        const float g = k2 * (th - t0[q]) / sn * sc;
+        const float eax = ax * ia, eay = ay * ia, eaz = az * ia, ebx = bx * ib, eby = by * ib, ebz = bz * ib;
+        const float fix = g * (ebx - c * eax) * ia, fiy = g * (eby - c * eay) * ia, fiz = g * (ebz - c * eaz) * ia;
+        const float fkx = g * (eax - c * ebx) * ib, fky = g * (eay - c * eby) * ib, fkz = g * (eaz - c * ebz) * ib;
+        if (fdet) {     // a triplet's orientation is fixed by its definition
+            // the vertex takes minus the sum of the two rounded ends, so the
+            // triplet's terms cancel exactly
+            const float S = 4294967296.0f;
+            const long long qi[3] = {__float2ll_rn(fix * S), __float2ll_rn(fiy * S), __float2ll_rn(fiz * S)};
+            const long long qk[3] = {__float2ll_rn(fkx * S), __float2ll_rn(fky * S), __float2ll_rn(fkz * S)};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                atomicAdd(&fdet[3 * (int64_t)i + d], (unsigned long long)qi[d]);
+                atomicAdd(&fdet[3 * (int64_t)k + d], (unsigned long long)qk[d]);
+                atomicAdd(&fdet[3 * (int64_t)j + d], (unsigned long long)(-(qi[d] + qk[d])));
+            }
+        } else {
+            scatter(f, i, fix, fiy, fiz);
+            scatter(f, k, fkx, fky, fkz);
+            scatter(f, j, -(fix + fkx), -(fiy + fky), -(fiz + fkz));
+        }
+        if (VIR) {
+            w.add_rf(ax, ay, az, fix, fiy, fiz);
+            w.add_rf(bx, by, bz, fkx, fky, fkz);
+        }
+    }
+    if (VIR) flush_virial(vir, w);
+}
+
 inline unsigned blocks_for(int64_t n) { return (unsigned)(n > 0 ? (n + MSM_TPB - 1) / MSM_TPB : 1); }
 
 }  // namespace
@@ -810,6 +874,17 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
                                                                             (float)(2.0 * c.k_bond), s->x32, out[2],
                                                                             s->geom, s->ds, s->vir_acc, a.due, s->tag_s,
                                                                            a.fdet);
+        }
+        if (s->na > 0) {
+            if (virial)
+                k_angles<true><<<blocks_for(s->na), MSM_TPB, 0, s->stream>>>(
+                    s->na, s->angle_ijk, s->angle_t0, (float)(2.0 * c.k_angle), s->x32, out[2], s->geom, s->ds,
+                    s->vir_acc, a.due, s->tag_s, a.fdet);
+            else
+                k_angles<false><<<blocks_for(s->na), MSM_TPB, 0, s->stream>>>(
+                    s->na, s->angle_ijk, s->angle_t0, (float)(2.0 * c.k_angle), s->x32, out[2], s->geom, s->ds,
+                    s->vir_acc, a.due, s->tag_s, a.fdet);
+            MSM_COUNT(s, 1);
         }
         a.rows = s->n_plt;
         a.row_idx = s->plt_sorted;

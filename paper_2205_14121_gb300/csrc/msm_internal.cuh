@@ -85,6 +85,7 @@ struct md_system {
     // deterministic mode (MD_FORCE_DETERMINISTIC): fixed-point sums per level
     unsigned long long *fdet[3];  // [3 n] each
     unsigned det_levels = 0;      // levels of the last deterministic md_forces (0: none current)
+    bool det_step = false;        // md_mts_step with MD_SCHED_DETERMINISTIC: every force from fixed-point sums
     int32_t *tag_s;              // tags in sorted order
     int32_t *cellid, *slot, *perm, *pos_of_id;
     double *alt64;               // 3n
@@ -106,6 +107,11 @@ struct md_system {
     // bonds (stored grouped by platelet: bonds of p are [bond_off[p], bond_off[p+1]))
     int32_t *bond_id, *bond_ij;
     float *bond_r0;
+    // angle triplets (ids; slots remapped at each sort) and rest angles
+    int64_t na = 0;
+    int32_t *angle_id = nullptr, *angle_ijk = nullptr;
+    float *angle_t0 = nullptr;
+    bool have_angles = false;
 
     // per-platelet measurements (K8)
     int32_t *plt_off, *plt_ids;  // member ids of platelet p: plt_ids[plt_off[p] .. plt_off[p+1])

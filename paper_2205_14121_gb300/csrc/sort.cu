@@ -201,6 +201,16 @@ __global__ void k_remap_bonds(int64_t nb, const int32_t *__restrict__ bond_id, c
     bond_ij[b] = pos_of_id[bond_id[b]];
 }
 
+// ids -> current storage slots for `count` entries (angle ends)
+__global__ void k_remap_ids(int64_t count, const int32_t *__restrict__ ids, const int32_t *__restrict__ pos_of_id,
+                            int32_t *__restrict__ slots, const int32_t *gate)
+{
+    if (gate_closed(gate)) return;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= count) return;
+    slots[q] = pos_of_id[ids[q]];
+}
+
 __global__ void k_compact_subsets(int64_t n, const int32_t *__restrict__ tag, int32_t *plt_idx, int32_t *rec_idx,
                                   int32_t *ctl, int64_t n_plt, int64_t n_rec, const int32_t *gate)
 {
@@ -302,6 +312,9 @@ cudaError_t launch_rebuild(md_system *s, const int32_t *gate, unsigned carry)
     k_copyback<<<blocks_for(n), MSM_TPB, 0, st>>>(ca, gate);
     if (s->nb > 0)
         k_remap_bonds<<<blocks_for(2 * s->nb), MSM_TPB, 0, st>>>(s->nb, s->bond_id, s->pos_of_id, s->bond_ij, gate);
+    if (s->na > 0)   // the same id -> slot map for the 3 na angle ends
+        k_remap_ids<<<blocks_for(3 * s->na), MSM_TPB, 0, st>>>(3 * s->na, s->angle_id, s->pos_of_id, s->angle_ijk,
+                                                              gate);
 
     if (s->n_plt > 0) {
         k_compact_subsets<<<blocks_for(n), MSM_TPB, 0, st>>>(n, s->tag_s, s->plt_idx, s->rec_idx, s->ctl,
@@ -334,6 +347,6 @@ cudaError_t launch_rebuild(md_system *s, const int32_t *gate, unsigned carry)
     if (e != cudaSuccess) return e;
     k_finish_build<<<1, 1, 0, st>>>(s->ctl, s->ds, gate);
     // zero, bin, scatter, gather, copyback, finish (+ remap) (+ subset passes)
-    MSM_COUNT(s, 6 + (s->nb > 0 ? 1 : 0) + (s->n_plt > 0 ? 4 + (s->n_rec > 0 ? 3 : 0) : 0));
+    MSM_COUNT(s, 6 + (s->nb > 0 ? 1 : 0) + (s->na > 0 ? 1 : 0) + (s->n_plt > 0 ? 4 + (s->n_rec > 0 ? 3 : 0) : 0));
     return cudaGetLastError();
 }

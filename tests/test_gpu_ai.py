@@ -148,3 +148,68 @@ def test_training_reduces_losses(setup):
     hs = [ctl.train_step(x, Ctl.TRAIN_HEADS, 3e-3, k_class=kc, log_hold=lh) for _ in range(60)]
     assert min(hs[-10:]) < 0.5 * h0, np.round(hs[::10], 4)
     ctl.set_params(p0)
+
+
+def _between(vals, q):
+    """A float32 threshold strictly between two neighbouring sorted values at
+    quantile q (so that no value sits on it and both sides compare alike)."""
+    v = np.sort(np.asarray(vals, np.float32))
+    i = min(max(int(q * len(v)), 1), len(v) - 1)
+    return np.float32(0.5 * (float(v[i - 1]) + float(v[i])))
+
+
+def test_device_decision_matches_trust_bound(setup):
+    """Table 2 steps 5-6 on the device (md_ai_decide): the ratio, hold and
+    reason bits equal the oracle's trust rule applied to the device's own
+    probabilities, reconstruction errors and log holds (the argmax and the
+    threshold tests then see the same FP32 values on both sides); the bounds
+    are set so that windows hit each fallback reason and some stay trusted."""
+    from paper_2205_14121_gb300 import ai_mts as AM
+    Ctl, cfg, ctl, p = setup
+    ctl.set_norm(np.full(12, 2.0), np.full(12, 0.7))
+    raw = (2.0 + windows(24, 5)).astype(np.float32)
+    raw[3, 40, 9] = 50.0           # a bond-strain spike in window 3
+    raw[17, 100, 9] = 60.0
+    pred = ctl.predict(raw)
+    pm = _between(pred["prob"].max(1), 0.3)
+    rm = _between(pred["rec_err"], 0.8)
+    trust = AM.TrustBound(p_min=float(pm), rec_max=float(rm), strain_max=10.0, fallback_k=10)
+    d = ctl.decide(raw, trust)
+    k, hold, why = A.trust_decision(pred["prob"], pred["rec_err"], pred["log_hold"], raw, p_min=pm,
+                                    rec_threshold=rm, strain_max=10.0, strain_col=9, fallback_k=10)
+    assert d["k"].tolist() == k.tolist()
+    assert d["why"].tolist() == why.tolist()
+    assert np.abs(d["hold"] - hold).max() <= 1          # expf vs exp at a whole-step boundary
+    assert (why & A.UNSURE_PROB).any() and (why & A.UNSURE_REC).any() and (why & A.UNSURE_STRAIN).any()
+    assert (why == 0).any()
+
+
+def test_device_decision_on_the_system_ring():
+    """md_ai_decide_system gathers the last 128 records of every platelet from
+    the system's feature ring on the device and decides exactly as
+    md_ai_decide on the same windows read back to the host."""
+    import paper_2205_14121_gb300 as M
+    from paper_2205_14121_gb300 import ai_mts as AM
+    from paper_2205_14121_gb300 import controller as Ctl
+    import synth
+    s = synth.platelet_system((14.0, 12.0, 12.0), 3 * 14 * 12 * 12, 2, 300, synth.scaled_radii(300), walls=True,
+                              body_force=0.01, seed=41, centers=[(4.0, 6.0, 6.0), (10.0, 6.0, 6.0)])
+    g = M.System(s.box, s.x, s.v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, angles=s.angles, theta0=s.theta0,
+                 walls=True, wall=s.wall,
+                 body_force=s.body_force)
+    with pytest.raises(M.MdError):
+        ctl0 = Ctl.Controller(Ctl.default_config(batch_max=8))
+        ctl0.set_params(AM.init_params(ctl0.cfg, seed=1))
+        ctl0.decide_system(g, AM.TrustBound())           # no records yet
+    g.mts_step(150, mode=M.MD_MODE_RESPA, k_p=2, record=True)   # the ring wraps past 128
+    ctl = Ctl.Controller(Ctl.default_config(batch_max=8))
+    ctl.set_params(AM.init_params(ctl.cfg, seed=2))
+    win, count = g.read_feature_ring()
+    assert count == 150 and win.shape == (2, 128, 12)
+    ctl.set_norm(win.reshape(-1, 12).mean(0), win.reshape(-1, 12).std(0) + 1e-6)
+    trust = AM.TrustBound(p_min=0.3, strain_max=float(np.median(win[:, :, 9].max(1))), fallback_k=10)
+    a = ctl.decide_system(g, trust)
+    b = ctl.decide(win, trust)
+    for key in ("k", "hold", "why"):
+        assert a[key].tolist() == b[key].tolist()
+    g.close()

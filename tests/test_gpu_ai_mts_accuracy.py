@@ -39,7 +39,8 @@ def test_ai_mts_matches_fine_step_sts():
     import paper_2205_14121_gb300 as M
     from paper_2205_14121_gb300 import ai_mts as A
     s = channel()
-    kw = dict(walls=s.walls, wall=s.wall, body_force=s.body_force, X0=s.X0, bonds=s.bonds, r0=s.r0)
+    kw = dict(walls=s.walls, wall=s.wall, body_force=s.body_force, X0=s.X0, bonds=s.bonds, r0=s.r0,
+              angles=s.angles, theta0=s.theta0)
     eq = M.System(s.box, s.x, s.v, s.tag, dt=0.01, **kw)
     eq.mts_step(300, mode=M.MD_MODE_RESPA, k_m=1, k_p=10)            # out of the synthetic start
     x0, v0, _ = eq.read_particles()

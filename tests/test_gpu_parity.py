@@ -24,7 +24,7 @@ def f32(a):
 
 def make_gpu(s, step0=0, x=None, v=None, **kw):
     import paper_2205_14121_gb300 as M
-    return M.System(s.box, s.x if x is None else x, s.v if v is None else v, s.tag, X0=s.X0, bonds=s.bonds,
+    return M.System(s.box, s.x if x is None else x, s.v if v is None else v, s.tag, X0=s.X0, angles=s.angles, theta0=s.theta0, bonds=s.bonds,
                     r0=s.r0, walls=s.walls, wall=s.wall, shear_rate=s.shear_rate, body_force=s.body_force,
                     step0=step0, **kw)
 
