@@ -121,6 +121,8 @@ def lib():
                                        C.c_uint32, C.c_uint32, C.c_uint32, C.c_double,
                                        C.c_uint32, C.c_uint32, C.c_double,
                                        C.c_int32, ip, dp, dp]
+        L.orc_pair_forces.argtypes = [P, C.c_int32, dp, dp, ip, ip, dp, C.c_uint32, C.c_uint32, C.c_uint32,
+                                      C.c_double, C.c_uint32, C.c_uint32, C.c_double, C.c_int64, ip, ip, dp]
         L.orc_r2_f32.argtypes = [fp, fp, fp, C.c_int32, C.c_int32, C.c_float]
         L.orc_r2_f32.restype = C.c_float
         L.orc_pairs_f32.argtypes = [C.c_int32, fp, ip, fp, fp, C.c_int32, C.c_int32, C.c_float,
@@ -197,6 +199,27 @@ def forces_brute(p, x, v, tag, X0=None, bonds=None, r0=None, ids=None, level_mas
                            f.ctypes.data_as(C.POINTER(C.c_double)),
                            acc.ctypes.data_as(C.POINTER(C.c_double)))
     return f, dict(epot=acc[0], vir=acc[1:10].reshape(3, 3), vir_c=acc[10:19].reshape(3, 3))
+
+
+def pair_forces(p, x, v, tag, pairs, X0=None, ids=None, level_mask=LVL_ALL, n_time=0, c_sub=0, dt=0.01,
+                n_time_m=None, c_sub_m=None, dt_m=None):
+    """F_ij of Eq. 1-4 for listed pairs [npair, 2] of rows (zero where the
+    pair does not interact); the same pair force the all-pairs sum adds up."""
+    n = x.shape[0]
+    x, xp = _d(x)
+    v, vp = _d(v)
+    tag, tp = _i(tag)
+    ids, idp = _i(np.arange(n) if ids is None else ids)
+    X0, X0p = _d(x if X0 is None else X0)
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    pi, pip = _i(pairs[:, 0])
+    pj, pjp = _i(pairs[:, 1])
+    F = np.zeros((pairs.shape[0], 3))
+    lib().orc_pair_forces(C.byref(p), n, xp, vp, idp, tp, X0p, level_mask, n_time, c_sub, dt,
+                          n_time if n_time_m is None else n_time_m, c_sub if c_sub_m is None else c_sub_m,
+                          dt if dt_m is None else dt_m, pairs.shape[0], pip, pjp,
+                          F.ctypes.data_as(C.POINTER(C.c_double)))
+    return F
 
 
 def bond_csr(n, bonds, r0):

@@ -465,6 +465,28 @@ void orc_forces_brute(const orc_params *p, int32_t n, const double *x, const dou
     }
 }
 
+/*
+ * Pair forces F_ij (Eq. 1-4, the levels in level_mask) for npair listed
+ * pairs (pi[q], pj[q]) of particle rows: F[3 q ..] = force on pi[q] from
+ * pj[q] (zero for a pair that does not interact).  Bonds and angles are not
+ * pairs of this kind and are not included.
+ */
+void orc_pair_forces(const orc_params *p, int32_t n, const double *x, const double *v,
+                     const int32_t *id, const int32_t *tag, const double *X0,
+                     uint32_t level_mask, uint32_t n_time_f, uint32_t c_sub_f, double dt_f,
+                     uint32_t n_time_m, uint32_t c_sub_m, double dt_m,
+                     int64_t npair, const int32_t *pi, const int32_t *pj, double *F_out)
+{
+    pair_ctx c = {p, n, x, v, X0, id, tag, level_mask, n_time_f, c_sub_f, n_time_m, c_sub_m,
+                  1.0 / sqrt(dt_f), 1.0 / sqrt(dt_m)};
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < npair; ++q) {
+        double F[3] = {0, 0, 0}, Fc[3], u, rij[3];
+        if (!pair_force(&c, pi[q], pj[q], F, Fc, &u, rij)) F[0] = F[1] = F[2] = 0.0;
+        F_out[3 * q] = F[0]; F_out[3 * q + 1] = F[1]; F_out[3 * q + 2] = F[2];
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* cell-list forces on selected particles (same definition, fewer pairs)     */
 /* ------------------------------------------------------------------------ */

@@ -939,3 +939,24 @@ def test_nve_energy_drift_of_a_shell_with_bonds_and_angles():
     e = abs(es.mean())
     assert np.abs(es - es[0]).max() < 1e-4 * e
     assert abs(np.polyfit(np.arange(11), es, 1)[0] * 10) < 1e-4 * e
+
+
+def test_listed_pair_forces_add_up_to_the_all_pairs_sum():
+    """The oracle's per-pair forces F_ij over every pair (both orders) sum to
+    the all-pairs forces, and F_ji = -F_ij (Eq. 1 noise symmetric in i, j)."""
+    s = small_platelet_system(seed=5)
+    p = O.system_params(s, le_offset=0.7)
+    n = s.n
+    ii, jj = np.triu_indices(n, 1)
+    pairs = np.stack([ii, jj], 1)
+    F = O.pair_forces(p, s.x, s.v, s.tag, pairs, X0=s.X0, n_time=2)
+    Fr = O.pair_forces(p, s.x, s.v, s.tag, pairs[:, ::-1], X0=s.X0, n_time=2)
+    assert np.array_equal(F, -Fr)
+    f = np.zeros((n, 3))
+    np.add.at(f, ii, F)
+    np.add.at(f, jj, -F)
+    f[s.tag != synth.TAG_WALL, 0] += p.g
+    # bonds and angles are not pairs of this kind: compare with them switched off
+    p0 = O.system_params(s, le_offset=0.7, k_b=0.0, k_a=0.0)
+    fb0, _ = O.forces_brute(p0, s.x, s.v, s.tag, X0=s.X0, n_time=2)
+    assert np.abs(f - fb0).max() < 1e-10 * (np.abs(fb0).max() + 1)
