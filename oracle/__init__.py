@@ -134,6 +134,8 @@ def lib():
         L.orc_kinetics.argtypes = [P, C.c_int32, dp, dp, ip, C.c_int32, dp, dp, dp]
         L.orc_run_sts.argtypes = [P, C.c_int32, C.c_int32, dp, dp, ip, ip, dp, ip, dp,
                                   C.c_double, C.c_int32, C.c_uint32, C.c_double, C.c_int32, dp]
+        L.orc_run_nested.argtypes = [P, C.c_int32, C.c_int32, dp, dp, ip, ip, dp, ip, dp, ip, C.c_int32, ip,
+                                     C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_uint32, C.c_double, dp, dp]
         L.orc_run_ai_respa.argtypes = [P, C.c_int32, C.c_int32, dp, dp, ip, ip, dp, ip, dp, ip, C.c_int32, C.c_int32,
                                        C.c_double, C.c_int32, C.c_int32, C.c_uint32, C.c_double, C.c_int32,
                                        dp, dp, dp]
@@ -352,6 +354,9 @@ def run_ai_respa(p, x, v, tag, plt_k, X0=None, bonds=None, r0=None, ids=None, dt
     bonds, bp = _i(bonds)
     r0, rp = _d(r0)
     pk, pkp = _i(plt_k)
+    tg = np.asarray(tag)
+    if (tg >= 0).any() and len(pk) < int((tg[tg >= 0] & ~(1 << 30)).max() + 1):
+        raise ValueError("run_ai_respa: one ratio per platelet")
     K = 1
     for k in pk:
         K = K * int(k) // math.gcd(K, int(k))
@@ -366,6 +371,37 @@ def run_ai_respa(p, x, v, tag, plt_k, X0=None, bonds=None, r0=None, ids=None, dt
                            X0p, bp, rp, pkp, len(pk), K, dt_f, k_m, n_outer, n0, t0, init, ff.ctypes.data_as(dp),
                            fm.ctypes.data_as(dp), fpl.ctypes.data_as(dp))
     return x, v, (ff, fm, fpl)
+
+
+def run_nested(p, x, v, tag, plt_level, ratios, X0=None, bonds=None, r0=None, ids=None, dt_f=0.01, k_m=1,
+               n_outer=1, n0=0, t0=0.0):
+    """Table 1 as printed: platelets in nested sublevels (plt_level[P] in
+    1..C, level 1 one step per interface substep, level l ratios[l - 1]
+    steps per step of level l - 1; ratios[0] = 1), the innermost level
+    drifting every particle.  Forces evaluated at entry.  Returns (x, v)."""
+    n = x.shape[0]
+    x = np.array(x, dtype=np.float64, order="C")
+    v = np.array(v, dtype=np.float64, order="C")
+    tag, tp = _i(tag)
+    ids, idp = _i(np.arange(n) if ids is None else ids)
+    X0, X0p = _d(x.copy() if X0 is None else X0)
+    if bonds is None or len(bonds) == 0:
+        bonds = np.zeros((0, 2), np.int32)
+        r0 = np.zeros(0)
+    bonds, bp = _i(bonds)
+    r0, rp = _d(r0)
+    lv, lvp = _i(plt_level)
+    kr, krp = _i(ratios)
+    tg = np.asarray(tag)
+    P = int(((tg[tg >= 0] & ~(1 << 30)).max() + 1)) if (tg >= 0).any() else 0
+    if len(lv) < P or kr[0] != 1 or lv.min(initial=1) < 1 or lv.max(initial=1) > len(kr):
+        raise ValueError("run_nested: one level in 1..len(ratios) per platelet, ratios[0] = 1")
+    ff, fm = np.zeros((n, 3)), np.zeros((n, 3))
+    dp = C.POINTER(C.c_double)
+    lib().orc_run_nested(C.byref(p), n, bonds.shape[0], x.ctypes.data_as(dp), v.ctypes.data_as(dp), idp, tp, X0p,
+                         bp, rp, lvp, len(lv), krp, len(kr), dt_f, k_m, n_outer, n0, t0, ff.ctypes.data_as(dp),
+                         fm.ctypes.data_as(dp))
+    return x, v
 
 
 def run_sts(p, x, v, tag, X0=None, bonds=None, r0=None, ids=None, dt=0.01, n_steps=1, n0=0, t0=0.0,

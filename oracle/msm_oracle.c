@@ -1007,6 +1007,96 @@ void orc_run_ai_respa(orc_params *p, int32_t n, int32_t nb, double *x, double *v
 }
 
 /*
+ * Table 1 as printed: the platelet subsystem in nested sublevels inside each
+ * interface substep.  Level 1 takes one step dt_1 = dt_m per interface
+ * substep (the flowing platelets), level l > 1 takes kr[l - 1] steps
+ * dt_l = dt_{l-1} / kr[l - 1] inside each step of level l - 1, and the
+ * innermost level C (the aggregating platelets) drifts every particle.  A
+ * step of level l: half kick with the level-l forces, the substeps of the
+ * next level (or the drift), the level-l forces at the new state, half kick.
+ * The level-l forces are the platelet-level terms whose finer platelet is on
+ * level l (plt_level[P] in 1..C).
+ */
+typedef struct {
+    orc_params *p;
+    const orc_state *s;
+    const bond_csr_t *csr;
+    int32_t C;
+    const int32_t *kr;          /* kr[0] = 1, kr[l - 1] = dt_{l-1} / dt_l */
+    const int32_t *pK;          /* per platelet: dt_m / dt of its level */
+    int32_t *Kl;                /* per level: dt_m / dt_l */
+    double **F;                 /* per level forces [3n] */
+    double dt_m;
+    double *t;
+} nest_ctx;
+
+static void nest_forces(nest_ctx *c, int32_t l)
+{
+    c->p->plt_k = c->pK;
+    c->p->lvl_k = c->Kl[l - 1];
+    eval_level(c->p, c->s, c->csr, LVL_PLT, 0, 0, 1.0, c->dt_m, c->F[l - 1]);
+    c->p->plt_k = NULL;
+}
+
+static void nest_step(nest_ctx *c, int32_t l, double dt_l)
+{
+    kick(c->s, c->F[l - 1], 0.5 * dt_l);
+    if (l == c->C) {
+        drift(c->p, c->s, dt_l, c->t);
+    } else {
+        const int32_t k = c->kr[l];
+        for (int32_t q = 0; q < k; ++q) nest_step(c, l + 1, dt_l / k);
+    }
+    nest_forces(c, l);
+    kick(c->s, c->F[l - 1], 0.5 * dt_l);
+}
+
+void orc_run_nested(orc_params *p, int32_t n, int32_t nb, double *x, double *v,
+                    const int32_t *id, const int32_t *tag, const double *X0,
+                    const int32_t *bonds, const double *r0, const int32_t *plt_level, int32_t P,
+                    const int32_t *kr, int32_t C, double dt_f, int32_t k_m, int32_t n_outer, uint32_t n0,
+                    double t0, double *f_f, double *f_m)
+{
+    orc_state s = {n, nb, x, v, id, tag, X0, bonds, r0};
+    bond_csr_t csr;
+    bond_csr_build(n, nb, bonds, r0, &csr);
+    const double dt_m = dt_f / k_m;
+    double t = t0;
+    if (p->le) {
+        p->le_offset = fmod(p->le_rate * p->L[1] * t, p->L[0]);
+        if (p->le_offset < 0.0) p->le_offset += p->L[0];
+    }
+    int32_t *Kl = (int32_t *)malloc((size_t)C * sizeof(int32_t));
+    int32_t *pK = (int32_t *)malloc((size_t)(P > 0 ? P : 1) * sizeof(int32_t));
+    double **F = (double **)malloc((size_t)C * sizeof(double *));
+    Kl[0] = 1;
+    for (int32_t l = 1; l < C; ++l) Kl[l] = Kl[l - 1] * kr[l];
+    for (int32_t q = 0; q < P; ++q) pK[q] = Kl[plt_level[q] - 1];
+    for (int32_t l = 0; l < C; ++l) F[l] = (double *)calloc((size_t)3 * (n > 0 ? n : 1), sizeof(double));
+    nest_ctx c = {p, &s, &csr, C, kr, pK, Kl, F, dt_m, &t};
+    eval_level(p, &s, &csr, LVL_FLUID, n0, 0, dt_f, dt_m, f_f);
+    eval_level(p, &s, &csr, LVL_IFACE, n0, 0, dt_f, dt_m, f_m);
+    for (int32_t l = 1; l <= C; ++l) nest_forces(&c, l);
+    for (int32_t so = 0; so < n_outer; ++so) {
+        uint32_t nn = n0 + (uint32_t)so;
+        kick(&s, f_f, 0.5 * dt_f);
+        for (int32_t cm = 0; cm < k_m; ++cm) {
+            kick(&s, f_m, 0.5 * dt_m);
+            nest_step(&c, 1, dt_m);
+            uint32_t nt = (cm + 1 == k_m) ? nn + 1 : nn;
+            uint32_t cs = (cm + 1 == k_m) ? 0u : (uint32_t)(cm + 1);
+            eval_level(p, &s, &csr, LVL_IFACE, nt, cs, dt_f, dt_m, f_m);
+            kick(&s, f_m, 0.5 * dt_m);
+        }
+        eval_level(p, &s, &csr, LVL_FLUID, nn + 1, 0, dt_f, dt_m, f_f);
+        kick(&s, f_f, 0.5 * dt_f);
+    }
+    for (int32_t l = 0; l < C; ++l) free(F[l]);
+    free(F); free(Kl); free(pK);
+    free(csr.off); free(csr.nbr); free(csr.r0);
+}
+
+/*
  * Single time step (STS, the reference run of Sec. 4.1): velocity-Verlet in
  * which all forces of Eq. 1-4 are evaluated together, at the drifted
  * positions and the half-kicked velocities:

@@ -413,6 +413,29 @@ def test_ai_mts_mixed_ratios_track_oracle(plt_wall_sys):
     assert np.abs(d2).max() > 1e-6
 
 
+def test_ai_mts_tracks_table1_nested_sublevels(plt_wall_sys):
+    """Table 1's nested sublevels as printed (oracle: a flowing platelet on
+    level 1, one step per interface substep; an aggregating one on level 2,
+    five steps inside each; the inner level drifting every particle) against
+    the device's per-platelet ratio grid with k = (1, 5): the same
+    trajectory within the fixed-k RESPA bound."""
+    import paper_2205_14121_gb300 as M
+    s = plt_wall_sys
+    x0, v0 = f32(s.x), f32(s.v)
+    g = make_gpu(s, x=x0, v=v0)
+    g.set_platelet_levels([1, 5])
+    g.mts_step(3, mode=M.MD_MODE_AI, k_m=2)
+    xg, vg, _ = g.read_particles()
+    p = O.system_params(s)
+    xo, vo = O.run_nested(p, x0, v0, s.tag, [1, 2], [1, 5], X0=f32(s.X0), bonds=s.bonds, r0=f32(s.r0), dt_f=0.01,
+                          k_m=2, n_outer=3)
+    dx = xg - xo
+    L = np.array(s.box)
+    dx -= L * np.round(dx / L)
+    assert np.abs(dx).max() < 1e-4
+    assert np.abs(vg - vo).max() < 5e-3 * np.sqrt((vo ** 2).mean())
+
+
 def test_ai_mts_equal_ratios_match_respa_on_gpu(plt_wall_sys):
     """With every k_p = 4 the AI-MTS kernels take the fixed-k RESPA steps."""
     import paper_2205_14121_gb300 as M

@@ -960,3 +960,35 @@ def test_listed_pair_forces_add_up_to_the_all_pairs_sum():
     p0 = O.system_params(s, le_offset=0.7, k_b=0.0, k_a=0.0)
     fb0, _ = O.forces_brute(p0, s.x, s.v, s.tag, X0=s.X0, n_time=2)
     assert np.abs(f - fb0).max() < 1e-10 * (np.abs(fb0).max() + 1)
+
+
+def three_contact_shells(seed=8):
+    """Three 120-particle platelets in plasma, close enough for LJ and Morse
+    between neighbours, in a walled box."""
+    s = synth.platelet_system((12.0, 8.0, 8.0), 2300, 3, 120, synth.scaled_radii(120), walls=True,
+                              body_force=0.02, seed=seed, centers=[(2.8, 4.0, 4.0), (5.6, 4.0, 4.0), (8.4, 4.1, 4.0)])
+    rng = np.random.default_rng(seed)
+    plt = s.tag >= 0
+    s.x[plt] += 0.03 * rng.standard_normal((int(plt.sum()), 3))
+    return s
+
+
+@pytest.mark.parametrize("levels,ratios", [([1, 2, 2], [1, 4]), ([1, 2, 3], [1, 2, 5]), ([3, 1, 2], [1, 2, 2])])
+def test_table1_nested_sublevels_equal_the_ratio_grid(levels, ratios):
+    """Table 1 as printed -- flowing platelets on level 1 (one step per
+    interface substep), finer levels nested inside it, the innermost
+    (aggregating) level drifting every particle -- performs the kicks and
+    drifts of the per-platelet ratio grid (each platelet's k = dt_m / dt of
+    its level, a term on the finer platelet's grid): the same trajectory to
+    rounding, with interface substeps (k_m = 2), plasma, walls and the
+    inter-platelet LJ and Morse terms between levels."""
+    s = three_contact_shells()
+    p = O.system_params(s)
+    K = np.cumprod(ratios)
+    plt_k = [int(K[l - 1]) for l in levels]
+    kw = dict(X0=s.X0, bonds=s.bonds, r0=s.r0, dt_f=0.01, k_m=2, n_outer=3)
+    xa, va = O.run_nested(p, s.x, s.v, s.tag, levels, ratios, **kw)
+    xb, vb, _ = O.run_ai_respa(p, s.x, s.v, s.tag, plt_k, **kw)
+    assert np.abs(xa - s.x).max() > 1e-3            # the particles moved
+    assert np.abs(xa - xb).max() < 1e-11
+    assert np.abs(va - vb).max() < 1e-9
