@@ -145,3 +145,71 @@ def test_trust_decision_reasons_and_fallback():
     assert k.tolist() == [5, 10, 10, 10, 10]
     assert why.tolist() == [0, A.UNSURE_PROB, A.UNSURE_REC, A.UNSURE_STRAIN, A.UNSURE_PROB]
     assert hold.tolist() == [100, 150, 2000, 999, 100]
+
+
+# ---------------------------------------------------------------------------
+# the paper's LSTM variant (Sec. 3.3)
+# ---------------------------------------------------------------------------
+
+def test_lstm_forward_matches_torch():
+    """The oracle's LSTM layer equals torch.nn.LSTM with the same weights
+    (gate order i, f, g, o; zero initial state)."""
+    torch = pytest.importorskip("torch")
+    from oracle import lstm as L
+    rng = np.random.default_rng(21)
+    layer = L._lstm(rng, 6, 16)
+    xs = rng.standard_normal((7, 5, 6))
+    hs, cs, _ = L.lstm_forward(layer, xs)
+    m = torch.nn.LSTM(6, 16).double()
+    with torch.no_grad():
+        m.weight_ih_l0.copy_(torch.from_numpy(layer["W_ih"]))
+        m.weight_hh_l0.copy_(torch.from_numpy(layer["W_hh"]))
+        m.bias_ih_l0.copy_(torch.from_numpy(layer["b_ih"]))
+        m.bias_hh_l0.copy_(torch.from_numpy(layer["b_hh"]))
+        out, (hT, cT) = m(torch.from_numpy(xs))
+    assert np.abs(hs - out.numpy()).max() < 1e-12
+    assert np.abs(cs[-1] - cT.numpy()[0]).max() < 1e-12
+
+
+def _fd_check(loss_fn, p, g, names, n=6, seed=0, h=1e-6):
+    rng = np.random.default_rng(seed)
+    for name in names:
+        blocks = name.split(".")
+        arr = p
+        garr = g
+        for b in blocks:
+            arr = arr[int(b)] if isinstance(arr, list) else arr[b]
+            garr = garr[int(b)] if isinstance(garr, list) else garr[b]
+        for _ in range(n):
+            idx = tuple(rng.integers(0, s) for s in arr.shape)
+            old = arr[idx]
+            arr[idx] = old + h
+            lp = loss_fn()
+            arr[idx] = old - h
+            lm = loss_fn()
+            arr[idx] = old
+            assert garr[idx] == pytest.approx((lp - lm) / (2 * h), rel=1e-5, abs=1e-9), (name, idx)
+
+
+def test_lstm_autoencoder_and_fcn_gradients_match_finite_differences():
+    """Backpropagation through time of the LSTM autoencoder (latent = last
+    hidden and cell state of the 4-unit layer) and of the FCN on log k, against
+    FP64 central differences, every parameter block."""
+    from oracle import lstm as L
+    p = L.init_params(seed=3)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((3, 9, 6))
+    loss, g = L.ae_loss_and_grads(p, x)
+    names = [f"{blk}.{w}" for blk in ("enc1", "enc2", "dec1", "dec2") for w in ("W_ih", "W_hh", "b_ih")]
+    _fd_check(lambda: L.ae_loss_and_grads(p, x)[0], p, g, names + ["out.W", "out.b"])
+    z, _ = L.encode(p, x)
+    t = np.log([2.0, 5.0, 10.0])
+    loss, g = L.fcn_loss_and_grads(p, z, t)
+    _fd_check(lambda: L.fcn_loss_and_grads(p, z, t)[0], p, g, [f"fcn.{i}.W" for i in range(4)] + ["fcn.3.b"])
+
+
+def test_lstm_categorise_to_nearest_level():
+    """Table 2 step 5: log k to the nearest class of {1, 2, 5, 10, 20} in log space."""
+    from oracle import lstm as L
+    lk = np.log([1.0, 1.4, 1.5, 3.2, 3.1, 7.0, 7.1, 14.0, 14.2, 100.0, 0.01])
+    assert L.categorise(lk).tolist() == [0, 0, 1, 2, 1, 2, 3, 3, 4, 4, 0]
