@@ -498,6 +498,62 @@ int md_ai_decide(md_ai *ai, const float *raw, int32_t B, int32_t where, const md
 int md_ai_decide_system(md_ai *ai, md_system *sys, const md_ai_trust *trust, const int32_t *k_values,
                         int32_t *k_out, int32_t *hold_out, int32_t *why_out);
 
+/* ---- the paper's own controller variant (Sec. 3.3) ------------------------ */
+/*
+ * The last T = 50 steps of F = 6 per-platelet measurements, denoised and
+ * normalised as in md_ai_predict (Table 2 step 2), through a two-layer LSTM
+ * autoencoder of H1 = 16 and H2 = 4 units; the latent is the second layer's
+ * final hidden and cell state (2 H2 = 8 features); a mirrored decoder (LSTM
+ * 2 H2 -> H2, LSTM H2 -> H1, linear H1 -> F at every step, fed the repeated
+ * latent) reconstructs the window; a four-layer FCN (fcn[0..2] = 32, 16, 8
+ * ReLU units, one linear output) gives log k, the ratio of the fluid step to
+ * the platelet step (Table 2 step 4).
+ * LSTM cell, gates stacked (i, f, g, o) along the rows of W_ih [4H][in] and
+ * W_hh [4H][H]: i = s(W_ii x + b_ii + W_hi h + b_hi), f, o alike, g = tanh(..),
+ * c' = f c + i g, h' = o tanh(c'); zero initial state.  FP32 throughout
+ * (the layers are a few units wide).
+ *
+ * Flat FP32 parameter layout (md_lstm_param_count entries), in order:
+ *   enc1 {W_ih[4 H1][F], W_hh[4 H1][H1], b_ih[4 H1], b_hh[4 H1]},
+ *   enc2 {W_ih[4 H2][H1], W_hh[4 H2][H2], b_ih, b_hh},
+ *   dec1 {W_ih[4 H2][2 H2], W_hh[4 H2][H2], b_ih, b_hh},
+ *   dec2 {W_ih[4 H1][H2], W_hh[4 H1][H1], b_ih, b_hh}, out {W[F][H1], b[F]},
+ *   fcn {W0[fcn0][2 H2], b0, W1[fcn1][fcn0], b1, W2[fcn2][fcn1], b2, W3[1][fcn2], b3}.
+ */
+typedef struct md_lstm_config {
+    int32_t T, F;           /* window length (even, <= 256), measurements      */
+    int32_t H1, H2;         /* LSTM widths (16, 4)                             */
+    int32_t fcn[3];         /* FCN hidden widths (32, 16, 8)                   */
+    int32_t batch_max;      /* largest batch of windows                        */
+} md_lstm_config;
+
+typedef struct md_lstm md_lstm;
+
+int md_lstm_config_defaults(md_lstm_config *cfg);      /* T 50, F 6, H 16/4, FCN 32/16/8, B 256 */
+int md_lstm_param_count(const md_lstm_config *cfg, int64_t *n);
+int md_lstm_workspace_size(const md_lstm_config *cfg, size_t *bytes);
+/* Create over a caller-owned device workspace (>= md_lstm_workspace_size). */
+int md_lstm_init(const md_lstm_config *cfg, void *workspace, size_t bytes, void *cuda_stream, md_lstm **out);
+void md_lstm_destroy(md_lstm *m);
+const char *md_lstm_last_error(const md_lstm *m);
+int md_lstm_set_params(md_lstm *m, const float *params, int64_t n);   /* HOST; resets Adam */
+int md_lstm_get_params(md_lstm *m, float *params, int64_t n);
+int md_lstm_set_norm(md_lstm *m, const float *mean, const float *stdv);
+/* B raw windows [B][T][F] (host or device per `where`) -> HOST out[B][2]:
+ * predicted log k, reconstruction error (mean square over the window). */
+int md_lstm_predict(md_lstm *m, const float *raw, int32_t B, int32_t where, float *out);
+/*
+ * Loss and gradient (HOST grads[n_params], may be NULL) on denoised,
+ * normalised HOST windows x[B][T][F]: what = MD_AI_TRAIN_AE (reconstruction
+ * MSE over B T F) or MD_AI_TRAIN_HEADS (mean squared error of the FCN's
+ * log k against log_k[B]); the other part's gradient is zero.
+ * md_lstm_train_step also takes one Adam step (b1 0.9, b2 0.999, eps 1e-8,
+ * learning rate lr) on that part.  Errors: MD_EINVAL, MD_ENOTRAINED, MD_ECUDA.
+ */
+int md_lstm_grads(md_lstm *m, const float *x, const float *log_k, int32_t B, int32_t what, float *grads, float *loss);
+int md_lstm_train_step(md_lstm *m, const float *x, const float *log_k, int32_t B, int32_t what, float lr,
+                       float *loss);
+
 /* ---- diagnostics ---------------------------------------------------------- */
 #define MD_PROF_FLUID   0  /* K3 plasma-plasma / plasma-wall DPD pass          */
 #define MD_PROF_IFACE   1  /* K3 interface DPD pass                            */

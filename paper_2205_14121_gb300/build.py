@@ -19,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmsm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "sort.cu", "neighbor.cu", "forces.cu", "integrate.cu", "reduce.cu", "diag.cu", "features.cu",
-           "ai.cu"]
+           "ai.cu", "lstm.cu"]
 
 
 def nvcc():

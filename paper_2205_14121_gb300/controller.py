@@ -265,3 +265,157 @@ class Controller:
         self._check(_bind().md_ai_train_step(self.h, xp, kp, lp, B, what, float(lr), C.byref(loss)),
                     "md_ai_train_step")
         return loss.value
+
+
+# ---------------------------------------------------------------------------
+# the paper's own controller variant (Sec. 3.3): LSTM autoencoder + FCN
+# ---------------------------------------------------------------------------
+
+class md_lstm_config(C.Structure):
+    _fields_ = [("T", C.c_int32), ("F", C.c_int32), ("H1", C.c_int32), ("H2", C.c_int32), ("fcn", C.c_int32 * 3),
+                ("batch_max", C.c_int32)]
+
+
+_lstm_bound = False
+
+# measurement columns the variant reads (of the 12 recorded per platelet):
+# angular velocity (3), centre-of-mass velocity along the flow, plasma flow
+# speed at the centre of mass, largest bond strain
+LSTM_COLUMNS = (3, 4, 5, 0, 11, 9)
+
+
+def _bind_lstm():
+    global _lstm_bound
+    L = lib()
+    if _lstm_bound:
+        return L
+    vp, fp = C.c_void_p, C.POINTER(C.c_float)
+    cp = C.POINTER(md_lstm_config)
+    L.md_lstm_config_defaults.argtypes = [cp]
+    L.md_lstm_param_count.argtypes = [cp, C.POINTER(C.c_int64)]
+    L.md_lstm_workspace_size.argtypes = [cp, C.POINTER(C.c_size_t)]
+    L.md_lstm_init.argtypes = [cp, vp, C.c_size_t, vp, C.POINTER(vp)]
+    L.md_lstm_destroy.argtypes = [vp]
+    L.md_lstm_destroy.restype = None
+    L.md_lstm_last_error.argtypes = [vp]
+    L.md_lstm_last_error.restype = C.c_char_p
+    L.md_lstm_set_params.argtypes = [vp, fp, C.c_int64]
+    L.md_lstm_get_params.argtypes = [vp, fp, C.c_int64]
+    L.md_lstm_set_norm.argtypes = [vp, fp, fp]
+    L.md_lstm_predict.argtypes = [vp, vp, C.c_int32, C.c_int32, fp]
+    L.md_lstm_grads.argtypes = [vp, fp, fp, C.c_int32, C.c_int32, fp, fp]
+    L.md_lstm_train_step.argtypes = [vp, fp, fp, C.c_int32, C.c_int32, C.c_float, fp]
+    for n in ("md_lstm_config_defaults", "md_lstm_param_count", "md_lstm_workspace_size", "md_lstm_init",
+              "md_lstm_set_params", "md_lstm_get_params", "md_lstm_set_norm", "md_lstm_predict", "md_lstm_grads",
+              "md_lstm_train_step"):
+        getattr(L, n).restype = C.c_int
+    _lstm_bound = True
+    return L
+
+
+def lstm_config(batch_max=256):
+    c = md_lstm_config()
+    _bind_lstm().md_lstm_config_defaults(C.byref(c))
+    c.batch_max = batch_max
+    return c
+
+
+def lstm_param_layout(cfg):
+    """(name, shape) of every parameter block in the flat layout of msm.h."""
+    H1, H2, F = cfg.H1, cfg.H2, cfg.F
+    out = []
+    for name, nin, h in (("enc1", F, H1), ("enc2", H1, H2), ("dec1", 2 * H2, H2), ("dec2", H2, H1)):
+        out += [(f"{name}.W_ih", (4 * h, nin)), (f"{name}.W_hh", (4 * h, h)), (f"{name}.b_ih", (4 * h,)),
+                (f"{name}.b_hh", (4 * h,))]
+    out += [("out.W", (F, H1)), ("out.b", (F,))]
+    dims = (2 * H2,) + tuple(cfg.fcn) + (1,)
+    for i in range(4):
+        out += [(f"fcn.{i}.W", (dims[i + 1], dims[i])), (f"fcn.{i}.b", (dims[i + 1],))]
+    return out
+
+
+class LSTMController:
+    """The paper's LSTM autoencoder + FCN (Sec. 3.3) over a torch-allocated
+    device workspace: argument marshalling only."""
+
+    def __init__(self, cfg=None, stream=None):
+        import torch
+        L = _bind_lstm()
+        self.cfg = cfg if cfg is not None else lstm_config()
+        n = C.c_int64()
+        nb = C.c_size_t()
+        if L.md_lstm_param_count(C.byref(self.cfg), C.byref(n)) or L.md_lstm_workspace_size(C.byref(self.cfg),
+                                                                                            C.byref(nb)):
+            raise MdError(-1, "invalid LSTM controller configuration")
+        self.n_params = n.value
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        rc = L.md_lstm_init(C.byref(self.cfg), C.c_void_p(self.workspace.data_ptr()), nb.value,
+                            C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc:
+            raise MdError(rc, "md_lstm_init")
+        self.h = h
+
+    def _check(self, rc, what):
+        if rc:
+            raise MdError(rc, f"{what}: {_bind_lstm().md_lstm_last_error(self.h).decode()}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            _bind_lstm().md_lstm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    _f = staticmethod(Controller._f)
+
+    def set_params(self, vec):
+        vec, p = self._f(vec)
+        self._check(_bind_lstm().md_lstm_set_params(self.h, p, vec.size), "md_lstm_set_params")
+
+    def get_params(self):
+        out = np.zeros(self.n_params, np.float32)
+        self._check(_bind_lstm().md_lstm_get_params(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), self.n_params),
+                    "md_lstm_get_params")
+        return out
+
+    def set_norm(self, mean, std):
+        m, mp = self._f(mean)
+        s, sp = self._f(std)
+        self._check(_bind_lstm().md_lstm_set_norm(self.h, mp, sp), "md_lstm_set_norm")
+
+    def predict(self, raw):
+        """raw [B][T][F] -> dict(log_k, cls, k, rec_err); cls the nearest
+        class of log k (Table 2 step 5)."""
+        raw, rp = self._f(raw)
+        B = raw.shape[0]
+        out = np.zeros((B, 2), np.float32)
+        self._check(_bind_lstm().md_lstm_predict(self.h, C.cast(rp, C.c_void_p), B, AI_HOST,
+                                                 out.ctypes.data_as(C.POINTER(C.c_float))), "md_lstm_predict")
+        lk = np.log(np.asarray(K_SET, np.float64))
+        cls = np.abs(out[:, 0:1].astype(np.float64) - lk[None, :]).argmin(1)
+        return dict(log_k=out[:, 0], cls=cls, k=np.asarray(K_SET)[cls], rec_err=out[:, 1])
+
+    def grads(self, x, what, log_k=None):
+        x, xp = self._f(x)
+        B = x.shape[0]
+        lk = None if log_k is None else np.ascontiguousarray(log_k, np.float32)
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_float()
+        self._check(_bind_lstm().md_lstm_grads(self.h, xp, None if lk is None else lk.ctypes.data_as(
+            C.POINTER(C.c_float)), B, what, g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)), "md_lstm_grads")
+        return float(loss.value), g
+
+    def train_step(self, x, what, lr, log_k=None):
+        x, xp = self._f(x)
+        B = x.shape[0]
+        lk = None if log_k is None else np.ascontiguousarray(log_k, np.float32)
+        loss = C.c_float()
+        self._check(_bind_lstm().md_lstm_train_step(self.h, xp, None if lk is None else lk.ctypes.data_as(
+            C.POINTER(C.c_float)), B, what, float(lr), C.byref(loss)), "md_lstm_train_step")
+        return float(loss.value)

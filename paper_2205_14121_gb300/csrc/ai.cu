@@ -510,6 +510,23 @@ unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t > 0 ? 
 
 }  // namespace
 
+// Table 2 step 2 and Adam for the other controller variant (lstm.cu)
+cudaError_t ai_launch_denoise(const float *raw, int B, int T, int F, const float *mean, const float *stdv, float *out,
+                              cudaStream_t st)
+{
+    k_denoise<<<nblk((int64_t)B * F, 128), 128, 0, st>>>(raw, B, T, F, mean, stdv, out);
+    return cudaGetLastError();
+}
+
+cudaError_t ai_launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, int64_t t,
+                           cudaStream_t st)
+{
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    k_adam<<<nblk(n), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, 1e-8f, c1, c2);
+    return cudaGetLastError();
+}
+
 // ===========================================================================
 // controller object
 // ===========================================================================

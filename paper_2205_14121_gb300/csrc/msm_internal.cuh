@@ -568,6 +568,12 @@ cudaError_t launch_features(md_system *s, double *out_dev, const float4 *f_plt =
                             const float *hk = nullptr);
 // append feat to the ring at the device record counter, then advance it
 cudaError_t launch_feature_ring(md_system *s, const double *feat);
+// ai.cu: the denoising filter (raw [B][T][F] -> normalised time-major
+// [T][B][F]) and an Adam step (b1 0.9, b2 0.999, eps 1e-8, step count t)
+cudaError_t ai_launch_denoise(const float *raw, int B, int T, int F, const float *mean, const float *stdv, float *out,
+                              cudaStream_t st);
+cudaError_t ai_launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, int64_t t,
+                           cudaStream_t st);
 // api.cu helpers
 int set_error(md_system *s, int code, const char *msg);
 int cuda_fail(md_system *s, cudaError_t e, const char *where);
