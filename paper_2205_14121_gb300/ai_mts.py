@@ -319,14 +319,18 @@ def evaluate(ctl, windows, err_s, err_v, trust, batch=128):
     the mean step ratio (cost of the platelet level) of the controller and of
     every fixed ratio."""
     n = windows.shape[0]
-    ks = []
+    ks, unsure = [], []
     for b in range(0, n, batch):
-        k, _, _ = decide(ctl, windows[b:b + batch], trust)
+        k, _, u = decide(ctl, windows[b:b + batch], trust)
         ks.append(k)
+        unsure.append(u)
     k = np.concatenate(ks)
+    unsure = np.concatenate(unsure)
     col = np.searchsorted(np.array(K_SET), k)
     viol = lambda c: float(np.mean((err_s[np.arange(n), c] > GATE_STRESS) | (err_v[np.arange(n), c] > GATE_VCOM)))
-    out = {"controller": {"violations": viol(col), "mean_k": float(k.mean())}}
+    out = {"controller": {"violations": viol(col), "mean_k": float(k.mean()),
+                          "fallback_fraction": float(unsure.mean()),
+                          "k_counts": [int((k == kk).sum()) for kk in K_SET]}}
     for j, kk in enumerate(K_SET):
         out[f"fixed_k{kk}"] = {"violations": viol(np.full(n, j)), "mean_k": float(kk)}
     return out

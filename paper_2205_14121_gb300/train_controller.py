@@ -30,6 +30,7 @@ def main(argv=None):
     ap.add_argument("--windows", type=int, default=8)
     ap.add_argument("--horizon", type=int, default=50)
     ap.add_argument("--n-shell", type=int, default=2000)
+    ap.add_argument("--k-m", type=int, default=2, help="interface substeps per fluid step (Table 1 k_m)")
     ap.add_argument("--epochs-ae", type=int, default=40)
     ap.add_argument("--epochs-heads", type=int, default=80)
     ap.add_argument("--dataset", default=None, help="save / reuse the labelled windows here (.npz)")
@@ -51,7 +52,7 @@ def main(argv=None):
         tr = [d[f"train_{k}"] for k in ("w", "c", "h", "es", "ev")]
         te = [d[f"test_{k}"] for k in ("w", "c", "h", "es", "ev")]
     else:
-        kw = dict(n_windows=args.windows, horizon=args.horizon, n_shell=args.n_shell, progress=progress)
+        kw = dict(n_windows=args.windows, horizon=args.horizon, n_shell=args.n_shell, progress=progress, k_m=args.k_m)
         tr = A.generate(seeds_train, **kw).arrays()
         te = A.generate(seeds_test, **kw).arrays()
         if args.dataset:
@@ -84,7 +85,7 @@ def main(argv=None):
                    strain_p99=float(art["strain_p99"]),
                    loss_ae=art["history"]["ae"][-1], loss_heads=art["history"]["heads"][-1],
                    seconds_data=t_data, seconds_train=t_train,
-                   horizon=args.horizon, windows_per_trajectory=args.windows, n_shell=args.n_shell)
+                   horizon=args.horizon, windows_per_trajectory=args.windows, n_shell=args.n_shell, k_m=args.k_m)
     with open(os.path.splitext(args.out)[0] + ".json", "w") as f:
         json.dump(summary, f, indent=1)
     print(json.dumps(summary), flush=True)

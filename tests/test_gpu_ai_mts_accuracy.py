@@ -1,11 +1,20 @@
-"""AI-MTS against fine-step STS on the same synthetic channel (Sec. 4.2): the
-flow profile and the per-platelet stresses of AI-MTS (dt_f = 0.01, ratios
-from the trained controller) agree with fine-step STS (dt = 0.001 for every
-particle): over three noise realisations of each arm, the mean flow profiles
-differ by no more than three times the spread expected between such means
-(estimated from the fine-step runs), the mean per-platelet stresses by no
-more than the paper's 3% plus that spread, and temperature and pressure by
-the paper's 0.7% and 1.2%.  Fixed-k RESPA (k = 10) is measured beside it."""
+"""AI-MTS against fine-step STS on the same synthetic channel (Sec. 4.2).
+
+Arms from one developed state of a walled 36 x 18 x 16 channel with two
+2,000-particle platelets (bonds and angles):
+  * fine-step STS: velocity-Verlet with dt = 0.001 for every particle;
+  * AI-MTS: dt_f = 0.01 with k_m = 2 interface substeps (Table 1's middle
+    level) and per-platelet ratios decided on the device by the trained
+    controller, asked again after each predicted hold;
+  * fixed-k RESPA (k = 10, k_m = 2) for comparison.
+Three noise realisations of 12 time units each per arm.  Gates, as the
+paper states them (Sec. 4.2, Table 4): mean per-platelet principal stresses
+within 3%, the mean flow profile within 1% (relative L2), temperature within
+0.7% and pressure within 1.2% of fine-step STS -- and each gate must exceed
+twice the sampling spread of the compared means, so that it resolves the
+difference.  The body force gives a wall shear rate of 0.5 (ten times the
+configurations' 0.05): at 0.05 the thermal noise of a 12-unit profile mean
+in this channel is several percent, far above the 1% gate."""
 import os
 
 import numpy as np
@@ -14,12 +23,15 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 DATA = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2205_14121_gb300", "data")
+K_M = 2
+TAU = 12.0            # averaged time units per run
+SEEDS = (5, 6, 7)
 
 
 def channel():
     import synth
     box = (36.0, 18.0, 16.0)
-    g = synth.poiseuille_g(0.05, synth.ETA_DPD, 3.0, box[1])
+    g = synth.poiseuille_g(0.5, synth.ETA_DPD, 3.0, box[1])
     return synth.platelet_system(box, int(3 * 36 * 18 * 16), 2, 2000, synth.scaled_radii(2000), walls=True,
                                  body_force=g, seed=31, developed_flow=True)
 
@@ -35,6 +47,10 @@ def sample(g, acc):
     acc["P"].append(o["pressure"])
 
 
+def new_acc():
+    return {"prof": [], "stress": [], "T": [], "P": []}
+
+
 def test_ai_mts_matches_fine_step_sts():
     import paper_2205_14121_gb300 as M
     from paper_2205_14121_gb300 import ai_mts as A
@@ -42,15 +58,16 @@ def test_ai_mts_matches_fine_step_sts():
     kw = dict(walls=s.walls, wall=s.wall, body_force=s.body_force, X0=s.X0, bonds=s.bonds, r0=s.r0,
               angles=s.angles, theta0=s.theta0)
     eq = M.System(s.box, s.x, s.v, s.tag, dt=0.01, **kw)
-    eq.mts_step(300, mode=M.MD_MODE_RESPA, k_m=1, k_p=10)            # out of the synthetic start
+    eq.mts_step(300, mode=M.MD_MODE_RESPA, k_m=K_M, k_p=10)          # out of the synthetic start
     x0, v0, _ = eq.read_particles()
     eq.close()
+    n_samples = int(TAU / 0.05)
 
     def fine(seed):
         g = M.System(s.box, x0, v0, s.tag, dt=0.001, seed=seed, **kw)
         g.mts_step(1280)                                   # the AI arm's first window
-        acc = {"prof": [], "stress": [], "T": [], "P": []}
-        for _ in range(60):
+        acc = new_acc()
+        for _ in range(n_samples):
             g.mts_step(50)
             sample(g, acc)
         g.close()
@@ -60,66 +77,57 @@ def test_ai_mts_matches_fine_step_sts():
 
     def ai_run(seed):
         g = M.System(s.box, x0, v0, s.tag, dt=0.01, seed=seed, **kw)
-        g.set_platelet_levels([trust.fallback_k] * 2)
-        g.mts_step(128, mode=M.MD_MODE_AI, k_m=1, record=True)
-        windows, _ = g.read_feature_ring()
-        k, _, _ = A.decide(ctl.predict(windows), windows, trust)
-        g.set_platelet_levels(k)
-        acc = {"prof": [], "stress": [], "T": [], "P": [], "k": k.tolist()}
-        for _ in range(60):
-            g.mts_step(5, mode=M.MD_MODE_AI, k_m=1)
+        log = []
+        A.run_ai_mts(g, ctl, 128, k_m=K_M, trust=trust, log=log)      # the first window
+        acc = new_acc()
+        for _ in range(n_samples):
+            A.run_ai_mts(g, ctl, 5, k_m=K_M, trust=trust, log=log)
             sample(g, acc)
+        acc["k"] = [d["k"] for d in log]
         g.close()
         return acc
 
-    # three noise realisations per arm; the fine runs cover the same 3 tau
-    # after the same 1.28 tau lead-in as the AI arm's first window
-    ais = [ai_run(sd) for sd in (5, 6, 7)]
-    fines = [fine(sd) for sd in (11, 12, 13)]
-
-    def respa_run(seed):             # fixed k = 10 for both platelets, for comparison
+    def respa_run(seed):
         g = M.System(s.box, x0, v0, s.tag, dt=0.01, seed=seed, **kw)
-        g.mts_step(128, mode=M.MD_MODE_RESPA, k_m=1, k_p=10)
-        acc = {"prof": [], "stress": [], "T": [], "P": []}
-        for _ in range(60):
-            g.mts_step(5, mode=M.MD_MODE_RESPA, k_m=1, k_p=10)
+        g.mts_step(128, mode=M.MD_MODE_RESPA, k_m=K_M, k_p=10)
+        acc = new_acc()
+        for _ in range(n_samples):
+            g.mts_step(5, mode=M.MD_MODE_RESPA, k_m=K_M, k_p=10)
             sample(g, acc)
         g.close()
         return acc
 
-    respas = [respa_run(sd) for sd in (5, 6, 7)]
+    ais = [ai_run(sd) for sd in SEEDS]
+    fines = [fine(sd + 6) for sd in SEEDS]
+    respas = [respa_run(sd) for sd in SEEDS]
 
     def mean_of(runs, key):
         return np.mean([np.mean(r[key], 0) for r in runs], 0)
 
-    pf, pa = mean_of(fines, "prof"), mean_of(ais, "prof")
-    sf, sa = mean_of(fines, "stress"), mean_of(ais, "stress")
-    Tf, Ta = mean_of(fines, "T"), mean_of(ais, "T")
-    Pf, Pa = mean_of(fines, "P"), mean_of(ais, "P")
-    # the spread of one run about another, from the fine pairs; the
-    # difference of two 3-run means has 1/sqrt(3) of it
-    pairs = [(0, 1), (0, 2), (1, 2)]
-    fp = [np.mean(r["prof"], 0) for r in fines]
-    fs = [np.mean(r["stress"], 0) for r in fines]
-    noise_p = np.mean([np.linalg.norm(fp[a] - fp[b]) for a, b in pairs]) / np.linalg.norm(pf) / np.sqrt(3.0)
-    noise_s = np.mean([np.abs(fs[a] - fs[b]).max() for a, b in pairs]) / np.abs(sf).max() / np.sqrt(3.0)
-    err_p = np.linalg.norm(pa - pf) / np.linalg.norm(pf)
-    err_s = np.abs(sa - sf).max() / np.abs(sf).max()
-    pr, sr = mean_of(respas, "prof"), mean_of(respas, "stress")
-    err_p_k10 = np.linalg.norm(pr - pf) / np.linalg.norm(pf)
-    err_s_k10 = np.abs(sr - sf).max() / np.abs(sf).max()
-    vmax = np.abs(pf).max()
-    fT = [np.mean(r["T"]) for r in fines]
-    fP = [np.mean(r["P"]) for r in fines]
-    print(dict(k=[r["k"] for r in ais], vmax=vmax, profile_err=err_p, profile_noise=noise_p, stress_err=err_s,
-               stress_noise=noise_s, profile_err_k10=err_p_k10, stress_err_k10=err_s_k10, T_fine=fT, T_ai=[np.mean(r["T"]) for r in ais],
-               P_fine=fP, P_ai=[np.mean(r["P"]) for r in ais]))
-    assert vmax > 0.05                                  # the channel flows
-    assert err_p <= 3.0 * noise_p + 0.005
-    # per-platelet stresses: the paper's 3% (Sec. 4.2) on top of the sampling noise
-    assert err_s <= 0.03 + 3.0 * noise_s
-    # temperature and pressure against the fine-step mean: within the paper's
-    # 0.7% and 1.2% (Sec. 4.2), or twice the spread of the fine runs' means
-    # where the noise of these short averages is larger
-    assert abs(Ta - Tf) <= max(0.007 * Tf, 2.0 * np.std(fT))
-    assert abs(Pa - Pf) <= max(0.012 * abs(Pf), 2.0 * np.std(fP))
+    def spread(runs, key, norm):
+        """Spread of the difference of two 3-run means, from the pairs of runs."""
+        ms = [np.mean(r[key], 0) for r in runs]
+        pairs = [(0, 1), (0, 2), (1, 2)]
+        return np.mean([norm(ms[a] - ms[b]) for a, b in pairs]) / np.sqrt(3.0)
+
+    l2 = np.linalg.norm
+    mx = lambda d: np.abs(d).max()
+    pf, sf = mean_of(fines, "prof"), mean_of(fines, "stress")
+    Tf, Pf = mean_of(fines, "T"), mean_of(fines, "P")
+    res = {}
+    for name, runs in (("ai_mts", ais), ("respa_k10", respas)):
+        pa, sa = mean_of(runs, "prof"), mean_of(runs, "stress")
+        res[name] = dict(profile_err=l2(pa - pf) / l2(pf), stress_err=mx(sa - sf) / mx(sf),
+                         T_err=abs(mean_of(runs, "T") - Tf) / Tf, P_err=abs(mean_of(runs, "P") - Pf) / abs(Pf))
+    noise = dict(profile=spread(fines, "prof", l2) / l2(pf), stress=spread(fines, "stress", mx) / mx(sf),
+                 T=spread(fines, "T", abs) / Tf, P=spread(fines, "P", abs) / abs(Pf))
+    print(dict(k_m=K_M, vmax=mx(pf), ks=[r["k"] for r in ais], noise=noise, **res))
+    assert mx(pf) > 0.5                                  # the channel flows
+    gates = dict(profile=0.01, stress=0.03, T=0.007, P=0.012)
+    for key, gate in gates.items():
+        assert 2.0 * noise[key] < gate, f"{key}: sampling spread {noise[key]:.4f} too large for the gate {gate}"
+    r = res["ai_mts"]
+    assert r["profile_err"] <= gates["profile"]
+    assert r["stress_err"] <= gates["stress"]
+    assert r["T_err"] <= gates["T"]
+    assert r["P_err"] <= gates["P"]
