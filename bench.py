@@ -321,6 +321,14 @@ def issue_limiter(workload_name, launch_ms, n, sm_mhz):
         return None
 
 
+_T0 = time.time()
+
+
+def progress(msg):
+    """Phase marks on stderr (the JSON line goes to stdout)."""
+    print(f"[bench {time.time() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -352,6 +360,7 @@ def main():
     s, wl = workload(args.workload, seed=seed)
     t_gen = time.perf_counter() - t_gen
     n = s.n
+    progress(f"generated {args.workload}: {n} particles in {t_gen:.1f} s")
     platelets = args.workload != "dpd1m"
     g = make_system(M, s, wl["dt"], wl["skin"], seed, wl.get("skin_plt", 0.0))
 
@@ -387,6 +396,7 @@ def main():
         def step(k):
             g.mts_step(k, direct=args.direct)
         g.mts_step(args.relax, direct=args.direct)
+    progress(f"relaxed: {mode_info.get('relax')}")
     # the relaxed state every comparison arm starts from
     x_rel, v_rel, _ = g.read_particles()
 
@@ -395,6 +405,7 @@ def main():
     torch.cuda.synchronize()
     decisions.clear()
 
+    progress("warm-up done")
     # ---- timed region --------------------------------------------------
     g.profile_read(reset=True)
     builds0 = g.observables()["n_builds"]
@@ -420,6 +431,7 @@ def main():
     else:
         mode_info["mode"] = "STS"
 
+    progress(f"timed: {ms / args.steps:.2f} ms per step, {mode_info.get('decisions')} decisions")
     # ---- roofline pass: per-class CUDA events on the launching stream -----
     g.profile_enable(True)
     n_prof = min(args.steps, 100)
@@ -453,6 +465,7 @@ def main():
                     "share_of_step_at_mean_hold": (us * 1e-3 / hold_min) / (ms / args.steps) if hold_min else None,
                     "mean_hold": float(np.mean(holds)) if holds else None}
 
+    progress("roofline pass and controller timing done")
     # ---- end to end through the C ABI with host buffers ------------------
     e2e = None
     if args.e2e_steps > 0:
@@ -502,6 +515,7 @@ def main():
     del g
     torch.cuda.empty_cache()
 
+    progress(f"e2e done: {e2e['value'] if e2e else None}")
     # ---- comparison arms on the same system, from the relaxed state -------
     compare = {}
     if platelets and not args.no_compare:
@@ -527,6 +541,7 @@ def main():
             h.close()
             del h
             torch.cuda.empty_cache()
+            progress(f"arm {name}: {compare[name]['ms_per_step']:.2f} ms per step")
         compare["speedup_vs_fine_sts"] = value / compare["fine_sts"]["ns_per_day"]
         compare["speedup_vs_respa_k10"] = value / compare["respa_k10"]["ns_per_day"]
         compare["note"] = ("every arm starts from the same relaxed state; speed-ups are of the timed arm "

@@ -1216,11 +1216,9 @@ int md_mts_step(md_system *s, int64_t n_outer, const md_mts_schedule *sched)
     const bool det = (sched->flags & MD_SCHED_DETERMINISTIC) != 0;
     if (det && mode == MD_MODE_AI)
         return set_error(s, MD_EINVAL, "md_mts_step: deterministic steps cover STS and RESPA, not AI-MTS");
-    if (det != s->det_step) {
-        // the forces at hand were summed the other way: evaluate them again
-        s->det_step = det;
-        s->forces_stale = true;
-    }
+    // the forces at hand (computed, or restored from a checkpoint) are part of
+    // the state and are kept; the mode applies to every later evaluation
+    s->det_step = det;
     int k_m = sched->k_m > 0 ? sched->k_m : 1;
     int k_p = sched->k_p > 0 ? sched->k_p : 1;
     if (mode == MD_MODE_STS) { k_m = 1; k_p = 1; }

@@ -237,11 +237,13 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 
 // Standard normal from two 32-bit words: Box-Muller on their top 24 bits,
 // u1 = (k+1) 2^-24 in (0,1], u2 in [0,1), zeta = sqrt(-2 ln u1) cos(2 pi u2).
-// -2 ln u1 comes from the hardware log2 except near u1 = 1, where the
-// absolute error of that approximation would dominate its small result; there
-// the Taylor series of -ln(1 - v), v = 1 - u1 (exact), is summed to v^8.
-// cos(2 pi u2) = -cos(2 pi (u2 - 1/2)) keeps the hardware cosine's argument
-// in [-pi, pi).
+// -2 ln u1 comes from the hardware log2 except near u1 = 1 (v = 1 - u1 below
+// 2^-6, v exact), where the absolute error of that approximation would
+// dominate its small result; there the Taylor series of -ln(1 - v) is summed
+// to v^5 (relative truncation below 2^-30).  Both are evaluated and one is
+// selected, with no branch: a lane near u1 = 1 would otherwise make its whole
+// warp run both paths.  cos(2 pi u2) = -cos(2 pi (u2 - 1/2)) keeps the
+// hardware cosine's argument in [-pi, pi).
 __device__ __forceinline__ float gauss_from_bits(uint32_t r0, uint32_t r1);
 
 // Uniform variate of zero mean and unit variance from the top 24 bits b of
@@ -257,15 +259,9 @@ __device__ __forceinline__ float gauss_from_bits(uint32_t r0, uint32_t r1)
 {
     const uint32_t k = r0 >> 8;
     const float v = (float)(0xFFFFFFu - k) * (1.0f / 16777216.0f);
-    float t;
-    if (v < 0.0625f) {
-        t = 2.0f * v *
-            (1.0f + v * (0.5f + v * (0.33333334f + v * (0.25f + v * (0.2f + v * (0.16666667f +
-                                                                              v * (0.14285715f + v * 0.125f)))))));
-    } else {
-        const float u1 = (float)(k + 1u) * (1.0f / 16777216.0f);
-        t = -1.38629436f * __log2f(u1);
-    }
+    const float ser = 2.0f * v * (1.0f + v * (0.5f + v * (0.33333334f + v * (0.25f + v * 0.2f))));
+    const float lg = -1.38629436f * __log2f((float)(k + 1u) * (1.0f / 16777216.0f));
+    const float t = v < 0.015625f ? ser : lg;
     const float u2 = (float)(r1 >> 8) * (1.0f / 16777216.0f) - 0.5f;
     return -(t * rsqrtf(fmaxf(t, 1e-30f))) * __cosf(6.28318531f * u2);
 }

@@ -124,16 +124,14 @@ def knn_bonds(points, k=6):
 # Bending triplets: at each vertex j, every bonded neighbour i paired with
 # the bonded neighbour k across from it (the largest angle i-j-k, if above
 # 150 degrees) -- three nearly straight lines through each vertex of the
-# membrane, as in a triangulated sheet.  Their reference angle is pi (a flat
-# membrane, no spontaneous curvature): the (theta - theta0)^2 form of Eq. 2
-# has a cone point at theta = pi, where the force turns over unless theta0 is
-# pi itself, and thermal bending of the shells crosses it.
+# membrane, as in a triangulated sheet -- with their rest angles as the
+# reference, so that a shell starts without bending stress.
 ANGLE_MIN = 5.0 * math.pi / 6.0
 
 
 def angle_triplets(points, pairs, min_angle=ANGLE_MIN):
     """Bending triplets (i, j, k) of a bonded shell, j the vertex and i < k,
-    and their reference angles (pi)."""
+    and their rest angles (rounded to binary32)."""
     n = points.shape[0]
     nb = [[] for _ in range(n)]
     for a, b in pairs:
@@ -156,7 +154,13 @@ def angle_triplets(points, pairs, min_angle=ANGLE_MIN):
     if not tri:
         return np.zeros((0, 3), np.int32), np.zeros(0)
     t = np.asarray(sorted(tri), np.int32)
-    return t, np.full(len(t), math.pi)
+    return t, _f32(triplet_angles(points, t.astype(np.int64)))
+
+
+def _f32(a):
+    """Rest values rounded to binary32 (the precision the device stores), so
+    that the device and the FP64 checks read the same numbers."""
+    return np.asarray(a, np.float32).astype(np.float64)
 
 
 def triplet_angles(points, t):
@@ -302,7 +306,7 @@ def _assemble(box, fluid_x, wall_x, plts, rng, n_shell, receptor_frac, kT=1.0, b
             b = topo
             r0 = np.linalg.norm(pts[b[:, 0]] - pts[b[:, 1]], axis=1)
             at = atopo
-            th0 = np.full(len(at), math.pi)
+            th0 = _f32(triplet_angles(pts, at.astype(np.int64)))
         bonds.append(b + off)
         r0s.append(r0)
         angs.append(at + off)

@@ -92,11 +92,10 @@ def test_corrupt_configuration_is_rejected(bad):
             make(s, dt=-0.01)
         elif bad == "walls_and_le":
             M.System(s.box, s.x, s.v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, angles=s.angles,
-                     theta0=s.theta0, walls=True, wall=s.wall,
-                     shear_rate=0.05)
+                     theta0=s.theta0, walls=True, wall=s.wall, flags=M.MD_CFG_LEES_EDWARDS)
         elif bad == "receptors":
             tag = s.tag.copy()
-            tag[tag >= 0] |= M.RECEPTOR_BIT      # the counts no longer match the configuration
+            tag[tag >= 0] |= 1 << 30             # every platelet particle a receptor: the counts no longer match
             g = make(s)
             g.set_particles(s.x, s.v, tag, s.X0)
         else:
