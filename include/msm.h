@@ -542,6 +542,8 @@ int md_lstm_set_norm(md_lstm *m, const float *mean, const float *stdv);
 /* B raw windows [B][T][F] (host or device per `where`) -> HOST out[B][2]:
  * predicted log k, reconstruction error (mean square over the window). */
 int md_lstm_predict(md_lstm *m, const float *raw, int32_t B, int32_t where, float *out);
+/* Table 2 steps 1-2 only: raw windows -> denoised, normalised HOST out[B][T][F]. */
+int md_lstm_prepare(md_lstm *m, const float *raw, int32_t B, int32_t where, float *out);
 /*
  * Loss and gradient (HOST grads[n_params], may be NULL) on denoised,
  * normalised HOST windows x[B][T][F]: what = MD_AI_TRAIN_AE (reconstruction

@@ -334,3 +334,59 @@ def evaluate(ctl, windows, err_s, err_v, trust, batch=128):
     for j, kk in enumerate(K_SET):
         out[f"fixed_k{kk}"] = {"violations": viol(np.full(n, j)), "mean_k": float(kk)}
     return out
+
+
+# ---------------------------------------------------------------------------
+# the paper's own variant (Sec. 3.3): LSTM autoencoder + FCN on log k
+# ---------------------------------------------------------------------------
+
+def lstm_windows(windows, T=50):
+    """The variant's input from recorded windows: the last T steps of its six
+    measurement columns (controller.LSTM_COLUMNS)."""
+    from .controller import LSTM_COLUMNS
+    return np.ascontiguousarray(windows[:, -T:, list(LSTM_COLUMNS)], np.float32)
+
+
+def train_lstm(windows, classes, epochs_ae=60, epochs_fcn=120, batch=128, lr_ae=3e-3, lr_fcn=3e-3, seed=0):
+    """The variant trained on the same labelled windows: the autoencoder
+    first, then the FCN on log k of the label (Sec. 3.3 trains them
+    separately).  Returns (model, artefacts)."""
+    from .controller import LSTMController, lstm_config, lstm_param_layout
+    cfg = lstm_config(batch_max=batch)
+    m = LSTMController(cfg)
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, shape in lstm_param_layout(cfg):
+        if ".W" in name:
+            bound = 1.0 / math.sqrt(shape[-1])
+            parts.append(rng.uniform(-bound, bound, size=shape).astype(np.float32).ravel())
+        else:
+            parts.append(np.zeros(int(np.prod(shape)), np.float32))
+    m.set_params(np.concatenate(parts))
+    raw = lstm_windows(windows)
+    n = raw.shape[0]
+    den = np.concatenate([m.prepare(raw[b:b + batch]) for b in range(0, n, batch)])
+    mean = den.reshape(-1, cfg.F).mean(0)
+    std = den.reshape(-1, cfg.F).std(0) + 1e-6
+    m.set_norm(mean, std)
+    x = np.concatenate([m.prepare(raw[b:b + batch]) for b in range(0, n, batch)])
+    lk = np.log(np.asarray(K_SET, np.float64)[classes]).astype(np.float32)
+    hist = {"ae": [], "fcn": []}
+    for _ in range(epochs_ae):
+        hist["ae"].append(float(np.mean([m.train_step(x[i], TRAIN_AE, lr_ae) for i in _batches(n, batch, rng)])))
+    for _ in range(epochs_fcn):
+        hist["fcn"].append(float(np.mean([m.train_step(x[i], TRAIN_HEADS, lr_fcn, log_k=lk[i])
+                                          for i in _batches(n, batch, rng)])))
+    return m, dict(params=m.get_params(), mean=mean.astype(np.float32), std=std.astype(np.float32), history=hist)
+
+
+def evaluate_lstm(m, windows, err_s, err_v, batch=128):
+    """The variant's policy on labelled windows (the class nearest its log k;
+    the paper describes no trust bound for it)."""
+    n = windows.shape[0]
+    raw = lstm_windows(windows)
+    k = np.concatenate([m.predict(raw[b:b + batch])["k"] for b in range(0, n, batch)])
+    col = np.searchsorted(np.array(K_SET), k)
+    bad = (err_s[np.arange(n), col] > GATE_STRESS) | (err_v[np.arange(n), col] > GATE_VCOM)
+    return {"violations": float(bad.mean()), "mean_k": float(k.mean()),
+            "k_counts": [int((k == kk).sum()) for kk in K_SET]}

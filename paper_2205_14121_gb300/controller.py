@@ -303,11 +303,12 @@ def _bind_lstm():
     L.md_lstm_get_params.argtypes = [vp, fp, C.c_int64]
     L.md_lstm_set_norm.argtypes = [vp, fp, fp]
     L.md_lstm_predict.argtypes = [vp, vp, C.c_int32, C.c_int32, fp]
+    L.md_lstm_prepare.argtypes = [vp, vp, C.c_int32, C.c_int32, fp]
     L.md_lstm_grads.argtypes = [vp, fp, fp, C.c_int32, C.c_int32, fp, fp]
     L.md_lstm_train_step.argtypes = [vp, fp, fp, C.c_int32, C.c_int32, C.c_float, fp]
     for n in ("md_lstm_config_defaults", "md_lstm_param_count", "md_lstm_workspace_size", "md_lstm_init",
               "md_lstm_set_params", "md_lstm_get_params", "md_lstm_set_norm", "md_lstm_predict", "md_lstm_grads",
-              "md_lstm_train_step"):
+              "md_lstm_train_step", "md_lstm_prepare"):
         getattr(L, n).restype = C.c_int
     _lstm_bound = True
     return L
@@ -400,6 +401,15 @@ class LSTMController:
         lk = np.log(np.asarray(K_SET, np.float64))
         cls = np.abs(out[:, 0:1].astype(np.float64) - lk[None, :]).argmin(1)
         return dict(log_k=out[:, 0], cls=cls, k=np.asarray(K_SET)[cls], rec_err=out[:, 1])
+
+    def prepare(self, raw):
+        """Denoised, normalised windows [B][T][F] (Table 2 steps 1-2, on the device)."""
+        raw, rp = self._f(raw)
+        B = raw.shape[0]
+        out = np.zeros((B, self.cfg.T, self.cfg.F), np.float32)
+        self._check(_bind_lstm().md_lstm_prepare(self.h, C.cast(rp, C.c_void_p), B, AI_HOST,
+                                                 out.ctypes.data_as(C.POINTER(C.c_float))), "md_lstm_prepare")
+        return out
 
     def grads(self, x, what, log_k=None):
         x, xp = self._f(x)

@@ -542,6 +542,21 @@ int md_lstm_predict(md_lstm *m, const float *raw, int32_t B, int32_t where, floa
     return MD_OK;
 }
 
+int md_lstm_prepare(md_lstm *m, const float *raw, int32_t B, int32_t where, float *out)
+{
+    if (!m || !raw || !out || B < 1 || B > m->c.batch_max) return MD_EINVAL;
+    int rc = stage(m, raw, B, where, true);
+    if (rc) return rc;
+    const int T = m->c.T, F = m->c.F;
+    std::vector<float> tm((size_t)T * B * F);
+    LK(cudaMemcpyAsync(tm.data(), m->X, sizeof(float) * tm.size(), cudaMemcpyDeviceToHost, m->st), "windows");
+    LK(cudaStreamSynchronize(m->st), "sync");
+    for (int t = 0; t < T; ++t)          // time-major [T][B][F] -> [B][T][F]
+        for (int b = 0; b < B; ++b)
+            for (int f = 0; f < F; ++f) out[((int64_t)b * T + t) * F + f] = tm[((size_t)t * B + b) * F + f];
+    return MD_OK;
+}
+
 int md_lstm_grads(md_lstm *m, const float *x, const float *log_k, int32_t B, int32_t what, float *grads,
                   float *loss)
 {

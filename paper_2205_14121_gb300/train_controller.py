@@ -74,14 +74,20 @@ def main(argv=None):
     ev_train = A.evaluate(ctl, w_tr, es_tr, ev_tr, trust)
     ev_test = A.evaluate(ctl, w_te, es_te, ev_te, trust)
     pred_te = np.concatenate([ctl.predict(w_te[b:b + 128])["cls"] for b in range(0, len(c_te), 128)])
+    # the paper's own LSTM variant on the same windows, for comparison
+    lstm, lart = A.train_lstm(w_tr, c_tr)
+    lstm_test = A.evaluate_lstm(lstm, w_te, es_te, ev_te)
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     A.save(args.out, art)
+    np.savez(os.path.splitext(args.out)[0] + "_lstm.npz", params=lart["params"], mean=lart["mean"], std=lart["std"])
     np.savez(os.path.splitext(args.out)[0] + "_heldout.npz", w=w_te, c=c_te, h=h_te, es=es_te, ev=ev_te)
     summary = dict(train_windows=int(len(c_tr)), test_windows=int(len(c_te)),
                    class_counts_train=np.bincount(c_tr, minlength=5).tolist(),
                    class_counts_test=np.bincount(c_te, minlength=5).tolist(),
                    test_class_accuracy=float(np.mean(pred_te == c_te)),
-                   eval_train=ev_train, eval_test=ev_test, rec_p99=float(art["rec_p99"]),
+                   eval_train=ev_train, eval_test=ev_test, lstm_variant_test=lstm_test,
+                   lstm_loss_ae=lart["history"]["ae"][-1], lstm_loss_fcn=lart["history"]["fcn"][-1],
+                   rec_p99=float(art["rec_p99"]),
                    strain_p99=float(art["strain_p99"]),
                    loss_ae=art["history"]["ae"][-1], loss_heads=art["history"]["heads"][-1],
                    seconds_data=t_data, seconds_train=t_train,
