@@ -87,7 +87,7 @@ extern "C" {
  * sigma = 3, rc = 1; Eq. 3 interface DPD a_fp = 50; Eq. 2 LJ eps = 1,
  * sigma = 0.8, cut-off 2.5 sigma, between particles of different platelets
  * (lj_excl = 1e30: a same-platelet pair feels LJ only when its rest distance
- * is at least lj_excl), k_b = 100, angle constant k_theta = 20 on the bending
+ * is at least lj_excl), k_b = 100, angle constant k_theta = 5 on the bending
  * triplets given to md_set_angles; Eq. 2/4 Morse D = 2, alpha = 2, r0 = 1 with
  * cut-off 5.
  */
@@ -117,7 +117,7 @@ typedef struct md_config {
                                  platelet particle trips a rebuild at skin_plt/2 */
     int64_t  n_angles;        /* angle triplets of the Eq. 2 angle term          */
     double   k_angle;         /* its constant k_theta in U = k_theta (theta -
-                                 theta0)^2 (as printed, no 1/2); default 20      */
+                                 theta0)^2 (as printed, no 1/2); default 5       */
 } md_config;
 
 /* Fill *cfg with the defaults above for n particles in box (no platelets). */

@@ -54,7 +54,7 @@ class Params(C.Structure):
 
 DEFAULTS = dict(rc=1.0, a_ff=25.0, a_fw=25.0, a_fp=50.0, gamma=4.5, sigma=3.0,
                 lj_eps=1.0, lj_sigma=0.8, lj_rc=2.0, lj_excl=1e30,
-                m_D=2.0, m_alpha=2.0, m_r0=1.0, m_rc=5.0, f_A=0.0, k_b=100.0, k_a=20.0)
+                m_D=2.0, m_alpha=2.0, m_r0=1.0, m_rc=5.0, f_A=0.0, k_b=100.0, k_a=5.0)
 
 
 def make_params(box, walls=False, le_rate=0.0, le_offset=0.0, g=0.0, seed=20220528, angles=None, theta0=None,

@@ -749,7 +749,7 @@ int md_config_defaults(md_config *c)
     c->lj_eps = 1.0; c->lj_sigma = 0.8; c->lj_rc = 2.0; c->lj_excl = 1e30;   // no LJ within one platelet
     c->morse_D = 2.0; c->morse_alpha = 2.0; c->morse_r0 = 1.0; c->morse_rc = 5.0; c->f_A = 0.0;
     c->k_bond = 100.0;
-    c->k_angle = 20.0;
+    c->k_angle = 5.0;
     c->seed = 20220528ull;
     return MD_OK;
 }

@@ -347,7 +347,7 @@ int ae_bwd(md_lstm *m, int B)
 {
     const int T = m->c.T, F = m->c.F, H1 = m->c.H1, H2 = m->c.H2;
     const int TB = T * B;
-    k_dense_wgrad<<<nb(F * (H1 + 1)), 128, 0, m->st>>>(m->Hs[3], m->dY, TB, H1, F, m->G + m->off_out[0],
+    k_dense_wgrad<<<nb(F * (H1 + 1), 128), 128, 0, m->st>>>(m->Hs[3], m->dY, TB, H1, F, m->G + m->off_out[0],
                                                       m->G + m->off_out[1]);
     k_dense_xgrad<<<nb((int64_t)TB * H1), 256, 0, m->st>>>(m->dY, TB, H1, F, m->P + m->off_out[0], nullptr, 0,
                                                          m->dA);
@@ -382,7 +382,7 @@ int fcn_bwd(md_lstm *m, int B)
     float *d = m->dact[0];
     for (int l = 3; l >= 0; --l) {
         const float *in = l == 0 ? m->Z : m->act[l];
-        k_dense_wgrad<<<nb(m->hd[l + 1] * (m->hd[l] + 1)), 128, 0, m->st>>>(in, d, B, m->hd[l], m->hd[l + 1],
+        k_dense_wgrad<<<nb(m->hd[l + 1] * (m->hd[l] + 1), 128), 128, 0, m->st>>>(in, d, B, m->hd[l], m->hd[l + 1],
                                                                            m->G + m->off_fcn[l][0],
                                                                            m->G + m->off_fcn[l][1]);
         LK(cudaGetLastError(), "fcn wgrad");

@@ -107,16 +107,20 @@ def test_corrupt_configuration_is_rejected(bad):
 
 
 def test_deterministic_steps_resume_bitwise_from_a_checkpoint():
-    """Deterministic step mode (MD_SCHED_DETERMINISTIC): a RESPA run of 12
-    outer steps equals, bit for bit, 5 steps, md_get_state, a fresh system
-    restored by md_set_state, and 7 more steps -- positions, velocities and
-    forces (the counter-based pair noise resumes at the restored time index,
-    and fixed-point force sums do not depend on the particle order the new
-    system's lists give)."""
+    """Deterministic step mode (MD_SCHED_DETERMINISTIC): a RESPA run of 5 and
+    then 7 outer steps on one system equals, bit for bit, 5 steps,
+    md_get_state, a fresh system restored by md_set_state, and 7 more steps
+    -- positions, velocities and forces (the counter-based pair noise resumes
+    at the restored time index, and fixed-point force sums do not depend on
+    the particle order the new system's lists give).  Both runs end a call
+    after step 5: a call closes its last step's fluid-level half kick
+    separately, where consecutive steps inside one call fuse it with the next
+    opening half kick."""
     import paper_2205_14121_gb300 as M
     s = small_shells(seed=53)
     a = make(s)
-    a.mts_step(12, mode=M.MD_MODE_RESPA, k_p=4, deterministic=True)
+    a.mts_step(5, mode=M.MD_MODE_RESPA, k_p=4, deterministic=True)
+    a.mts_step(7, mode=M.MD_MODE_RESPA, k_p=4, deterministic=True)
     xa, va, _ = a.read_particles()
     fa = a.read_forces(M.MD_LEVEL_ALL)
     b = make(s)

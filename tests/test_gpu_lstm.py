@@ -85,7 +85,11 @@ def test_lstm_gradients_match_oracle(setup, what):
         lo, go = OL.fcn_loss_and_grads(p, z, lk.astype(np.float64))
     assert loss == pytest.approx(lo, rel=1e-4)
     gb = blocks(g, cfg, Ctl)
-    ref = named(go) if what == "ae" else {f"fcn.{i}.{k}": go["fcn"][i][k] for i in range(4) for k in ("W", "b")}
+    if what == "ae":
+        ref = {f"{k}.{q}": go[k][q] for k in ("enc1", "enc2", "dec1", "dec2") for q in ("W_ih", "W_hh", "b_ih")}
+        ref.update({"out.W": go["out"]["W"], "out.b": go["out"]["b"]})
+    else:
+        ref = {f"fcn.{i}.{k}": go["fcn"][i][k] for i in range(4) for k in ("W", "b")}
     for name, r in ref.items():
         if name.endswith("b_hh"):
             continue                     # the same gradient as b_ih

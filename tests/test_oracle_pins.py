@@ -919,7 +919,7 @@ def test_shell_angles_bend_straight_through_vertices_and_rest_at_theta0():
 @pytest.mark.slow
 def test_nve_energy_of_a_shell_with_bonds_and_angles_is_second_order():
     """CGMD in NVE: one bonded 200-particle shell with the Eq. 2 angle term on
-    its bending triplets (k = 20, rest angles as reference), velocity-Verlet
+    its bending triplets (k = 5, rest angles as reference), velocity-Verlet
     from Maxwell velocities at kT = 1 over 5 time units.  The printed form
     has a cone point at theta = pi, which the nearly straight triplets cross
     under thermal bending (the force direction turns over there), so the
@@ -929,7 +929,7 @@ def test_nve_energy_of_a_shell_with_bonds_and_angles_is_second_order():
     s = synth.platelet_system((30.0, 30.0, 30.0), 0, 1, 200, synth.scaled_radii(200), seed=11,
                               centers=[(15.0, 15.0, 15.0)])
     p = O.system_params(s, m_rc=2.0)
-    assert p.n_angles == len(s.angles) > 400 and p.k_a == 20.0
+    assert p.n_angles == len(s.angles) > 400 and p.k_a == 5.0
 
     def energy(x, v):
         _, acc = O.forces_brute(p, x, v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, level_mask=O.LVL_PLT)
