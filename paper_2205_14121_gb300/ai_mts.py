@@ -18,7 +18,7 @@ label is how long that label stays unchanged along the trajectory, clipped to
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 
 import numpy as np
 
@@ -300,18 +300,45 @@ def train(windows, classes, holds, epochs_ae=40, epochs_heads=80, batch=128, lr_
 
 
 def load_controller(path, batch=256):
-    """Controller with the parameters and normalisation saved by `save`."""
+    """Controller with the parameters, normalisation and trust bound saved by `save`."""
     d = np.load(path)
     ctl = Controller(default_config(batch_max=batch))
     ctl.set_params(d["params"])
     ctl.set_norm(d["mean"], d["std"])
     strain = float(d["strain_p99"]) if "strain_p99" in d.files else TrustBound.strain_max
-    return ctl, TrustBound(rec_max=float(d["rec_p99"]), strain_max=strain)
+    p_min = float(d["p_min"]) if "p_min" in d.files else TrustBound.p_min
+    return ctl, TrustBound(rec_max=float(d["rec_p99"]), strain_max=strain, p_min=p_min)
 
 
 def save(path, art):
     np.savez(path, params=art["params"], mean=art["mean"], std=art["std"], rec_p99=art["rec_p99"],
-             strain_p99=art["strain_p99"])
+             strain_p99=art["strain_p99"], p_min=art.get("p_min", TrustBound.p_min))
+
+
+def gains(c, fb):
+    """A policy's gain over another: strictly better on one of (violations,
+    mean ratio) and no worse on the other."""
+    return ((c["violations"] <= fb["violations"] and c["mean_k"] < fb["mean_k"]) or
+            (c["violations"] < fb["violations"] and c["mean_k"] <= fb["mean_k"]))
+
+
+P_MIN_GRID = (0.4, 0.45, 0.5, 0.55, 0.6, 0.65, 0.7, 0.8)
+
+
+def select_trust(ctl, trust, windows, err_s, err_v, grid=P_MIN_GRID):
+    """The top-probability bound of the trust test chosen on training windows:
+    among the bounds whose policy gains over fixed-k at the fallback ratio,
+    the one with the fewest violations (then the lowest mean ratio); the
+    given bound when none gains.  Returns (trust, the evaluations per bound)."""
+    best, table = None, {}
+    for p in grid:
+        t = replace(trust, p_min=float(p))
+        r = evaluate(ctl, windows, err_s, err_v, t)
+        c, fb = r["controller"], r[f"fixed_k{t.fallback_k}"]
+        table[float(p)] = dict(c, gain=gains(c, fb))
+        if gains(c, fb) and (best is None or (c["violations"], c["mean_k"]) < best[0]):
+            best = ((c["violations"], c["mean_k"]), t)
+    return (best[1] if best else trust), table
 
 
 def evaluate(ctl, windows, err_s, err_v, trust, batch=128):

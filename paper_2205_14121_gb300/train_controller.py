@@ -34,12 +34,16 @@ def main(argv=None):
     ap.add_argument("--epochs-ae", type=int, default=40)
     ap.add_argument("--epochs-heads", type=int, default=80)
     ap.add_argument("--dataset", default=None, help="save / reuse the labelled windows here (.npz)")
+    ap.add_argument("--select-only", action="store_true",
+                    help="keep the trained parameters in --out; choose the trust bound again on --dataset")
     args = ap.parse_args(argv)
 
     from paper_2205_14121_gb300 import ai_mts as A
     from paper_2205_14121_gb300 import build as Bld
     Bld.build()
 
+    if args.select_only:
+        return reselect(args, A)
     t0 = time.time()
     seeds_train = list(range(1000, 1000 + args.train_seeds))
     seeds_test = list(range(5000, 5000 + args.test_seeds))
@@ -71,6 +75,8 @@ def main(argv=None):
     ctl, art = A.train(w_tr, c_tr, h_tr, epochs_ae=args.epochs_ae, epochs_heads=args.epochs_heads, progress=prog)
     t_train = time.time() - t0 - t_data
     trust = A.TrustBound(rec_max=float(art["rec_p99"]), strain_max=float(art["strain_p99"]))
+    trust, p_table = A.select_trust(ctl, trust, w_tr, es_tr, ev_tr)
+    art["p_min"] = trust.p_min
     ev_train = A.evaluate(ctl, w_tr, es_tr, ev_tr, trust)
     ev_test = A.evaluate(ctl, w_te, es_te, ev_te, trust)
     pred_te = np.concatenate([ctl.predict(w_te[b:b + 128])["cls"] for b in range(0, len(c_te), 128)])
@@ -87,12 +93,32 @@ def main(argv=None):
                    test_class_accuracy=float(np.mean(pred_te == c_te)),
                    eval_train=ev_train, eval_test=ev_test, lstm_variant_test=lstm_test,
                    lstm_loss_ae=lart["history"]["ae"][-1], lstm_loss_fcn=lart["history"]["fcn"][-1],
+                   p_min=trust.p_min, p_min_table_train=p_table,
                    rec_p99=float(art["rec_p99"]),
                    strain_p99=float(art["strain_p99"]),
                    loss_ae=art["history"]["ae"][-1], loss_heads=art["history"]["heads"][-1],
                    seconds_data=t_data, seconds_train=t_train,
                    horizon=args.horizon, windows_per_trajectory=args.windows, n_shell=args.n_shell, k_m=args.k_m)
-    with open(os.path.splitext(args.out)[0] + ".json", "w") as f:
+    with open(os.path.splitext(args.out)[0] + "_training.json", "w") as f:
+        json.dump(summary, f, indent=1)
+    print(json.dumps(summary), flush=True)
+
+
+def reselect(args, A):
+    """Choose the trust bound of a trained controller again (its parameters
+    unchanged) and refresh the evaluations of its summary."""
+    d = np.load(args.dataset)
+    ctl, trust = A.load_controller(args.out)
+    trust, p_table = A.select_trust(ctl, trust, d["train_w"], d["train_es"], d["train_ev"])
+    saved = dict(np.load(args.out))
+    saved["p_min"] = trust.p_min
+    A.save(args.out, saved)
+    js = os.path.splitext(args.out)[0] + "_training.json"
+    summary = json.load(open(js)) if os.path.exists(js) else {}
+    summary.update(p_min=trust.p_min, p_min_table_train=p_table,
+                   eval_train=A.evaluate(ctl, d["train_w"], d["train_es"], d["train_ev"], trust),
+                   eval_test=A.evaluate(ctl, d["test_w"], d["test_es"], d["test_ev"], trust))
+    with open(js, "w") as f:
         json.dump(summary, f, indent=1)
     print(json.dumps(summary), flush=True)
 
