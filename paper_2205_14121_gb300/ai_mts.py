@@ -325,19 +325,31 @@ def gains(c, fb):
 P_MIN_GRID = (0.4, 0.45, 0.5, 0.55, 0.6, 0.65, 0.7, 0.8)
 
 
+def gain_margin(c, fb):
+    """The larger of the policy's two ratios to the other's (violations, mean
+    ratio): below 1 on both axes means a gain on both, and the smaller the
+    value, the wider the gain on the weaker axis."""
+    if fb["violations"] > 0:
+        rv = c["violations"] / fb["violations"]
+    else:
+        rv = 0.0 if c["violations"] == 0 else math.inf
+    return max(rv, c["mean_k"] / fb["mean_k"])
+
+
 def select_trust(ctl, trust, windows, err_s, err_v, grid=P_MIN_GRID):
     """The top-probability bound of the trust test chosen on training windows:
     among the bounds whose policy gains over fixed-k at the fallback ratio,
-    the one with the fewest violations (then the lowest mean ratio); the
-    given bound when none gains.  Returns (trust, the evaluations per bound)."""
+    the one with the widest gain on its weaker axis (smallest gain_margin);
+    the given bound when none gains.  Returns (trust, evaluations per bound)."""
     best, table = None, {}
     for p in grid:
         t = replace(trust, p_min=float(p))
         r = evaluate(ctl, windows, err_s, err_v, t)
         c, fb = r["controller"], r[f"fixed_k{t.fallback_k}"]
-        table[float(p)] = dict(c, gain=gains(c, fb))
-        if gains(c, fb) and (best is None or (c["violations"], c["mean_k"]) < best[0]):
-            best = ((c["violations"], c["mean_k"]), t)
+        m = gain_margin(c, fb)
+        table[float(p)] = dict(c, gain=gains(c, fb), margin=m)
+        if gains(c, fb) and (best is None or m < best[0]):
+            best = (m, t)
     return (best[1] if best else trust), table
 
 
