@@ -8,8 +8,8 @@ coarse-grained particles (two wall-attached aggregates of 90 on opposite
 walls at the same x, 70 in the flow) and plasma at rho = 3 around and inside
 them.  The system is first relaxed from its synthetic start and a full
 feature window recorded, untimed; the timed arm is AI-MTS: outer steps of
-dt_f = 0.01 (one reduced time unit = 166.4 ns, so 1.664 ns per step), one
-interface substep, per-platelet step ratios from the trained controller
+dt_f = 0.01 (one reduced time unit = 166.4 ns, so 1.664 ns per step), two
+interface substeps, per-platelet step ratios from the trained controller
 (decided on the device).  Beside it, from the same relaxed state, fine-step
 STS (velocity-Verlet with dt = 0.001 for every particle, the reference of
 Sec. 4.1) and fixed-k RESPA (k = 10).
@@ -41,6 +41,8 @@ NS_PER_TAU = 166.4          # 1 tau = 166.4 ns (dt_f = 0.01 tau = 1.664 ns)
 METRIC = "simulated ns/day & particle-steps/s, AI-MTS vs fine-step STS on 1 GB300"
 FALLBACK_HBM_GBS = 6800.0
 CONTROLLER = os.path.join(ROOT, "paper_2205_14121_gb300", "data", "controller.npz")
+K_M = 2                     # interface substeps per fluid step (Table 1), the ratio the controller was trained at
+PAPER_LJ_RC = 0.8 * 2.0 ** (1.0 / 6.0)
 
 
 def parse(argv=None):
@@ -50,7 +52,7 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=150)
     ap.add_argument("--impl", default="msm", choices=["msm", "reference"])
     ap.add_argument("--workload", default="paper", choices=["paper", "channel", "dpd1m"])
-    ap.add_argument("--relax", type=int, default=150,
+    ap.add_argument("--relax", type=int, default=400,
                     help="untimed outer steps that relax the synthetic start before the feature window")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the fine-STS and fixed-k arms")
@@ -71,17 +73,29 @@ def workload(name, seed):
             desc="dpd-only throughput: 1,000,000 plasma particles, rho=3, 69.336^3 box, walls in y, g=0.02, "
                  "STS velocity-Verlet dt=0.01, skin 0.3")
     if name == "paper":
+        from paper_2205_14121_gb300._binding import MD_CFG_MORSE_STANDARD
+        # Inter-platelet terms of the 40,000-particle shells (23 particles
+        # per unit area, spacing 0.21 against sigma = 0.8): LJ cut at its
+        # minimum, 2^(1/6) sigma (excluded volume only; with the 2.5 sigma
+        # cut-off the summed attraction of two such membranes zips the
+        # aggregates' shells together and their LJ rows grow past 800), and
+        # the receptor Morse term in its standard form with range alpha = 2
+        # (with the printed form's range alpha / (2 r0) = 1 the aggregates'
+        # shells overlap within about 100 outer steps).
         return synth.config_paper_scale(seed=seed), dict(
-            dt=0.01, skin=0.3, skin_plt=0.5,
+            dt=0.01, skin=0.3, skin_plt=0.5, flags=MD_CFG_MORSE_STANDARD, params=dict(lj_rc=PAPER_LJ_RC),
             desc="paper-scale clot channel: ~101M particles, plasma at rho=3 in 1100x300x93, y walls, Poiseuille g "
-                 "for wall shear rate 0.05, 250 platelets x 40,000 CG particles (5% receptors; two wall-attached "
-                 "aggregates of 90 at the same x on opposite walls, 70 in the flow); AI-MTS dt_f=0.01, k_m=1, "
-                 "per-platelet k from the controller vs fine-step STS dt=0.001; skin 0.3, platelet skin 0.5")
+                 "for wall shear rate 0.05, 250 platelets x 40,000 CG particles (5% receptors; LJ eps=1, "
+                 "sigma=0.8 cut at 2^(1/6) sigma; standard-form Morse D=2, alpha=2, r0=1; two wall-attached "
+                 "aggregates of 90 at the same x on opposite walls, 70 in the flow); AI-MTS dt_f=0.01, "
+                 f"k_m={K_M}, per-platelet k from the controller vs fine-step STS dt=0.001; skin 0.3, "
+                 "platelet skin 0.5")
     if name == "channel":
         return synth.config_channel_platelets(seed=seed), dict(
             dt=0.01, skin=0.3, skin_plt=0.5,
             desc="platelet channel: 8,040,000 plasma at rho=3 in 400x100x67, y walls, Poiseuille g for wall "
-                 "shear rate 0.05, 16 platelets x 10,000 CG particles (5% receptors); AI-MTS dt_f=0.01, k_m=1, "
+                 "shear rate 0.05, 16 platelets x 10,000 CG particles (5% receptors); AI-MTS dt_f=0.01, "
+                 f"k_m={K_M}, "
                  "per-platelet k from the controller vs fine-step STS dt=0.001; skin 0.3, platelet skin 0.5")
     raise ValueError(name)
 
@@ -130,7 +144,7 @@ class OracleSample:
             s = synth.platelet_system((20.0, 10.0, 8.0), 4800, 1, 600, synth.scaled_radii(600), walls=True,
                                       body_force=g, seed=seed, centers=[(10.0, 5.0, 4.0)])
             self.what = "AI-MTS outer steps (k = 10)"
-            self.kw = dict(X0=s.X0, bonds=s.bonds, r0=s.r0, dt_f=0.01, k_m=1)
+            self.kw = dict(X0=s.X0, bonds=s.bonds, r0=s.r0, dt_f=0.01, k_m=K_M)
             self.fn = O.run_ai_respa
             self.extra = ([10],)
         self.s = s
@@ -258,11 +272,11 @@ def run_reference(args, rank, world):
 FINE_SKIN_PLT = 0.0      # fine-step STS: the plasma skin for the platelets too
 
 
-def make_system(M, s, dt, skin, seed, skin_plt=0.0, flags=0):
+def make_system(M, s, dt, skin, seed, skin_plt=0.0, flags=0, params=None):
     return M.System(s.box, s.x, s.v, s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, angles=s.angles,
                     theta0=s.theta0, walls=s.walls, wall=s.wall,
                     shear_rate=s.shear_rate, body_force=s.body_force, dt=dt, skin=skin, seed=seed,
-                    skin_plt=skin_plt, flags=flags)
+                    skin_plt=skin_plt, flags=flags, **(params or {}))
 
 
 def timed(g, step, n, barrier):
@@ -362,7 +376,7 @@ def main():
     n = s.n
     progress(f"generated {args.workload}: {n} particles in {t_gen:.1f} s")
     platelets = args.workload != "dpd1m"
-    g = make_system(M, s, wl["dt"], wl["skin"], seed, wl.get("skin_plt", 0.0))
+    g = make_system(M, s, wl["dt"], wl["skin"], seed, wl.get("skin_plt", 0.0), wl.get("flags", 0), wl.get("params"))
 
     mode_info = {"generation_s": t_gen}
     decisions = []
@@ -378,17 +392,17 @@ def main():
         def step(k):
             if ctl is None:
                 g.set_platelet_levels(np.full(g.cfg.n_platelets, trust.fallback_k, np.int32))
-                g.mts_step(k, mode=M.MD_MODE_AI, k_m=1, direct=args.direct, record=True)
+                g.mts_step(k, mode=M.MD_MODE_AI, k_m=K_M, direct=args.direct, record=True)
             else:
-                A.run_ai_mts(g, ctl, k, k_m=1, trust=trust, log=decisions)
+                A.run_ai_mts(g, ctl, k, k_m=K_M, trust=trust, log=decisions)
 
         # an equilibrated start independent of --warmup: relax the synthetic
         # state at the fallback ratio, then record one full feature window
         g.set_platelet_levels(np.full(g.cfg.n_platelets, trust.fallback_k, np.int32))
         t_rel = time.perf_counter()
-        g.mts_step(args.relax, mode=M.MD_MODE_AI, k_m=1, direct=args.direct)
+        g.mts_step(args.relax, mode=M.MD_MODE_AI, k_m=K_M, direct=args.direct)
         if ctl is not None:
-            A.run_ai_mts(g, ctl, 128, k_m=1, trust=trust)        # fills the window, no decision yet
+            A.run_ai_mts(g, ctl, 128, k_m=K_M, trust=trust)        # fills the window, no decision yet
         torch.cuda.synchronize()
         mode_info["relax"] = {"steps": args.relax + (128 if ctl is not None else 0),
                               "s": time.perf_counter() - t_rel, "temperature": g.observables()["temperature"]}
@@ -487,7 +501,7 @@ def main():
             g.set_xv(xh, vh, step0=k)
             if platelets:
                 g.set_platelet_levels(levels)
-                g.mts_step(1, mode=M.MD_MODE_AI, k_m=1)
+                g.mts_step(1, mode=M.MD_MODE_AI, k_m=K_M)
             else:
                 g.mts_step(1)
             return g.observables()
@@ -524,14 +538,15 @@ def main():
         # fine-step STS rebuilds rarely and prefers the shorter lists of skin
         # 0.2; the dt = 0.01 arms' platelet particles, which tripped most
         # rebuilds, get a skin of 0.5)
-        respa = lambda h, k: h.mts_step(k, mode=M.MD_MODE_RESPA, k_m=1, k_p=10, direct=args.direct)
-        arms = [("fine_sts", 0.001, 0.2, FINE_SKIN_PLT, lambda h, k: h.mts_step(k, direct=args.direct), 0),
-                ("respa_k10", 0.01, wl["skin"], wl["skin_plt"], respa, 0)]
+        respa = lambda h, k: h.mts_step(k, mode=M.MD_MODE_RESPA, k_m=K_M, k_p=10, direct=args.direct)
+        fl = wl.get("flags", 0)
+        arms = [("fine_sts", 0.001, 0.2, FINE_SKIN_PLT, lambda h, k: h.mts_step(k, direct=args.direct), fl),
+                ("respa_k10", 0.01, wl["skin"], wl["skin_plt"], respa, fl)]
         rel = type(s)(box=s.box, x=x_rel, v=v_rel, tag=s.tag, X0=s.X0, bonds=s.bonds, r0=s.r0, angles=s.angles,
                       theta0=s.theta0, walls=s.walls,
                       wall=s.wall, shear_rate=s.shear_rate, body_force=s.body_force, n_platelets=s.n_platelets)
         for name, dt, skin, skin_plt, fn, flags in arms:
-            h = make_system(M, rel, dt, skin, seed, skin_plt, flags)
+            h = make_system(M, rel, dt, skin, seed, skin_plt, flags, wl.get("params"))
             fn(h, max(args.warmup, 3))
             t_ms = timed(h, lambda k: fn(h, k), args.steps, barrier)
             u2, s2 = whole_job_rate(n * args.steps, t_ms / 1e3, world, device="cuda")
