@@ -126,6 +126,40 @@ def test_plasma_list_bit_exact_with_walls(wall_sys):
     assert gs == set(map(tuple, ref.tolist()))
 
 
+@pytest.mark.parametrize("box,walls", [((7.9, 9.1, 8.3), False), ((10.4, 6.0, 9.75), True)])
+def test_plasma_list_bit_exact_uneven_cells(box, walls):
+    """The plasma list without Lees-Edwards images: a fully periodic box with
+    uneven cell counts per axis, and a walled box whose cells span the list
+    reach with little to spare."""
+    s = synth.plasma_box(box=box, walls=walls, body_force=0.02 if walls else 0.0, seed=14)
+    g = make_gpu(s, step0=2)
+    g.neighbor_build(force=True)
+    got = g.neighbor_pairs(0)
+    _, _, x32 = g.read_particles()
+    ref = O.pairs_f32(x32, s.tag, np.array(s.box, np.float32), 0, np.float32(1.3 * 1.3), walls=walls)
+    gs = set(map(tuple, got.tolist()))
+    assert len(got) == len(gs)
+    assert gs == set(map(tuple, ref.tolist()))
+    assert len(gs) > 0
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_neighbor_sets_bit_exact_walls_platelets(plt_wall_sys, kind):
+    """Plasma and interface lists of the walled two-shell channel: platelet
+    particles have no plasma-list row and are no plasma-list partner."""
+    s = plt_wall_sys
+    g = make_gpu(s, step0=4)
+    g.neighbor_build(force=True)
+    got = g.neighbor_pairs(kind)
+    _, _, x32 = g.read_particles()
+    cut = [1.3, 1.3][kind]
+    ref = O.pairs_f32(x32, s.tag, np.array(s.box, np.float32), kind, np.float32(cut * cut), walls=True)
+    gs = set(map(tuple, got.tolist()))
+    assert len(got) == len(gs)
+    assert gs == set(map(tuple, ref.tolist()))
+    assert len(gs) > 0
+
+
 def test_forces_match_oracle_all_levels(plt_sys):
     s = plt_sys
     import paper_2205_14121_gb300 as M
