@@ -394,7 +394,7 @@ def main():
                 g.set_platelet_levels(np.full(g.cfg.n_platelets, trust.fallback_k, np.int32))
                 g.mts_step(k, mode=M.MD_MODE_AI, k_m=K_M, direct=args.direct, record=True)
             else:
-                A.run_ai_mts(g, ctl, k, k_m=K_M, trust=trust, log=decisions)
+                A.run_ai_mts(g, ctl, k, k_m=K_M, trust=trust, log=decisions, direct=args.direct)
 
         # an equilibrated start independent of --warmup: relax the synthetic
         # state at the fallback ratio, then record one full feature window
@@ -402,7 +402,7 @@ def main():
         t_rel = time.perf_counter()
         g.mts_step(args.relax, mode=M.MD_MODE_AI, k_m=K_M, direct=args.direct)
         if ctl is not None:
-            A.run_ai_mts(g, ctl, 128, k_m=K_M, trust=trust)        # fills the window, no decision yet
+            A.run_ai_mts(g, ctl, 128, k_m=K_M, trust=trust, direct=args.direct)        # fills the window, no decision yet
         torch.cuda.synchronize()
         mode_info["relax"] = {"steps": args.relax + (128 if ctl is not None else 0),
                               "s": time.perf_counter() - t_rel, "temperature": g.observables()["temperature"]}

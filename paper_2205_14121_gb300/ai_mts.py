@@ -67,11 +67,12 @@ def decide(controller, windows, trust):
     return d["k"], d["hold"], d["unsure"]
 
 
-def run_ai_mts(system, controller, n_steps, k_m=1, trust=None, T=128, log=None):
+def run_ai_mts(system, controller, n_steps, k_m=1, trust=None, T=128, log=None, direct=False):
     """Advance n_steps outer steps under AI-MTS: the measurements of the T
     steps before each decision go to the feature ring from inside the step
     graph; with a full window the controller sets each platelet's ratio and
-    is asked again after the shortest predicted hold."""
+    is asked again after the shortest predicted hold.  direct: launch every
+    kernel from the host instead of replaying the step graph."""
     trust = trust or TrustBound()
     P = system.cfg.n_platelets
     # the ratios and the count of consecutive records at the end of the ring
@@ -100,9 +101,9 @@ def run_ai_mts(system, controller, n_steps, k_m=1, trust=None, T=128, log=None):
         # only the T steps before the next decision need recording
         quiet = max(0, run - T)
         if quiet:
-            system.mts_step(quiet, mode=B.MD_MODE_AI, k_m=k_m)
+            system.mts_step(quiet, mode=B.MD_MODE_AI, k_m=k_m, direct=direct)
             fresh = 0
-        system.mts_step(run - quiet, mode=B.MD_MODE_AI, k_m=k_m, record=True)
+        system.mts_step(run - quiet, mode=B.MD_MODE_AI, k_m=k_m, record=True, direct=direct)
         fresh += run - quiet
         done += run
     state["fresh"] = fresh
