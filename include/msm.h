@@ -603,13 +603,11 @@ int md_philox(const uint32_t *ctr, const uint32_t key[2], int64_t n, uint32_t *o
  * instead of cudaMalloc'd scratch.  No cudaMalloc, cudaFree or allocating
  * library routine is called.
  *  - n > MD_PHILOX_STATIC_MAX returns MD_ETOOLARGE before any CUDA call.
- *  - The array's device address is looked up (cudaGetSymbolAddress) once per
- *    device, at the first call made with that device current; make that
- *    first call before any stream capture begins on the device.  The
- *    address is cached for the life of the process: a cudaDeviceReset (or
- *    any teardown of the device's primary context) unloads the module and
- *    voids it, so do not call this entry point on a device after resetting
- *    it.
+ *  - The array's device address is looked up (cudaGetSymbolAddress, which
+ *    does not allocate) in the current context on every call, so a context
+ *    rebuilt after a cudaDeviceReset is served like a new one.  The first
+ *    call on a device may load the library's module: make it before any
+ *    stream capture begins on that device.
  *  - The array keeps the last call's counters and outputs.  Nothing in it
  *    has to start at zero: a call copies its n counters in before the kernel
  *    reads them, and the kernel writes the n outputs before they are copied

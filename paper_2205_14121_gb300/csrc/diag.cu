@@ -3,7 +3,6 @@
 // cuRAND's generator for cross-checking.
 #include <curand_kernel.h>
 
-#include <mutex>
 
 #include "msm_internal.cuh"
 
@@ -73,12 +72,6 @@ void prof_end(md_system *s)
 // [MAX, 2 MAX).  Keeps the last call's contents; calls on one device share it.
 static __device__ __align__(256) uint4 philox_scratch[2 * MD_PHILOX_STATIC_MAX];
 
-namespace {
-constexpr int SCRATCH_DEVICES = 64;
-std::mutex scratch_mu;
-uint4 *scratch_addr[SCRATCH_DEVICES] = {};   // device address per device ordinal
-}  // namespace
-
 extern "C" {
 
 int md_profile_enable(md_system *s, int enable)
@@ -146,22 +139,12 @@ int md_philox_static(const uint32_t *ctr, const uint32_t key[2], int64_t n, uint
     if (use_library)
         for (int64_t k = 0; k < n; ++k)
             if (ctr[4 * k + 1] >= (1u << 30)) return MD_EINVAL;  // 4*counter must fit the 64-bit offset
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    // the array's address in the current context, looked up on every call
+    // (no allocation; a context rebuilt after a device reset has its own)
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, philox_scratch);
     if (e != cudaSuccess) return MD_ECUDA;
-    if (dev < 0 || dev >= SCRATCH_DEVICES) return MD_EINVAL;
-    uint4 *base = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(scratch_mu);
-        if (!scratch_addr[dev]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, philox_scratch);
-            if (e != cudaSuccess) return MD_ECUDA;
-            scratch_addr[dev] = (uint4 *)p;
-        }
-        base = scratch_addr[dev];
-    }
-    uint4 *d_ctr = base, *d_out = base + MD_PHILOX_STATIC_MAX;
+    uint4 *d_ctr = (uint4 *)p, *d_out = (uint4 *)p + MD_PHILOX_STATIC_MAX;
     e = cudaMemcpy(d_ctr, ctr, sizeof(uint4) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         const unsigned blocks = (unsigned)((n + 255) / 256);

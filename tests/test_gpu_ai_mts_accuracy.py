@@ -164,6 +164,9 @@ def test_ai_mts_matches_fine_step_sts():
     for key, gate in gates.items():
         assert 2.0 * noise[key] < gate, f"{key}: sampling spread {noise[key]:.4f} too large for the gate {gate}"
     r = res["ai_mts"]
+    # no worse than the method without the controller (fixed k = 10), beyond the spread
+    for key in gates:
+        assert r[f"{key}_err"] <= res["respa_k10"][f"{key}_err"] + 2.0 * noise[key], key
     assert r["profile_err"] <= gates["profile"]
     assert r["stress_err"] <= gates["stress"]
     assert r["T_err"] <= gates["T"]
