@@ -208,13 +208,16 @@ class Dataset:
                 cat(self.err_v))
 
 
-def generate(seeds, n_windows=8, warmup=50, horizon=50, k_m=1, k_record=10, T=128, n_shell=2000, progress=None):
+def generate(seeds, n_windows=8, warmup=50, horizon=50, k_m=1, k_record=10, T=128, n_shell=2000, progress=None,
+             system_kw=None):
     """Windows of per-platelet measurements under fixed-k RESPA (k_record),
-    each labelled from the continuations at its end."""
+    each labelled from the continuations at its end.  system_kw: further
+    System configuration (force-field fields and flags)."""
     data = Dataset()
     for seed in seeds:
         # platelets in contact: long LJ rows
-        sys = make_system(training_system(seed, n_shell=n_shell), seed=int(seed), caps={"lj": 4096})
+        sys = make_system(training_system(seed, n_shell=n_shell), seed=int(seed), caps={"lj": 4096},
+                          **(system_kw or {}))
         try:
             sys.mts_step(warmup, mode=B.MD_MODE_RESPA, k_m=k_m, k_p=k_record)
         except B.MdError as e:

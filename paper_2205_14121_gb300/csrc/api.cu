@@ -178,6 +178,9 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
         s.plt_off = cv.take<int32_t>(P + 1);
         s.plt_ids = cv.take<int32_t>(s.n_plt);
         s.bond_off = cv.take<int32_t>(P + 1);
+        if (s.na > 0) s.angle_off = cv.take<int32_t>(P + 1);
+        s.plt_cmask = cv.take<unsigned long long>(P);
+        s.plt_stride = cv.take<int32_t>(P);
         s.plt_contacts = cv.take<int32_t>(P);
         s.feat = cv.take<double>(12 * P);
         s.ring = cv.take<float>(P * (int64_t)s.ring_T * 12);
@@ -488,10 +491,10 @@ int enqueue_forces(md_system *s, unsigned levels)
 }
 
 int enqueue_kd(md_system *s, const float h[3], int kick_which, double dt, int drift_which, unsigned zero,
-               bool plt_rows)
+               bool plt_rows, int stride_q = -1)
 {
     prof_begin(s, MD_PROF_INTEG);
-    CK(launch_kick_drift(s, h, kick_which, dt, drift_which, zero, plt_rows), "kick-drift");
+    CK(launch_kick_drift(s, h, kick_which, dt, drift_which, zero, plt_rows, stride_q), "kick-drift");
     prof_end(s);
     return MD_OK;
 }
@@ -585,7 +588,7 @@ int enqueue_outer_step(md_system *s, int mode, int k_m, int k_p, bool first, cap
             for (int q = 0; q < K; ++q) {
                 RC(enqueue_time(s, dn, c_end, tc + (q + 1) * dts));
                 const float hq[3] = {0.f, 0.f, q == 0 ? 0.5f : 1.0f};
-                RC(enqueue_kd(s, hq, DRIFT_PLT, dts, DRIFT_PLT, MD_LEVEL_PLT, true));
+                RC(enqueue_kd(s, hq, DRIFT_PLT, dts, DRIFT_PLT, MD_LEVEL_PLT, true, q));
                 s->due_on = true;
                 s->due_q = q + 1;
                 s->due_dtm = dtm;
@@ -1074,7 +1077,8 @@ int md_set_angles(md_system *s, const int32_t *ijk, const double *theta0, int64_
     if (na == 0) return MD_OK;
     if (!ijk || !theta0) return set_error(s, MD_EINVAL, "md_set_angles: null argument");
     if ((int64_t)s->h_tag.size() != s->n) return set_error(s, MD_EINVAL, "md_set_angles: set particles first");
-    std::vector<float> t0((size_t)na);
+    const int P = s->cfg.n_platelets;
+    std::vector<int32_t> plt_of((size_t)na), off((size_t)P + 1, 0);
     for (int64_t q = 0; q < na; ++q) {
         int32_t pl = -1;
         for (int e = 0; e < 3; ++e) {
@@ -1088,10 +1092,23 @@ int md_set_angles(md_system *s, const int32_t *ijk, const double *theta0, int64_
         }
         if (!(theta0[q] >= 0.0 && theta0[q] <= 3.14159265358979323846))
             return set_error(s, MD_EINVAL, "md_set_angles: rest angle outside [0, pi]");
-        t0[(size_t)q] = (float)theta0[q];
+        plt_of[(size_t)q] = pl;
+        off[(size_t)pl + 1]++;
     }
-    CK(cudaMemcpyAsync(s->angle_id, ijk, sizeof(int32_t) * 3 * na, cudaMemcpyHostToDevice, s->stream), "angles");
+    for (int p = 0; p < P; ++p) off[(size_t)p + 1] += off[(size_t)p];
+    // stored grouped by platelet (the angle kernel is order-independent)
+    std::vector<int32_t> ids((size_t)(3 * na)), fill(off.begin(), off.end() - 1);
+    std::vector<float> t0((size_t)na);
+    for (int64_t q = 0; q < na; ++q) {
+        const int32_t r = fill[(size_t)plt_of[(size_t)q]]++;
+        for (int e = 0; e < 3; ++e) ids[(size_t)(3 * r + e)] = ijk[3 * q + e];
+        t0[(size_t)r] = (float)theta0[q];
+    }
+    CK(cudaMemcpyAsync(s->angle_id, ids.data(), sizeof(int32_t) * 3 * na, cudaMemcpyHostToDevice, s->stream),
+       "angles");
     CK(cudaMemcpyAsync(s->angle_t0, t0.data(), sizeof(float) * na, cudaMemcpyHostToDevice, s->stream), "theta0");
+    CK(cudaMemcpyAsync(s->angle_off, off.data(), sizeof(int32_t) * (P + 1), cudaMemcpyHostToDevice, s->stream),
+       "angle offsets");
     CK(cudaStreamSynchronize(s->stream), "set_angles sync");
     s->have_angles = true;
     s->lists_stale = true;   // the remap of the triplets happens in the rebuild
@@ -1118,6 +1135,10 @@ int md_set_platelet_levels(md_system *s, const int32_t *k)
     s->h_plt_k.assign(k, k + P);
     s->plt_K = (int)K;
     s->have_levels = true;
+    if (!s->lists_stale) {     // else the next build sets the strides
+        CK(launch_strides(s, nullptr), "drift strides");
+        CK(cudaStreamSynchronize(s->stream), "strides sync");
+    }
     return MD_OK;
 }
 

@@ -140,7 +140,7 @@ struct dpd_smem {
     float4 vi[DPD_WARPS][32];          // row velocities (w: tag)
     float4 fi[DPD_WARPS][32];          // row force sums
     float4 qa[DPD_WARPS][DPD_QCAP];    // queued pairs (a ring): dx, dy, dz, image v-shift
-    int4 qb[DPD_WARPS][DPD_QCAP];      // j, source row (lane), id_j, id_i
+    int2 qb[DPD_WARPS][DPD_QCAP];      // j | source row (lane) << 27, id_j (id_i: the row's xi.w)
 };
 
 // Eq. 1 for one pair, the particle with the lower id first (deterministic
@@ -178,9 +178,10 @@ __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int 
 {
     if (DET) {
         if (valid) {
-            const int4 b = sm.qb[warp][slot];
-            const int32_t i = a.row_idx ? a.row_idx[r0 + b.y] : (int32_t)(r0 + b.y);
-            dpd_pair_fixed<VIR, IF>(a, i, b.x, pq, w);
+            const int2 b = sm.qb[warp][slot];
+            const int rr = (int)((uint32_t)b.x >> MSM_STREAM_SHIFT);
+            const int32_t i = a.row_idx ? a.row_idx[r0 + rr] : (int32_t)(r0 + rr);
+            dpd_pair_fixed<VIR, IF>(a, i, b.x & MSM_STREAM_JMASK, pq, w);
         }
         return;
     }
@@ -188,10 +189,12 @@ __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int 
     int src = -1;
     if (valid) {
         const float4 q = sm.qa[warp][slot];
-        const int4 b = sm.qb[warp][slot];
-        src = b.y;
+        const int2 b = sm.qb[warp][slot];
+        const int32_t jq = b.x & MSM_STREAM_JMASK;
+        src = (int)((uint32_t)b.x >> MSM_STREAM_SHIFT);
+        const uint32_t id_iq = (uint32_t)__float_as_int(sm.xi[warp][src].w) & MSM_ID_MASK;
         const float4 vi = sm.vi[warp][src];
-        const float4 vj = a.v[b.x];
+        const float4 vj = a.v[jq];
         const float r2 = q.x * q.x + q.y * q.y + q.z * q.z;
         const bool wall = tag_of(vi) == MD_TAG_WALL || tag_of(vj) == MD_TAG_WALL;
         const float aij = wall ? a.a_wall : a.a_same;
@@ -199,11 +202,11 @@ __device__ __forceinline__ void dpd_batch(const pair_args &a, dpd_smem &sm, int 
         const float wr = 1.0f - r2 * inv_r * a.inv_rc;
         const float ex = q.x * inv_r, ey = q.y * inv_r, ez = q.z * inv_r;
         const float edv = ex * (vi.x - vj.x - q.w) + ey * (vi.y - vj.y) + ez * (vi.z - vj.z);
-        const float zeta = pair_zeta_pre<UNI ? 1 : 0>((uint32_t)b.w, (uint32_t)b.z, pq);
+        const float zeta = pair_zeta_pre<UNI ? 1 : 0>(id_iq, (uint32_t)b.y, pq);
         const float fc = dpd_conservative<IF>(a, aij, wr, r2, inv_r);
         const float fp = fc - a.gamma * wr * wr * edv + a.sig_isdt * wr * zeta;
         px = fp * ex; py = fp * ey; pz = fp * ez;
-        scatter(a.f, b.x, -px, -py, -pz);
+        scatter(a.f, jq, -px, -py, -pz);
         if (VIR) w.add(q.x, q.y, q.z, fc * inv_r);
     }
     // segmented sum over runs of equal src (entries are in row order): lane
@@ -311,7 +314,7 @@ __device__ __forceinline__ void dpd_rows(const pair_args &a, dpd_smem &sm)
         if (hit) {
             const int pos = (qh + qn + __popc(m & lt)) & (DPD_QCAP - 1);
             sm.qa[warp][pos] = make_float4(dx, dy, dz, vsh);
-            sm.qb[warp][pos] = make_int4(j_c, row_c, (int)id_of(xj_c), (int)id_i);
+            sm.qb[warp][pos] = make_int2(j_c | (row_c << MSM_STREAM_SHIFT), (int)id_of(xj_c));
         }
         qn += __popc(m);
         __syncwarp();
@@ -598,8 +601,18 @@ template <bool VIR>
 __global__ void __launch_bounds__(MSM_TPB) k_bonds(int64_t nb, const int32_t *__restrict__ ij,
                                                   const float *__restrict__ r0, float kb2, const float4 *__restrict__ x32,
                                                   float4 *f, md_geom geom, const md_dstate *ds, double *vir, md_due due,
-                                                  const int32_t *tag, unsigned long long *fdet)
+                                                  const int32_t *tag, unsigned long long *fdet,
+                                                  const int32_t *__restrict__ off, int P)
 {
+    if (due.plt_k) {     // AI-MTS substep: skip a block whose platelets are off this grid point
+        __shared__ int block_due;
+        if (threadIdx.x == 0) {
+            const int64_t t0 = (int64_t)blockIdx.x * blockDim.x;
+            block_due = group_due(due, off, P, t0, min(t0 + (int64_t)blockDim.x, nb) - 1);
+        }
+        __syncthreads();
+        if (!block_due) return;
+    }
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     vir6 w = {0, 0, 0, 0, 0, 0};
     // both ends belong to one platelet: the bond lives on that platelet's grid
@@ -637,8 +650,17 @@ __global__ void __launch_bounds__(MSM_TPB) k_angles(int64_t na, const int32_t *_
                                                    const float *__restrict__ t0, float k2,
                                                    const float4 *__restrict__ x32, float4 *f, md_geom geom,
                                                    const md_dstate *ds, double *vir, md_due due, const int32_t *tag,
-                                                   unsigned long long *fdet)
+                                                   unsigned long long *fdet, const int32_t *__restrict__ off, int P)
 {
+    if (due.plt_k) {     // AI-MTS substep: skip a block whose platelets are off this grid point
+        __shared__ int block_due;
+        if (threadIdx.x == 0) {
+            const int64_t t0 = (int64_t)blockIdx.x * blockDim.x;
+            block_due = group_due(due, off, P, t0, min(t0 + (int64_t)blockDim.x, na) - 1);
+        }
+        __syncthreads();
+        if (!block_due) return;
+    }
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     vir6 w = {0, 0, 0, 0, 0, 0};
     // the triplet lies on one platelet: it lives on that platelet's grid
@@ -868,22 +890,22 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
                 k_bonds<true><<<blocks_for(s->nb), MSM_TPB, 0, s->stream>>>(s->nb, s->bond_ij, s->bond_r0,
                                                                            (float)(2.0 * c.k_bond), s->x32, out[2],
                                                                            s->geom, s->ds, s->vir_acc, a.due, s->tag_s,
-                                                                           a.fdet);
+                                                                           a.fdet, s->bond_off, s->cfg.n_platelets);
             else
                 k_bonds<false><<<blocks_for(s->nb), MSM_TPB, 0, s->stream>>>(s->nb, s->bond_ij, s->bond_r0,
                                                                             (float)(2.0 * c.k_bond), s->x32, out[2],
                                                                             s->geom, s->ds, s->vir_acc, a.due, s->tag_s,
-                                                                           a.fdet);
+                                                                           a.fdet, s->bond_off, s->cfg.n_platelets);
         }
         if (s->na > 0) {
             if (virial)
                 k_angles<true><<<blocks_for(s->na), MSM_TPB, 0, s->stream>>>(
                     s->na, s->angle_ijk, s->angle_t0, (float)(2.0 * c.k_angle), s->x32, out[2], s->geom, s->ds,
-                    s->vir_acc, a.due, s->tag_s, a.fdet);
+                    s->vir_acc, a.due, s->tag_s, a.fdet, s->angle_off, s->cfg.n_platelets);
             else
                 k_angles<false><<<blocks_for(s->na), MSM_TPB, 0, s->stream>>>(
                     s->na, s->angle_ijk, s->angle_t0, (float)(2.0 * c.k_angle), s->x32, out[2], s->geom, s->ds,
-                    s->vir_acc, a.due, s->tag_s, a.fdet);
+                    s->vir_acc, a.due, s->tag_s, a.fdet, s->angle_off, s->cfg.n_platelets);
             MSM_COUNT(s, 1);
         }
         a.rows = s->n_plt;

@@ -42,6 +42,8 @@ struct kd_args {
     int32_t *fast_idx;     // plasma beyond skin/2 and within the skin: listed here
     uint32_t *fast_flag;
     int64_t fast_max;
+    const int32_t *stride; // AI-MTS substep q of the K grid: per-platelet drift strides (null: every substep)
+    int q;
 };
 
 __device__ __forceinline__ bool selected(int which, int32_t t)
@@ -96,6 +98,15 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
         if (fl.x == 0.0f && fl.y == 0.0f && fl.z == 0.0f) return;
     }
     const int32_t t = a.tag[k];
+    double dt = a.dt;
+    if (a.stride && t >= 0) {
+        // AI-MTS: every term that involves this platelet is due at multiples
+        // of its stride only, so no force acts on it in between: it is
+        // kicked and moved there, by stride substeps at once
+        const int st = a.stride[t & ~MD_RECEPTOR_BIT];
+        if (a.q % st != 0) return;
+        dt *= st;
+    }
     const bool kick = selected(a.kick_which, t);
     const bool drift = selected(a.drift_which, t);
     unsigned zero_seen = 0u;   // levels read as exactly zero: no need to clear them
@@ -119,9 +130,9 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
             // the wrap decisions are taken on the rounded FP32 copies (a
             // double >= L always rounds to a float >= (float)L) and the FP64
             // arithmetic is redone only for the few particles that wrap.
-            double x = fma(a.dt, (double)vv.x, a.xs[k]);
-            double y = fma(a.dt, (double)vv.y, a.ys[k]);
-            double z = fma(a.dt, (double)vv.z, a.zs[k]);
+            double x = fma(dt, (double)vv.x, a.xs[k]);
+            double y = fma(dt, (double)vv.y, a.ys[k]);
+            double z = fma(dt, (double)vv.z, a.zs[k]);
             const double Lx = a.L[0], Ly = a.L[1], Lz = a.L[2];
             float xf = (float)x, yf = (float)y, zf = (float)z;
             if (a.geom.walls) {
@@ -326,6 +337,8 @@ kd_args base_args(md_system *s)
     a.fast_idx = s->fast_idx;
     a.fast_flag = s->fast_flag;
     a.fast_max = s->fast_max;
+    a.stride = nullptr;
+    a.q = 0;
     return a;
 }
 
@@ -335,9 +348,13 @@ kd_args base_args(md_system *s)
 // drift_which subset + zeroing of zero_levels.  plt_rows: iterate only over
 // the platelet particles (the subset rows) instead of every particle.
 cudaError_t launch_kick_drift(md_system *s, const float h[3], int kick_which, double dt, int drift_which,
-                              unsigned zero_levels, bool plt_rows)
+                              unsigned zero_levels, bool plt_rows, int stride_q)
 {
     kd_args a = base_args(s);
+    if (stride_q >= 0 && s->have_levels && s->plt_stride) {
+        a.stride = s->plt_stride;
+        a.q = stride_q;
+    }
     for (int l = 0; l < 3; ++l) a.h[l] = h[l];
     a.kick_which = kick_which;
     a.drift_which = drift_which;

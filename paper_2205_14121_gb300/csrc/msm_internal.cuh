@@ -111,6 +111,11 @@ struct md_system {
     int64_t na = 0;
     int32_t *angle_id = nullptr, *angle_ijk = nullptr;
     float *angle_t0 = nullptr;
+    int32_t *angle_off = nullptr;   // triplets grouped by platelet: [angle_off[p], angle_off[p+1])
+    // AI-MTS: step ratios (bit k - 1) of the platelets each platelet has LJ
+    // or receptor pairs with, and its drift stride on the K-substep grid
+    unsigned long long *plt_cmask = nullptr;
+    int32_t *plt_stride = nullptr;
     bool have_angles = false;
 
     // per-platelet measurements (K8)
@@ -507,6 +512,26 @@ struct md_due {
     float dtm;
 };
 
+// Whether the terms [t0, t1] of an array grouped by platelet (platelet p's
+// terms at [off[p], off[p+1]), P platelets) hold one due at this point: a
+// block whose terms are all off the grid point skips its loads.
+__device__ __forceinline__ bool group_due(const md_due &d, const int32_t *off, int P, int64_t t0, int64_t t1)
+{
+    auto plt_of = [&](int64_t t) {      // the last p with off[p] <= t
+        int lo = 0, hi = P - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    const int p1 = plt_of(t1);
+    for (int p = plt_of(t0); p <= p1; ++p)
+        if (off[p + 1] > off[p] && (d.qe % (d.K / d.plt_k[p])) == 0) return true;
+    return false;
+}
+
 __device__ __forceinline__ float term_scale(const md_due &d, int32_t ti, int32_t tj)
 {
     if (!d.plt_k) return 1.0f;
@@ -525,6 +550,9 @@ cudaError_t launch_scan(md_system *s, const int32_t *in, int32_t *out, int64_t c
                         const int32_t *gate);
 // neighbor.cu
 cudaError_t launch_build_lists(md_system *s, const int32_t *gate);
+// AI-MTS drift strides from the current LJ / receptor lists and step ratios
+// (run after every build and every change of the ratios)
+cudaError_t launch_strides(md_system *s, const int32_t *gate);
 // forces.cu
 // with_fast: also the fast-particle pass of the DPD levels (launch_fast_pairs);
 // fdet: deterministic mode, every pair term added to these 64-bit fixed-point
@@ -537,8 +565,10 @@ cudaError_t launch_fast_pairs(md_system *s, unsigned level_mask, float4 *const o
 // a level's fixed-point sums to its FP32 buffer
 cudaError_t launch_fixed_to_f4(md_system *s, const unsigned long long *q, float4 *f);
 // integrate.cu
+// stride_q >= 0: AI-MTS substep stride_q of the K grid, platelet particles
+// kicked and drifted by their platelet's stride (launch_strides)
 cudaError_t launch_kick_drift(md_system *s, const float h[3], int kick_which, double dt, int drift_which,
-                              unsigned zero_levels, bool plt_rows);
+                              unsigned zero_levels, bool plt_rows, int stride_q = -1);
 cudaError_t launch_set_time(md_system *s, int64_t n, int32_t c, double t);
 cudaError_t launch_outer_begin(md_system *s, cudaGraphConditionalHandle loop, bool use_loop);
 cudaError_t launch_time_rel(md_system *s, int dn, int c, double t_off);

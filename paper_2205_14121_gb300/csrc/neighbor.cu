@@ -177,6 +177,64 @@ done:
     }
 }
 
+// AI-MTS drift strides.  cmask[p] collects the step ratios (bit k - 1) of
+// the platelets that share an LJ or receptor list pair with p -- a superset
+// of the pairs that can act before the next build -- and stride[p] = K /
+// lcm(k_p, those ratios): every term that involves p (its own at multiples of
+// K / k_p, a pair with q at multiples of K / max(k_p, k_q)) is due at
+// multiples of stride[p] only.
+__global__ void __launch_bounds__(256) k_zero_u64(unsigned long long *p, int n, const int32_t *gate)
+{
+    if (gate_closed(gate)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 0ull;
+}
+
+__global__ void __launch_bounds__(MSM_TPB) k_contact_levels(int64_t rows, const int32_t *__restrict__ row_idx,
+                                                            const int32_t *__restrict__ nl,
+                                                            const int32_t *__restrict__ nc, int cap,
+                                                            const int32_t *__restrict__ tag,
+                                                            const int32_t *__restrict__ plt_k,
+                                                            unsigned long long *cmask, const int32_t *gate)
+{
+    if (gate_closed(gate)) return;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int c = min(nc[r], cap);
+    if (c <= 0) return;
+    const int32_t p = tag[row_idx[r]] & ~MD_RECEPTOR_BIT;
+    const unsigned long long bit_p = 1ull << (plt_k[p] - 1);
+    unsigned long long mine = 0ull;
+    int32_t last = -1;
+    for (int e = 0; e < c; ++e) {
+        const int32_t q = tag[nl[r * (int64_t)cap + e]] & ~MD_RECEPTOR_BIT;
+        if (q == p) continue;
+        mine |= 1ull << (plt_k[q] - 1);
+        if (q != last) {           // partners of one platelet tend to come in runs
+            atomicOr(&cmask[q], bit_p);
+            last = q;
+        }
+    }
+    if (mine) atomicOr(&cmask[p], mine);
+}
+
+__global__ void __launch_bounds__(256) k_strides(int P, int K, const int32_t *__restrict__ plt_k,
+                                                 const unsigned long long *__restrict__ cmask, int32_t *stride,
+                                                 const int32_t *gate)
+{
+    if (gate_closed(gate)) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    int L = plt_k[p];
+    for (unsigned long long m = cmask[p]; m; m &= m - 1) {
+        const int k = __ffsll((long long)m);     // the ratio of bit k - 1
+        int a = L, b = k;
+        while (b) { const int t = a % b; a = b; b = t; }
+        L = L / a * k;
+    }
+    stride[p] = K / L;      // every ratio divides K, so L does
+}
+
 // Bounding sphere of every platelet at the build, over blocks (p, chunk):
 // pass 1 sums the member offsets from the first member (minimum image) into
 // bound[p].xyz, pass 2 the largest squared distance from the centre of mass
@@ -384,6 +442,31 @@ cudaError_t launch_build_lists(md_system *s, const int32_t *gate)
             k_build<MD_LIST_MORSE><<<blocks_for(a.rows), MSM_TPB, 0, s->stream>>>(a, gate);
         }
     }
+    if (s->n_plt > 0 && s->have_levels) {
+        cudaError_t e = launch_strides(s, gate);
+        if (e != cudaSuccess) return e;
+    }
     MSM_COUNT(s, 1 + (s->n_plt > 0 ? 2 + (s->n_rec > 0 ? 1 : 0) + (s->cfg.lj_excl > 1e20 ? 4 + (s->n_rec > 0 ? 1 : 0) : 0) : 0));
     return cudaGetLastError();
 }
+
+cudaError_t launch_strides(md_system *s, const int32_t *gate)
+{
+    const int P = s->cfg.n_platelets;
+    if (s->n_plt <= 0 || P <= 0 || !s->plt_stride) return cudaSuccess;
+    k_zero_u64<<<(P + 255) / 256, 256, 0, s->stream>>>(s->plt_cmask, P, gate);
+    k_contact_levels<<<blocks_for(s->n_plt), MSM_TPB, 0, s->stream>>>(
+        s->n_plt, s->plt_sorted, s->nl[MD_LIST_LJ], s->nc[MD_LIST_LJ], s->cap[MD_LIST_LJ], s->tag_s, s->plt_k,
+        s->plt_cmask, gate);
+    int n = 3;
+    if (s->n_rec > 0) {
+        k_contact_levels<<<blocks_for(s->n_rec), MSM_TPB, 0, s->stream>>>(
+            s->n_rec, s->rec_sorted, s->nl[MD_LIST_MORSE], s->nc[MD_LIST_MORSE], s->cap[MD_LIST_MORSE], s->tag_s,
+            s->plt_k, s->plt_cmask, gate);
+        ++n;
+    }
+    k_strides<<<(P + 255) / 256, 256, 0, s->stream>>>(P, s->plt_K, s->plt_k, s->plt_cmask, s->plt_stride, gate);
+    MSM_COUNT(s, n);
+    return cudaGetLastError();
+}
+

@@ -34,12 +34,17 @@ def main(argv=None):
     ap.add_argument("--epochs-ae", type=int, default=40)
     ap.add_argument("--epochs-heads", type=int, default=80)
     ap.add_argument("--dataset", default=None, help="save / reuse the labelled windows here (.npz)")
+    ap.add_argument("--lj-rc", type=float, default=None,
+                    help="inter-platelet LJ cut-off of the training systems (default: the configuration's 2.0)")
+    ap.add_argument("--morse-standard", action="store_true",
+                    help="receptor Morse term in its standard form (MD_CFG_MORSE_STANDARD)")
     ap.add_argument("--select-only", action="store_true",
                     help="keep the trained parameters in --out; choose the trust bound again on --dataset")
     args = ap.parse_args(argv)
 
     from paper_2205_14121_gb300 import ai_mts as A
     from paper_2205_14121_gb300 import build as Bld
+    from paper_2205_14121_gb300._binding import MD_CFG_MORSE_STANDARD
     Bld.build()
 
     if args.select_only:
@@ -56,7 +61,13 @@ def main(argv=None):
         tr = [d[f"train_{k}"] for k in ("w", "c", "h", "es", "ev")]
         te = [d[f"test_{k}"] for k in ("w", "c", "h", "es", "ev")]
     else:
-        kw = dict(n_windows=args.windows, horizon=args.horizon, n_shell=args.n_shell, progress=progress, k_m=args.k_m)
+        system_kw = {}
+        if args.lj_rc is not None:
+            system_kw["lj_rc"] = args.lj_rc
+        if args.morse_standard:
+            system_kw["flags"] = MD_CFG_MORSE_STANDARD
+        kw = dict(n_windows=args.windows, horizon=args.horizon, n_shell=args.n_shell, progress=progress, k_m=args.k_m,
+                  system_kw=system_kw)
         tr = A.generate(seeds_train, **kw).arrays()
         te = A.generate(seeds_test, **kw).arrays()
         if args.dataset:
@@ -98,7 +109,9 @@ def main(argv=None):
                    strain_p99=float(art["strain_p99"]),
                    loss_ae=art["history"]["ae"][-1], loss_heads=art["history"]["heads"][-1],
                    seconds_data=t_data, seconds_train=t_train,
-                   horizon=args.horizon, windows_per_trajectory=args.windows, n_shell=args.n_shell, k_m=args.k_m)
+                   horizon=args.horizon, windows_per_trajectory=args.windows, n_shell=args.n_shell, k_m=args.k_m,
+                   lj_rc=args.lj_rc, morse_standard=bool(args.morse_standard),
+                   strain_p50_train=float(np.median(w_tr[:, :, A.F_STRAIN].max(1))))
     with open(os.path.splitext(args.out)[0] + "_training.json", "w") as f:
         json.dump(summary, f, indent=1)
     print(json.dumps(summary), flush=True)
