@@ -316,10 +316,11 @@ def traffic_entry(workload_name, skin, n):
 
 
 def issue_limiter(workload_name, launch_ms, n, sm_mhz):
-    """Warp-instruction issue rate of the fluid DPD pass against the issue
-    limit (152 SMs x 4 schedulers x 1 per cycle at the sampled SM clock), with
-    the instructions per row of a committed ncu capture of the current kernel
-    source; None without one."""
+    """The fluid DPD pass against its two on-chip limits at the sampled SM
+    clock: warp-instruction issue (152 SMs x 4 schedulers x 1 per cycle) and
+    the L1 data pipe (152 SMs x 1 LSU wavefront per cycle), with the per-row
+    counts of a committed ncu capture of the current kernel source (the
+    channel's); None without one."""
     path = os.path.join(ROOT, "profiles", "k_dpd_traffic.json")
     try:
         d = json.load(open(path))
@@ -327,10 +328,16 @@ def issue_limiter(workload_name, launch_ms, n, sm_mhz):
         if not e or e.get("source_hash") != kernel_source_hash() or not sm_mhz:
             return None
         per_row = float(e["warp_inst_per_row"])
-        rate = per_row * n / (launch_ms * 1e-3)
-        limit = 152 * 4 * sm_mhz * 1e6
-        return {"warp_inst_per_row": per_row, "issue_fraction": rate / limit,
-                "source": e.get("command", "")}
+        sec = launch_ms * 1e-3
+        out = {"warp_inst_per_row": per_row,
+               "issue_fraction": per_row * n / sec / (152 * 4 * sm_mhz * 1e6),
+               "source": e.get("command", "")}
+        c = d.get("channel", {})
+        if c.get("source_hash") == kernel_source_hash() and c.get("l1_wavefronts_per_launch"):
+            wf = float(c["l1_wavefronts_per_launch"]) / float(c["rows"])
+            out["l1_wavefronts_per_row"] = wf
+            out["l1_wavefront_fraction"] = wf * n / sec / (152 * sm_mhz * 1e6)
+        return out
     except Exception:
         return None
 
