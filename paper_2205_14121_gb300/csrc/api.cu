@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "msm_internal.cuh"
@@ -178,9 +179,11 @@ bool plan(const md_config &c, md_system &s, carver &cv, std::string &err)
         s.plt_off = cv.take<int32_t>(P + 1);
         s.plt_ids = cv.take<int32_t>(s.n_plt);
         s.bond_off = cv.take<int32_t>(P + 1);
-        if (s.na > 0) s.angle_off = cv.take<int32_t>(P + 1);
+        if (s.nb > 0) s.bond_blk = cv.take<int2>((s.nb + MSM_TPB - 1) / MSM_TPB);
+        if (s.na > 0) s.angle_blk = cv.take<int2>((s.na + MSM_TPB - 1) / MSM_TPB);
         s.plt_cmask = cv.take<unsigned long long>(P);
         s.plt_stride = cv.take<int32_t>(P);
+        s.plt_row_stride = cv.take<int32_t>(s.n_plt);
         s.plt_contacts = cv.take<int32_t>(P);
         s.feat = cv.take<double>(12 * P);
         s.ring = cv.take<float>(P * (int64_t)s.ring_T * 12);
@@ -1028,6 +1031,23 @@ int md_set_xv(md_system *s, const double *x, const double *v, int64_t step0)
     return finish_set_xv(s, step0);
 }
 
+// First and last platelet of every block of MSM_TPB terms of an array
+// grouped by platelet (platelet p's terms at [off[p], off[p+1])).
+static std::vector<int2> block_platelets(const std::vector<int32_t> &off, int64_t n)
+{
+    const int64_t nblk = (n + MSM_TPB - 1) / MSM_TPB;
+    std::vector<int2> blk((size_t)nblk);
+    int p = 0;
+    for (int64_t b = 0; b < nblk; ++b) {
+        const int64_t t0 = b * MSM_TPB, t1 = std::min(t0 + MSM_TPB, n) - 1;
+        while (off[(size_t)p + 1] <= t0) ++p;
+        int q = p;
+        while (off[(size_t)q + 1] <= t1) ++q;
+        blk[(size_t)b] = make_int2(p, q);
+    }
+    return blk;
+}
+
 int md_set_bonds(md_system *s, const int32_t *ij, const double *r0, int64_t nb)
 {
     if (!s) return MD_EINVAL;
@@ -1063,6 +1083,9 @@ int md_set_bonds(md_system *s, const int32_t *ij, const double *r0, int64_t nb)
     CK(cudaMemcpyAsync(s->bond_r0, r0f.data(), sizeof(float) * nb, cudaMemcpyHostToDevice, s->stream), "upload r0");
     CK(cudaMemcpyAsync(s->bond_off, off.data(), sizeof(int32_t) * (P + 1), cudaMemcpyHostToDevice, s->stream),
        "upload bond offsets");
+    std::vector<int2> blk = block_platelets(off, nb);
+    CK(cudaMemcpyAsync(s->bond_blk, blk.data(), sizeof(int2) * blk.size(), cudaMemcpyHostToDevice, s->stream),
+       "upload bond blocks");
     CK(cudaStreamSynchronize(s->stream), "set_bonds sync");
     s->have_bonds = true;
     s->lists_stale = true;   // the remap of bond ends happens in the rebuild
@@ -1107,8 +1130,9 @@ int md_set_angles(md_system *s, const int32_t *ijk, const double *theta0, int64_
     CK(cudaMemcpyAsync(s->angle_id, ids.data(), sizeof(int32_t) * 3 * na, cudaMemcpyHostToDevice, s->stream),
        "angles");
     CK(cudaMemcpyAsync(s->angle_t0, t0.data(), sizeof(float) * na, cudaMemcpyHostToDevice, s->stream), "theta0");
-    CK(cudaMemcpyAsync(s->angle_off, off.data(), sizeof(int32_t) * (P + 1), cudaMemcpyHostToDevice, s->stream),
-       "angle offsets");
+    std::vector<int2> blk = block_platelets(off, na);
+    CK(cudaMemcpyAsync(s->angle_blk, blk.data(), sizeof(int2) * blk.size(), cudaMemcpyHostToDevice, s->stream),
+       "upload angle blocks");
     CK(cudaStreamSynchronize(s->stream), "set_angles sync");
     s->have_angles = true;
     s->lists_stale = true;   // the remap of the triplets happens in the rebuild

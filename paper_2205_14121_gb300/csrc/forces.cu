@@ -602,17 +602,11 @@ __global__ void __launch_bounds__(MSM_TPB) k_bonds(int64_t nb, const int32_t *__
                                                   const float *__restrict__ r0, float kb2, const float4 *__restrict__ x32,
                                                   float4 *f, md_geom geom, const md_dstate *ds, double *vir, md_due due,
                                                   const int32_t *tag, unsigned long long *fdet,
-                                                  const int32_t *__restrict__ off, int P)
+                                                  const int2 *__restrict__ blk)
 {
-    if (due.plt_k) {     // AI-MTS substep: skip a block whose platelets are off this grid point
-        __shared__ int block_due;
-        if (threadIdx.x == 0) {
-            const int64_t t0 = (int64_t)blockIdx.x * blockDim.x;
-            block_due = group_due(due, off, P, t0, min(t0 + (int64_t)blockDim.x, nb) - 1);
-        }
-        __syncthreads();
-        if (!block_due) return;
-    }
+    // AI-MTS substep: a block whose platelets are all off this grid point
+    // returns before any load (the decision is uniform over the block)
+    if (due.plt_k && !block_due(due, blk[blockIdx.x])) return;
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     vir6 w = {0, 0, 0, 0, 0, 0};
     // both ends belong to one platelet: the bond lives on that platelet's grid
@@ -650,17 +644,11 @@ __global__ void __launch_bounds__(MSM_TPB) k_angles(int64_t na, const int32_t *_
                                                    const float *__restrict__ t0, float k2,
                                                    const float4 *__restrict__ x32, float4 *f, md_geom geom,
                                                    const md_dstate *ds, double *vir, md_due due, const int32_t *tag,
-                                                   unsigned long long *fdet, const int32_t *__restrict__ off, int P)
+                                                   unsigned long long *fdet, const int2 *__restrict__ blk)
 {
-    if (due.plt_k) {     // AI-MTS substep: skip a block whose platelets are off this grid point
-        __shared__ int block_due;
-        if (threadIdx.x == 0) {
-            const int64_t t0 = (int64_t)blockIdx.x * blockDim.x;
-            block_due = group_due(due, off, P, t0, min(t0 + (int64_t)blockDim.x, na) - 1);
-        }
-        __syncthreads();
-        if (!block_due) return;
-    }
+    // AI-MTS substep: a block whose platelets are all off this grid point
+    // returns before any load (the decision is uniform over the block)
+    if (due.plt_k && !block_due(due, blk[blockIdx.x])) return;
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     vir6 w = {0, 0, 0, 0, 0, 0};
     // the triplet lies on one platelet: it lives on that platelet's grid
@@ -890,22 +878,22 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
                 k_bonds<true><<<blocks_for(s->nb), MSM_TPB, 0, s->stream>>>(s->nb, s->bond_ij, s->bond_r0,
                                                                            (float)(2.0 * c.k_bond), s->x32, out[2],
                                                                            s->geom, s->ds, s->vir_acc, a.due, s->tag_s,
-                                                                           a.fdet, s->bond_off, s->cfg.n_platelets);
+                                                                           a.fdet, s->bond_blk);
             else
                 k_bonds<false><<<blocks_for(s->nb), MSM_TPB, 0, s->stream>>>(s->nb, s->bond_ij, s->bond_r0,
                                                                             (float)(2.0 * c.k_bond), s->x32, out[2],
                                                                             s->geom, s->ds, s->vir_acc, a.due, s->tag_s,
-                                                                           a.fdet, s->bond_off, s->cfg.n_platelets);
+                                                                           a.fdet, s->bond_blk);
         }
         if (s->na > 0) {
             if (virial)
                 k_angles<true><<<blocks_for(s->na), MSM_TPB, 0, s->stream>>>(
                     s->na, s->angle_ijk, s->angle_t0, (float)(2.0 * c.k_angle), s->x32, out[2], s->geom, s->ds,
-                    s->vir_acc, a.due, s->tag_s, a.fdet, s->angle_off, s->cfg.n_platelets);
+                    s->vir_acc, a.due, s->tag_s, a.fdet, s->angle_blk);
             else
                 k_angles<false><<<blocks_for(s->na), MSM_TPB, 0, s->stream>>>(
                     s->na, s->angle_ijk, s->angle_t0, (float)(2.0 * c.k_angle), s->x32, out[2], s->geom, s->ds,
-                    s->vir_acc, a.due, s->tag_s, a.fdet, s->angle_off, s->cfg.n_platelets);
+                    s->vir_acc, a.due, s->tag_s, a.fdet, s->angle_blk);
             MSM_COUNT(s, 1);
         }
         a.rows = s->n_plt;

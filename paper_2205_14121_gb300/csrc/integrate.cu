@@ -42,7 +42,7 @@ struct kd_args {
     int32_t *fast_idx;     // plasma beyond skin/2 and within the skin: listed here
     uint32_t *fast_flag;
     int64_t fast_max;
-    const int32_t *stride; // AI-MTS substep q of the K grid: per-platelet drift strides (null: every substep)
+    const int32_t *row_stride;  // AI-MTS substep q of the K grid: drift stride of each platelet row (null: every substep)
     int q;
 };
 
@@ -91,6 +91,15 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= a.n) return;
+    double dt = a.dt;
+    if (a.row_stride) {
+        // AI-MTS platelet rows: every term that involves this row's platelet
+        // is due at multiples of its stride only, so no force acts on it in
+        // between: it is kicked and moved there, by stride substeps at once
+        const int st = a.row_stride[r];
+        if (a.q % st != 0) return;
+        dt *= st;
+    }
     const int64_t k = a.idx ? a.idx[r] : r;
     if (a.sparse_level >= 0) {
         // interface half kicks: only particles near a platelet carry a force
@@ -98,15 +107,6 @@ __global__ void __launch_bounds__(MSM_TPB) k_kick_drift(kd_args a)
         if (fl.x == 0.0f && fl.y == 0.0f && fl.z == 0.0f) return;
     }
     const int32_t t = a.tag[k];
-    double dt = a.dt;
-    if (a.stride && t >= 0) {
-        // AI-MTS: every term that involves this platelet is due at multiples
-        // of its stride only, so no force acts on it in between: it is
-        // kicked and moved there, by stride substeps at once
-        const int st = a.stride[t & ~MD_RECEPTOR_BIT];
-        if (a.q % st != 0) return;
-        dt *= st;
-    }
     const bool kick = selected(a.kick_which, t);
     const bool drift = selected(a.drift_which, t);
     unsigned zero_seen = 0u;   // levels read as exactly zero: no need to clear them
@@ -337,7 +337,7 @@ kd_args base_args(md_system *s)
     a.fast_idx = s->fast_idx;
     a.fast_flag = s->fast_flag;
     a.fast_max = s->fast_max;
-    a.stride = nullptr;
+    a.row_stride = nullptr;
     a.q = 0;
     return a;
 }
@@ -351,8 +351,8 @@ cudaError_t launch_kick_drift(md_system *s, const float h[3], int kick_which, do
                               unsigned zero_levels, bool plt_rows, int stride_q)
 {
     kd_args a = base_args(s);
-    if (stride_q >= 0 && s->have_levels && s->plt_stride) {
-        a.stride = s->plt_stride;
+    if (stride_q >= 0 && plt_rows && s->have_levels && s->plt_row_stride) {
+        a.row_stride = s->plt_row_stride;
         a.q = stride_q;
     }
     for (int l = 0; l < 3; ++l) a.h[l] = h[l];

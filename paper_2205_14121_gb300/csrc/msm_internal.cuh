@@ -111,11 +111,12 @@ struct md_system {
     int64_t na = 0;
     int32_t *angle_id = nullptr, *angle_ijk = nullptr;
     float *angle_t0 = nullptr;
-    int32_t *angle_off = nullptr;   // triplets grouped by platelet: [angle_off[p], angle_off[p+1])
+    int2 *bond_blk = nullptr, *angle_blk = nullptr;   // per block of MSM_TPB terms: first and last platelet
     // AI-MTS: step ratios (bit k - 1) of the platelets each platelet has LJ
     // or receptor pairs with, and its drift stride on the K-substep grid
     unsigned long long *plt_cmask = nullptr;
     int32_t *plt_stride = nullptr;
+    int32_t *plt_row_stride = nullptr;   // the stride of each platelet row (plt_sorted order)
     bool have_angles = false;
 
     // per-platelet measurements (K8)
@@ -512,23 +513,13 @@ struct md_due {
     float dtm;
 };
 
-// Whether the terms [t0, t1] of an array grouped by platelet (platelet p's
-// terms at [off[p], off[p+1]), P platelets) hold one due at this point: a
-// block whose terms are all off the grid point skips its loads.
-__device__ __forceinline__ bool group_due(const md_due &d, const int32_t *off, int P, int64_t t0, int64_t t1)
+// AI-MTS: whether any platelet of a block of terms is due at this point
+// (r: the first and last platelet of the block's terms, which are stored
+// grouped by platelet); a block with none skips its loads.
+__device__ __forceinline__ bool block_due(const md_due &d, int2 r)
 {
-    auto plt_of = [&](int64_t t) {      // the last p with off[p] <= t
-        int lo = 0, hi = P - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (off[mid] <= t) lo = mid;
-            else hi = mid - 1;
-        }
-        return lo;
-    };
-    const int p1 = plt_of(t1);
-    for (int p = plt_of(t0); p <= p1; ++p)
-        if (off[p + 1] > off[p] && (d.qe % (d.K / d.plt_k[p])) == 0) return true;
+    for (int p = r.x; p <= r.y; ++p)
+        if ((d.qe % (d.K / d.plt_k[p])) == 0) return true;
     return false;
 }
 

@@ -235,6 +235,16 @@ __global__ void __launch_bounds__(256) k_strides(int P, int K, const int32_t *__
     stride[p] = K / L;      // every ratio divides K, so L does
 }
 
+__global__ void __launch_bounds__(MSM_TPB) k_row_strides(int64_t rows, const int32_t *__restrict__ row_idx,
+                                                         const int32_t *__restrict__ tag,
+                                                         const int32_t *__restrict__ stride, int32_t *row_stride,
+                                                         const int32_t *gate)
+{
+    if (gate_closed(gate)) return;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < rows) row_stride[r] = stride[tag[row_idx[r]] & ~MD_RECEPTOR_BIT];
+}
+
 // Bounding sphere of every platelet at the build, over blocks (p, chunk):
 // pass 1 sums the member offsets from the first member (minimum image) into
 // bound[p].xyz, pass 2 the largest squared distance from the centre of mass
@@ -466,7 +476,9 @@ cudaError_t launch_strides(md_system *s, const int32_t *gate)
         ++n;
     }
     k_strides<<<(P + 255) / 256, 256, 0, s->stream>>>(P, s->plt_K, s->plt_k, s->plt_cmask, s->plt_stride, gate);
-    MSM_COUNT(s, n);
+    k_row_strides<<<blocks_for(s->n_plt), MSM_TPB, 0, s->stream>>>(s->n_plt, s->plt_sorted, s->tag_s, s->plt_stride,
+                                                                  s->plt_row_stride, gate);
+    MSM_COUNT(s, n + 1);
     return cudaGetLastError();
 }
 
