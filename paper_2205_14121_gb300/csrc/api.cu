@@ -574,10 +574,12 @@ int enqueue_outer_step(md_system *s, int mode, int k_m, int k_p, bool first, cap
         const double tc = ci * dtm;
         RC(enqueue_time(s, dn, c_end, tc + dtm));
         // A: fluid kick (first substep; fused with the previous outer step's
-        //    closing half-kick) + opening interface half-kick; plasma drift
+        //    closing half-kick) + opening interface half-kick (after the first
+        //    substep fused with the previous substep's closing one: no force
+        //    is evaluated between them); plasma drift
         float h[3] = {0.f, 0.f, 0.f};
         if (ci == 0) h[0] = (float)(first ? 0.5 * dtf : dtf);
-        h[1] = plt ? (float)(0.5 * dtm) : 0.f;
+        h[1] = plt ? (float)(ci == 0 ? 0.5 * dtm : dtm) : 0.f;
         const unsigned zero = (plt ? MD_LEVEL_IFACE : 0u) | (ci == 0 ? MD_LEVEL_FLUID : 0u);
         RC(enqueue_kd(s, h, DRIFT_ALL, dtm, plt ? DRIFT_FLUID : DRIFT_ALL, zero, false));
         if (plt && mode == MD_MODE_AI) {
@@ -618,8 +620,14 @@ int enqueue_outer_step(md_system *s, int mode, int k_m, int k_p, bool first, cap
         RC(enqueue_rebuild(s, cap, plt ? MD_LEVEL_PLT : 0u));
         if (plt) {
             RC(enqueue_forces(s, MD_LEVEL_IFACE));
-            const float hm[3] = {0.f, (float)(0.5 * dtm), 0.f};
-            RC(enqueue_kd(s, hm, DRIFT_ALL, 0.0, -1, 0u, false));
+            // the closing interface half-kick; before the next interface
+            // substep it is fused into that substep's opening kick, before the
+            // fluid forces (velocity dependent: Eq. 1's dissipative term) it
+            // is not
+            if (last_c) {
+                const float hm[3] = {0.f, (float)(0.5 * dtm), 0.f};
+                RC(enqueue_kd(s, hm, DRIFT_ALL, 0.0, -1, 0u, false));
+            }
         }
     }
     RC(enqueue_forces(s, MD_LEVEL_FLUID));
