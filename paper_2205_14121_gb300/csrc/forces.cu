@@ -515,8 +515,12 @@ __global__ void __launch_bounds__(MSM_TPB) k_lj(pair_args a)
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     vir6 w = {0, 0, 0, 0, 0, 0};
     if (r < a.rows) {
+        // AI-MTS: off its platelet's stride points no term of the row is due
+        // (the stride divides K / max(k_i, k_j) for every partner j listed),
+        // so the row's list is not read
+        const bool idle = a.due.row_stride && (a.due.qe % a.due.row_stride[r]) != 0;
         const int32_t i = a.row_idx[r];
-        const int cnt = min(a.nc[r], a.cap);
+        const int cnt = idle ? 0 : min(a.nc[r], a.cap);
         if (cnt > 0) {
             const float4 xi = a.x32[i];
             const float delta = a.ds->le_offset_f;
@@ -560,11 +564,13 @@ __global__ void __launch_bounds__(MSM_TPB) k_morse(pair_args a)
     vir6 w = {0, 0, 0, 0, 0, 0};
     if (r < a.rows) {
         const int32_t i = a.row_idx[r];
-        const int cnt = min(a.nc[r], a.cap);
+        const int32_t ti = a.due.plt_k ? a.tag[i] : 0;
+        // AI-MTS: as for the LJ rows, by the stride of the row's platelet
+        const bool idle = a.due.stride && (a.due.qe % a.due.stride[ti & ~MD_RECEPTOR_BIT]) != 0;
+        const int cnt = idle ? 0 : min(a.nc[r], a.cap);
         if (cnt > 0) {
             const float4 xi = a.x32[i];
             const float delta = a.ds->le_offset_f;
-            const int32_t ti = a.due.plt_k ? a.tag[i] : 0;
             float fx = 0.f, fy = 0.f, fz = 0.f;
             for (int k = 0; k < cnt; ++k) {
                 const int32_t j = a.nl[r * a.cap + k];
@@ -836,6 +842,9 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
     a.due.qe = s->due_q;
     a.due.K = s->plt_K;
     a.due.dtm = (float)s->due_dtm;
+    const bool strided = a.due.plt_k && s->have_levels;      // the strides follow every build and ratio change
+    a.due.stride = strided ? s->plt_stride : nullptr;
+    a.due.row_stride = strided ? s->plt_row_stride : nullptr;
     const int km = s->cfg_k_m > 0 ? s->cfg_k_m : 1;
     set_variants(s, a, false);
 

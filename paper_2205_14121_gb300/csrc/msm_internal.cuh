@@ -511,6 +511,9 @@ struct md_due {
     const int32_t *plt_k;   // null: plain forces (STS, fixed-k RESPA)
     int qe, K;
     float dtm;
+    // the drift stride K / lcm(k_p, k of p's listed contact partners), per
+    // platelet and per platelet row (plt_sorted order); null: not in use
+    const int32_t *stride, *row_stride;
 };
 
 // AI-MTS: whether any platelet of a block of terms is due at this point

@@ -472,6 +472,32 @@ def test_ai_mts_platelets_apart_drift_on_their_own_grids():
     assert np.abs(vg - vo).max() < 5e-3 * np.sqrt((vo ** 2).mean())
 
 
+def test_ai_mts_contact_pair_skips_rows_between_its_stride_points():
+    """Three platelets, k = (1, 2, 5) on the K = 10 grid: the first two touch
+    (LJ and receptor pairs between them) and share the drift stride
+    10 / lcm(1, 2) = 5, so their LJ and Morse rows are not read at the
+    substeps in between, where none of their terms is due; the third lies
+    apart (stride 2).  The trajectory matches the oracle's, which evaluates
+    every pair at every substep and scales it by whether it is due."""
+    import paper_2205_14121_gb300 as M
+    s = synth.platelet_system((16.0, 16.0, 16.0), 12288, 3, 400, synth.scaled_radii(400), walls=True,
+                              body_force=0.02, seed=19, centers=[(4.0, 8.0, 4.0), (8.0, 8.0, 4.0), (12.0, 8.0, 12.0)])
+    x0, v0 = f32(s.x), f32(s.v)
+    g = make_gpu(s, x=x0, v=v0)
+    g.set_platelet_levels([1, 2, 5])
+    g.mts_step(3, mode=M.MD_MODE_AI, k_m=2)
+    assert g.neighbor_count(M.MD_LIST_LJ) > 0 and g.neighbor_count(M.MD_LIST_MORSE) > 0
+    xg, vg, _ = g.read_particles()
+    p = O.system_params(s)
+    xo, vo, _ = O.run_ai_respa(p, x0, v0, s.tag, [1, 2, 5], X0=f32(s.X0), bonds=s.bonds, r0=f32(s.r0), dt_f=0.01,
+                               k_m=2, n_outer=3)
+    dx = xg - xo
+    L = np.array(s.box)
+    dx -= L * np.round(dx / L)
+    assert np.abs(dx).max() < 1e-4
+    assert np.abs(vg - vo).max() < 5e-3 * np.sqrt((vo ** 2).mean())
+
+
 def test_ai_mts_tracks_table1_nested_sublevels(plt_wall_sys):
     """Table 1's nested sublevels as printed (oracle: a flowing platelet on
     level 1, one step per interface substep; an aggregating one on level 2,
