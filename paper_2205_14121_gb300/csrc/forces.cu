@@ -610,30 +610,36 @@ __global__ void __launch_bounds__(MSM_TPB) k_bonds(int64_t nb, const int32_t *__
                                                   const int32_t *tag, unsigned long long *fdet,
                                                   const int2 *__restrict__ blk)
 {
-    // AI-MTS substep: a block whose platelets are all off this grid point
-    // returns before any load (the decision is uniform over the block)
-    if (due.plt_k && !block_due(due, blk[blockIdx.x])) return;
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     vir6 w = {0, 0, 0, 0, 0, 0};
-    // both ends belong to one platelet: the bond lives on that platelet's grid
-    const float sc = (b < nb && due.plt_k) ? term_scale(due, tag[ij[2 * b]], tag[ij[2 * b]]) : 1.0f;
-    if (b < nb && sc != 0.0f) {
-        const int32_t i = ij[2 * b], j = ij[2 * b + 1];
-        float dx, dy, dz, vsh;
-        min_image_f32(geom, ds->le_offset_f, x32[i], x32[j], dx, dy, dz, vsh);
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 > 0.0f) {
-            const float inv_r = rsqrtf(r2);
-            const float rr = r2 * inv_r;
-            const float s = -kb2 * (rr - r0[b]) * inv_r * sc;
-            if (fdet) {     // a bond's orientation is fixed by its definition
-                put_fixed(fdet, i, s * dx, s * dy, s * dz);
-                put_fixed(fdet, j, -s * dx, -s * dy, -s * dz);
-            } else {
-                scatter(f, i, s * dx, s * dy, s * dz);
-                scatter(f, j, -s * dx, -s * dy, -s * dz);
+    // the CTAs stride over the blocks of MSM_TPB bonds: an AI-MTS substep
+    // that skips most blocks costs a pass over their table, not a launch of
+    // them all
+    const int64_t nblk = (nb + MSM_TPB - 1) / MSM_TPB;
+    for (int64_t vb = blockIdx.x; vb < nblk; vb += gridDim.x) {
+        // AI-MTS substep: a block whose platelets are all off this grid point
+        // skips its loads (the decision is uniform over the CTA)
+        if (due.plt_k && !block_due(due, blk[vb])) continue;
+        const int64_t b = vb * MSM_TPB + threadIdx.x;
+        // both ends belong to one platelet: the bond lives on that platelet's grid
+        const float sc = (b < nb && due.plt_k) ? term_scale(due, tag[ij[2 * b]], tag[ij[2 * b]]) : 1.0f;
+        if (b < nb && sc != 0.0f) {
+            const int32_t i = ij[2 * b], j = ij[2 * b + 1];
+            float dx, dy, dz, vsh;
+            min_image_f32(geom, ds->le_offset_f, x32[i], x32[j], dx, dy, dz, vsh);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 > 0.0f) {
+                const float inv_r = rsqrtf(r2);
+                const float rr = r2 * inv_r;
+                const float s = -kb2 * (rr - r0[b]) * inv_r * sc;
+                if (fdet) {     // a bond's orientation is fixed by its definition
+                    put_fixed(fdet, i, s * dx, s * dy, s * dz);
+                    put_fixed(fdet, j, -s * dx, -s * dy, -s * dz);
+                } else {
+                    scatter(f, i, s * dx, s * dy, s * dz);
+                    scatter(f, j, -s * dx, -s * dy, -s * dz);
+                }
+                if (VIR) w.add(dx, dy, dz, s);
             }
-            if (VIR) w.add(dx, dy, dz, s);
         }
     }
     if (VIR) flush_virial(vir, w);
@@ -652,56 +658,62 @@ __global__ void __launch_bounds__(MSM_TPB) k_angles(int64_t na, const int32_t *_
                                                    const md_dstate *ds, double *vir, md_due due, const int32_t *tag,
                                                    unsigned long long *fdet, const int2 *__restrict__ blk)
 {
-    // AI-MTS substep: a block whose platelets are all off this grid point
-    // returns before any load (the decision is uniform over the block)
-    if (due.plt_k && !block_due(due, blk[blockIdx.x])) return;
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     vir6 w = {0, 0, 0, 0, 0, 0};
-    // the triplet lies on one platelet: it lives on that platelet's grid
-    const float sc = (q < na && due.plt_k) ? term_scale(due, tag[ijk[3 * q + 1]], tag[ijk[3 * q + 1]]) : 1.0f;
-    if (q < na && sc != 0.0f) {
-        const int32_t i = ijk[3 * q], j = ijk[3 * q + 1], k = ijk[3 * q + 2];
-        const float4 xj = x32[j];
-        float ax, ay, az, bx, by, bz, vs;
-        min_image_f32(geom, ds->le_offset_f, x32[i], xj, ax, ay, az, vs);
-        min_image_f32(geom, ds->le_offset_f, x32[k], xj, bx, by, bz, vs);
-        const float ia = rsqrtf(ax * ax + ay * ay + az * az), ib = rsqrtf(bx * bx + by * by + bz * bz);
-        const float dot = ax * bx + ay * by + az * bz;
-        const float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
-        const float crs = sqrtf(cx * cx + cy * cy + cz * cz);
-        const float th = atan2f(crs, dot);
-        const float c = dot * ia * ib;
-        const float sn = fmaxf(crs * ia * ib, 1e-3f);
-        const float g = k2 * (th - t0[q]) / sn * sc;
-        const float eax = ax * ia, eay = ay * ia, eaz = az * ia, ebx = bx * ib, eby = by * ib, ebz = bz * ib;
-        const float fix = g * (ebx - c * eax) * ia, fiy = g * (eby - c * eay) * ia, fiz = g * (ebz - c * eaz) * ia;
-        const float fkx = g * (eax - c * ebx) * ib, fky = g * (eay - c * eby) * ib, fkz = g * (eaz - c * ebz) * ib;
-        if (fdet) {     // a triplet's orientation is fixed by its definition
-            // the vertex takes minus the sum of the two rounded ends, so the
-            // triplet's terms cancel exactly
-            const float S = 4294967296.0f;
-            const long long qi[3] = {__float2ll_rn(fix * S), __float2ll_rn(fiy * S), __float2ll_rn(fiz * S)};
-            const long long qk[3] = {__float2ll_rn(fkx * S), __float2ll_rn(fky * S), __float2ll_rn(fkz * S)};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                atomicAdd(&fdet[3 * (int64_t)i + d], (unsigned long long)qi[d]);
-                atomicAdd(&fdet[3 * (int64_t)k + d], (unsigned long long)qk[d]);
-                atomicAdd(&fdet[3 * (int64_t)j + d], (unsigned long long)(-(qi[d] + qk[d])));
+    // the CTAs stride over the blocks of MSM_TPB triplets, as in k_bonds
+    const int64_t nblk = (na + MSM_TPB - 1) / MSM_TPB;
+    for (int64_t vb = blockIdx.x; vb < nblk; vb += gridDim.x) {
+        if (due.plt_k && !block_due(due, blk[vb])) continue;
+        const int64_t q = vb * MSM_TPB + threadIdx.x;
+        // the triplet lies on one platelet: it lives on that platelet's grid
+        const float sc = (q < na && due.plt_k) ? term_scale(due, tag[ijk[3 * q + 1]], tag[ijk[3 * q + 1]]) : 1.0f;
+        if (q < na && sc != 0.0f) {
+            const int32_t i = ijk[3 * q], j = ijk[3 * q + 1], k = ijk[3 * q + 2];
+            const float4 xj = x32[j];
+            float ax, ay, az, bx, by, bz, vs;
+            min_image_f32(geom, ds->le_offset_f, x32[i], xj, ax, ay, az, vs);
+            min_image_f32(geom, ds->le_offset_f, x32[k], xj, bx, by, bz, vs);
+            const float ia = rsqrtf(ax * ax + ay * ay + az * az), ib = rsqrtf(bx * bx + by * by + bz * bz);
+            const float dot = ax * bx + ay * by + az * bz;
+            const float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
+            const float crs = sqrtf(cx * cx + cy * cy + cz * cz);
+            const float th = atan2f(crs, dot);
+            const float c = dot * ia * ib;
+            const float sn = fmaxf(crs * ia * ib, 1e-3f);
+            const float g = k2 * (th - t0[q]) / sn * sc;
+            const float eax = ax * ia, eay = ay * ia, eaz = az * ia, ebx = bx * ib, eby = by * ib, ebz = bz * ib;
+            const float fix = g * (ebx - c * eax) * ia, fiy = g * (eby - c * eay) * ia, fiz = g * (ebz - c * eaz) * ia;
+            const float fkx = g * (eax - c * ebx) * ib, fky = g * (eay - c * eby) * ib, fkz = g * (eaz - c * ebz) * ib;
+            if (fdet) {     // a triplet's orientation is fixed by its definition
+                // the vertex takes minus the sum of the two rounded ends, so the
+                // triplet's terms cancel exactly
+                const float S = 4294967296.0f;
+                const long long qi[3] = {__float2ll_rn(fix * S), __float2ll_rn(fiy * S), __float2ll_rn(fiz * S)};
+                const long long qk[3] = {__float2ll_rn(fkx * S), __float2ll_rn(fky * S), __float2ll_rn(fkz * S)};
+    #pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    atomicAdd(&fdet[3 * (int64_t)i + d], (unsigned long long)qi[d]);
+                    atomicAdd(&fdet[3 * (int64_t)k + d], (unsigned long long)qk[d]);
+                    atomicAdd(&fdet[3 * (int64_t)j + d], (unsigned long long)(-(qi[d] + qk[d])));
+                }
+            } else {
+                scatter(f, i, fix, fiy, fiz);
+                scatter(f, k, fkx, fky, fkz);
+                scatter(f, j, -(fix + fkx), -(fiy + fky), -(fiz + fkz));
             }
-        } else {
-            scatter(f, i, fix, fiy, fiz);
-            scatter(f, k, fkx, fky, fkz);
-            scatter(f, j, -(fix + fkx), -(fiy + fky), -(fiz + fkz));
-        }
-        if (VIR) {
-            w.add_rf(ax, ay, az, fix, fiy, fiz);
-            w.add_rf(bx, by, bz, fkx, fky, fkz);
+            if (VIR) {
+                w.add_rf(ax, ay, az, fix, fiy, fiz);
+                w.add_rf(bx, by, bz, fkx, fky, fkz);
+            }
         }
     }
     if (VIR) flush_virial(vir, w);
 }
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)(n > 0 ? (n + MSM_TPB - 1) / MSM_TPB : 1); }
+// bond and angle CTAs striding over their blocks of terms: eight resident
+// per SM of the 152
+constexpr unsigned TERM_BLOCKS = 1216;
+inline unsigned term_grid(int64_t n) { return blocks_for(n) < TERM_BLOCKS ? blocks_for(n) : TERM_BLOCKS; }
 
 }  // namespace
 
@@ -884,23 +896,23 @@ cudaError_t launch_forces(md_system *s, unsigned level_mask, float4 *const out[3
     if ((level_mask & MD_LEVEL_PLT) && s->n_plt > 0) {
         if (s->nb > 0) {
             if (virial)
-                k_bonds<true><<<blocks_for(s->nb), MSM_TPB, 0, s->stream>>>(s->nb, s->bond_ij, s->bond_r0,
+                k_bonds<true><<<term_grid(s->nb), MSM_TPB, 0, s->stream>>>(s->nb, s->bond_ij, s->bond_r0,
                                                                            (float)(2.0 * c.k_bond), s->x32, out[2],
                                                                            s->geom, s->ds, s->vir_acc, a.due, s->tag_s,
                                                                            a.fdet, s->bond_blk);
             else
-                k_bonds<false><<<blocks_for(s->nb), MSM_TPB, 0, s->stream>>>(s->nb, s->bond_ij, s->bond_r0,
+                k_bonds<false><<<term_grid(s->nb), MSM_TPB, 0, s->stream>>>(s->nb, s->bond_ij, s->bond_r0,
                                                                             (float)(2.0 * c.k_bond), s->x32, out[2],
                                                                             s->geom, s->ds, s->vir_acc, a.due, s->tag_s,
                                                                            a.fdet, s->bond_blk);
         }
         if (s->na > 0) {
             if (virial)
-                k_angles<true><<<blocks_for(s->na), MSM_TPB, 0, s->stream>>>(
+                k_angles<true><<<term_grid(s->na), MSM_TPB, 0, s->stream>>>(
                     s->na, s->angle_ijk, s->angle_t0, (float)(2.0 * c.k_angle), s->x32, out[2], s->geom, s->ds,
                     s->vir_acc, a.due, s->tag_s, a.fdet, s->angle_blk);
             else
-                k_angles<false><<<blocks_for(s->na), MSM_TPB, 0, s->stream>>>(
+                k_angles<false><<<term_grid(s->na), MSM_TPB, 0, s->stream>>>(
                     s->na, s->angle_ijk, s->angle_t0, (float)(2.0 * c.k_angle), s->x32, out[2], s->geom, s->ds,
                     s->vir_acc, a.due, s->tag_s, a.fdet, s->angle_blk);
             MSM_COUNT(s, 1);
