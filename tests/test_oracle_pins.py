@@ -652,8 +652,8 @@ def couette():
 @pytest.mark.slow
 def test_couette_linear_profile_under_lees_edwards(couette):
     """Lees-Edwards shear gives a linear v_x(y) with the imposed slope: within 5%
-    and R^2 > 0.99, at a shear rate of 0.5 over 13.5 tau.  (At the survey's
-    0.05 the thermal noise of the slope in this box is about 15% after 30 tau;
+    and R^2 > 0.99, at a shear rate of 0.5 over 13.5 tau.  (At the
+    channel's 0.05 the thermal noise of the slope in this box is about 15% after 30 tau;
     the tenfold rate keeps the pin within seconds.)"""
     s, profs, _ = couette
     prof = profs.mean(0)
